@@ -1,0 +1,180 @@
+"""CPU FP64 oracle for the short-coherence statistic and its candidate reduction.
+
+TEST INFRASTRUCTURE ONLY: only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline
+leg may import this package.  It shares no code with the CUDA path
+(paper_2411_18370_b300/); the only module both sides import is ftsynth (seeded inputs).
+
+Functions and the passages of arXiv 2411.18370 they follow:
+
+* statistic()        Eq. (short_coh_general) with Eq. (track), a_p = 0, plus an f1 term;
+                     bins by the canonical Q32 rule (C source ft_oracle.c).  FP64.
+* bins(), bins_fp64() the canonical Q32 track bins and the direct FP64 rounding of
+                     f(t) T_SFT, Eq. (track).
+* mu_sigma(), zscore() Sec. II.B.1: mu_G = 2 sum w, sigma_G^2 = 4 sum w^2, and the critical
+                     ratio z = (s - mu_G)/sigma_G, Eq. (critical_ratio).
+* topk_per_subband() Sec. IV.B (ahead-of-time clustering): the loudest templates of each
+                     disjoint box, here the 1-D boxes "f0 bin j // subband_bins", ordered by
+                     s descending, then template index ascending.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [
+        ("power", ctypes.c_void_p),
+        ("n_sft", ctypes.c_int64),
+        ("W", ctypes.c_int64),
+        ("k_lo", ctypes.c_int64),
+        ("t_mid", ctypes.c_void_p),
+        ("v", ctypes.c_void_p),
+        ("w", ctypes.c_void_p),
+        ("t0", ctypes.c_double),
+        ("t_sft", ctypes.c_double),
+        ("K0", ctypes.c_int64),
+        ("n_f0", ctypes.c_int64),
+        ("n_f1", ctypes.c_int64),
+        ("f1", ctypes.c_void_p),
+        ("n_sky", ctypes.c_int64),
+        ("sky", ctypes.c_void_p),
+    ]
+
+
+def load_library(path):
+    """Open an oracle shared library and declare its signatures."""
+    L = ctypes.CDLL(path)
+    L.or_bin_q32.restype = ctypes.c_int64
+    L.or_bin_q32.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                             ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
+    L.or_bin_fp64.restype = ctypes.c_int64
+    L.or_bin_fp64.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                              ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.or_statistic.restype = None
+    L.or_statistic.argtypes = [ctypes.POINTER(_Problem), ctypes.c_void_p, ctypes.c_int64,
+                               ctypes.c_void_p, ctypes.c_void_p]
+    L.or_bins.restype = None
+    L.or_bins.argtypes = [ctypes.POINTER(_Problem), ctypes.c_void_p, ctypes.c_int64,
+                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.or_num_threads.restype = ctypes.c_int
+    return L
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = load_library(_build.build())
+    return _lib
+
+
+def num_threads() -> int:
+    return int(lib().or_num_threads())
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class _Keep:
+    """Holds the numpy arrays a _Problem points into."""
+
+    def __init__(self, sfts, bank, w):
+        self.power = _c(sfts.power, np.float64)
+        self.t_mid = _c(sfts.t_mid, np.float64)
+        self.v = _c(sfts.v, np.float64)
+        self.w = None if w is None else _c(w, np.float64)
+        self.f1 = _c(bank.f1, np.float64)
+        self.sky = _c(bank.sky, np.float64)
+        p = _Problem()
+        p.power = self.power.ctypes.data
+        p.n_sft = self.power.shape[0]
+        p.W = self.power.shape[1]
+        p.k_lo = int(sfts.k_lo)
+        p.t_mid = self.t_mid.ctypes.data
+        p.v = self.v.ctypes.data
+        p.w = None if self.w is None else self.w.ctypes.data
+        p.t0 = float(sfts.t0)
+        p.t_sft = float(sfts.t_sft)
+        p.K0 = int(bank.k0)
+        p.n_f0 = int(bank.n_f0)
+        p.n_f1 = len(self.f1)
+        p.f1 = self.f1.ctypes.data
+        p.n_sky = len(self.sky)
+        p.sky = self.sky.ctypes.data
+        self.p = p
+
+
+def statistic(sfts, bank, templates=None, w=None):
+    """FP64 s for the given template indices (all when None) and out-of-window counts."""
+    k = _Keep(sfts, bank, w)
+    if templates is None:
+        n = bank.n_templates
+        tp = None
+        tarr = None
+    else:
+        tarr = _c(templates, np.int64)
+        n = len(tarr)
+        tp = tarr.ctypes.data
+    s = np.empty(n, np.float64)
+    oob = np.empty(n, np.int32)
+    lib().or_statistic(ctypes.byref(k.p), tp, n, s.ctypes.data, oob.ctypes.data)
+    return s, oob
+
+
+def bins(sfts, bank, templates, with_fp64=False):
+    """Canonical Q32 bins [n, N_SFT]; with_fp64 also returns direct FP64 bins and the
+    distance of the real-valued track from the rounding boundary."""
+    k = _Keep(sfts, bank, None)
+    tarr = _c(templates, np.int64)
+    n = len(tarr)
+    N = k.power.shape[0]
+    b = np.empty((n, N), np.int64)
+    if not with_fp64:
+        lib().or_bins(ctypes.byref(k.p), tarr.ctypes.data, n, b.ctypes.data, None, None)
+        return b
+    bf = np.empty((n, N), np.int64)
+    d = np.empty((n, N), np.float64)
+    lib().or_bins(ctypes.byref(k.p), tarr.ctypes.data, n, b.ctypes.data, bf.ctypes.data,
+                  d.ctypes.data)
+    return b, bf, d
+
+
+def mu_sigma(n_sft: int, w=None):
+    """mu_G = 2 sum w, sigma_G = sqrt(4 sum w^2) (Sec. II.B.1, Gaussian limit)."""
+    if w is None:
+        return 2.0 * n_sft, math.sqrt(4.0 * n_sft)
+    w = np.asarray(w, np.float64)
+    return 2.0 * float(w.sum()), math.sqrt(4.0 * float((w * w).sum()))
+
+
+def zscore(s, n_sft: int, w=None):
+    """Critical ratio z = (s - mu_G) / sigma_G, Eq. (critical_ratio)."""
+    mu, sig = mu_sigma(n_sft, w)
+    return (np.asarray(s, np.float64) - mu) / sig
+
+
+def topk_per_subband(s, bank, k: int, templates=None):
+    """Per sub-band b (templates whose f0 index j has j // subband_bins == b), the k largest
+    s, ties broken by the smaller template index.  Returns (idx[n_sub, k], val[n_sub, k]);
+    slots beyond the sub-band's population hold idx -1 and val -inf."""
+    s = np.asarray(s, np.float64)
+    t = np.arange(len(s), dtype=np.int64) if templates is None else np.asarray(templates, np.int64)
+    j = t % bank.n_f0
+    sub = j // bank.subband_bins
+    nsub = bank.n_subbands
+    idx = np.full((nsub, k), -1, np.int64)
+    val = np.full((nsub, k), -np.inf)
+    for b in range(nsub):
+        m = sub == b
+        tb, sb = t[m], s[m]
+        order = np.lexsort((tb, -sb))[:k]
+        idx[b, : len(order)] = tb[order]
+        val[b, : len(order)] = sb[order]
+    return idx, val

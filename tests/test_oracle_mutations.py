@@ -1,0 +1,89 @@
+"""Planted mistakes: each plausible error in the oracle must make at least one pin fail.
+
+Each mutation edits a temporary copy of oracle/ft_oracle.c (the oracle itself is never
+touched), compiles it with the same flags, swaps it in for the duration of the check and
+runs the pins of tests/test_oracle_pins.py against it.
+"""
+import os
+import subprocess
+import tempfile
+
+import pytest
+
+import oracle
+from oracle import build as obuild
+from tests import test_oracle_pins as pins
+
+MUTATIONS = {
+    "eps_sign": ("return fma(v[2], n[2], fma(v[1], n[1], v[0] * n[0]));",
+                 "return -fma(v[2], n[2], fma(v[1], n[1], v[0] * n[0]));"),
+    "eps_drop_z": ("return fma(v[2], n[2], fma(v[1], n[1], v[0] * n[0]));",
+                   "return fma(v[1], n[1], v[0] * n[0]);"),
+    "drop_f1_doppler_cross_term": ("int64_t X0 = C + G + floor_div_2_32((__int128)G * (__int128)E);",
+                                   "int64_t X0 = C + G;"),
+    "drop_j_eps": ("(__int128)X0 + (__int128)j * (__int128)E + ((__int128)1 << 31);",
+                   "(__int128)X0 + ((__int128)1 << 31);"),
+    "floor_not_round": ("(__int128)X0 + (__int128)j * (__int128)E + ((__int128)1 << 31);",
+                        "(__int128)X0 + (__int128)j * (__int128)E;"),
+    "k_lo_sign": ("llrint(fma((double)K0, eps, (double)(K0 - k_lo)) * TWO32);",
+                  "llrint(fma((double)K0, eps, (double)(K0 + k_lo)) * TWO32);"),
+    "start_time_not_mid": ("return (p->t_mid[a] - p->t0) * p->t_sft;",
+                           "return (p->t_mid[a] - 0.5 * p->t_sft - p->t0) * p->t_sft;"),
+    "weight_dropped": ("s += w * p->power[a * p->W + k];", "s += p->power[a * p->W + k];"),
+    "mirrored_column": ("s += w * p->power[a * p->W + k];", "s += w * p->power[a * p->W + (p->W - 1 - k)];"),
+    "f1_sign": ("int64_t G = llrint((f1 * tau) * TWO32);", "int64_t G = llrint((-f1 * tau) * TWO32);"),
+}
+
+PINS = [
+    pins.test_zero_doppler_fixed_bins,
+    pins.test_zero_doppler_spindown_closed_form,
+    pins.test_f0_neighbours_one_bin_apart,
+    pins.test_q32_bins_equal_exact_rational,
+    pins.test_q32_bins_large_spindown_exact_rational,
+    pins.test_doppler_direction_and_size,
+    pins.test_noise_free_injection_recovers_summed_power,
+    pins.test_weights_scale_and_z_invariance,
+    pins.test_weighted_statistic_bruteforce,
+]
+
+
+def _compile(src: str, out: str):
+    cfile = out[:-3] + ".c"
+    with open(cfile, "w") as f:
+        f.write(src)
+    subprocess.check_call(["gcc", "-O1", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+                           "-std=gnu11", cfile, "-o", out, "-lm"])
+
+
+def _runs_clean(lib):
+    saved = oracle._lib
+    oracle._lib = lib
+    try:
+        failed = []
+        for p in PINS:
+            try:
+                p()
+            except AssertionError:
+                failed.append(p.__name__)
+        return failed
+    finally:
+        oracle._lib = saved
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name):
+    src = open(obuild.SRC).read()
+    old, new = MUTATIONS[name]
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    with tempfile.TemporaryDirectory() as d:
+        so = os.path.join(d, f"mut_{name}.so")
+        _compile(src.replace(old, new), so)
+        failed = _runs_clean(oracle.load_library(so))
+    assert failed, f"no pin caught mutation {name}"
+
+
+def test_unmutated_oracle_passes_all_pins():
+    with tempfile.TemporaryDirectory() as d:
+        so = os.path.join(d, "clean.so")
+        _compile(open(obuild.SRC).read(), so)
+        assert _runs_clean(oracle.load_library(so)) == []
