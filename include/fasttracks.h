@@ -1,0 +1,199 @@
+/*
+ * fasttracks.h -- C ABI of the B300 (sm_103a) short-coherence search engine.
+ *
+ * The engine evaluates, by brute force, the short-coherence detection statistic of
+ * arXiv 2411.18370 over a regular template bank and reduces it to per-sub-band candidates:
+ *
+ *   s(lambda) = sum_{X,alpha} w_{X alpha} P_X[alpha][k_{X alpha}(lambda)]      Sec. II.B, Eq. (short_coh_general)
+ *   k = round-half-up of f(t_alpha) T_SFT - k_lo,
+ *   f(t) = (f0 + f1 (t - t0)) (1 + v(t).n / c)                                 Sec. II.A, Eq. (track), a_p = 0
+ *   z = (s - mu_G) / sigma_G, mu_G = 2 sum w, sigma_G^2 = 4 sum w^2            Sec. II.B.1, Eq. (critical_ratio)
+ *   candidates: the k loudest templates of each disjoint f0 sub-band           Sec. IV.B (ahead-of-time boxes)
+ *
+ * Track bins are computed exactly: per (sky, SFT) eps = v.n in FP64 with a pinned operation
+ * order, then integer Q32 fixed-point arithmetic (see ft_track_bins below for the rule).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every function returns FT_OK (0) or a negative FT_ERR_* code; ft_last_error() gives a
+ *   human-readable message for the calling thread's last failure.
+ * - Handles (ft_ctx, ft_band, ft_bank) are opaque and owned by the library; release them
+ *   with the matching *_destroy.  A band or bank is bound to the context (device) that
+ *   created it.
+ * - Input arrays passed as host pointers are copied before the call returns; the caller
+ *   keeps ownership.
+ * - Output buffers are caller-owned.  `out_on_device` = 1 means the pointers are device
+ *   pointers on the context's device: the call is asynchronous on `stream`.  0 means host
+ *   pointers: the call copies the results back and synchronises `stream` before returning.
+ * - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ * - Device-side failures (a bounded wait that ran out) are reported as FT_ERR_TIMEOUT by
+ *   the next synchronising call or by ft_check_status().
+ * - Sizes: template indices are int64; at most 2^31-1 SFT rows, 2^20 bins per row,
+ *   |v/c| < 1e-3, |f1 (t - t0) T_SFT| < 2^20 bins.
+ */
+#ifndef FASTTRACKS_H
+#define FASTTRACKS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define FT_API __attribute__((visibility("default")))
+#else
+#define FT_API
+#endif
+
+#define FT_ABI_VERSION 1
+
+#define FT_OK 0
+#define FT_ERR_ARG (-1)         /* invalid argument / descriptor / NaN input          */
+#define FT_ERR_CUDA (-2)        /* a CUDA runtime call failed                           */
+#define FT_ERR_OOM (-3)         /* device allocation failed                             */
+#define FT_ERR_TIMEOUT (-4)     /* a device-side bounded wait ran out                   */
+#define FT_ERR_RANGE (-5)       /* sizes or values beyond the documented limits         */
+#define FT_ERR_UNSUPPORTED (-6) /* feature not available (e.g. no sm_103 device)       */
+
+/* element types */
+#define FT_F32 0
+#define FT_F16 1
+#define FT_BF16 2
+#define FT_F64 3
+
+typedef struct ft_ctx ft_ctx;
+typedef struct ft_band ft_band;
+typedef struct ft_bank ft_bank;
+
+/* Message of the calling thread's most recent error ("" if none).  Valid until the
+ * thread's next failing call. */
+FT_API const char *ft_last_error(void);
+
+/* FT_ABI_VERSION of the loaded library. */
+FT_API int ft_abi_version(void);
+
+/* Create a context on CUDA device `device`.  Fails with FT_ERR_UNSUPPORTED when the
+ * device is not compute capability 10.3 (the kernels are built for sm_103a only). */
+FT_API int ft_create(ft_ctx **ctx, int device);
+FT_API void ft_destroy(ft_ctx *ctx);
+
+/* Synchronise `stream` and report any device-side failure recorded since the last check
+ * (FT_ERR_TIMEOUT), then clear it. */
+FT_API int ft_check_status(ft_ctx *ctx, void *stream);
+
+/* ----------------------------------------------------------------------------- SFTs --
+ * A narrow band of normalised SFT power, P = 4|x~|^2/(T_SFT S_n) (Sec. II.B, Eq. (s_tf)),
+ * for n_det detectors.  Rows are detector-major: detector 0's n_sft[0] SFTs, then
+ * detector 1's, ...; row alpha holds bins k_lo .. k_lo + n_bins - 1 (bin = f T_SFT).
+ */
+typedef struct {
+    int n_det;          /* number of detectors X (>= 1)                                */
+    const int *n_sft;   /* host [n_det]: SFTs per detector (>= 0 each, total >= 1)      */
+    int n_bins;         /* W: bins per row (1 .. 2^20)                                  */
+    int64_t k_lo;       /* global bin index of column 0                                 */
+    double t_sft;       /* SFT duration T_SFT (s)                                       */
+    double t0;          /* reference time at which f0 is defined (s)                    */
+    int dtype;          /* storage type of the power on the device: FT_F32/F16/BF16     */
+} ft_band_desc;
+
+/* Copy one band of SFT power to the device, converting to desc->dtype (round to nearest
+ * even) into a padded row-major layout.
+ *   power            [N_SFT][row_stride] elements of power_dtype (FT_F32 or FT_F64), host
+ *                    or device (power_on_device); only the first n_bins of each row are read.
+ *   t_mid            host [N_SFT] SFT mid-times (s).
+ *   v_over_c         host [N_SFT][3] detector velocity / c at t_mid (equatorial frame).
+ *   w                host [N_SFT] per-SFT weights w_alpha >= 0, or NULL for w = 1
+ *                    (Sec. II.B: weights are defined up to a constant).
+ *   s_n              host [N_SFT] PSD levels, or NULL (kept for injections only).
+ * Errors: FT_ERR_ARG on an inconsistent descriptor or non-finite power/metadata,
+ * FT_ERR_RANGE beyond the size/velocity limits, FT_ERR_OOM.  Synchronises `stream`. */
+FT_API int ft_load_sfts(ft_ctx *ctx, const ft_band_desc *desc, const void *power, int power_dtype,
+                 int64_t row_stride, int power_on_device, const double *t_mid,
+                 const double *v_over_c, const float *w, const double *s_n, void *stream,
+                 ft_band **out);
+FT_API void ft_band_destroy(ft_band *band);
+
+/* Band facts: total SFT rows, bins, padded row stride (elements), storage dtype,
+ * mu_G = 2 sum w and sigma_G = sqrt(4 sum w^2) (Sec. II.B.1).  Any pointer may be NULL. */
+FT_API int ft_band_info(const ft_band *band, int64_t *n_sft_total, int *n_bins, int *row_stride,
+                 int *dtype, double *mu_g, double *sigma_g);
+
+/* ----------------------------------------------------------------------------- bank --
+ * Regular bank: f0_j = (k0 + j)/T_SFT, j < n_f0 (delta f0 = 1/T_SFT, App. A); a list of
+ * f1 values; a list of sky unit vectors n.  Template index
+ *     t = (i_sky * n_f1 + i_f1) * n_f0 + j       (f0 fastest).
+ * Candidate sub-band of a template: j / subband_bins (the 1-D ahead-of-time boxes).
+ */
+typedef struct {
+    int64_t k0;          /* global bin of f0 index 0                                    */
+    int n_f0;            /* 1 .. 2^24                                                   */
+    int n_f1;            /* 1 .. 65535                                                  */
+    const double *f1;    /* host [n_f1] spindown values (Hz/s)                          */
+    int64_t n_sky;       /* >= 1                                                        */
+    const double *sky;   /* host [n_sky][3] unit vectors (equatorial)                   */
+    int subband_bins;    /* >= 1                                                        */
+} ft_bank_desc;
+
+/* Upload a bank for use with `band` (it precomputes per-(f1, SFT) integer track terms).
+ * The bank stays valid while `band` lives.  It records whether every track provably stays
+ * inside the band's window (then the fast unchecked kernel runs); otherwise reads outside
+ * the window contribute 0 and are counted (see ft_eval_statistic).
+ * Errors: FT_ERR_ARG (bad descriptor, non-unit sky vector), FT_ERR_RANGE, FT_ERR_OOM. */
+FT_API int ft_make_bank(ft_ctx *ctx, const ft_band *band, const ft_bank_desc *desc, void *stream,
+                 ft_bank **out);
+FT_API void ft_bank_destroy(ft_bank *bank);
+
+/* Bank facts: template count, sub-band count, and whether every track stays inside the
+ * window (1) or the bounds-checked kernel is used (0).  Any pointer may be NULL. */
+FT_API int ft_bank_info(const ft_bank *bank, int64_t *n_templates, int *n_subbands, int *window_safe);
+
+/* Wings needed so that every track of the bank stays inside the window: the number of
+ * bins required below bin k0 (lo) and above bin k0 + n_f0 - 1 (hi), from the conservative
+ * bound |v.n| <= |v|.  desc->k_lo and desc->n_bins are ignored.  Host-only computation. */
+FT_API int ft_required_wings(const ft_band_desc *desc, const double *t_mid, const double *v_over_c,
+                      const ft_bank_desc *bank, int *lo, int *hi);
+
+/* ----------------------------------------------------------------------------- statistic --
+ * Evaluate s for every template of `bank` (Eq. (short_coh_general)) and optionally
+ * z = (s - mu_G)/sigma_G (Eq. (critical_ratio)) and the per-template count of SFTs whose
+ * track bin falls outside the window (those contribute 0).
+ *   s_out     [n_templates] float, required
+ *   z_out     [n_templates] float or NULL
+ *   n_oob_out [n_templates] int32 or NULL
+ * Accumulation: FP32 partial sums over stages of SFTs, combined with a compensated (2Sum)
+ * FP32 pair; z is formed in FP64 from that pair. */
+FT_API int ft_eval_statistic(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, float *s_out,
+                      float *z_out, int32_t *n_oob_out, int out_on_device, void *stream);
+
+/* One candidate: template index (-1 for an empty slot), its s and z. */
+typedef struct {
+    int64_t template_idx;
+    float s;
+    float z;
+} ft_candidate;
+
+/* Per sub-band b (templates with j / subband_bins == b), the k loudest templates ordered
+ * by s descending, ties by smaller template index (Sec. IV.B: loudest per disjoint box).
+ * out: [n_subbands][k] ft_candidate; slots beyond a sub-band's population have
+ * template_idx = -1, s = -inf.  1 <= k <= 32.  The statistic is not written to memory: the
+ * selection is fused into the evaluation kernel, followed by one merge kernel. */
+FT_API int ft_topk_per_band(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int k,
+                     ft_candidate *out, int out_on_device, void *stream);
+
+/* Track bins used by the evaluation kernels, for a list of templates (a checking aid):
+ * bins[i][alpha] = k_{alpha}(templates[i]) relative to column 0 (may lie outside
+ * [0, n_bins)).  The rule (Eq. (track), a_p = 0, exact integer form):
+ *   eps = fma(vz, nz, fma(vy, ny, vx*nx)); E = rint(eps 2^32); C = rint(fma(k0, eps, k0-k_lo) 2^32)
+ *   G = rint((f1 tau) 2^32), tau = (t_mid - t0) T_SFT; X0 = C + G + floor(G E / 2^32)
+ *   k_j = j + floor((X0 + j E + 2^31) / 2^32)
+ * templates and bins are both host or both device pointers (on_device). */
+FT_API int ft_track_bins(ft_ctx *ctx, const ft_band *band, const ft_bank *bank,
+                  const int64_t *templates, int64_t n, int32_t *bins, int on_device,
+                  void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FASTTRACKS_H */

@@ -1,0 +1,292 @@
+"""Python binding of the fasttracks C ABI (include/fasttracks.h) for B300 / sm_103a.
+
+Argument marshalling only: every step of the search runs in libfasttracks.so's CUDA
+kernels.  Function names follow the C ABI without the ``ft_`` prefix.  Arrays may be numpy
+arrays (host memory) or torch tensors (device tensors on the context's device are passed
+as device pointers; the call is then asynchronous on ``stream``, by default torch's current
+stream).  If the library is not built the import still works but every call raises
+FtError: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfasttracks.so")
+
+FT_F32, FT_F16, FT_BF16, FT_F64 = 0, 1, 2, 3
+DTYPES = {"f32": FT_F32, "f16": FT_F16, "bf16": FT_BF16}
+ERRORS = {-1: "FT_ERR_ARG", -2: "FT_ERR_CUDA", -3: "FT_ERR_OOM", -4: "FT_ERR_TIMEOUT",
+          -5: "FT_ERR_RANGE", -6: "FT_ERR_UNSUPPORTED"}
+
+# ft_candidate {int64 template_idx; float s; float z}
+CANDIDATE_DTYPE = np.dtype([("template_idx", "<i8"), ("s", "<f4"), ("z", "<f4")])
+
+
+class FtError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _BandDesc(ctypes.Structure):
+    _fields_ = [("n_det", ctypes.c_int), ("n_sft", ctypes.POINTER(ctypes.c_int)),
+                ("n_bins", ctypes.c_int), ("k_lo", ctypes.c_int64), ("t_sft", ctypes.c_double),
+                ("t0", ctypes.c_double), ("dtype", ctypes.c_int)]
+
+
+class _BankDesc(ctypes.Structure):
+    _fields_ = [("k0", ctypes.c_int64), ("n_f0", ctypes.c_int), ("n_f1", ctypes.c_int),
+                ("f1", ctypes.c_void_p), ("n_sky", ctypes.c_int64), ("sky", ctypes.c_void_p),
+                ("subband_bins", ctypes.c_int)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+
+
+def lib():
+    """The loaded libfasttracks.so (raises FtError when it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise FtError(-6, f"{LIB_PATH} is not built (python -m paper_2411_18370_b300.build)")
+        L = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "ft_last_error": (ctypes.c_char_p, []),
+            "ft_abi_version": (_I, []),
+            "ft_create": (_I, [ctypes.POINTER(_P), _I]),
+            "ft_destroy": (None, [_P]),
+            "ft_check_status": (_I, [_P, _P]),
+            "ft_load_sfts": (_I, [_P, ctypes.POINTER(_BandDesc), _P, _I, _I64, _I, _P, _P, _P, _P,
+                                  _P, ctypes.POINTER(_P)]),
+            "ft_band_destroy": (None, [_P]),
+            "ft_band_info": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                  ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double)]),
+            "ft_make_bank": (_I, [_P, _P, ctypes.POINTER(_BankDesc), _P, ctypes.POINTER(_P)]),
+            "ft_bank_destroy": (None, [_P]),
+            "ft_bank_info": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+            "ft_required_wings": (_I, [ctypes.POINTER(_BandDesc), _P, _P, ctypes.POINTER(_BankDesc),
+                                       ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+            "ft_eval_statistic": (_I, [_P, _P, _P, _P, _P, _P, _I, _P]),
+            "ft_topk_per_band": (_I, [_P, _P, _P, _I, _P, _I, _P]),
+            "ft_track_bins": (_I, [_P, _P, _P, _P, _I64, _P, _I, _P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise FtError(rc, lib().ft_last_error().decode())
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """(pointer, on_device) of a numpy array or torch tensor; None -> (None, False)."""
+    if x is None:
+        return None, False
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), bool(x.is_cuda)
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return x.ctypes.data, False
+
+
+def _stream(stream, on_device):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    if on_device:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    return None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Context:
+    def __init__(self, device: int = 0):
+        h = _P()
+        _check(lib().ft_create(ctypes.byref(h), device))
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            lib().ft_destroy(self.handle)
+            self.handle = None
+
+    def check_status(self, stream=None):
+        _check(lib().ft_check_status(self.handle, _stream(stream, True)))
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Band:
+    def __init__(self, ctx, handle):
+        self.ctx = ctx
+        self.handle = handle
+        n, w, st, dt = _I64(), _I(), _I(), _I()
+        mu, sg = ctypes.c_double(), ctypes.c_double()
+        _check(lib().ft_band_info(handle, ctypes.byref(n), ctypes.byref(w), ctypes.byref(st),
+                                  ctypes.byref(dt), ctypes.byref(mu), ctypes.byref(sg)))
+        self.n_sft, self.n_bins, self.row_stride, self.dtype = n.value, w.value, st.value, dt.value
+        self.mu_g, self.sigma_g = mu.value, sg.value
+
+    def close(self):
+        if self.handle:
+            lib().ft_band_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Bank:
+    def __init__(self, band, handle):
+        self.band = band
+        self.handle = handle
+        nt, ns, ws = _I64(), _I(), _I()
+        _check(lib().ft_bank_info(handle, ctypes.byref(nt), ctypes.byref(ns), ctypes.byref(ws)))
+        self.n_templates, self.n_subbands, self.window_safe = nt.value, ns.value, bool(ws.value)
+
+    def close(self):
+        if self.handle:
+            lib().ft_bank_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def abi_version() -> int:
+    return lib().ft_abi_version()
+
+
+def create(device: int = 0) -> Context:
+    return Context(device)
+
+
+def _band_desc(n_sft, n_bins, k_lo, t_sft, t0, dtype):
+    arr = (ctypes.c_int * len(n_sft))(*[int(x) for x in n_sft])
+    d = _BandDesc(len(n_sft), arr, int(n_bins), int(k_lo), float(t_sft), float(t0),
+                  DTYPES[dtype] if isinstance(dtype, str) else int(dtype))
+    return d, arr
+
+
+def _bank_desc(k0, n_f0, f1, sky, subband_bins):
+    f1 = _f64(f1)
+    sky = _f64(sky).reshape(-1, 3)
+    d = _BankDesc(int(k0), int(n_f0), len(f1), f1.ctypes.data, len(sky), sky.ctypes.data,
+                  int(subband_bins))
+    return d, (f1, sky)
+
+
+def load_sfts(ctx, power, t_mid, v_over_c, n_sft, k_lo, t_sft, t0, dtype="f32", w=None,
+              s_n=None, n_bins=None, stream=None) -> Band:
+    """ft_load_sfts: power [N, stride] float32/float64 (numpy or torch, host or device)."""
+    if _is_torch(power):
+        import torch
+
+        pdt = {torch.float32: FT_F32, torch.float64: FT_F64}[power.dtype]
+    else:
+        power = np.ascontiguousarray(power)
+        pdt = {np.dtype(np.float32): FT_F32, np.dtype(np.float64): FT_F64}[power.dtype]
+    stride = int(power.shape[1])
+    n_bins = stride if n_bins is None else int(n_bins)
+    desc, keep = _band_desc(n_sft, n_bins, k_lo, t_sft, t0, dtype)
+    pp, on_dev = _ptr(power)
+    t_mid = _f64(t_mid)
+    v = _f64(v_over_c).reshape(-1, 3)
+    wv = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
+    sn = None if s_n is None else _f64(s_n)
+    h = _P()
+    _check(lib().ft_load_sfts(ctx.handle, ctypes.byref(desc), pp, pdt, stride, int(on_dev),
+                              t_mid.ctypes.data, v.ctypes.data,
+                              None if wv is None else wv.ctypes.data,
+                              None if sn is None else sn.ctypes.data,
+                              _stream(stream, on_dev), ctypes.byref(h)))
+    return Band(ctx, h)
+
+
+def make_bank(ctx, band, k0, n_f0, f1, sky, subband_bins, stream=None) -> Bank:
+    desc, keep = _bank_desc(k0, n_f0, f1, sky, subband_bins)
+    h = _P()
+    _check(lib().ft_make_bank(ctx.handle, band.handle, ctypes.byref(desc), _stream(stream, False),
+                              ctypes.byref(h)))
+    return Bank(band, h)
+
+
+def required_wings(n_sft, t_mid, v_over_c, t_sft, t0, k0, n_f0, f1, sky, subband_bins=1):
+    bd, keep1 = _band_desc(n_sft, 1, 0, t_sft, t0, "f32")
+    kd, keep2 = _bank_desc(k0, n_f0, f1, sky, subband_bins)
+    t_mid = _f64(t_mid)
+    v = _f64(v_over_c).reshape(-1, 3)
+    lo, hi = _I(), _I()
+    _check(lib().ft_required_wings(ctypes.byref(bd), t_mid.ctypes.data, v.ctypes.data,
+                                   ctypes.byref(kd), ctypes.byref(lo), ctypes.byref(hi)))
+    return lo.value, hi.value
+
+
+def eval_statistic(ctx, band, bank, s_out, z_out=None, n_oob_out=None, stream=None):
+    """ft_eval_statistic into caller-owned float32 s_out (and z_out, int32 n_oob_out)."""
+    ps, dev = _ptr(s_out)
+    pz, _ = _ptr(z_out)
+    po, _ = _ptr(n_oob_out)
+    _check(lib().ft_eval_statistic(ctx.handle, band.handle, bank.handle, ps, pz, po, int(dev),
+                                   _stream(stream, dev)))
+
+
+def topk_per_band(ctx, band, bank, k, out, stream=None):
+    """ft_topk_per_band into `out`: a host numpy array of CANDIDATE_DTYPE [n_sub, k] or a
+    device byte tensor of n_sub * k * 16 bytes (decode with decode_candidates)."""
+    po, dev = _ptr(out)
+    _check(lib().ft_topk_per_band(ctx.handle, band.handle, bank.handle, int(k), po, int(dev),
+                                  _stream(stream, dev)))
+
+
+def decode_candidates(buf, n_sub, k):
+    """(template_idx int64 [n_sub, k], s float32, z float32) from a candidate buffer."""
+    if _is_torch(buf):
+        buf = buf.cpu().numpy()
+    arr = np.frombuffer(np.ascontiguousarray(buf).tobytes(), dtype=CANDIDATE_DTYPE).reshape(n_sub, k)
+    return arr["template_idx"].copy(), arr["s"].copy(), arr["z"].copy()
+
+
+def track_bins(ctx, band, bank, templates, out, stream=None):
+    """ft_track_bins: templates int64 [n], out int32 [n, N_SFT]; both host or both device."""
+    pt, dev = _ptr(templates)
+    pb, dev2 = _ptr(out)
+    if dev != dev2:
+        raise ValueError("templates and out must both be host or both device")
+    n = templates.shape[0]
+    _check(lib().ft_track_bins(ctx.handle, band.handle, bank.handle, pt, n, pb, int(dev),
+                               _stream(stream, dev)))

@@ -1,0 +1,145 @@
+// ft_internal.cuh -- shared internals of the fasttracks CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fasttracks.h"
+
+// ------------------------------------------------------------------ host error plumbing
+
+void ft_set_error(const std::string &msg);
+
+#define FT_FAIL(code, msg)              \
+    do {                                \
+        ft_set_error(msg);              \
+        return (code);                  \
+    } while (0)
+
+#define FT_CUDA(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            ft_set_error(std::string(#call) + ": " + cudaGetErrorString(e_));              \
+            return (e_ == cudaErrorMemoryAllocation) ? FT_ERR_OOM : FT_ERR_CUDA;           \
+        }                                                                                  \
+    } while (0)
+
+#define FT_TRY(call)            \
+    do {                        \
+        int rc_ = (call);       \
+        if (rc_ != FT_OK)       \
+            return rc_;         \
+    } while (0)
+
+// device status word bits
+#define FT_STATUS_TIMEOUT 1u
+#define FT_STATUS_NONFINITE 2u
+
+// ------------------------------------------------------------------ handles
+
+struct ft_ctx {
+    int device = 0;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    unsigned int *d_status = nullptr;  // device status word (FT_STATUS_*)
+    void *scratch = nullptr;           // grown on demand; candidate lists etc.
+    size_t scratch_bytes = 0;
+    void *outbuf = nullptr;            // device staging for host outputs
+    size_t outbuf_bytes = 0;
+};
+
+struct ft_band {
+    ft_ctx *ctx = nullptr;
+    int n_det = 0;
+    std::vector<int> n_sft;
+    int64_t N = 0;        // total rows
+    int W = 0;            // bins per row
+    int Wp = 0;           // padded row stride (elements)
+    int64_t k_lo = 0;
+    double t_sft = 0, t0 = 0;
+    int dtype = FT_F32;
+    void *d_power = nullptr;  // [N][Wp] storage dtype
+    double *d_tau = nullptr;  // [N] (t_mid - t0) * T_SFT
+    double *d_v = nullptr;    // [N][3]
+    float *d_w = nullptr;     // [N]
+    double *d_sn = nullptr;   // [N] or null
+    double mu = 0, sigma = 0;
+    bool weighted = false;
+    std::vector<double> h_tau, h_vabs;
+};
+
+struct ft_bank {
+    ft_ctx *ctx = nullptr;
+    const ft_band *band = nullptr;
+    int64_t k0 = 0;
+    int n_f0 = 0, n_f1 = 0;
+    int64_t n_sky = 0;
+    int sub = 1;
+    int n_sub = 0;
+    double *d_f1 = nullptr;    // [n_f1]
+    double *d_sky = nullptr;   // [n_sky][3]
+    long long *d_G = nullptr;  // [n_f1][N] Q32 f1*tau
+    bool window_safe = false;
+};
+
+int ft_ctx_scratch(ft_ctx *ctx, size_t bytes, void **p);
+int ft_ctx_outbuf(ft_ctx *ctx, size_t bytes, void **p);
+
+// ------------------------------------------------------------------ kernel parameters
+
+struct FtCand {
+    float s;
+    float z;
+    long long t;
+};
+
+struct EvalParams {
+    const void *power;
+    int Wp, W;
+    long long N;
+    const double *tau;
+    const double *v;
+    const float *w;
+    const double *sky;
+    const long long *G;  // [n_f1][N]
+    long long K0, k_lo;
+    int n_f0, n_f1;
+    long long n_sky;
+    int n_f1g, n_f0t;  // f1 groups (warps per CTA = F) and f0 tiles (32*R each)
+    int S, n_stages;   // SFT rows per stage
+    double mu, sigma;
+    float *s_out;
+    float *z_out;
+    int *oob_out;
+    FtCand *cand;  // per-CTA candidate lists [n_cta][lsub_max][k]
+    int k, sub, lsub_max;
+    unsigned int *status;
+};
+
+// launch helpers implemented in ft_eval.cu
+struct EvalShape {
+    int R;       // f0 slots per lane (tile width 32*R)
+    int F;       // warps (f1 values) per CTA
+    int S;       // SFT rows per stage
+    int nbuf;    // stage buffers
+};
+
+size_t ft_eval_smem_bytes(const ft_band *band, const EvalShape &sh, int k);
+EvalShape ft_default_shape(const ft_ctx *ctx, const ft_band *band, const ft_bank *bank);
+int ft_launch_eval(const ft_band *band, const ft_bank *bank, const EvalShape &sh, EvalParams p,
+                   cudaStream_t st);
+int ft_launch_merge(const ft_bank *bank, const EvalShape &sh, const FtCand *cand, int k,
+                    int lsub_max, ft_candidate *out, cudaStream_t st);
+int ft_launch_convert(const void *src, int src_dtype, long long src_stride, void *dst,
+                      int dst_dtype, long long N, int W, int Wp, unsigned int *status,
+                      cudaStream_t st);
+int ft_launch_gtable(const double *f1, int n_f1, const double *tau, long long N,
+                     long long *G, cudaStream_t st);
+int ft_launch_track_bins(const ft_band *band, const ft_bank *bank, const long long *tmpl,
+                         long long n, int *bins, cudaStream_t st);
