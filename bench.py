@@ -1,0 +1,370 @@
+"""Throughput of the brute-force short-coherence search on B300 (template x SFT evals/s).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--dtype f16|bf16|f32] [--n-sky 10000] [--no-cpu-baseline] [--no-e2e]
+
+One step = the whole hot path over the search-shaped workload: for every template of the
+bank (180 f0 x 20 f1 x 1e4 sky = 3.6e7 templates) and every SFT (2 detectors x 1 yr at 70%
+duty = 24,419 SFTs) the track bin, the power gather and the sum, then the critical ratio
+and the top-10 per 0.01 Hz sub-band (ft_topk_per_band: one evaluation kernel with the
+selection fused in, plus one merge kernel).  Inputs are synthetic (seeded) and resident in
+HBM before timing; L2 is flushed (256 MB write) between timed steps, outside the events.
+
+Under torchrun (N > 1) every rank runs its own replica of the workload (weak scaling, no
+data-path collective); rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "template·SFT evals/s on 1 B300, chosen vs plain FP32 at stated rel. error"
+UNIT = "evals/s"
+SMEM_BYTES_PER_CLK_PER_SM = 128  # 32 banks x 4 B
+ESIZE = {"f32": 4, "f16": 2, "bf16": 2}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_desc(sfts, bank, dtype):
+    return {
+        "workload": "search-shaped band 200.0-200.1 Hz: 2 detectors x 1 yr of 1800 s SFTs at 70% "
+                    f"duty ({sfts.n_total} SFTs, {sfts.n_bins}-bin window incl. Doppler/spindown "
+                    f"wings); bank {bank.n_f0} f0 x {bank.n_f1} f1 x {bank.n_sky} Fibonacci sky = "
+                    f"{bank.n_templates} templates; top-10 per 0.01 Hz sub-band",
+        "n_sft": sfts.n_total,
+        "n_templates": bank.n_templates,
+        "evals_per_step": bank.n_templates * sfts.n_total,
+        "storage": dtype,
+        "accumulate": "f32 (compensated across SFT stages)",
+        "track_bins": "FP64 eps + exact Q32 integer",
+        "l2": "flushed between timed steps (256 MB write, outside the per-step events)",
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms",
+                 "100", "-i", str(self.device)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def time_steps(fn, steps, warmup, stream, flush):
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for i in range(steps):
+        flush()
+        ev[i][0].record(stream)
+        fn()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def cpu_baseline(sfts, bank, target_s, seed=7):
+    """The CPU FP64 oracle, as it stands, on a bounded template sample of the same workload."""
+    import oracle
+
+    g = np.random.default_rng(seed)
+    n = 256
+    t0 = time.perf_counter()
+    samp = g.choice(bank.n_templates, n, replace=False)
+    s_or, _ = oracle.statistic(sfts, bank, samp)
+    dt = time.perf_counter() - t0
+    if dt < target_s:
+        n2 = int(min(bank.n_templates, max(n, n * target_s / max(dt, 1e-3))))
+        samp = g.choice(bank.n_templates, n2, replace=False)
+        t0 = time.perf_counter()
+        s_or, _ = oracle.statistic(sfts, bank, samp)
+        dt = time.perf_counter() - t0
+    evals = len(samp) * sfts.n_total
+    return {"value": evals / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{len(samp)} random templates of the same bank x all {sfts.n_total} SFTs "
+                      f"({evals:.3g} evals, {dt:.1f} s, FP64, OpenMP over templates)",
+            "seconds": dt}, samp, s_or
+
+
+def rel_error(s_gpu, s_or):
+    r = np.abs(np.asarray(s_gpu, np.float64) - s_or) / np.abs(s_or)
+    return {"max": float(r.max()), "rms": float(math.sqrt(np.mean(r * r))), "n": int(len(r))}
+
+
+def run_reference(args):
+    """Reference arm: the CPU FP64 oracle on the host cores, bounded sample per step."""
+    import ftsynth
+    import oracle
+
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    sfts, bank = ftsynth.config1(n_sky=args.n_sky)
+    g = np.random.default_rng(11)
+    per_step = 128
+    t0 = time.perf_counter()
+    oracle.statistic(sfts, bank, g.choice(bank.n_templates, per_step, replace=False))
+    dt = time.perf_counter() - t0
+    per_step = int(max(64, per_step * args.ref_step_s / max(dt, 1e-3)))
+    for _ in range(args.warmup):
+        oracle.statistic(sfts, bank, g.choice(bank.n_templates, per_step, replace=False))
+    times = []
+    for _ in range(args.steps):
+        samp = g.choice(bank.n_templates, per_step, replace=False)
+        t0 = time.perf_counter()
+        oracle.statistic(sfts, bank, samp)
+        times.append(time.perf_counter() - t0)
+    evals = per_step * sfts.n_total
+    value = evals * len(times) / sum(times)
+    cfg = workload_desc(sfts, bank, "f64")
+    cfg["storage"] = "f64 (oracle)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": f"{per_step} random templates x {sfts.n_total} SFTs per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="f16", choices=["f16", "bf16", "f32"])
+    ap.add_argument("--n-sky", type=int, default=10_000)
+    ap.add_argument("--k", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-step-s", type=float, default=4.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import ftsynth
+    import paper_2411_18370_b300 as ft
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if pg is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        return float(t.item())
+
+    sfts, bank = ftsynth.config1(n_sky=args.n_sky)
+    ctx = ft.create(local)
+    stream = torch.cuda.current_stream()
+    P32 = torch.from_numpy(sfts.power.astype(np.float32))
+    P32d = P32.cuda()
+    flushbuf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def flush():
+        flushbuf.fill_(1)
+
+    def mk(dtype):
+        band = ft.load_sfts(ctx, P32d, sfts.t_mid, sfts.v, sfts.n_sft, sfts.k_lo, sfts.t_sft,
+                            sfts.t0, dtype=dtype, s_n=sfts.s_n)
+        bk = ft.make_bank(ctx, band, bank.k0, bank.n_f0, bank.f1, bank.sky, bank.subband_bins)
+        return band, bk
+
+    cand = torch.empty(bank.n_subbands * args.k * 16, dtype=torch.uint8, device="cuda")
+    evals = bank.n_templates * sfts.n_total
+    runs = {}
+    for dtype in dict.fromkeys([args.dtype, "f32"]):
+        band, bk = mk(dtype)
+        assert bk.window_safe
+        step = lambda: ft.topk_per_band(ctx, band, bk, args.k, cand, stream=stream)
+        barrier()
+        with ClockSampler(local) as clk:
+            times = time_steps(step, args.steps if dtype == args.dtype else max(5, args.steps // 2),
+                               args.warmup, stream, flush)
+        barrier()
+        ctx.check_status()
+        mean_ms = statistics.mean(times)
+        runs[dtype] = {"band": band, "bank": bk, "times": times, "mean_ms": mean_ms,
+                       "mean_ms_max": max_over_ranks(mean_ms), "clocks": clk.summary()}
+
+    chosen = runs[args.dtype]
+    value = ws * evals / (chosen["mean_ms_max"] / 1e3)
+    clocks = chosen["clocks"] or {}
+    sm_mhz = clocks.get("sm_mhz")
+    esize = ESIZE[args.dtype]
+    achieved_gbs = evals * esize / (chosen["mean_ms"] / 1e3) / 1e9
+    peak_max_clk = 148 * SMEM_BYTES_PER_CLK_PER_SM * 2032e6 / 1e9
+    roofline = {
+        "bound": "smem",
+        "kernel": "k_eval (gather-accumulate, fused top-k epilogue)",
+        "achieved": achieved_gbs,
+        "peak": peak_max_clk,
+        "unit": "GB/s",
+        "frac": achieved_gbs / peak_max_clk,
+        "peak_basis": "derived: 148 SMs x 128 B/clk shared-memory load bandwidth x 2032 MHz max "
+                      "SM clock (no measured shared-memory peak exists in MEASURED_PEAKS.json)",
+        "algorithmic_bytes_per_launch": evals * esize,
+        "bytes_per_eval": esize,
+        "frac_at_sampled_clock": (achieved_gbs / (148 * SMEM_BYTES_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e9)
+                                  if sm_mhz else None),
+        "traffic": None,
+    }
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": chosen["mean_ms_max"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_desc(sfts, bank, args.dtype),
+        "roofline": roofline,
+        "gpu_launches": 2 * args.steps,
+        "clocks": chosen["clocks"],
+        "plain_fp32": {"value": ws * evals / (runs["f32"]["mean_ms_max"] / 1e3),
+                       "ms_per_step": runs["f32"]["mean_ms_max"], "clocks": runs["f32"]["clocks"]},
+    }
+
+    if rank == 0 and not args.no_cpu_baseline:
+        cb, samp, s_or = cpu_baseline(sfts, bank, args.cpu_seconds)
+        out["cpu_baseline"] = {k: v for k, v in cb.items() if k != "seconds"}
+        # relative error of each storage type at the oracle's sample (computed in this leg)
+        errs = {}
+        idx = torch.from_numpy(samp.astype(np.int64)).cuda()
+        for dtype, r in runs.items():
+            s_d = torch.empty(bank.n_templates, dtype=torch.float32, device="cuda")
+            ft.eval_statistic(ctx, r["band"], r["bank"], s_d, stream=stream)
+            errs[dtype] = rel_error(s_d[idx].cpu().numpy(), s_or)
+            del s_d
+        out["rel_error_vs_oracle"] = errs
+
+    if not args.no_e2e:
+        # end to end through the C ABI with host buffers: H2D of the SFT power and metadata,
+        # bank upload, search, D2H of the candidates; wall clock per step
+        Ph = P32.pin_memory()
+        cand_h = np.zeros((bank.n_subbands, args.k), dtype=ft.CANDIDATE_DTYPE)
+
+        def e2e_step():
+            band = ft.load_sfts(ctx, Ph, sfts.t_mid, sfts.v, sfts.n_sft, sfts.k_lo, sfts.t_sft,
+                                sfts.t0, dtype=args.dtype, s_n=sfts.s_n)
+            bk = ft.make_bank(ctx, band, bank.k0, bank.n_f0, bank.f1, bank.sky, bank.subband_bins)
+            ft.topk_per_band(ctx, band, bk, args.k, cand_h)
+            bk.close()
+            band.close()
+
+        e2e_steps = max(3, args.steps // 4)
+        for _ in range(2):
+            e2e_step()
+        barrier()
+        wall = []
+        for _ in range(e2e_steps):
+            flush()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_step()
+            wall.append(time.perf_counter() - t0)
+        barrier()
+        e2e_mean = max_over_ranks(statistics.mean(wall))
+        h2d = (P32.numel() * 4 + sfts.t_mid.nbytes + sfts.v.nbytes + sfts.s_n.nbytes
+               + bank.f1.nbytes + bank.sky.nbytes + 4 * len(sfts.n_sft))
+        d2h = cand_h.nbytes + 4
+        out["e2e"] = {"value": ws * evals / e2e_mean, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_mean,
+                      "steps": e2e_steps, "gpu_launches_per_step": 4}
+
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -260,7 +260,7 @@ int ft_load_sfts(ft_ctx *ctx, const ft_band_desc *d, const void *power, int powe
     b->n_sft.assign(d->n_sft, d->n_sft + d->n_det);
     b->N = N;
     b->W = d->n_bins;
-    b->Wp = (d->n_bins + 31) / 32 * 32;
+    b->Wp = d->dtype == FT_F32 ? (d->n_bins + 31) / 32 * 32 : (d->n_bins + 63) / 64 * 64;
     b->k_lo = d->k_lo;
     b->t_sft = d->t_sft;
     b->t0 = d->t0;
@@ -292,8 +292,7 @@ int ft_load_sfts(ft_ctx *ctx, const ft_band_desc *d, const void *power, int powe
         ft_band_destroy(b);
         return rc;
     };
-    const size_t esize = d->dtype == FT_F32 ? 4 : 2;
-    if (cudaMalloc(&b->d_power, static_cast<size_t>(N) * b->Wp * esize) != cudaSuccess) {
+    if (cudaMalloc(&b->d_power, static_cast<size_t>(N) * b->Wp * 4) != cudaSuccess) {
         b->d_power = nullptr;
         ft_set_error("load_sfts: power allocation failed");
         return fail(FT_ERR_OOM);
@@ -455,7 +454,6 @@ static EvalParams base_params(const ft_band *band, const ft_bank *bank)
     EvalParams p;
     std::memset(&p, 0, sizeof(p));
     p.power = band->d_power;
-    p.Wp = band->Wp;
     p.W = band->W;
     p.N = band->N;
     p.tau = band->d_tau;
@@ -535,7 +533,7 @@ int ft_topk_per_band(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int 
     DeviceGuard g(ctx->device);
     cudaStream_t st = as_stream(stream);
     const EvalShape sh = ft_default_shape(ctx, band, bank);
-    const int J = 32 * sh.R;
+    const int J = sh.J;
     const long long n_f0t = (bank->n_f0 + J - 1) / J;
     const long long n_f1g = (bank->n_f1 + sh.F - 1) / sh.F;
     const long long n_cta = bank->n_sky * n_f1g * n_f0t;

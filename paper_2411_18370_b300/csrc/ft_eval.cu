@@ -10,16 +10,16 @@
 //     X0  = C + G + floor(G E / 2^32)
 //     k_j = j + floor((X0 + 2^31 + j E) / 2^32)
 //
-// Work decomposition (one CTA = one sky point x F consecutive f1 values x 32R consecutive
-// f0 indices; warp w <-> f1 value, lane <-> f0 index j0 + lane + 32 r, r < R):
-//   * SFT rows are streamed through shared memory in stages of S rows, each stage one
-//     contiguous cp.async.bulk (TMA) copy completing on an mbarrier, double-buffered.
-//   * per stage the CTA computes E, C per SFT (FP64, one thread per row) and X0 per
-//     (f1, SFT) (integer), so the per-evaluation work is one IMAD.WIDE, one shared-memory
-//     load and one FFMA; lanes of a warp read consecutive bins (conflict-free).
-//   * FP32 partial sums per stage are folded into a compensated (2Sum) FP32 pair.
-//   * epilogue: either write s (and z, out-of-window counts) or select, per sub-band, the
-//     k loudest templates of the CTA into a candidate list (merged by k_topk_merge).
+// Work decomposition: one CTA = one sky point x F consecutive f1 values (one warp each) x
+// a tile of J consecutive f0 indices.  SFT rows stream through shared memory in stages of S
+// rows, each stage one contiguous cp.async.bulk (TMA) copy completing on an mbarrier,
+// double-buffered.  Per stage the CTA computes E, C per SFT (FP64) and each warp the track
+// origin of its f1 value per SFT (integer).  Two kernels:
+//   * k_eval_fast (tracks provably inside the window): shifted-row sums, see below;
+//   * k_eval_checked (otherwise): the full bin per (template, SFT) with a bounds check.
+// FP32 partial sums per stage are folded into a compensated (2Sum) FP32 pair.  The
+// epilogue writes s (and z, out-of-window counts) or selects, per sub-band, the k loudest
+// templates of the CTA into a candidate list that k_topk_merge reduces.
 #include "ft_internal.cuh"
 
 #include <climits>
@@ -150,16 +150,21 @@ __device__ __forceinline__ float to_float<__nv_bfloat16>(__nv_bfloat16 x)
 
 // ------------------------------------------------------------------ shared-memory layout
 
-struct SmemLayout {
-    size_t bars, tabE, tabW, tabC, tabX, buf, total, buf_bytes;
-};
-
 __host__ __device__ inline size_t align_up(size_t x, size_t a)
 {
     return (x + a - 1) / a * a;
 }
 
-__host__ __device__ inline SmemLayout smem_layout(int S, int F, int Wp, int esize, int R, bool topk)
+// Offsets (bytes) of the per-CTA shared-memory regions.  Stage tables are double-buffered
+// (index tb = stage & 1); power stages use kNbuf buffers of S rows x row_bytes each, plus a
+// guard tail so that lanes past the end of the f0 range may read (and discard) past the
+// last row without leaving the allocation.
+struct SmemLayout {
+    size_t bars, tabE, tabW, tabC, tabX, evA, evK, evN, buf, total, stage_bytes;
+};
+
+__host__ __device__ inline SmemLayout smem_layout(int S, int F, int row_bytes, int J, bool fast,
+                                                  bool topk)
 {
     SmemLayout L;
     size_t o = 0;
@@ -171,245 +176,127 @@ __host__ __device__ inline SmemLayout smem_layout(int S, int F, int Wp, int esiz
     o = align_up(o + 2 * S * sizeof(float), 16);
     L.tabC = o;
     o = align_up(o + 2 * S * sizeof(long long), 16);
-    L.tabX = o;
-    o = align_up(o + 2 * (size_t)F * S * sizeof(long long), 128);
+    L.tabX = o;  // checked kernel: X0 [2][F][S] int64; fast kernel: word offsets [2][F][S] int
+    o = align_up(o + 2 * (size_t)F * S * (fast ? sizeof(int) : sizeof(long long)), 16);
+    L.evA = o;
+    o = align_up(o + (fast ? 2 * (size_t)F * S * sizeof(int) : 0), 16);
+    L.evK = o;
+    o = align_up(o + (fast ? 2 * (size_t)F * S * sizeof(int) : 0), 16);
+    L.evN = o;
+    o = align_up(o + (fast ? 2 * (size_t)F * sizeof(int) : 0), 128);
     L.buf = o;
-    size_t stage_bytes = (size_t)kNbuf * S * Wp * esize;
-    size_t topk_bytes = topk ? (size_t)F * 32 * R * 2 * sizeof(float) : 0;
-    L.buf_bytes = stage_bytes > topk_bytes ? stage_bytes : topk_bytes;
-    o += L.buf_bytes;
+    L.stage_bytes = (size_t)S * row_bytes;
+    const size_t pipe = kNbuf * L.stage_bytes + (size_t)(J + 64) * 4;
+    const size_t tk = topk ? (size_t)F * J * 2 * sizeof(float) : 0;
+    o += pipe > tk ? pipe : tk;
     L.total = o;
     return L;
 }
 
-// ------------------------------------------------------------------ evaluation kernel
+// ------------------------------------------------------------------ pieces shared by kernels
 
-template <typename T, int R, bool CHECKED>
-__global__ void __launch_bounds__(1024, 1) k_eval(const EvalParams p)
+struct CtaTile {
+    long long cta, sky;
+    int f0t, f1g, j0;
+    double n0, n1, n2;
+};
+
+__device__ __forceinline__ CtaTile decode_tile(const EvalParams &p, int J)
 {
-    extern __shared__ __align__(128) unsigned char smem[];
+    CtaTile c;
+    c.cta = blockIdx.x;
+    c.f0t = static_cast<int>(c.cta % p.n_f0t);
+    const long long rest = c.cta / p.n_f0t;
+    c.f1g = static_cast<int>(rest % p.n_f1g);
+    c.sky = rest / p.n_f1g;
+    c.j0 = c.f0t * J;
+    c.n0 = p.sky[3 * c.sky];
+    c.n1 = p.sky[3 * c.sky + 1];
+    c.n2 = p.sky[3 * c.sky + 2];
+    return c;
+}
+
+__device__ __forceinline__ int rows_in_stage(const EvalParams &p, int st)
+{
+    const long long left = p.N - static_cast<long long>(st) * p.S;
+    return static_cast<int>(left < p.S ? left : p.S);
+}
+
+// Thread 0: expect the stage's bytes on its buffer's mbarrier and start the bulk copy.
+__device__ __forceinline__ void issue_stage(const EvalParams &p, unsigned char *buf,
+                                            unsigned long long *bars, size_t stage_bytes, int st)
+{
+    const int nb = st % kNbuf;
+    const unsigned bytes = static_cast<unsigned>(rows_in_stage(p, st)) * p.row_bytes;
+    mbar_arrive_expect_tx(&bars[nb], bytes);
+    bulk_copy_g2s(buf + nb * stage_bytes,
+                  static_cast<const unsigned char *>(p.power) + static_cast<size_t>(st) * stage_bytes,
+                  bytes, &bars[nb]);
+}
+
+// Per-SFT terms of stage st for this CTA's sky point: E, C (track arithmetic) and w.
+__device__ __forceinline__ void stage_table_a(const EvalParams &p, const CtaTile &c, int st,
+                                              int *tabE, long long *tabC, float *tabW)
+{
+    const int tb = st & 1;
+    const int nr = rows_in_stage(p, st);
+    for (int a = threadIdx.x; a < nr; a += blockDim.x) {
+        const long long alpha = static_cast<long long>(st) * p.S + a;
+        int E;
+        long long C;
+        track_ec(p.v + 3 * alpha, c.n0, c.n1, c.n2, p.K0, p.k_lo, E, C);
+        tabE[tb * p.S + a] = E;
+        tabC[tb * p.S + a] = C;
+        tabW[tb * p.S + a] = p.w[alpha];
+    }
+}
+
+// Thread 0 after a failed wait: record the timeout and let copies still in flight land
+// before the CTA's shared memory is released.
+__device__ void abandon_tile(const EvalParams &p, unsigned long long *bars, int st)
+{
+    if (threadIdx.x == 0) {
+        atomicOr(p.status, FT_STATUS_TIMEOUT);
+        for (int s2 = st; s2 < p.n_stages && s2 < st + kNbuf; ++s2)
+            (void)mbar_wait_bounded(&bars[s2 % kNbuf], (s2 / kNbuf) & 1);
+    }
+}
+
+// Fused candidate selection: vs/vz hold [F][J] values of this CTA's templates (index
+// = f1 slot * J + j - j0).  Per sub-band, one warp extracts the k best by (s desc, t asc)
+// in k rounds of a warp arg-max restricted to keys ranked after the previous pick.
+__device__ void cta_topk(const EvalParams &p, const CtaTile &c, int J, const float *vs,
+                         const float *vz)
+{
     const int F = blockDim.x >> 5;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int S = p.S;
-    const SmemLayout L = smem_layout(S, F, p.Wp, sizeof(T), R, p.cand != nullptr);
-    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + L.bars);
-    int *tabE = reinterpret_cast<int *>(smem + L.tabE);
-    float *tabW = reinterpret_cast<float *>(smem + L.tabW);
-    long long *tabC = reinterpret_cast<long long *>(smem + L.tabC);
-    long long *tabX = reinterpret_cast<long long *>(smem + L.tabX);
-    T *buf = reinterpret_cast<T *>(smem + L.buf);
-
-    const long long cta = blockIdx.x;
-    const int f0t = static_cast<int>(cta % p.n_f0t);
-    const long long rest = cta / p.n_f0t;
-    const int f1g = static_cast<int>(rest % p.n_f1g);
-    const long long sky = rest / p.n_f1g;
-    const int j0 = f0t * 32 * R;
-    const int f = f1g * F + warp;
-    const bool f_ok = f < p.n_f1;
-    const double n0 = p.sky[3 * sky], n1 = p.sky[3 * sky + 1], n2 = p.sky[3 * sky + 2];
-
-    int jr[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int j = j0 + lane + 32 * r;
-        jr[r] = j < p.n_f0 ? j : p.n_f0 - 1;
-    }
-
-    const size_t stage_elems = static_cast<size_t>(S) * p.Wp;
-    const long long N = p.N;
-    const int n_stages = p.n_stages;
-
-    auto rows_in_stage = [&](int st) -> int {
-        const long long left = N - static_cast<long long>(st) * S;
-        return static_cast<int>(left < S ? left : S);
-    };
-    auto issue = [&](int st) {
-        const int nb = st % kNbuf;
-        const unsigned bytes = static_cast<unsigned>(rows_in_stage(st)) * p.Wp * sizeof(T);
-        mbar_arrive_expect_tx(&bars[nb], bytes);
-        bulk_copy_g2s(buf + nb * stage_elems,
-                      static_cast<const T *>(p.power) + static_cast<size_t>(st) * stage_elems, bytes,
-                      &bars[nb]);
-    };
-    // per-SFT terms of stage st: E, w, C
-    auto table_a = [&](int st) {
-        const int tb = st & 1;
-        const int nr = rows_in_stage(st);
-        for (int a = tid; a < nr; a += blockDim.x) {
-            const long long alpha = static_cast<long long>(st) * S + a;
-            int E;
-            long long C;
-            track_ec(p.v + 3 * alpha, n0, n1, n2, p.K0, p.k_lo, E, C);
-            tabE[tb * S + a] = E;
-            tabC[tb * S + a] = C;
-            tabW[tb * S + a] = p.w[alpha];
-        }
-    };
-    // per-(f1, SFT) origins of stage st: X0 + 2^31
-    auto table_b = [&](int st) {
-        const int tb = st & 1;
-        const int nr = rows_in_stage(st);
-        for (int i = tid; i < F * nr; i += blockDim.x) {
-            const int fl = i / nr, a = i - fl * nr;
-            int fg = f1g * F + fl;
-            fg = fg < p.n_f1 ? fg : p.n_f1 - 1;
-            const long long alpha = static_cast<long long>(st) * S + a;
-            const long long G = p.G[static_cast<long long>(fg) * N + alpha];
-            tabX[(static_cast<size_t>(tb) * F + fl) * S + a] =
-                track_x0(tabC[tb * S + a], G, tabE[tb * S + a]) + (1ll << 31);
-        }
-    };
-
-    if (tid == 0) {
-        for (int b = 0; b < kNbuf; ++b)
-            mbar_init(&bars[b], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
-        for (int st = 0; st < kNbuf && st < n_stages; ++st)
-            issue(st);
-    }
-    table_a(0);
-    __syncthreads();
-    table_b(0);
-
-    float part[R], hi[R], lo[R];
-    int oob[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        part[r] = 0.f;
-        hi[r] = 0.f;
-        lo[r] = 0.f;
-        oob[r] = 0;
-    }
-
-    bool ok = true;
-    int st = 0;
-    for (; st < n_stages; ++st) {
-        const int tb = st & 1;
-        if (st + 1 < n_stages)
-            table_a(st + 1);
-        const bool got = mbar_wait_bounded(&bars[st % kNbuf], (st / kNbuf) & 1);
-        if (!__syncthreads_and(got)) {
-            ok = false;
-            break;
-        }
-        const T *rows = buf + (st % kNbuf) * stage_elems;
-        const int nr = rows_in_stage(st);
-        const int *tE = tabE + tb * S;
-        const float *tW = tabW + tb * S;
-        const long long *tX = tabX + (static_cast<size_t>(tb) * F + warp) * S;
-#pragma unroll 2
-        for (int a = 0; a < nr; ++a) {
-            const T *row = rows + static_cast<size_t>(a) * p.Wp;
-            const int E = tE[a];
-            const float wa = tW[a];
-            const long long X = tX[a];
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int k = track_bin(X, E, jr[r]);
-                float val;
-                if (CHECKED) {
-                    const bool in = static_cast<unsigned>(k) < static_cast<unsigned>(p.W);
-                    const int kc = min(max(k, 0), p.W - 1);
-                    val = in ? to_float<T>(row[kc]) : 0.f;
-                    oob[r] += in ? 0 : 1;
-                } else {
-                    val = to_float<T>(row[k]);
-                }
-                part[r] = __fmaf_rn(wa, val, part[r]);
-            }
-        }
-        // fold the stage partial into the compensated pair (2Sum)
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const float s = __fadd_rn(hi[r], part[r]);
-            const float bp = __fsub_rn(s, hi[r]);
-            const float e = __fadd_rn(__fsub_rn(hi[r], __fsub_rn(s, bp)), __fsub_rn(part[r], bp));
-            lo[r] = __fadd_rn(lo[r], e);
-            hi[r] = s;
-            part[r] = 0.f;
-        }
-        if (st + 1 < n_stages)
-            table_b(st + 1);
-        __syncthreads();
-        if (tid == 0 && st + kNbuf < n_stages)
-            issue(st + kNbuf);
-    }
-
-    if (!ok) {
-        if (tid == 0) {
-            atomicOr(p.status, FT_STATUS_TIMEOUT);
-            // let copies still in flight land before the CTA's shared memory is released
-            for (int s2 = st; s2 < n_stages && s2 < st + kNbuf; ++s2)
-                (void)mbar_wait_bounded(&bars[s2 % kNbuf], (s2 / kNbuf) & 1);
-        }
-        return;
-    }
-
-    // ---------------------------------------------------------------- epilogue
-    const long long trow = (sky * p.n_f1 + f) * static_cast<long long>(p.n_f0);
-    float sv[R], zv[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        sv[r] = __fadd_rn(hi[r], lo[r]);
-        zv[r] = static_cast<float>(
-            (static_cast<double>(hi[r]) + static_cast<double>(lo[r]) - p.mu) / p.sigma);
-    }
-    if (p.s_out != nullptr && f_ok) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int j = j0 + lane + 32 * r;
-            if (j < p.n_f0) {
-                p.s_out[trow + j] = sv[r];
-                if (p.z_out)
-                    p.z_out[trow + j] = zv[r];
-                if (p.oob_out)
-                    p.oob_out[trow + j] = oob[r];
-            }
-        }
-    }
-    if (p.cand == nullptr)
-        return;
-
-    // fused candidate selection: per sub-band, the k loudest templates of this CTA
-    const int J = 32 * R;
-    float *vs = reinterpret_cast<float *>(buf);
-    float *vz = vs + F * J;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        vs[warp * J + lane + 32 * r] = sv[r];
-        vz[warp * J + lane + 32 * r] = zv[r];
-    }
-    __syncthreads();
-    const int jhi = min(j0 + J, p.n_f0);
-    const int lb0 = j0 / p.sub, lb1 = (jhi - 1) / p.sub;
-    const int nf = min(F, p.n_f1 - f1g * F);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int jhi = min(c.j0 + J, p.n_f0);
+    const int lb0 = c.j0 / p.sub, lb1 = (jhi - 1) / p.sub;
+    const int nf = min(F, p.n_f1 - c.f1g * F);
     for (int lb = lb0 + warp; lb <= lb1; lb += F) {
-        const int ja = max(j0, lb * p.sub), jb = min(jhi, (lb + 1) * p.sub);
+        const int ja = max(c.j0, lb * p.sub), jb = min(jhi, (lb + 1) * p.sub);
         const int width = jb - ja;
         const int count = nf * width;
         float last_s = INFINITY;
         long long last_t = -1;
-        ft_candidate *out = reinterpret_cast<ft_candidate *>(p.cand) +
-                            (cta * p.lsub_max + (lb - lb0)) * p.k;
+        ft_candidate *out =
+            reinterpret_cast<ft_candidate *>(p.cand) + (c.cta * p.lsub_max + (lb - lb0)) * p.k;
         for (int i = 0; i < p.k; ++i) {
             bool have = false;
             float bs = -INFINITY, bz = 0.f;
             long long bt = LLONG_MAX;
-            for (int c = lane; c < count; c += 32) {
-                const int fl = c / width, jj = ja + (c - fl * width);
-                const float s = vs[fl * J + (jj - j0)];
-                const long long t = (sky * p.n_f1 + f1g * F + fl) * static_cast<long long>(p.n_f0) + jj;
+            for (int q = lane; q < count; q += 32) {
+                const int fl = q / width, jj = ja + (q - fl * width);
+                const float s = vs[fl * J + (jj - c.j0)];
+                const long long t =
+                    (c.sky * p.n_f1 + c.f1g * F + fl) * static_cast<long long>(p.n_f0) + jj;
                 const bool elig = (s < last_s) || (s == last_s && t > last_t);
                 const bool better = !have || (s > bs) || (s == bs && t < bt);
                 if (elig && better) {
                     have = true;
                     bs = s;
                     bt = t;
-                    bz = vz[fl * J + (jj - j0)];
+                    bz = vz[fl * J + (jj - c.j0)];
                 }
             }
 #pragma unroll
@@ -426,16 +313,420 @@ __global__ void __launch_bounds__(1024, 1) k_eval(const EvalParams p)
                 }
             }
             if (lane == 0) {
-                ft_candidate c;
-                c.template_idx = have ? bt : -1;
-                c.s = have ? bs : -INFINITY;
-                c.z = have ? bz : 0.f;
-                out[i] = c;
+                ft_candidate cd;
+                cd.template_idx = have ? bt : -1;
+                cd.s = have ? bs : -INFINITY;
+                cd.z = have ? bz : 0.f;
+                out[i] = cd;
             }
             last_s = bs;
             last_t = bt;
         }
     }
+}
+
+// Fold a stage's FP32 partial into the compensated pair (hi, lo) with 2Sum.
+__device__ __forceinline__ void fold2sum(float &hi, float &lo, float &part)
+{
+    const float s = __fadd_rn(hi, part);
+    const float bp = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(part, bp));
+    lo = __fadd_rn(lo, e);
+    hi = s;
+    part = 0.f;
+}
+
+// Epilogue shared by both kernels: s = hi + lo, z in FP64; write and/or select.
+template <int NS>
+__device__ __forceinline__ void finish_tile(const EvalParams &p, const CtaTile &c, int J,
+                                            const int (&jrel)[NS], const float (&hi)[NS],
+                                            const float (&lo)[NS], const int (&oob)[NS],
+                                            unsigned char *buf)
+{
+    const int F = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5;
+    const int f = c.f1g * F + warp;
+    const bool f_ok = f < p.n_f1;
+    const long long trow = (c.sky * p.n_f1 + f) * static_cast<long long>(p.n_f0);
+    float sv[NS], zv[NS];
+#pragma unroll
+    for (int r = 0; r < NS; ++r) {
+        sv[r] = __fadd_rn(hi[r], lo[r]);
+        zv[r] = static_cast<float>(
+            (static_cast<double>(hi[r]) + static_cast<double>(lo[r]) - p.mu) / p.sigma);
+    }
+    if (p.s_out != nullptr && f_ok) {
+#pragma unroll
+        for (int r = 0; r < NS; ++r) {
+            const int j = c.j0 + jrel[r];
+            if (j < p.n_f0) {
+                p.s_out[trow + j] = sv[r];
+                if (p.z_out)
+                    p.z_out[trow + j] = zv[r];
+                if (p.oob_out)
+                    p.oob_out[trow + j] = oob[r];
+            }
+        }
+    }
+    if (p.cand == nullptr)
+        return;
+    float *vs = reinterpret_cast<float *>(buf);
+    float *vz = vs + F * J;
+#pragma unroll
+    for (int r = 0; r < NS; ++r) {
+        vs[warp * J + jrel[r]] = sv[r];
+        vz[warp * J + jrel[r]] = zv[r];
+    }
+    __syncthreads();
+    cta_topk(p, c, J, vs, vz);
+}
+
+// ------------------------------------------------------------------ checked kernel
+//
+// General evaluation kernel: per (template, SFT) the full Q32 bin with a bounds check.
+// Used when the bank's tracks may leave the band's window (reads outside contribute 0 and
+// are counted).  Power rows hold plain elements of T at p.row_elems elements per row.
+
+template <typename T, int R>
+__global__ void __launch_bounds__(1024, 1) k_eval_checked(const EvalParams p)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int J = 32 * R;
+    const int F = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int S = p.S;
+    const SmemLayout L = smem_layout(S, F, p.row_bytes, J, false, p.cand != nullptr);
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + L.bars);
+    int *tabE = reinterpret_cast<int *>(smem + L.tabE);
+    float *tabW = reinterpret_cast<float *>(smem + L.tabW);
+    long long *tabC = reinterpret_cast<long long *>(smem + L.tabC);
+    long long *tabX = reinterpret_cast<long long *>(smem + L.tabX);
+    unsigned char *buf = smem + L.buf;
+    const CtaTile c = decode_tile(p, J);
+
+    int jrel[R], jr[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        jrel[r] = lane + 32 * r;
+        const int j = c.j0 + jrel[r];
+        jr[r] = j < p.n_f0 ? j : p.n_f0 - 1;
+    }
+    auto table_b = [&](int st) {
+        const int tb = st & 1;
+        const int nr = rows_in_stage(p, st);
+        for (int i = threadIdx.x; i < F * nr; i += blockDim.x) {
+            const int fl = i / nr, a = i - fl * nr;
+            int fg = c.f1g * F + fl;
+            fg = fg < p.n_f1 ? fg : p.n_f1 - 1;
+            const long long alpha = static_cast<long long>(st) * S + a;
+            const long long G = p.G[static_cast<long long>(fg) * p.N + alpha];
+            tabX[(static_cast<size_t>(tb) * F + fl) * S + a] =
+                track_x0(tabC[tb * S + a], G, tabE[tb * S + a]) + (1ll << 31);
+        }
+    };
+
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < kNbuf; ++b)
+            mbar_init(&bars[b], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int st = 0; st < kNbuf && st < p.n_stages; ++st)
+            issue_stage(p, buf, bars, L.stage_bytes, st);
+    stage_table_a(p, c, 0, tabE, tabC, tabW);
+    __syncthreads();
+    table_b(0);
+
+    float part[R], hi[R], lo[R];
+    int oob[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        part[r] = hi[r] = lo[r] = 0.f;
+        oob[r] = 0;
+    }
+    for (int st = 0; st < p.n_stages; ++st) {
+        const int tb = st & 1;
+        if (st + 1 < p.n_stages)
+            stage_table_a(p, c, st + 1, tabE, tabC, tabW);
+        const bool got = mbar_wait_bounded(&bars[st % kNbuf], (st / kNbuf) & 1);
+        if (!__syncthreads_and(got)) {
+            abandon_tile(p, bars, st);
+            return;
+        }
+        const T *rows = reinterpret_cast<const T *>(buf + (st % kNbuf) * L.stage_bytes);
+        const int nr = rows_in_stage(p, st);
+        const int *tE = tabE + tb * S;
+        const float *tW = tabW + tb * S;
+        const long long *tX = tabX + (static_cast<size_t>(tb) * F + warp) * S;
+        for (int a = 0; a < nr; ++a) {
+            const T *row = rows + static_cast<size_t>(a) * p.row_elems;
+            const int E = tE[a];
+            const float wa = tW[a];
+            const long long X = tX[a];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int k = track_bin(X, E, jr[r]);
+                const bool in = static_cast<unsigned>(k) < static_cast<unsigned>(p.W);
+                const int kc = min(max(k, 0), p.W - 1);
+                const float val = in ? to_float<T>(row[kc]) : 0.f;
+                oob[r] += in ? 0 : 1;
+                part[r] = __fmaf_rn(wa, val, part[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            fold2sum(hi[r], lo[r], part[r]);
+        if (st + 1 < p.n_stages)
+            table_b(st + 1);
+        __syncthreads();
+        if (threadIdx.x == 0 && st + kNbuf < p.n_stages)
+            issue_stage(p, buf, bars, L.stage_bytes, st + kNbuf);
+    }
+    finish_tile<R>(p, c, J, jrel, hi, lo, oob, buf);
+}
+
+// ------------------------------------------------------------------ fast kernel
+//
+// For a fixed (sky, f1, SFT) the bins of a tile's f0 values are k(j0 + u) = base + u,
+// plus at most one step of sign(E) from some u = jc on, because the tile is narrower than
+// 1/|eps| bins (J |E| < 2^32).  Per stage, each warp derives for its own f1 value and
+// every SFT row the word offset of `base` in shared memory and, for the rare rows whose
+// step falls inside the tile, an entry in its correction list.  The main loop is then a
+// plain shifted-row sum: one shared load (lanes on consecutive words) and one FMA per
+// evaluation; the corrections add w (P[k + s] - P[k]) for the affected f0 afterwards.
+//
+// MODE_F32: rows of FP32, lane <-> f0 offset lane + 32 r.
+// MODE_F16 / MODE_BF16: each row is stored twice as 32-bit pairs, even-aligned
+// (P[2m], P[2m+1]) and odd-aligned (P[2m+1], P[2m+2]); the copy matching the parity of
+// `base` gives every lane the pair of bins (base + 2 lane + 64 r, +1) in one aligned,
+// conflict-free 32-bit load.  Without weights the pair is accumulated by two
+// mixed-precision FMAs (16-bit input, FP32 accumulator), i.e. with no conversion step.
+
+enum { MODE_F32 = 0, MODE_F16 = 1, MODE_BF16 = 2 };
+constexpr int kFastMaxWarps = 20;
+
+template <int MODE>
+__device__ __forceinline__ float lo_to_float(unsigned u)
+{
+    if (MODE == MODE_F16)
+        return __half2float(__ushort_as_half(static_cast<unsigned short>(u & 0xffffu)));
+    return __uint_as_float(u << 16);
+}
+
+template <int MODE>
+__device__ __forceinline__ float hi_to_float(unsigned u)
+{
+    if (MODE == MODE_F16)
+        return __half2float(__ushort_as_half(static_cast<unsigned short>(u >> 16)));
+    return __uint_as_float(u & 0xffff0000u);
+}
+
+// a0 += lo(u), a1 += hi(u) with 16-bit inputs and FP32 accumulators (exact products by 1).
+template <int MODE>
+__device__ __forceinline__ void acc_pair(float &a0, float &a1, unsigned u)
+{
+    if (MODE == MODE_F16) {
+        asm("{\n\t.reg .b16 l, h, one;\n\t"
+            "mov.b32 {l, h}, %2;\n\t"
+            "mov.b16 one, 0x3C00;\n\t"
+            "fma.rn.f32.f16 %0, l, one, %0;\n\t"
+            "fma.rn.f32.f16 %1, h, one, %1;\n\t}"
+            : "+f"(a0), "+f"(a1)
+            : "r"(u));
+    } else {
+        asm("{\n\t.reg .b16 l, h, one;\n\t"
+            "mov.b32 {l, h}, %2;\n\t"
+            "mov.b16 one, 0x3F80;\n\t"
+            "fma.rn.f32.bf16 %0, l, one, %0;\n\t"
+            "fma.rn.f32.bf16 %1, h, one, %1;\n\t}"
+            : "+f"(a0), "+f"(a1)
+            : "r"(u));
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ float read_bin(const unsigned char *rows, int row_words, int a, int k)
+{
+    if (MODE == MODE_F32)
+        return reinterpret_cast<const float *>(rows)[static_cast<size_t>(a) * row_words + k];
+    const unsigned u =
+        reinterpret_cast<const unsigned *>(rows)[static_cast<size_t>(a) * row_words + (k >> 1)];
+    return (k & 1) ? hi_to_float<MODE>(u) : lo_to_float<MODE>(u);
+}
+
+template <int MODE, int R, bool WEIGHTED>
+__global__ void __launch_bounds__(32 * kFastMaxWarps, 2) k_eval_fast(const EvalParams p)
+{
+    constexpr bool PAIR = MODE != MODE_F32;
+    constexpr int NS = PAIR ? 2 * R : R;  // accumulator slots per thread
+    constexpr int J = 32 * NS;            // f0 per tile
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int F = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int S = p.S;
+    const int row_words = p.row_bytes >> 2;
+    const SmemLayout L = smem_layout(S, F, p.row_bytes, J, true, p.cand != nullptr);
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + L.bars);
+    int *tabE = reinterpret_cast<int *>(smem + L.tabE);
+    float *tabW = reinterpret_cast<float *>(smem + L.tabW);
+    long long *tabC = reinterpret_cast<long long *>(smem + L.tabC);
+    int *tabB = reinterpret_cast<int *>(smem + L.tabX);
+    int *evA = reinterpret_cast<int *>(smem + L.evA);
+    int *evK = reinterpret_cast<int *>(smem + L.evK);
+    int *evN = reinterpret_cast<int *>(smem + L.evN);
+    unsigned char *buf = smem + L.buf;
+    const CtaTile c = decode_tile(p, J);
+    const int fg = min(c.f1g * F + warp, p.n_f1 - 1);
+
+    int jrel[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+        jrel[i] = PAIR ? 2 * lane + 64 * (i >> 1) + (i & 1) : lane + 32 * i;
+
+    // per-warp tables of stage st for f1 value fg: base word offsets and corrections
+    auto table_b = [&](int st) {
+        const int tb = st & 1;
+        const int nr = rows_in_stage(p, st);
+        const size_t wbase = (static_cast<size_t>(tb) * F + warp) * S;
+        int cnt = 0;
+        for (int a0 = 0; a0 < nr; a0 += 32) {
+            const int a = a0 + lane;
+            bool ev = false;
+            int packed = 0, basev = 0;
+            if (a < nr) {
+                const long long alpha = static_cast<long long>(st) * S + a;
+                const int E = tabE[tb * S + a];
+                const long long G = p.G[static_cast<long long>(fg) * p.N + alpha];
+                const long long X0p = track_x0(tabC[tb * S + a], G, E) + (1ll << 31);
+                const long long acc0 = X0p + static_cast<long long>(c.j0) * E;
+                const int hb = static_cast<int>(acc0 >> 32);
+                const unsigned L0 = static_cast<unsigned>(acc0);
+                const int base = c.j0 + hb;
+                int jc = J;
+                if (E > 0) {
+                    if (static_cast<unsigned long long>(L0) +
+                            static_cast<unsigned long long>(J - 1) * static_cast<unsigned>(E) >=
+                        0x100000000ull)
+                        jc = static_cast<int>((0x100000000ull - L0 + static_cast<unsigned>(E) - 1) /
+                                              static_cast<unsigned>(E));
+                } else if (E < 0) {
+                    if (static_cast<long long>(L0) + static_cast<long long>(J - 1) * E < 0)
+                        jc = static_cast<int>(L0 / static_cast<unsigned>(-E)) + 1;
+                }
+                tabB[wbase + a] = PAIR ? a * row_words + (base & 1) * (row_words >> 1) + (base >> 1)
+                                       : a * row_words + base;
+                ev = jc < J;
+                packed = a | (jc << 8) | (E < 0 ? (1 << 20) : 0);
+                basev = base;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, ev);
+            if (ev) {
+                const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+                evA[wbase + pos] = packed;
+                evK[wbase + pos] = basev;
+            }
+            cnt += __popc(m);
+        }
+        if (lane == 0)
+            evN[tb * F + warp] = cnt;
+    };
+
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < kNbuf; ++b)
+            mbar_init(&bars[b], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int st = 0; st < kNbuf && st < p.n_stages; ++st)
+            issue_stage(p, buf, bars, L.stage_bytes, st);
+    stage_table_a(p, c, 0, tabE, tabC, tabW);
+    __syncthreads();
+    table_b(0);
+
+    float part[NS], hi[NS], lo[NS];
+    int oob[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        part[i] = hi[i] = lo[i] = 0.f;
+        oob[i] = 0;
+    }
+    for (int st = 0; st < p.n_stages; ++st) {
+        const int tb = st & 1;
+        if (st + 1 < p.n_stages)
+            stage_table_a(p, c, st + 1, tabE, tabC, tabW);
+        const bool got = mbar_wait_bounded(&bars[st % kNbuf], (st / kNbuf) & 1);
+        if (!__syncthreads_and(got)) {
+            abandon_tile(p, bars, st);
+            return;
+        }
+        const unsigned char *rows = buf + (st % kNbuf) * L.stage_bytes;
+        const int nr = rows_in_stage(p, st);
+        const float *tW = tabW + tb * S;
+        const int *tB = tabB + (static_cast<size_t>(tb) * F + warp) * S;
+        // main loop: shifted-row sums
+#pragma unroll 4
+        for (int a = 0; a < nr; ++a) {
+            if (MODE == MODE_F32) {
+                const float *q = reinterpret_cast<const float *>(rows) + tB[a] + lane;
+                if (WEIGHTED) {
+                    const float wa = tW[a];
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        part[r] = __fmaf_rn(wa, q[32 * r], part[r]);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        part[r] = __fadd_rn(part[r], q[32 * r]);
+                }
+            } else {
+                const unsigned *q = reinterpret_cast<const unsigned *>(rows) + tB[a] + lane;
+                if (WEIGHTED) {
+                    const float wa = tW[a];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const unsigned u = q[32 * r];
+                        part[2 * r] = __fmaf_rn(wa, lo_to_float<MODE>(u), part[2 * r]);
+                        part[2 * r + 1] = __fmaf_rn(wa, hi_to_float<MODE>(u), part[2 * r + 1]);
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        acc_pair<MODE>(part[2 * r], part[2 * r + 1], q[32 * r]);
+                }
+            }
+        }
+        // corrections for the rows whose bin steps by sign(E) inside the tile
+        const int ne = evN[tb * F + warp];
+        const size_t wbase = (static_cast<size_t>(tb) * F + warp) * S;
+        for (int e = 0; e < ne; ++e) {
+            const int packed = evA[wbase + e];
+            const int a = packed & 0xff;
+            const int jc = (packed >> 8) & 0xfff;
+            const int sg = (packed >> 20) ? -1 : 1;
+            const int base = evK[wbase + e];
+            const float wa = tW[a];
+#pragma unroll
+            for (int i = 0; i < NS; ++i) {
+                if (jrel[i] >= jc && c.j0 + jrel[i] < p.n_f0) {
+                    const int k = base + jrel[i];
+                    const float d = __fsub_rn(read_bin<MODE>(rows, row_words, a, k + sg),
+                                              read_bin<MODE>(rows, row_words, a, k));
+                    part[i] = WEIGHTED ? __fmaf_rn(wa, d, part[i]) : __fadd_rn(part[i], d);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NS; ++i)
+            fold2sum(hi[i], lo[i], part[i]);
+        if (st + 1 < p.n_stages)
+            table_b(st + 1);
+        __syncthreads();
+        if (threadIdx.x == 0 && st + kNbuf < p.n_stages)
+            issue_stage(p, buf, bars, L.stage_bytes, st + kNbuf);
+    }
+    finish_tile<NS>(p, c, J, jrel, hi, lo, oob, buf);
 }
 
 // ------------------------------------------------------------------ candidate merge
@@ -570,14 +861,19 @@ __global__ void __launch_bounds__(kMergeThreads) k_topk_merge(const ft_candidate
 
 // ------------------------------------------------------------------ helpers
 
+// FP32/FP64 rows -> band layout.  FP32 storage: [N][Wp] floats.  16-bit storage: per row
+// the even copy P[0 .. Wp) followed by the odd copy P[1 .. Wp] (so 32-bit word m of the odd
+// copy is (P[2m+1], P[2m+2])); bins >= W are 0.  Conversion rounds to nearest even.
 __global__ void k_convert(const void *src, int sdt, long long sstride, void *dst, int ddt,
                           long long N, int W, int Wp, unsigned int *status)
 {
-    const long long total = N * Wp;
+    const int row_elems = ddt == FT_F32 ? Wp : 2 * Wp;
+    const long long total = N * row_elems;
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const long long row = i / Wp;
-        const int col = static_cast<int>(i - row * Wp);
+        const long long row = i / row_elems;
+        const int e = static_cast<int>(i - row * row_elems);
+        const int col = e < Wp ? e : e - Wp + 1;
         double x = 0.0;
         if (col < W) {
             x = (sdt == FT_F64) ? static_cast<const double *>(src)[row * sstride + col]
@@ -637,50 +933,79 @@ int grid_for(long long total, int threads)
     return static_cast<int>(g < 1 ? 1 : g);
 }
 
-template <typename T, int R, bool CHECKED>
-int launch_eval_t(const EvalShape &sh, const EvalParams &p, long long n_cta, size_t smem,
-                  cudaStream_t st)
+template <typename K>
+int launch_kernel(K fn, long long n_cta, int threads, size_t smem, const EvalParams &p,
+                  cudaStream_t st, size_t &configured)
 {
-    static size_t configured = 0;
-    auto fn = k_eval<T, R, CHECKED>;
     if (smem > configured) {
         FT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(smem)));
         configured = smem;
     }
-    fn<<<static_cast<unsigned>(n_cta), 32 * sh.F, smem, st>>>(p);
+    fn<<<static_cast<unsigned>(n_cta), threads, smem, st>>>(p);
     FT_CUDA(cudaGetLastError());
     return FT_OK;
 }
 
-template <typename T, bool CHECKED>
-int launch_eval_r(const EvalShape &sh, const EvalParams &p, long long n_cta, size_t smem,
-                  cudaStream_t st)
+template <typename T, int R>
+int launch_checked_t(long long n_cta, int threads, size_t smem, const EvalParams &p, cudaStream_t st)
 {
-    switch (sh.R) {
-    case 1: return launch_eval_t<T, 1, CHECKED>(sh, p, n_cta, smem, st);
-    case 2: return launch_eval_t<T, 2, CHECKED>(sh, p, n_cta, smem, st);
-    case 3: return launch_eval_t<T, 3, CHECKED>(sh, p, n_cta, smem, st);
-    case 4: return launch_eval_t<T, 4, CHECKED>(sh, p, n_cta, smem, st);
-    case 5: return launch_eval_t<T, 5, CHECKED>(sh, p, n_cta, smem, st);
-    case 6: return launch_eval_t<T, 6, CHECKED>(sh, p, n_cta, smem, st);
-    case 7: return launch_eval_t<T, 7, CHECKED>(sh, p, n_cta, smem, st);
-    case 8: return launch_eval_t<T, 8, CHECKED>(sh, p, n_cta, smem, st);
-    default: FT_FAIL(FT_ERR_ARG, "eval: unsupported tile width R");
-    }
+    static size_t configured = 0;
+    return launch_kernel(k_eval_checked<T, R>, n_cta, threads, smem, p, st, configured);
 }
 
 template <typename T>
-int launch_eval_c(bool checked, const EvalShape &sh, const EvalParams &p, long long n_cta,
-                  size_t smem, cudaStream_t st)
+int launch_checked(int R, long long n_cta, int threads, size_t smem, const EvalParams &p,
+                   cudaStream_t st)
 {
-    return checked ? launch_eval_r<T, true>(sh, p, n_cta, smem, st)
-                   : launch_eval_r<T, false>(sh, p, n_cta, smem, st);
+    switch (R) {
+    case 1: return launch_checked_t<T, 1>(n_cta, threads, smem, p, st);
+    case 2: return launch_checked_t<T, 2>(n_cta, threads, smem, p, st);
+    case 3: return launch_checked_t<T, 3>(n_cta, threads, smem, p, st);
+    case 4: return launch_checked_t<T, 4>(n_cta, threads, smem, p, st);
+    case 5: return launch_checked_t<T, 5>(n_cta, threads, smem, p, st);
+    case 6: return launch_checked_t<T, 6>(n_cta, threads, smem, p, st);
+    case 7: return launch_checked_t<T, 7>(n_cta, threads, smem, p, st);
+    case 8: return launch_checked_t<T, 8>(n_cta, threads, smem, p, st);
+    default: FT_FAIL(FT_ERR_ARG, "eval: unsupported tile width");
+    }
 }
 
-int esize_of(int dtype)
+template <int MODE, int R, bool W>
+int launch_fast_t(long long n_cta, int threads, size_t smem, const EvalParams &p, cudaStream_t st)
 {
-    return dtype == FT_F32 ? 4 : 2;
+    static size_t configured = 0;
+    return launch_kernel(k_eval_fast<MODE, R, W>, n_cta, threads, smem, p, st, configured);
+}
+
+template <int MODE, bool W>
+int launch_fast_w(int R, long long n_cta, int threads, size_t smem, const EvalParams &p,
+                  cudaStream_t st)
+{
+    switch (R) {
+    case 1: return launch_fast_t<MODE, 1, W>(n_cta, threads, smem, p, st);
+    case 2: return launch_fast_t<MODE, 2, W>(n_cta, threads, smem, p, st);
+    case 3: return launch_fast_t<MODE, 3, W>(n_cta, threads, smem, p, st);
+    case 4: return launch_fast_t<MODE, 4, W>(n_cta, threads, smem, p, st);
+    case 5: return MODE == MODE_F32 ? launch_fast_t<MODE_F32, 5, W>(n_cta, threads, smem, p, st) : FT_ERR_ARG;
+    case 6: return MODE == MODE_F32 ? launch_fast_t<MODE_F32, 6, W>(n_cta, threads, smem, p, st) : FT_ERR_ARG;
+    case 7: return MODE == MODE_F32 ? launch_fast_t<MODE_F32, 7, W>(n_cta, threads, smem, p, st) : FT_ERR_ARG;
+    case 8: return MODE == MODE_F32 ? launch_fast_t<MODE_F32, 8, W>(n_cta, threads, smem, p, st) : FT_ERR_ARG;
+    default: FT_FAIL(FT_ERR_ARG, "eval: unsupported tile width");
+    }
+}
+
+template <int MODE>
+int launch_fast(bool weighted, int R, long long n_cta, int threads, size_t smem,
+                const EvalParams &p, cudaStream_t st)
+{
+    return weighted ? launch_fast_w<MODE, true>(R, n_cta, threads, smem, p, st)
+                    : launch_fast_w<MODE, false>(R, n_cta, threads, smem, p, st);
+}
+
+int row_bytes_of(const ft_band *band)
+{
+    return band->Wp * 4;  // FP32 rows, or the two 16-bit copies of a row
 }
 
 }  // namespace
@@ -689,30 +1014,35 @@ int esize_of(int dtype)
 
 size_t ft_eval_smem_bytes(const ft_band *band, const EvalShape &sh, int k)
 {
-    return smem_layout(sh.S, sh.F, band->Wp, esize_of(band->dtype), sh.R, k > 0).total;
+    return smem_layout(sh.S, sh.F, row_bytes_of(band), sh.J, sh.fast, k > 0).total;
 }
 
 EvalShape ft_default_shape(const ft_ctx *ctx, const ft_band *band, const ft_bank *bank)
 {
     EvalShape sh;
-    const int groups = (bank->n_f1 + 31) / 32;
+    sh.fast = bank->window_safe;
+    const int maxw = sh.fast ? kFastMaxWarps : 32;
+    const int groups = (bank->n_f1 + maxw - 1) / maxw;
     sh.F = (bank->n_f1 + groups - 1) / groups;
-    // f0 slots per lane: fewest wasted lanes, then the widest tile
-    int best_r = 1;
+    // tile width J = 32 x slots per lane (pairs of slots for 16-bit storage): fewest idle
+    // lanes, then the widest tile
+    const bool pair = sh.fast && band->dtype != FT_F32;
+    const int step = pair ? 64 : 32;
+    const int max_units = pair ? 4 : 8;
+    int best = step;
     long long best_waste = LLONG_MAX;
-    for (int r = 1; r <= 8; ++r) {
-        const long long J = 32ll * r;
-        const long long tiles = (bank->n_f0 + J - 1) / J;
-        const long long waste = tiles * J - bank->n_f0;
-        if (waste < best_waste || (waste == best_waste && r > best_r)) {
+    for (int u = 1; u <= max_units; ++u) {
+        const long long J = static_cast<long long>(step) * u;
+        const long long waste = (bank->n_f0 + J - 1) / J * J - bank->n_f0;
+        if (waste < best_waste || (waste == best_waste && J > best)) {
             best_waste = waste;
-            best_r = r;
+            best = static_cast<int>(J);
         }
     }
-    sh.R = best_r;
+    sh.J = best;
     sh.nbuf = kNbuf;
-    const size_t row_bytes = static_cast<size_t>(band->Wp) * esize_of(band->dtype);
-    int S = static_cast<int>((96 * 1024) / (kNbuf * row_bytes));
+    const size_t rb = row_bytes_of(band);
+    int S = static_cast<int>((80 * 1024) / (kNbuf * rb));
     S = S > 64 ? 64 : S;
     S = S < 1 ? 1 : S;
     if (S >= 8)
@@ -725,22 +1055,36 @@ EvalShape ft_default_shape(const ft_ctx *ctx, const ft_band *band, const ft_bank
 int ft_launch_eval(const ft_band *band, const ft_bank *bank, const EvalShape &sh, EvalParams p,
                    cudaStream_t st)
 {
-    const int J = 32 * sh.R;
-    p.n_f0t = (bank->n_f0 + J - 1) / J;
+    p.n_f0t = (bank->n_f0 + sh.J - 1) / sh.J;
     p.n_f1g = (bank->n_f1 + sh.F - 1) / sh.F;
     p.S = sh.S;
     p.n_stages = static_cast<int>((band->N + sh.S - 1) / sh.S);
+    p.row_bytes = row_bytes_of(band);
+    p.row_elems = band->dtype == FT_F32 ? band->Wp : 2 * band->Wp;
     const long long n_cta = bank->n_sky * p.n_f1g * static_cast<long long>(p.n_f0t);
     if (n_cta <= 0 || n_cta > INT_MAX)
         FT_FAIL(FT_ERR_RANGE, "eval: grid too large (n_sky * f1 groups * f0 tiles >= 2^31)");
+    if (sh.fast && !bank->window_safe)
+        FT_FAIL(FT_ERR_ARG, "eval: the unchecked kernel needs a bank whose tracks stay in the window");
     const size_t smem = ft_eval_smem_bytes(band, sh, p.cand ? p.k : 0);
     if (smem > band->ctx->smem_optin)
         FT_FAIL(FT_ERR_RANGE, "eval: tile needs more shared memory than the device offers");
-    const bool checked = !bank->window_safe;
+    const int threads = 32 * sh.F;
+    if (!sh.fast) {
+        const int R = sh.J / 32;
+        switch (band->dtype) {
+        case FT_F32: return launch_checked<float>(R, n_cta, threads, smem, p, st);
+        case FT_F16: return launch_checked<__half>(R, n_cta, threads, smem, p, st);
+        case FT_BF16: return launch_checked<__nv_bfloat16>(R, n_cta, threads, smem, p, st);
+        default: FT_FAIL(FT_ERR_ARG, "eval: bad dtype");
+        }
+    }
+    if (sh.F > kFastMaxWarps)
+        FT_FAIL(FT_ERR_ARG, "eval: too many warps for the unchecked kernel");
     switch (band->dtype) {
-    case FT_F32: return launch_eval_c<float>(checked, sh, p, n_cta, smem, st);
-    case FT_F16: return launch_eval_c<__half>(checked, sh, p, n_cta, smem, st);
-    case FT_BF16: return launch_eval_c<__nv_bfloat16>(checked, sh, p, n_cta, smem, st);
+    case FT_F32: return launch_fast<MODE_F32>(band->weighted, sh.J / 32, n_cta, threads, smem, p, st);
+    case FT_F16: return launch_fast<MODE_F16>(band->weighted, sh.J / 64, n_cta, threads, smem, p, st);
+    case FT_BF16: return launch_fast<MODE_BF16>(band->weighted, sh.J / 64, n_cta, threads, smem, p, st);
     default: FT_FAIL(FT_ERR_ARG, "eval: bad dtype");
     }
 }
@@ -748,11 +1092,10 @@ int ft_launch_eval(const ft_band *band, const ft_bank *bank, const EvalShape &sh
 int ft_launch_merge(const ft_bank *bank, const EvalShape &sh, const FtCand *cand, int k,
                     int lsub_max, ft_candidate *out, cudaStream_t st)
 {
-    const int J = 32 * sh.R;
-    const int n_f0t = (bank->n_f0 + J - 1) / J;
+    const int n_f0t = (bank->n_f0 + sh.J - 1) / sh.J;
     const int n_f1g = (bank->n_f1 + sh.F - 1) / sh.F;
     k_topk_merge<<<bank->n_sub, kMergeThreads, 0, st>>>(
-        reinterpret_cast<const ft_candidate *>(cand), k, lsub_max, bank->n_sky, n_f1g, n_f0t, J,
+        reinterpret_cast<const ft_candidate *>(cand), k, lsub_max, bank->n_sky, n_f1g, n_f0t, sh.J,
         bank->sub, bank->n_f0, out);
     FT_CUDA(cudaGetLastError());
     return FT_OK;
@@ -762,8 +1105,9 @@ int ft_launch_convert(const void *src, int src_dtype, long long src_stride, void
                       int dst_dtype, long long N, int W, int Wp, unsigned int *status,
                       cudaStream_t st)
 {
-    k_convert<<<grid_for(N * Wp, 256), 256, 0, st>>>(src, src_dtype, src_stride, dst, dst_dtype,
-                                                      N, W, Wp, status);
+    const long long row_elems = dst_dtype == FT_F32 ? Wp : 2ll * Wp;
+    k_convert<<<grid_for(N * row_elems, 256), 256, 0, st>>>(src, src_dtype, src_stride, dst,
+                                                             dst_dtype, N, W, Wp, status);
     FT_CUDA(cudaGetLastError());
     return FT_OK;
 }

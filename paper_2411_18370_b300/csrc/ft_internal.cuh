@@ -60,11 +60,11 @@ struct ft_band {
     std::vector<int> n_sft;
     int64_t N = 0;        // total rows
     int W = 0;            // bins per row
-    int Wp = 0;           // padded row stride (elements)
+    int Wp = 0;           // padded bins per row copy (FP32: one copy; 16-bit: even + odd copies)
     int64_t k_lo = 0;
     double t_sft = 0, t0 = 0;
     int dtype = FT_F32;
-    void *d_power = nullptr;  // [N][Wp] storage dtype
+    void *d_power = nullptr;  // [N][Wp] FP32, or [N][2][Wp] 16-bit (even / odd-shifted copies)
     double *d_tau = nullptr;  // [N] (t_mid - t0) * T_SFT
     double *d_v = nullptr;    // [N][3]
     float *d_w = nullptr;     // [N]
@@ -101,7 +101,9 @@ struct FtCand {
 
 struct EvalParams {
     const void *power;
-    int Wp, W;
+    int row_bytes;  // bytes per stored row (FP32 row, or the two 16-bit copies)
+    int row_elems;  // storage elements per stored row
+    int W;
     long long N;
     const double *tau;
     const double *v;
@@ -124,10 +126,11 @@ struct EvalParams {
 
 // launch helpers implemented in ft_eval.cu
 struct EvalShape {
-    int R;       // f0 slots per lane (tile width 32*R)
+    int J;       // f0 values per CTA tile (32 x slots per lane)
     int F;       // warps (f1 values) per CTA
     int S;       // SFT rows per stage
     int nbuf;    // stage buffers
+    bool fast;   // shifted-row kernel (bank tracks provably inside the window)
 };
 
 size_t ft_eval_smem_bytes(const ft_band *band, const EvalShape &sh, int k);

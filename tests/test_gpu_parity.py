@@ -187,6 +187,38 @@ def test_search_shaped_reduced_precision_error(ctx, cfg1_slice, dtype, max_rel, 
     assert rel.max() < max_rel and np.sqrt(np.mean(rel ** 2)) < rms_rel
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+def test_search_shaped_integer_power_exact(ctx, cfg1_slice, dtype):
+    """Integer powers on the search-shaped data: every bin of the shifted-row kernel, its
+    per-row carry corrections and the 16-bit pair layout must reproduce the oracle's sum
+    exactly (sums < 2^24 are exact in FP32)."""
+    sfts, bank, _, _ = cfg1_slice
+    P = np.random.default_rng(77).integers(0, 256, sfts.power.shape).astype(np.float64)
+    sx = _with_power(sfts, P)
+    band = H.band_from(ctx, sx, dtype=dtype)
+    bk = H.bank_from(ctx, band, bank)
+    assert bk.window_safe
+    s, _, _ = H.eval_host(ctx, band, bk, bank.n_templates)
+    s_or, _ = oracle.statistic(sx, bank)
+    assert np.array_equal(s.astype(np.float64), s_or)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+def test_weighted_integer_power_exact(ctx, cfg0_auto, dtype):
+    """Power-of-two weights and integer powers: the weighted kernels are exact too."""
+    sfts, bank, _ = cfg0_auto
+    g = np.random.default_rng(78)
+    P = g.integers(0, 256, sfts.power.shape).astype(np.float64)
+    w = 2.0 ** g.integers(-2, 3, sfts.n_total)
+    sx = _with_power(sfts, P)
+    band = H.band_from(ctx, sx, dtype=dtype, w=w)
+    bk = H.bank_from(ctx, band, bank)
+    s, z, _ = H.eval_host(ctx, band, bk, bank.n_templates)
+    s_or, _ = oracle.statistic(sx, bank, w=w)
+    assert np.array_equal(s.astype(np.float64), s_or)
+    assert_z_close(z, s_or, sfts.n_total, w)
+
+
 def test_track_bins_search_shaped_sample(ctx, cfg1):
     sfts, bank = cfg1
     band = H.band_from(ctx, sfts, power_f32=True)
