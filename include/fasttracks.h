@@ -181,6 +181,22 @@ typedef struct {
 FT_API int ft_topk_per_band(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int k,
                      ft_candidate *out, int out_on_device, void *stream);
 
+/* ----------------------------------------------------------------------------- tuning --
+ * Launch shape of the evaluation kernels.  Zero fields keep the built-in choice.
+ *   rows_per_stage  SFT rows per shared-memory stage (fast kernel: multiple of 4, <= 32)
+ *   stages          pipeline stages in flight (fast kernel: 2 .. 4)
+ *   tile_f0         f0 values per CTA tile (multiple of 32; 16-bit storage: of 64; <= 256)
+ * A shape that does not fit the band (shared memory) makes the evaluation calls fail with
+ * FT_ERR_RANGE; nothing else about the results depends on it. */
+typedef struct {
+    int rows_per_stage;
+    int stages;
+    int tile_f0;
+} ft_tune;
+
+/* Set (tune != NULL) or clear (NULL) the context-wide launch-shape override. */
+FT_API int ft_set_tune(ft_ctx *ctx, const ft_tune *tune);
+
 /* Track bins used by the evaluation kernels, for a list of templates (a checking aid):
  * bins[i][alpha] = k_{alpha}(templates[i]) relative to column 0 (may lie outside
  * [0, n_bins)).  The rule (Eq. (track), a_p = 0, exact integer form):

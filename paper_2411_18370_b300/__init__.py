@@ -15,7 +15,7 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libfasttracks.so")
+LIB_PATH = os.environ.get("FASTTRACKS_LIB") or os.path.join(_HERE, "libfasttracks.so")
 
 FT_F32, FT_F16, FT_BF16, FT_F64 = 0, 1, 2, 3
 DTYPES = {"f32": FT_F32, "f16": FT_F16, "bf16": FT_BF16}
@@ -77,6 +77,7 @@ def lib():
             "ft_eval_statistic": (_I, [_P, _P, _P, _P, _P, _P, _I, _P]),
             "ft_topk_per_band": (_I, [_P, _P, _P, _I, _P, _I, _P]),
             "ft_track_bins": (_I, [_P, _P, _P, _P, _I64, _P, _I, _P]),
+            "ft_set_tune": (_I, [_P, _P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -185,6 +186,19 @@ class Bank:
             self.close()
         except Exception:
             pass
+
+
+class _Tune(ctypes.Structure):
+    _fields_ = [("rows_per_stage", ctypes.c_int), ("stages", ctypes.c_int), ("tile_f0", ctypes.c_int)]
+
+
+def set_tune(ctx, rows_per_stage=0, stages=0, tile_f0=0):
+    """ft_set_tune: launch-shape override for later calls on ctx (all zeros clears it)."""
+    if rows_per_stage == stages == tile_f0 == 0:
+        _check(lib().ft_set_tune(ctx.handle, None))
+        return
+    t = _Tune(int(rows_per_stage), int(stages), int(tile_f0))
+    _check(lib().ft_set_tune(ctx.handle, ctypes.byref(t)))
 
 
 def abi_version() -> int:

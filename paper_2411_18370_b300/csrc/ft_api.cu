@@ -200,6 +200,21 @@ void ft_destroy(ft_ctx *ctx)
     delete ctx;
 }
 
+int ft_set_tune(ft_ctx *ctx, const ft_tune *tune)
+{
+    if (!ctx)
+        FT_FAIL(FT_ERR_ARG, "set_tune: null ctx");
+    if (!tune) {
+        ctx->tune = ft_tune{0, 0, 0};
+        return FT_OK;
+    }
+    if (tune->rows_per_stage < 0 || tune->rows_per_stage > 64 || tune->stages < 0 ||
+        tune->stages > 4 || tune->tile_f0 < 0 || tune->tile_f0 > 256)
+        FT_FAIL(FT_ERR_RANGE, "set_tune: field out of range");
+    ctx->tune = *tune;
+    return FT_OK;
+}
+
 int ft_check_status(ft_ctx *ctx, void *stream)
 {
     if (!ctx)

@@ -57,6 +57,14 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, u
         : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes,
                                               unsigned long long *bar)
 {
@@ -265,10 +273,9 @@ __device__ void abandon_tile(const EvalParams &p, unsigned long long *bars, int 
 // Fused candidate selection: vs/vz hold [F][J] values of this CTA's templates (index
 // = f1 slot * J + j - j0).  Per sub-band, one warp extracts the k best by (s desc, t asc)
 // in k rounds of a warp arg-max restricted to keys ranked after the previous pick.
-__device__ void cta_topk(const EvalParams &p, const CtaTile &c, int J, const float *vs,
+__device__ void cta_topk(const EvalParams &p, const CtaTile &c, int F, int J, const float *vs,
                          const float *vz)
 {
-    const int F = blockDim.x >> 5;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int jhi = min(c.j0 + J, p.n_f0);
     const int lb0 = c.j0 / p.sub, lb1 = (jhi - 1) / p.sub;
@@ -336,17 +343,18 @@ __device__ __forceinline__ void fold2sum(float &hi, float &lo, float &part)
     part = 0.f;
 }
 
-// Epilogue shared by both kernels: s = hi + lo, z in FP64; write and/or select.
+// Epilogue shared by both kernels: s = hi + lo, z in FP64; write and/or select.  F is
+// the number of evaluating warps (warps >= F only take part in the barrier).
 template <int NS>
-__device__ __forceinline__ void finish_tile(const EvalParams &p, const CtaTile &c, int J,
+__device__ __forceinline__ void finish_tile(const EvalParams &p, const CtaTile &c, int F, int J,
                                             const int (&jrel)[NS], const float (&hi)[NS],
                                             const float (&lo)[NS], const int (&oob)[NS],
                                             unsigned char *buf)
 {
-    const int F = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5;
+    const bool active = warp < F;
     const int f = c.f1g * F + warp;
-    const bool f_ok = f < p.n_f1;
+    const bool f_ok = active && f < p.n_f1;
     const long long trow = (c.sky * p.n_f1 + f) * static_cast<long long>(p.n_f0);
     float sv[NS], zv[NS];
 #pragma unroll
@@ -372,13 +380,16 @@ __device__ __forceinline__ void finish_tile(const EvalParams &p, const CtaTile &
         return;
     float *vs = reinterpret_cast<float *>(buf);
     float *vz = vs + F * J;
+    if (active) {
 #pragma unroll
-    for (int r = 0; r < NS; ++r) {
-        vs[warp * J + jrel[r]] = sv[r];
-        vz[warp * J + jrel[r]] = zv[r];
+        for (int r = 0; r < NS; ++r) {
+            vs[warp * J + jrel[r]] = sv[r];
+            vz[warp * J + jrel[r]] = zv[r];
+        }
     }
     __syncthreads();
-    cta_topk(p, c, J, vs, vz);
+    if (active)
+        cta_topk(p, c, F, J, vs, vz);
 }
 
 // ------------------------------------------------------------------ checked kernel
@@ -483,7 +494,7 @@ __global__ void __launch_bounds__(1024, 1) k_eval_checked(const EvalParams p)
         if (threadIdx.x == 0 && st + kNbuf < p.n_stages)
             issue_stage(p, buf, bars, L.stage_bytes, st + kNbuf);
     }
-    finish_tile<R>(p, c, J, jrel, hi, lo, oob, buf);
+    finish_tile<R>(p, c, F, J, jrel, hi, lo, oob, buf);
 }
 
 // ------------------------------------------------------------------ fast kernel
@@ -555,178 +566,286 @@ __device__ __forceinline__ float read_bin(const unsigned char *rows, int row_wor
     return (k & 1) ? hi_to_float<MODE>(u) : lo_to_float<MODE>(u);
 }
 
+// Shared-memory layout of the fast kernel: nst pipeline slots, each with S <= 32 rows of
+// power and one 16-byte record per row (the per-SFT track terms E, C and the weight);
+// per evaluating warp its own row offsets and correction list for the slot it works on.
+constexpr int kMaxStages = 4;
+constexpr int kFoldRows = 64;  // FP32 partials cover at most this many SFT rows
+
+struct RowRec {
+    int E;
+    float w;
+    long long C;
+};
+
+struct FastLayout {
+    size_t full, empty, rec, tabB, evA, evK, buf, total, stage_bytes;
+};
+
+__host__ __device__ inline FastLayout fast_layout(int S, int F, int row_bytes, int J, bool topk,
+                                                  int nst)
+{
+    FastLayout L;
+    size_t o = 0;
+    L.full = o;
+    o += kMaxStages * 8;
+    L.empty = o;
+    o = align_up(o + kMaxStages * 8, 16);
+    L.rec = o;
+    o = align_up(o + (size_t)nst * S * sizeof(RowRec), 16);
+    L.tabB = o;
+    o = align_up(o + (size_t)F * S * sizeof(int), 16);
+    L.evA = o;
+    o = align_up(o + (size_t)F * S * sizeof(int), 16);
+    L.evK = o;
+    o = align_up(o + (size_t)F * S * sizeof(int), 128);
+    L.buf = o;
+    L.stage_bytes = (size_t)S * row_bytes;
+    const size_t pipe = (size_t)nst * L.stage_bytes + (size_t)(J + 64) * 4;
+    const size_t tk = topk ? (size_t)F * J * 2 * sizeof(float) : 0;
+    o += pipe > tk ? pipe : tk;
+    L.total = o;
+    return L;
+}
+
+// floor(G E / 2^32) exactly, for |G| < 2^52 and |E| < 2^31: with G = Gh 2^32 + Gl,
+// G E / 2^32 = Gh E + Gl E / 2^32, and Gl E fits in 64 bits.
+__device__ __forceinline__ long long cross_q32(long long G, int E)
+{
+    const int Gh = static_cast<int>(G >> 32);
+    const unsigned Gl = static_cast<unsigned>(G);
+    const long long lo = static_cast<long long>(static_cast<unsigned long long>(Gl) *
+                                                static_cast<unsigned long long>(static_cast<long long>(E)));
+    // lo above is Gl * E modulo 2^64, which is exact because |Gl E| < 2^63
+    return static_cast<long long>(Gh) * E + (lo >> 32);
+}
+
+// Warp roles: warps 0 .. F-1 evaluate (warp w <-> f1 value f1g*F + w); warp F produces.
+// Producer, per stage st (slot st % nst): wait until every evaluating lane released the
+// slot (empty barrier), compute E, C, w of the stage's rows (one lane per row), start the
+// bulk copy of the rows and arrive on the slot's full barrier (32 arrivals + the copy's
+// bytes).  Evaluating warp, per stage: wait for the full barrier, derive its own row
+// offsets and corrections (one lane per row), accumulate, release the slot.  No CTA-wide
+// barrier inside the loop.
+#ifndef FT_FAST_MAXNREG
+#define FT_FAST_MAXNREG 40
+#endif
 template <int MODE, int R, bool WEIGHTED>
-__global__ void __launch_bounds__(32 * kFastMaxWarps, 2) k_eval_fast(const EvalParams p)
+__global__ void __maxnreg__(FT_FAST_MAXNREG) k_eval_fast(const EvalParams p)
 {
     constexpr bool PAIR = MODE != MODE_F32;
     constexpr int NS = PAIR ? 2 * R : R;  // accumulator slots per thread
     constexpr int J = 32 * NS;            // f0 per tile
     extern __shared__ __align__(128) unsigned char smem[];
-    const int F = blockDim.x >> 5;
+    const int F = (blockDim.x >> 5) - 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int S = p.S;
+    const int nst = p.nst;
     const int row_words = p.row_bytes >> 2;
-    const SmemLayout L = smem_layout(S, F, p.row_bytes, J, true, p.cand != nullptr);
-    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + L.bars);
-    int *tabE = reinterpret_cast<int *>(smem + L.tabE);
-    float *tabW = reinterpret_cast<float *>(smem + L.tabW);
-    long long *tabC = reinterpret_cast<long long *>(smem + L.tabC);
-    int *tabB = reinterpret_cast<int *>(smem + L.tabX);
-    int *evA = reinterpret_cast<int *>(smem + L.evA);
-    int *evK = reinterpret_cast<int *>(smem + L.evK);
-    int *evN = reinterpret_cast<int *>(smem + L.evN);
+    const FastLayout L = fast_layout(S, F, p.row_bytes, J, p.cand != nullptr, nst);
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(smem + L.full);
+    unsigned long long *empty = reinterpret_cast<unsigned long long *>(smem + L.empty);
+    RowRec *rec = reinterpret_cast<RowRec *>(smem + L.rec);
     unsigned char *buf = smem + L.buf;
     const CtaTile c = decode_tile(p, J);
-    const int fg = min(c.f1g * F + warp, p.n_f1 - 1);
+    const int n_stages = p.n_stages;
+
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < nst; ++b) {
+            mbar_init(&full[b], 32);
+            mbar_init(&empty[b], 32 * F);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
 
     int jrel[NS];
 #pragma unroll
     for (int i = 0; i < NS; ++i)
         jrel[i] = PAIR ? 2 * lane + 64 * (i >> 1) + (i & 1) : lane + 32 * i;
-
-    // per-warp tables of stage st for f1 value fg: base word offsets and corrections
-    auto table_b = [&](int st) {
-        const int tb = st & 1;
-        const int nr = rows_in_stage(p, st);
-        const size_t wbase = (static_cast<size_t>(tb) * F + warp) * S;
-        int cnt = 0;
-        for (int a0 = 0; a0 < nr; a0 += 32) {
-            const int a = a0 + lane;
-            bool ev = false;
-            int packed = 0, basev = 0;
-            if (a < nr) {
-                const long long alpha = static_cast<long long>(st) * S + a;
-                const int E = tabE[tb * S + a];
-                const long long G = p.G[static_cast<long long>(fg) * p.N + alpha];
-                const long long X0p = track_x0(tabC[tb * S + a], G, E) + (1ll << 31);
-                const long long acc0 = X0p + static_cast<long long>(c.j0) * E;
-                const int hb = static_cast<int>(acc0 >> 32);
-                const unsigned L0 = static_cast<unsigned>(acc0);
-                const int base = c.j0 + hb;
-                int jc = J;
-                if (E > 0) {
-                    if (static_cast<unsigned long long>(L0) +
-                            static_cast<unsigned long long>(J - 1) * static_cast<unsigned>(E) >=
-                        0x100000000ull)
-                        jc = static_cast<int>((0x100000000ull - L0 + static_cast<unsigned>(E) - 1) /
-                                              static_cast<unsigned>(E));
-                } else if (E < 0) {
-                    if (static_cast<long long>(L0) + static_cast<long long>(J - 1) * E < 0)
-                        jc = static_cast<int>(L0 / static_cast<unsigned>(-E)) + 1;
-                }
-                tabB[wbase + a] = PAIR ? a * row_words + (base & 1) * (row_words >> 1) + (base >> 1)
-                                       : a * row_words + base;
-                ev = jc < J;
-                packed = a | (jc << 8) | (E < 0 ? (1 << 20) : 0);
-                basev = base;
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, ev);
-            if (ev) {
-                const int pos = cnt + __popc(m & ((1u << lane) - 1u));
-                evA[wbase + pos] = packed;
-                evK[wbase + pos] = basev;
-            }
-            cnt += __popc(m);
-        }
-        if (lane == 0)
-            evN[tb * F + warp] = cnt;
-    };
-
-    if (threadIdx.x == 0) {
-        for (int b = 0; b < kNbuf; ++b)
-            mbar_init(&bars[b], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0)
-        for (int st = 0; st < kNbuf && st < p.n_stages; ++st)
-            issue_stage(p, buf, bars, L.stage_bytes, st);
-    stage_table_a(p, c, 0, tabE, tabC, tabW);
-    __syncthreads();
-    table_b(0);
-
-    float part[NS], hi[NS], lo[NS];
+    float hi[NS], lo[NS];
     int oob[NS];
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
-        part[i] = hi[i] = lo[i] = 0.f;
+        hi[i] = lo[i] = 0.f;
         oob[i] = 0;
     }
-    for (int st = 0; st < p.n_stages; ++st) {
-        const int tb = st & 1;
-        if (st + 1 < p.n_stages)
-            stage_table_a(p, c, st + 1, tabE, tabC, tabW);
-        const bool got = mbar_wait_bounded(&bars[st % kNbuf], (st / kNbuf) & 1);
-        if (!__syncthreads_and(got)) {
-            abandon_tile(p, bars, st);
-            return;
-        }
-        const unsigned char *rows = buf + (st % kNbuf) * L.stage_bytes;
-        const int nr = rows_in_stage(p, st);
-        const float *tW = tabW + tb * S;
-        const int *tB = tabB + (static_cast<size_t>(tb) * F + warp) * S;
-        // main loop: shifted-row sums
-#pragma unroll 4
-        for (int a = 0; a < nr; ++a) {
-            if (MODE == MODE_F32) {
-                const float *q = reinterpret_cast<const float *>(rows) + tB[a] + lane;
-                if (WEIGHTED) {
-                    const float wa = tW[a];
-#pragma unroll
-                    for (int r = 0; r < R; ++r)
-                        part[r] = __fmaf_rn(wa, q[32 * r], part[r]);
-                } else {
-#pragma unroll
-                    for (int r = 0; r < R; ++r)
-                        part[r] = __fadd_rn(part[r], q[32 * r]);
-                }
+    bool ok = true;
+
+    if (warp == F) {
+        // ------------------------------------------------------------ producer warp
+        int st = 0, slot = 0, use = 0;
+        for (; st < n_stages; ++st) {
+            if (use > 0 && !mbar_wait_bounded(&empty[slot], (use - 1) & 1)) {
+                ok = false;
+                break;
+            }
+            const int nr = rows_in_stage(p, st);
+            if (lane < nr) {
+                const long long alpha = static_cast<long long>(st) * S + lane;
+                RowRec r;
+                track_ec(p.v + 3 * alpha, c.n0, c.n1, c.n2, p.K0, p.k_lo, r.E, r.C);
+                r.w = p.w[alpha];
+                rec[slot * S + lane] = r;
+            }
+            if (lane == 0) {
+                const unsigned bytes = static_cast<unsigned>(nr) * p.row_bytes;
+                mbar_arrive_expect_tx(&full[slot], bytes);
+                bulk_copy_g2s(buf + slot * L.stage_bytes,
+                              static_cast<const unsigned char *>(p.power) +
+                                  static_cast<size_t>(st) * L.stage_bytes,
+                              bytes, &full[slot]);
             } else {
-                const unsigned *q = reinterpret_cast<const unsigned *>(rows) + tB[a] + lane;
-                if (WEIGHTED) {
-                    const float wa = tW[a];
+                mbar_arrive(&full[slot]);
+            }
+            if (++slot == nst) {
+                slot = 0;
+                ++use;
+            }
+        }
+        if (lane == 0) {
+            if (!ok)
+                atomicOr(p.status, FT_STATUS_TIMEOUT);
+            // the last copies started have landed before shared memory is reused or released
+            for (int s2 = st - 1; s2 >= 0 && s2 >= st - nst; --s2)
+                (void)mbar_wait_bounded(&full[s2 % nst], (s2 / nst) & 1);
+        }
+    } else {
+        // ------------------------------------------------------------ evaluating warps
+        const int fg = min(c.f1g * F + warp, p.n_f1 - 1);
+        int *tabB = reinterpret_cast<int *>(smem + L.tabB) + warp * S;
+        int *evA = reinterpret_cast<int *>(smem + L.evA) + warp * S;
+        int *evK = reinterpret_cast<int *>(smem + L.evK) + warp * S;
+        float part[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i)
+            part[i] = 0.f;
+        int rows_since_fold = 0;
+        // G of this lane's row, loaded one stage ahead
+        const long long *Gf = p.G + static_cast<long long>(fg) * p.N;
+        long long g_cur = lane < rows_in_stage(p, 0) ? Gf[lane] : 0;
+        int slot = 0, use = 0;
+        for (int st = 0; st < n_stages; ++st) {
+            long long g_next = 0;
+            if (st + 1 < n_stages && lane < rows_in_stage(p, st + 1))
+                g_next = Gf[static_cast<long long>(st + 1) * S + lane];
+            if (!mbar_wait_bounded(&full[slot], use & 1)) {
+                ok = false;
+                break;
+            }
+            const int nr = rows_in_stage(p, st);
+            const unsigned char *rows = buf + slot * L.stage_bytes;
+            const RowRec *rr = rec + slot * S;
+            // row offset of this warp's track origin and, if the track steps by sign(E)
+            // inside the tile, a correction entry (lane = row)
+            bool ev = false;
+            int packed = 0, basev = 0;
+            if (lane < nr) {
+                const RowRec r = rr[lane];
+                const long long X0p = r.C + g_cur + cross_q32(g_cur, r.E) + (1ll << 31);
+                const long long acc0 = X0p + static_cast<long long>(c.j0) * r.E;
+                const int base = c.j0 + static_cast<int>(acc0 >> 32);
+                const unsigned L0 = static_cast<unsigned>(acc0);
+                const unsigned span = static_cast<unsigned>(J - 1) * static_cast<unsigned>(abs(r.E));
+                ev = r.E > 0 ? (span != 0u && L0 >= 0u - span) : (L0 < span);
+                tabB[lane] = PAIR ? lane * row_words + (base & 1) * (row_words >> 1) + (base >> 1)
+                                  : lane * row_words + base;
+                packed = lane | (r.E < 0 ? (1 << 20) : 0);
+                basev = base;
+                if (ev) {
+                    // first tile offset at which the bin steps (rare: one division)
+                    const int jc = r.E > 0 ? static_cast<int>((0x100000000ull - L0 + static_cast<unsigned>(r.E) - 1) /
+                                                              static_cast<unsigned>(r.E))
+                                           : static_cast<int>(L0 / static_cast<unsigned>(-r.E)) + 1;
+                    packed |= jc << 8;
+                }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, ev);
+            if (ev) {
+                const int pos = __popc(m & ((1u << lane) - 1u));
+                evA[pos] = packed;
+                evK[pos] = basev;
+            }
+            const int ne = __popc(m);
+            __syncwarp();
+            // main loop: shifted-row sums, four rows' offsets per vector load
+            const unsigned char *lane_rows = rows + 4 * lane;
+            auto row_sum = [&](int off, float wa) {
+                if (MODE == MODE_F32) {
+                    const float *q = reinterpret_cast<const float *>(lane_rows) + off;
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        part[r] = WEIGHTED ? __fmaf_rn(wa, q[32 * r], part[r]) : __fadd_rn(part[r], q[32 * r]);
+                } else {
+                    const unsigned *q = reinterpret_cast<const unsigned *>(lane_rows) + off;
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
                         const unsigned u = q[32 * r];
-                        part[2 * r] = __fmaf_rn(wa, lo_to_float<MODE>(u), part[2 * r]);
-                        part[2 * r + 1] = __fmaf_rn(wa, hi_to_float<MODE>(u), part[2 * r + 1]);
+                        if (WEIGHTED) {
+                            part[2 * r] = __fmaf_rn(wa, lo_to_float<MODE>(u), part[2 * r]);
+                            part[2 * r + 1] = __fmaf_rn(wa, hi_to_float<MODE>(u), part[2 * r + 1]);
+                        } else {
+                            acc_pair<MODE>(part[2 * r], part[2 * r + 1], u);
+                        }
                     }
+                }
+            };
+            const int nr4 = nr & ~3;
+            for (int a = 0; a < nr4; a += 4) {
+                const int4 o4 = *reinterpret_cast<const int4 *>(tabB + a);
+                if (WEIGHTED) {
+                    row_sum(o4.x, rr[a].w);
+                    row_sum(o4.y, rr[a + 1].w);
+                    row_sum(o4.z, rr[a + 2].w);
+                    row_sum(o4.w, rr[a + 3].w);
                 } else {
-#pragma unroll
-                    for (int r = 0; r < R; ++r)
-                        acc_pair<MODE>(part[2 * r], part[2 * r + 1], q[32 * r]);
+                    row_sum(o4.x, 1.f);
+                    row_sum(o4.y, 1.f);
+                    row_sum(o4.z, 1.f);
+                    row_sum(o4.w, 1.f);
                 }
             }
-        }
-        // corrections for the rows whose bin steps by sign(E) inside the tile
-        const int ne = evN[tb * F + warp];
-        const size_t wbase = (static_cast<size_t>(tb) * F + warp) * S;
-        for (int e = 0; e < ne; ++e) {
-            const int packed = evA[wbase + e];
-            const int a = packed & 0xff;
-            const int jc = (packed >> 8) & 0xfff;
-            const int sg = (packed >> 20) ? -1 : 1;
-            const int base = evK[wbase + e];
-            const float wa = tW[a];
+            for (int a = nr4; a < nr; ++a)
+                row_sum(tabB[a], WEIGHTED ? rr[a].w : 1.f);
+            // corrections for the rows whose bin steps by sign(E) inside the tile
+            for (int e = 0; e < ne; ++e) {
+                const int pk = evA[e];
+                const int a = pk & 0xff;
+                const int jc = (pk >> 8) & 0xfff;
+                const int sg = (pk >> 20) ? -1 : 1;
+                const int base = evK[e];
+                const float wa = rr[a].w;
 #pragma unroll
-            for (int i = 0; i < NS; ++i) {
-                if (jrel[i] >= jc && c.j0 + jrel[i] < p.n_f0) {
-                    const int k = base + jrel[i];
-                    const float d = __fsub_rn(read_bin<MODE>(rows, row_words, a, k + sg),
-                                              read_bin<MODE>(rows, row_words, a, k));
-                    part[i] = WEIGHTED ? __fmaf_rn(wa, d, part[i]) : __fadd_rn(part[i], d);
+                for (int i = 0; i < NS; ++i) {
+                    if (jrel[i] >= jc && c.j0 + jrel[i] < p.n_f0) {
+                        const int k = base + jrel[i];
+                        const float d = __fsub_rn(read_bin<MODE>(rows, row_words, a, k + sg),
+                                                  read_bin<MODE>(rows, row_words, a, k));
+                        part[i] = WEIGHTED ? __fmaf_rn(wa, d, part[i]) : __fadd_rn(part[i], d);
+                    }
                 }
             }
-        }
+            mbar_arrive(&empty[slot]);
+            if (++slot == nst) {
+                slot = 0;
+                ++use;
+            }
+            g_cur = g_next;
+            rows_since_fold += nr;
+            if (rows_since_fold >= kFoldRows || st == n_stages - 1) {
 #pragma unroll
-        for (int i = 0; i < NS; ++i)
-            fold2sum(hi[i], lo[i], part[i]);
-        if (st + 1 < p.n_stages)
-            table_b(st + 1);
-        __syncthreads();
-        if (threadIdx.x == 0 && st + kNbuf < p.n_stages)
-            issue_stage(p, buf, bars, L.stage_bytes, st + kNbuf);
+                for (int i = 0; i < NS; ++i)
+                    fold2sum(hi[i], lo[i], part[i]);
+                rows_since_fold = 0;
+            }
+        }
+        if (!ok && lane == 0)
+            atomicOr(p.status, FT_STATUS_TIMEOUT);
     }
-    finish_tile<NS>(p, c, J, jrel, hi, lo, oob, buf);
+    // every copy has landed: its slot was consumed, or the producer waited for it above
+    if (!__syncthreads_and(ok))
+        return;
+    finish_tile<NS>(p, c, F, J, jrel, hi, lo, oob, buf);
 }
 
 // ------------------------------------------------------------------ candidate merge
@@ -940,6 +1059,8 @@ int launch_kernel(K fn, long long n_cta, int threads, size_t smem, const EvalPar
     if (smem > configured) {
         FT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(smem)));
+        FT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared));
         configured = smem;
     }
     fn<<<static_cast<unsigned>(n_cta), threads, smem, st>>>(p);
@@ -1014,7 +1135,9 @@ int row_bytes_of(const ft_band *band)
 
 size_t ft_eval_smem_bytes(const ft_band *band, const EvalShape &sh, int k)
 {
-    return smem_layout(sh.S, sh.F, row_bytes_of(band), sh.J, sh.fast, k > 0).total;
+    if (sh.fast)
+        return fast_layout(sh.S, sh.F, row_bytes_of(band), sh.J, k > 0, sh.nbuf).total;
+    return smem_layout(sh.S, sh.F, row_bytes_of(band), sh.J, false, k > 0).total;
 }
 
 EvalShape ft_default_shape(const ft_ctx *ctx, const ft_band *band, const ft_bank *bank)
@@ -1040,15 +1163,29 @@ EvalShape ft_default_shape(const ft_ctx *ctx, const ft_band *band, const ft_bank
         }
     }
     sh.J = best;
-    sh.nbuf = kNbuf;
     const size_t rb = row_bytes_of(band);
-    int S = static_cast<int>((80 * 1024) / (kNbuf * rb));
-    S = S > 64 ? 64 : S;
-    S = S < 1 ? 1 : S;
-    if (S >= 8)
-        S &= ~7;
-    sh.S = S;
-    (void)ctx;
+    if (sh.fast) {
+        // two slots of up to 32 rows (a multiple of 4) in about 80 KB: two CTAs per SM
+        sh.nbuf = 2;
+        int S = static_cast<int>((80 * 1024) / (sh.nbuf * rb));
+        S = S > 32 ? 32 : S;
+        S = S < 4 ? 4 : S & ~3;
+        sh.S = S;
+    } else {
+        sh.nbuf = kNbuf;
+        int S = static_cast<int>((80 * 1024) / (kNbuf * rb));
+        S = S > 64 ? 64 : S;
+        S = S < 1 ? 1 : S;
+        if (S >= 8)
+            S &= ~7;
+        sh.S = S;
+    }
+    if (ctx->tune.tile_f0 > 0)
+        sh.J = ctx->tune.tile_f0;
+    if (ctx->tune.rows_per_stage > 0)
+        sh.S = ctx->tune.rows_per_stage;
+    if (ctx->tune.stages > 0 && sh.fast)
+        sh.nbuf = ctx->tune.stages;
     return sh;
 }
 
@@ -1060,6 +1197,7 @@ int ft_launch_eval(const ft_band *band, const ft_bank *bank, const EvalShape &sh
     p.S = sh.S;
     p.n_stages = static_cast<int>((band->N + sh.S - 1) / sh.S);
     p.row_bytes = row_bytes_of(band);
+    p.nst = sh.nbuf;
     p.row_elems = band->dtype == FT_F32 ? band->Wp : 2 * band->Wp;
     const long long n_cta = bank->n_sky * p.n_f1g * static_cast<long long>(p.n_f0t);
     if (n_cta <= 0 || n_cta > INT_MAX)
@@ -1070,6 +1208,9 @@ int ft_launch_eval(const ft_band *band, const ft_bank *bank, const EvalShape &sh
     if (smem > band->ctx->smem_optin)
         FT_FAIL(FT_ERR_RANGE, "eval: tile needs more shared memory than the device offers");
     const int threads = 32 * sh.F;
+    const int unit = (sh.fast && band->dtype != FT_F32) ? 64 : 32;
+    if (sh.J < unit || sh.J % unit != 0 || sh.J > 256)
+        FT_FAIL(FT_ERR_RANGE, "eval: tile_f0 must be a multiple of 32 (64 for 16-bit storage), <= 256");
     if (!sh.fast) {
         const int R = sh.J / 32;
         switch (band->dtype) {
@@ -1079,12 +1220,13 @@ int ft_launch_eval(const ft_band *band, const ft_bank *bank, const EvalShape &sh
         default: FT_FAIL(FT_ERR_ARG, "eval: bad dtype");
         }
     }
-    if (sh.F > kFastMaxWarps)
-        FT_FAIL(FT_ERR_ARG, "eval: too many warps for the unchecked kernel");
+    if (sh.F > kFastMaxWarps || sh.S % 4 != 0 || sh.S > 32 || sh.nbuf < 2 || sh.nbuf > kMaxStages)
+        FT_FAIL(FT_ERR_ARG, "eval: shape not supported by the unchecked kernel");
+    const int tf = threads + 32;  // plus the producer warp
     switch (band->dtype) {
-    case FT_F32: return launch_fast<MODE_F32>(band->weighted, sh.J / 32, n_cta, threads, smem, p, st);
-    case FT_F16: return launch_fast<MODE_F16>(band->weighted, sh.J / 64, n_cta, threads, smem, p, st);
-    case FT_BF16: return launch_fast<MODE_BF16>(band->weighted, sh.J / 64, n_cta, threads, smem, p, st);
+    case FT_F32: return launch_fast<MODE_F32>(band->weighted, sh.J / 32, n_cta, tf, smem, p, st);
+    case FT_F16: return launch_fast<MODE_F16>(band->weighted, sh.J / 64, n_cta, tf, smem, p, st);
+    case FT_BF16: return launch_fast<MODE_BF16>(band->weighted, sh.J / 64, n_cta, tf, smem, p, st);
     default: FT_FAIL(FT_ERR_ARG, "eval: bad dtype");
     }
 }

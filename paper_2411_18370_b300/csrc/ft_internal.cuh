@@ -52,6 +52,7 @@ struct ft_ctx {
     size_t scratch_bytes = 0;
     void *outbuf = nullptr;            // device staging for host outputs
     size_t outbuf_bytes = 0;
+    ft_tune tune = {0, 0, 0};          // launch-shape override (zeros: built-in choice)
 };
 
 struct ft_band {
@@ -115,6 +116,7 @@ struct EvalParams {
     long long n_sky;
     int n_f1g, n_f0t;  // f1 groups (warps per CTA = F) and f0 tiles (32*R each)
     int S, n_stages;   // SFT rows per stage
+    int nst;           // pipeline slots (fast kernel)
     double mu, sigma;
     float *s_out;
     float *z_out;
