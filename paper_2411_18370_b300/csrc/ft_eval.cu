@@ -570,7 +570,7 @@ __device__ __forceinline__ float read_bin(const unsigned char *rows, int row_wor
 // power and one 16-byte record per row (the per-SFT track terms E, C and the weight);
 // per evaluating warp its own row offsets and correction list for the slot it works on.
 constexpr int kMaxStages = 4;
-constexpr int kFoldRows = 64;  // FP32 partials cover at most this many SFT rows
+constexpr int kFoldRows = 128;  // FP32 partials cover at most this many SFT rows
 
 struct RowRec {
     int E;
