@@ -181,6 +181,30 @@ typedef struct {
 FT_API int ft_topk_per_band(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int k,
                      ft_candidate *out, int out_on_device, void *stream);
 
+/* Same search and same output as ft_topk_per_band, for callers that cannot let the library
+ * allocate device memory during the call: processes whose device memory is owned by another
+ * allocator (a framework's caching allocator or a budget fixed at start-up, where a new
+ * cudaMalloc may fail or fragment the device) and latency-critical loops that cannot take
+ * an allocation's implicit synchronisation.  There is no counterpart in the paper: this is
+ * purely a memory-management variant.
+ * - The candidate scratch lives in one file-scope device array of FT_NOALLOC_SCRATCH_BYTES
+ *   (16 MiB) that every device loading the library holds until the process exits.  A bank
+ *   needing more (n_sky x f1 groups x f0 tiles x sub-bands per tile x k x 16 bytes, plus the
+ *   output when out is on the host) is rejected with FT_ERR_RANGE; the search-shaped band
+ *   (1e4 sky x 20 f1 x 180 f0, k = 10) fits.
+ * - The call makes no cudaMalloc / cudaFree and calls no allocating library routine.  The
+ *   band, bank and context were allocated when they were created.
+ * - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *   with that device current; make that first call before any stream capture.
+ * - Every call shares the one array and the array keeps the last call's contents; calls
+ *   that overlap on the GPU (different streams, or different contexts on the same device)
+ *   race on it and must be serialised by the caller.  Nothing needs clearing between calls:
+ *   each call writes every slot it reads.
+ * Arguments, output layout and errors are those of ft_topk_per_band. */
+#define FT_NOALLOC_SCRATCH_BYTES (16u << 20)
+FT_API int ft_topk_per_band_noalloc(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int k,
+                                    ft_candidate *out, int out_on_device, void *stream);
+
 /* ----------------------------------------------------------------------------- tuning --
  * Launch shape of the evaluation kernels.  Zero fields keep the built-in choice.
  *   rows_per_stage  SFT rows per shared-memory stage (fast kernel: multiple of 4, <= 32)

@@ -78,6 +78,7 @@ def lib():
             "ft_topk_per_band": (_I, [_P, _P, _P, _I, _P, _I, _P]),
             "ft_track_bins": (_I, [_P, _P, _P, _P, _I64, _P, _I, _P]),
             "ft_set_tune": (_I, [_P, _P]),
+            "ft_topk_per_band_noalloc": (_I, [_P, _P, _P, _I, _P, _I, _P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -285,6 +286,14 @@ def topk_per_band(ctx, band, bank, k, out, stream=None):
     po, dev = _ptr(out)
     _check(lib().ft_topk_per_band(ctx.handle, band.handle, bank.handle, int(k), po, int(dev),
                                   _stream(stream, dev)))
+
+
+def topk_per_band_noalloc(ctx, band, bank, k, out, stream=None):
+    """ft_topk_per_band_noalloc: as topk_per_band, with the candidate scratch in the
+    library's fixed device array instead of memory allocated during the call."""
+    po, dev = _ptr(out)
+    _check(lib().ft_topk_per_band_noalloc(ctx.handle, band.handle, bank.handle, int(k), po,
+                                          int(dev), _stream(stream, dev)))
 
 
 def decode_candidates(buf, n_sub, k):
