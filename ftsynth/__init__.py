@@ -321,3 +321,26 @@ def config3_bands(n_bands: int = 64, sky_scale: float = 1.0, seed_stream: int = 
         out.append(dict(k_band=k_band, n_bins=n_bins, n_sky=max(n_sky, 1),
                         f_hi=(k_band + n_bins) / T_SFT))
     return out
+
+
+def config3(n_bands: int = 64, sky_scale: float = 1.0, n_slots: int = None, duty: float = 0.7,
+            max_sky: int = None, bands=None):
+    """The batching workload: bands from config3_bands() sharing one 2-detector timeline of
+    1800 s SFTs (70% duty), each with its own noise, wings sized for its top frequency,
+    10 f1 values in [-1e-9, 0] and N_sky Fibonacci sky points (scaled by sky_scale, capped
+    by max_sky).  Returns a list of (SFTSet, Bank)."""
+    if n_slots is None:
+        n_slots = int(round(YEAR_S / T_SFT))
+    t_obs = n_slots * T_SFT
+    starts = timeline(2, n_slots, T_SFT, duty, rng(3, 1))
+    specs = config3_bands(n_bands, sky_scale)
+    out = []
+    for b, spec in enumerate(specs if bands is None else [specs[i] for i in bands]):
+        wl, wh = wings_for(spec["f_hi"], -1e-9, t_obs, T_SFT)
+        sfts = make_sfts(3, 2, n_slots, T_SFT, duty, spec["k_band"], spec["n_bins"], wl, wh,
+                         psd_range=(0.8, 1.2), stream_base=10 * (b + 1), slot_starts=starts)
+        n_sky = spec["n_sky"] if max_sky is None else min(spec["n_sky"], max_sky)
+        bank = Bank(k0=spec["k_band"], n_f0=spec["n_bins"], f1=f1_grid(10, -1e-9, 0.0),
+                    sky=fibonacci_sky(max(n_sky, 1)), subband_bins=18)
+        out.append((sfts, bank))
+    return out

@@ -221,6 +221,34 @@ typedef struct {
 /* Set (tune != NULL) or clear (NULL) the context-wide launch-shape override. */
 FT_API int ft_set_tune(ft_ctx *ctx, const ft_tune *tune);
 
+/* ----------------------------------------------------------------------------- batches --
+ * Many bands of uneven width and sky density searched by one persistent launch (the
+ * batching pattern; each band's statistic and candidates are those of ft_topk_per_band).
+ * The tiles of all bands form one band-major work list that resident CTAs consume through a
+ * global ticket counter; each CTA merges its tiles' candidates into per-sub-band lists in
+ * shared memory.  The launch sequence (clear, persistent kernel, merge) is captured once in
+ * a CUDA graph at creation and replayed by ft_batch_run.
+ *   bands/banks  n_bands pairs; all bands share the storage type and weighting and every
+ *                bank's tracks must stay inside its band's window (FT_ERR_ARG otherwise)
+ *   tune         tile_f0 and stages of the persistent kernel; NULL or zero fields run the
+ *                autotuner, which times candidate shapes on a subset of every band's tiles
+ *                (cached per storage type, weighting, k, rows, f1 count and window widths)
+ *   out          [sum over bands of n_subbands][k] candidates, band after band
+ * Creation allocates device memory and synchronises `stream`; runs do not allocate. */
+typedef struct ft_batch ft_batch;
+FT_API int ft_batch_create(ft_ctx *ctx, int n_bands, const ft_band *const *bands,
+                           const ft_bank *const *banks, int k, const ft_tune *tune, void *stream,
+                           ft_batch **out);
+FT_API int ft_batch_run(ft_batch *batch, ft_candidate *out, int out_on_device, void *stream);
+/* Total candidate slots, evaluations per run, the launch shape in use, resident CTAs. */
+FT_API int ft_batch_info(const ft_batch *batch, int64_t *n_candidates, int64_t *evals,
+                         ft_tune *chosen, int *n_ctas);
+FT_API void ft_batch_destroy(ft_batch *batch);
+/* One-shot create + run + destroy; synchronises `stream` before returning. */
+FT_API int ft_eval_batched(ft_ctx *ctx, int n_bands, const ft_band *const *bands,
+                           const ft_bank *const *banks, int k, ft_candidate *out, int out_on_device,
+                           const ft_tune *tune, void *stream);
+
 /* Track bins used by the evaluation kernels, for a list of templates (a checking aid):
  * bins[i][alpha] = k_{alpha}(templates[i]) relative to column 0 (may lie outside
  * [0, n_bins)).  The rule (Eq. (track), a_p = 0, exact integer form):

@@ -79,6 +79,12 @@ def lib():
             "ft_track_bins": (_I, [_P, _P, _P, _P, _I64, _P, _I, _P]),
             "ft_set_tune": (_I, [_P, _P]),
             "ft_topk_per_band_noalloc": (_I, [_P, _P, _P, _I, _P, _I, _P]),
+            "ft_batch_create": (_I, [_P, _I, _P, _P, _I, _P, _P, ctypes.POINTER(_P)]),
+            "ft_batch_run": (_I, [_P, _P, _I, _P]),
+            "ft_batch_info": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), _P,
+                                   ctypes.POINTER(_I)]),
+            "ft_batch_destroy": (None, [_P]),
+            "ft_eval_batched": (_I, [_P, _I, _P, _P, _I, _P, _I, _P, _P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -200,6 +206,45 @@ def set_tune(ctx, rows_per_stage=0, stages=0, tile_f0=0):
         return
     t = _Tune(int(rows_per_stage), int(stages), int(tile_f0))
     _check(lib().ft_set_tune(ctx.handle, ctypes.byref(t)))
+
+
+class Batch:
+    """ft_batch: many (band, bank) pairs searched by one graph-captured persistent launch."""
+
+    def __init__(self, ctx, bands, banks, k, tile_f0=0, stages=0, stream=None):
+        n = len(bands)
+        self.ctx, self.bands, self.banks, self.k = ctx, list(bands), list(banks), int(k)
+        barr = (_P * n)(*[b.handle for b in bands])
+        karr = (_P * n)(*[b.handle for b in banks])
+        tune = None
+        if tile_f0 or stages:
+            tune = ctypes.byref(_Tune(0, int(stages), int(tile_f0)))
+        h = _P()
+        _check(lib().ft_batch_create(ctx.handle, n, barr, karr, self.k, tune,
+                                     _stream(stream, False), ctypes.byref(h)))
+        self.handle = h
+        nc, ev, nct = _I64(), _I64(), _I()
+        t = _Tune()
+        _check(lib().ft_batch_info(h, ctypes.byref(nc), ctypes.byref(ev), ctypes.byref(t),
+                                   ctypes.byref(nct)))
+        self.n_candidates, self.evals, self.n_ctas = nc.value, ev.value, nct.value
+        self.tile_f0, self.stages, self.rows_per_stage = t.tile_f0, t.stages, t.rows_per_stage
+        self.n_subbands = [b.n_subbands for b in banks]
+
+    def run(self, out, stream=None):
+        po, dev = _ptr(out)
+        _check(lib().ft_batch_run(self.handle, po, int(dev), _stream(stream, dev)))
+
+    def close(self):
+        if self.handle:
+            lib().ft_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def abi_version() -> int:

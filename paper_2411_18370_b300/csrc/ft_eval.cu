@@ -209,10 +209,10 @@ struct CtaTile {
     double n0, n1, n2;
 };
 
-__device__ __forceinline__ CtaTile decode_tile(const EvalParams &p, int J)
+__device__ __forceinline__ CtaTile decode_tile(const EvalParams &p, int J, long long tile)
 {
     CtaTile c;
-    c.cta = blockIdx.x;
+    c.cta = tile;
     c.f0t = static_cast<int>(c.cta % p.n_f0t);
     const long long rest = c.cta / p.n_f0t;
     c.f1g = static_cast<int>(rest % p.n_f1g);
@@ -274,7 +274,7 @@ __device__ void abandon_tile(const EvalParams &p, unsigned long long *bars, int 
 // = f1 slot * J + j - j0).  Per sub-band, one warp extracts the k best by (s desc, t asc)
 // in k rounds of a warp arg-max restricted to keys ranked after the previous pick.
 __device__ void cta_topk(const EvalParams &p, const CtaTile &c, int F, int J, const float *vs,
-                         const float *vz)
+                         const float *vz, ft_candidate *dst)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int jhi = min(c.j0 + J, p.n_f0);
@@ -286,8 +286,7 @@ __device__ void cta_topk(const EvalParams &p, const CtaTile &c, int F, int J, co
         const int count = nf * width;
         float last_s = INFINITY;
         long long last_t = -1;
-        ft_candidate *out =
-            reinterpret_cast<ft_candidate *>(p.cand) + (c.cta * p.lsub_max + (lb - lb0)) * p.k;
+        ft_candidate *out = dst + (lb - lb0) * p.k;
         for (int i = 0; i < p.k; ++i) {
             bool have = false;
             float bs = -INFINITY, bz = 0.f;
@@ -349,7 +348,7 @@ template <int NS>
 __device__ __forceinline__ void finish_tile(const EvalParams &p, const CtaTile &c, int F, int J,
                                             const int (&jrel)[NS], const float (&hi)[NS],
                                             const float (&lo)[NS], const int (&oob)[NS],
-                                            unsigned char *buf)
+                                            unsigned char *buf, ft_candidate *dst)
 {
     const int warp = threadIdx.x >> 5;
     const bool active = warp < F;
@@ -388,8 +387,11 @@ __device__ __forceinline__ void finish_tile(const EvalParams &p, const CtaTile &
         }
     }
     __syncthreads();
-    if (active)
-        cta_topk(p, c, F, J, vs, vz);
+    if (active) {
+        if (dst == nullptr)
+            dst = reinterpret_cast<ft_candidate *>(p.cand) + c.cta * p.lsub_max * p.k;
+        cta_topk(p, c, F, J, vs, vz, dst);
+    }
 }
 
 // ------------------------------------------------------------------ checked kernel
@@ -413,7 +415,7 @@ __global__ void __launch_bounds__(1024, 1) k_eval_checked(const EvalParams p)
     long long *tabC = reinterpret_cast<long long *>(smem + L.tabC);
     long long *tabX = reinterpret_cast<long long *>(smem + L.tabX);
     unsigned char *buf = smem + L.buf;
-    const CtaTile c = decode_tile(p, J);
+    const CtaTile c = decode_tile(p, J, blockIdx.x);
 
     int jrel[R], jr[R];
 #pragma unroll
@@ -494,7 +496,7 @@ __global__ void __launch_bounds__(1024, 1) k_eval_checked(const EvalParams p)
         if (threadIdx.x == 0 && st + kNbuf < p.n_stages)
             issue_stage(p, buf, bars, L.stage_bytes, st + kNbuf);
     }
-    finish_tile<R>(p, c, F, J, jrel, hi, lo, oob, buf);
+    finish_tile<R>(p, c, F, J, jrel, hi, lo, oob, buf, nullptr);
 }
 
 // ------------------------------------------------------------------ fast kernel
@@ -631,12 +633,12 @@ __device__ __forceinline__ long long cross_q32(long long G, int E)
 #define FT_FAST_MAXNREG 40
 #endif
 template <int MODE, int R, bool WEIGHTED>
-__global__ void __maxnreg__(FT_FAST_MAXNREG) k_eval_fast(const EvalParams p)
+__device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, unsigned char *smem,
+                                          ft_candidate *dst)
 {
     constexpr bool PAIR = MODE != MODE_F32;
     constexpr int NS = PAIR ? 2 * R : R;  // accumulator slots per thread
     constexpr int J = 32 * NS;            // f0 per tile
-    extern __shared__ __align__(128) unsigned char smem[];
     const int F = (blockDim.x >> 5) - 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int S = p.S;
@@ -647,7 +649,7 @@ __global__ void __maxnreg__(FT_FAST_MAXNREG) k_eval_fast(const EvalParams p)
     unsigned long long *empty = reinterpret_cast<unsigned long long *>(smem + L.empty);
     RowRec *rec = reinterpret_cast<RowRec *>(smem + L.rec);
     unsigned char *buf = smem + L.buf;
-    const CtaTile c = decode_tile(p, J);
+    const CtaTile c = decode_tile(p, J, tile);
     const int n_stages = p.n_stages;
 
     if (threadIdx.x == 0) {
@@ -844,8 +846,134 @@ __global__ void __maxnreg__(FT_FAST_MAXNREG) k_eval_fast(const EvalParams p)
     }
     // every copy has landed: its slot was consumed, or the producer waited for it above
     if (!__syncthreads_and(ok))
-        return;
-    finish_tile<NS>(p, c, F, J, jrel, hi, lo, oob, buf);
+        return false;
+    finish_tile<NS>(p, c, F, J, jrel, hi, lo, oob, buf, dst);
+    return true;
+}
+
+// One CTA per tile of the (sky, f1 group, f0 tile) grid.
+template <int MODE, int R, bool WEIGHTED>
+__global__ void __maxnreg__(FT_FAST_MAXNREG) k_eval_fast(const EvalParams p)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    fast_tile<MODE, R, WEIGHTED>(p, blockIdx.x, smem, nullptr);
+}
+
+// Persistent form for many bands: each CTA takes tiles from a global ticket counter over
+// a band-major work list (tile_prefix[b] = first ticket of band b) until it runs dry.  Each
+// tile's per-sub-band candidates are merged into running lists kept in shared memory for
+// the band the CTA is on; when the CTA moves to another band (or finishes) it writes those
+// lists to its slot scr[cta][band][sub-band][k] (slots never written stay empty).
+
+__device__ __forceinline__ bool cand_before(const ft_candidate &a, const ft_candidate &b)
+{
+    // (s desc, template index asc); empty entries (template_idx < 0) rank last
+    if (a.template_idx < 0)
+        return false;
+    if (b.template_idx < 0)
+        return true;
+    return a.s > b.s || (a.s == b.s && a.template_idx < b.template_idx);
+}
+
+// run[0..k) <- best k of the sorted lists run[0..k) and add[0..k) (one warp, k <= 32).
+__device__ __forceinline__ void warp_merge_lists(ft_candidate *run, const ft_candidate *add, int k)
+{
+    const int lane = threadIdx.x & 31;
+    ft_candidate a, b;
+    a.template_idx = b.template_idx = -1;
+    a.s = b.s = -INFINITY;
+    a.z = b.z = 0.f;
+    if (lane < k) {
+        a = run[lane];
+        b = add[lane];
+    }
+    int ra = lane, rb = lane;  // final ranks
+    for (int j = 0; j < k; ++j) {
+        ft_candidate bj, aj;
+        bj.template_idx = __shfl_sync(0xffffffffu, b.template_idx, j);
+        bj.s = __shfl_sync(0xffffffffu, b.s, j);
+        aj.template_idx = __shfl_sync(0xffffffffu, a.template_idx, j);
+        aj.s = __shfl_sync(0xffffffffu, a.s, j);
+        ra += cand_before(bj, a) ? 1 : 0;
+        rb += cand_before(aj, b) ? 1 : 0;
+    }
+    __syncwarp();
+    if (lane < k && ra < k)
+        run[ra] = a;
+    if (lane < k && rb < k)
+        run[rb] = b;
+    __syncwarp();
+}
+
+
+
+template <int MODE, int R, bool WEIGHTED>
+__global__ void __maxnreg__(FT_FAST_MAXNREG) k_eval_batched(const BatchParams bp)
+{
+    constexpr int NS = MODE != MODE_F32 ? 2 * R : R;
+    constexpr int J = 32 * NS;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ long long s_tile;
+    __shared__ int s_band;
+    ft_candidate *tl = reinterpret_cast<ft_candidate *>(smem + bp.list_off);
+    ft_candidate *run = tl + bp.lsub_max * bp.k;
+    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5;
+    const long long total = bp.tile_prefix[bp.n_bands];
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const long long t = static_cast<long long>(atomicAdd(bp.counter, 1ull));
+            int b = -1;
+            if (t < total) {
+                int lo = 0, hi = bp.n_bands - 1;  // last band whose prefix <= t
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (bp.tile_prefix[mid] <= t)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
+                }
+                b = lo;
+                s_tile = t - bp.tile_prefix[b];
+            }
+            s_band = b;
+        }
+        __syncthreads();
+        const int b = s_band;
+        const long long tile = s_tile;
+        if (b != cur) {
+            if (cur >= 0) {
+                const int m = bp.n_sub[cur] * bp.k;
+                ft_candidate *g = bp.scr + (static_cast<size_t>(blockIdx.x) * bp.n_bands + cur) *
+                                               bp.n_sub_max * bp.k;
+                for (int i = threadIdx.x; i < m; i += blockDim.x)
+                    g[i] = run[i];
+            }
+            if (b >= 0) {
+                const int m = bp.n_sub[b] * bp.k;
+                for (int i = threadIdx.x; i < m; i += blockDim.x) {
+                    run[i].template_idx = -1;
+                    run[i].s = -INFINITY;
+                    run[i].z = 0.f;
+                }
+            }
+            __syncthreads();
+            cur = b;
+        }
+        if (b < 0)
+            break;
+        const EvalParams &p = bp.params[b];
+        const bool done = fast_tile<MODE, R, WEIGHTED>(p, tile, smem, tl);
+        __syncthreads();
+        if (!done)
+            break;  // a bounded wait ran out (status already set): stop taking tiles
+        // merge this tile's lists into the band's running lists
+        const int j0 = static_cast<int>(tile % p.n_f0t) * J;
+        const int lb0 = j0 / p.sub, lb1 = (min(j0 + J, p.n_f0) - 1) / p.sub;
+        for (int lb = lb0 + warp; lb <= lb1; lb += nw)
+            warp_merge_lists(run + lb * bp.k, tl + (lb - lb0) * bp.k, bp.k);
+        __syncthreads();
+    }
 }
 
 // ------------------------------------------------------------------ candidate merge
@@ -858,15 +986,13 @@ __device__ __forceinline__ bool cand_better(const ft_candidate &a, const ft_cand
 constexpr int kKmax = 32;
 constexpr int kMergeThreads = 256;
 
-// One CTA per sub-band: gathers the per-CTA lists of every evaluation CTA whose f0 tile
+// One CTA per sub-band b: gathers the per-CTA lists of every evaluation CTA whose f0 tile
 // meets the sub-band and keeps the k best by (s desc, template index asc).
-__global__ void __launch_bounds__(kMergeThreads) k_topk_merge(const ft_candidate *cand, int k,
-                                                              int lsub_max, long long n_sky,
-                                                              int n_f1g, int n_f0t, int J, int sub,
-                                                              int n_f0, ft_candidate *out)
+__device__ __forceinline__ void merge_subband(const ft_candidate *cand, int k, int lsub_max,
+                                              long long n_sky, int n_f1g, int n_f0t, int J,
+                                              int sub, int n_f0, int b, ft_candidate *out)
 {
     __shared__ ft_candidate wl[kMergeThreads / 32][kKmax];
-    const int b = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ft_lo = (b * sub) / J;
     const int ft_hi = (min((b + 1) * sub, n_f0) - 1) / J;
@@ -974,6 +1100,133 @@ __global__ void __launch_bounds__(kMergeThreads) k_topk_merge(const ft_candidate
                 c.z = 0.f;
             }
             out[static_cast<long long>(b) * k + i] = c;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kMergeThreads) k_topk_merge(const ft_candidate *cand, int k,
+                                                              int lsub_max, long long n_sky,
+                                                              int n_f1g, int n_f0t, int J, int sub,
+                                                              int n_f0, ft_candidate *out)
+{
+    merge_subband(cand, k, lsub_max, n_sky, n_f1g, n_f0t, J, sub, n_f0, blockIdx.x, out);
+}
+
+// Merge for the persistent batch: block i handles sub-band j = i - sub_prefix[b] of band b
+// and keeps the k best of the n_ctas lists scr[c][b][j][0..k).
+__global__ void __launch_bounds__(kMergeThreads) k_topk_merge_persist(
+    const ft_candidate *scr, int n_ctas, int n_bands, int n_sub_max, int k, const int *sub_prefix,
+    ft_candidate *out)
+{
+    __shared__ ft_candidate wl[kMergeThreads / 32][kKmax];
+    const int i = blockIdx.x;
+    int lo = 0, hi = n_bands - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sub_prefix[mid] <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const int band = lo, j = i - sub_prefix[lo];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    ft_candidate Lst[kKmax];
+    int n = 0;
+    const long long total = static_cast<long long>(n_ctas) * k;
+    for (long long q = tid; q < total; q += blockDim.x) {
+        const long long cta = q / k;
+        const int e = static_cast<int>(q - cta * k);
+        const ft_candidate x = scr[((cta * n_bands + band) * n_sub_max + j) * k + e];
+        if (x.template_idx < 0)
+            continue;
+        if (n < k || cand_better(x, Lst[n - 1])) {
+            int pos = n < k ? n : k - 1;
+            while (pos > 0 && cand_better(x, Lst[pos - 1])) {
+                Lst[pos] = Lst[pos - 1];
+                --pos;
+            }
+            Lst[pos] = x;
+            if (n < k)
+                ++n;
+        }
+    }
+    // lanes -> warp list -> block list, k rounds of arg-max over list heads each
+    int h = 0;
+    for (int r = 0; r < k; ++r) {
+        ft_candidate c;
+        bool have = h < n;
+        if (have)
+            c = Lst[h];
+        else {
+            c.template_idx = LLONG_MAX;
+            c.s = -INFINITY;
+            c.z = 0.f;
+        }
+        int src = lane;
+        for (int off = 16; off > 0; off >>= 1) {
+            const float os = __shfl_xor_sync(0xffffffffu, c.s, off);
+            const float oz = __shfl_xor_sync(0xffffffffu, c.z, off);
+            const long long ot = __shfl_xor_sync(0xffffffffu, c.template_idx, off);
+            const int osrc = __shfl_xor_sync(0xffffffffu, src, off);
+            const bool oh = __shfl_xor_sync(0xffffffffu, have ? 1 : 0, off) != 0;
+            if (oh && (!have || os > c.s || (os == c.s && ot < c.template_idx))) {
+                have = true;
+                c.s = os;
+                c.z = oz;
+                c.template_idx = ot;
+                src = osrc;
+            }
+        }
+        if (have && lane == src)
+            ++h;
+        if (lane == 0) {
+            if (!have) {
+                c.template_idx = -1;
+                c.s = -INFINITY;
+                c.z = 0.f;
+            }
+            wl[warp][r] = c;
+        }
+    }
+    __syncthreads();
+    if (warp != 0)
+        return;
+    const int nw = blockDim.x >> 5;
+    h = 0;
+    for (int r = 0; r < k; ++r) {
+        ft_candidate c;
+        bool have = lane < nw && h < k && wl[lane][h].template_idx >= 0;
+        if (have)
+            c = wl[lane][h];
+        else {
+            c.template_idx = LLONG_MAX;
+            c.s = -INFINITY;
+            c.z = 0.f;
+        }
+        int src = lane;
+        for (int off = 16; off > 0; off >>= 1) {
+            const float os = __shfl_xor_sync(0xffffffffu, c.s, off);
+            const float oz = __shfl_xor_sync(0xffffffffu, c.z, off);
+            const long long ot = __shfl_xor_sync(0xffffffffu, c.template_idx, off);
+            const int osrc = __shfl_xor_sync(0xffffffffu, src, off);
+            const bool oh = __shfl_xor_sync(0xffffffffu, have ? 1 : 0, off) != 0;
+            if (oh && (!have || os > c.s || (os == c.s && ot < c.template_idx))) {
+                have = true;
+                c.s = os;
+                c.z = oz;
+                c.template_idx = ot;
+                src = osrc;
+            }
+        }
+        if (have && lane == src)
+            ++h;
+        if (lane == 0) {
+            if (!have) {
+                c.template_idx = -1;
+                c.s = -INFINITY;
+                c.z = 0.f;
+            }
+            out[static_cast<long long>(i) * k + r] = c;
         }
     }
 }
@@ -1269,6 +1522,93 @@ int ft_launch_track_bins(const ft_band *band, const ft_bank *bank, const long lo
     k_track_bins<<<grid_for(n * band->N, 256), 256, 0, st>>>(
         band->d_v, bank->d_sky, bank->d_G, band->N, bank->k0, band->k_lo, bank->n_f0, bank->n_f1,
         n_templates, tmpl, n, bins);
+    FT_CUDA(cudaGetLastError());
+    return FT_OK;
+}
+
+// ------------------------------------------------------------------ persistent batch
+
+namespace {
+
+template <int MODE, int R, bool W>
+int batched_t(const BatchParams &bp, int threads, size_t smem, int *grid_out, bool launch,
+              cudaStream_t st)
+{
+    static size_t configured = 0;
+    auto fn = k_eval_batched<MODE, R, W>;
+    if (smem > configured) {
+        FT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(smem)));
+        FT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared));
+        configured = smem;
+    }
+    int per_sm = 0;
+    FT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
+    if (per_sm < 1)
+        FT_FAIL(FT_ERR_RANGE, "batch: the persistent kernel does not fit on an SM with this shape");
+    int dev = 0, sms = 0;
+    FT_CUDA(cudaGetDevice(&dev));
+    FT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    *grid_out = per_sm * sms;
+    if (launch) {
+        fn<<<*grid_out, threads, smem, st>>>(bp);
+        FT_CUDA(cudaGetLastError());
+    }
+    return FT_OK;
+}
+
+template <int MODE, bool W>
+int batched_r(int R, const BatchParams &bp, int threads, size_t smem, int *grid, bool launch,
+              cudaStream_t st)
+{
+    switch (R) {
+    case 1: return batched_t<MODE, 1, W>(bp, threads, smem, grid, launch, st);
+    case 2: return batched_t<MODE, 2, W>(bp, threads, smem, grid, launch, st);
+    case 3: return batched_t<MODE, 3, W>(bp, threads, smem, grid, launch, st);
+    case 4: return batched_t<MODE, 4, W>(bp, threads, smem, grid, launch, st);
+    case 6: return MODE == MODE_F32 ? batched_t<MODE_F32, 6, W>(bp, threads, smem, grid, launch, st) : FT_ERR_ARG;
+    case 8: return MODE == MODE_F32 ? batched_t<MODE_F32, 8, W>(bp, threads, smem, grid, launch, st) : FT_ERR_ARG;
+    default: FT_FAIL(FT_ERR_ARG, "batch: unsupported tile width");
+    }
+}
+
+}  // namespace
+
+size_t ft_batch_tile_smem(const ft_band *band, int S, int F, int J, int nst)
+{
+    return fast_layout(S, F, row_bytes_of(band), J, true, nst).total;
+}
+
+int ft_batch_row_bytes(const ft_band *band)
+{
+    return row_bytes_of(band);
+}
+
+int ft_launch_batched(int dtype, bool weighted, int J, int F, const BatchParams &bp, size_t smem,
+                      int *grid, bool launch, cudaStream_t st)
+{
+    const int threads = 32 * (F + 1);
+    switch (dtype) {
+    case FT_F32:
+        return weighted ? batched_r<MODE_F32, true>(J / 32, bp, threads, smem, grid, launch, st)
+                        : batched_r<MODE_F32, false>(J / 32, bp, threads, smem, grid, launch, st);
+    case FT_F16:
+        return weighted ? batched_r<MODE_F16, true>(J / 64, bp, threads, smem, grid, launch, st)
+                        : batched_r<MODE_F16, false>(J / 64, bp, threads, smem, grid, launch, st);
+    case FT_BF16:
+        return weighted ? batched_r<MODE_BF16, true>(J / 64, bp, threads, smem, grid, launch, st)
+                        : batched_r<MODE_BF16, false>(J / 64, bp, threads, smem, grid, launch, st);
+    default: FT_FAIL(FT_ERR_ARG, "batch: bad dtype");
+    }
+}
+
+int ft_launch_merge_persist(const ft_candidate *scr, int n_ctas, int n_bands, int n_sub_max, int k,
+                            const int *sub_prefix, int n_sub_total, ft_candidate *out,
+                            cudaStream_t st)
+{
+    k_topk_merge_persist<<<n_sub_total, kMergeThreads, 0, st>>>(scr, n_ctas, n_bands, n_sub_max, k,
+                                                                sub_prefix, out);
     FT_CUDA(cudaGetLastError());
     return FT_OK;
 }

@@ -126,6 +126,20 @@ struct EvalParams {
     unsigned int *status;
 };
 
+// Persistent multi-band launch: band-major work list of tiles, running candidate lists.
+struct BatchParams {
+    const EvalParams *params;      // [n_bands], device
+    const long long *tile_prefix;  // [n_bands + 1], device
+    const int *n_sub;              // [n_bands] sub-bands per band
+    int n_bands;
+    int k;
+    int n_sub_max;                 // max sub-bands over the bands
+    int lsub_max;                  // max sub-bands met by one tile
+    size_t list_off;               // shared-memory offset of the candidate lists
+    unsigned long long *counter;   // zeroed before the launch
+    ft_candidate *scr;             // [gridDim.x][n_bands][n_sub_max][k], pre-filled empty
+};
+
 // launch helpers implemented in ft_eval.cu
 struct EvalShape {
     int J;       // f0 values per CTA tile (32 x slots per lane)
@@ -148,3 +162,11 @@ int ft_launch_gtable(const double *f1, int n_f1, const double *tau, long long N,
                      long long *G, cudaStream_t st);
 int ft_launch_track_bins(const ft_band *band, const ft_bank *bank, const long long *tmpl,
                          long long n, int *bins, cudaStream_t st);
+
+size_t ft_batch_tile_smem(const ft_band *band, int S, int F, int J, int nst);
+int ft_batch_row_bytes(const ft_band *band);
+int ft_launch_batched(int dtype, bool weighted, int J, int F, const BatchParams &bp, size_t smem,
+                      int *grid, bool launch, cudaStream_t st);
+int ft_launch_merge_persist(const ft_candidate *scr, int n_ctas, int n_bands, int n_sub_max, int k,
+                            const int *sub_prefix, int n_sub_total, ft_candidate *out,
+                            cudaStream_t st);
