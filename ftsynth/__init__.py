@@ -108,6 +108,27 @@ def detector_velocity(t: np.ndarray, det: int) -> np.ndarray:
     return (orb + rot) / C_LIGHT
 
 
+def detector_tensor(t: np.ndarray, det: int) -> np.ndarray:
+    """Detector tensor D = (u u^T - v v^T)/2 of site `det` at times t, in the equatorial
+    frame, as [len(t), 6] = (Dxx, Dxy, Dxz, Dyy, Dyz, Dzz).  u, v are the arm directions
+    (azimuths from north towards east in the local horizontal plane); the site turns with
+    the sidereal angle 2 pi t / T_sid + longitude (the same angle as detector_velocity)."""
+    site = SITES[det]
+    t = np.asarray(t, dtype=np.float64)
+    th = 2.0 * math.pi * t / SIDEREAL_DAY_S + math.radians(site.lon_deg)
+    lat = math.radians(site.lat_deg)
+    east = np.stack([-np.sin(th), np.cos(th), np.zeros_like(th)], axis=1)
+    north = np.stack([-math.sin(lat) * np.cos(th), -math.sin(lat) * np.sin(th),
+                      np.full_like(th, math.cos(lat))], axis=1)
+    arms = []
+    for az in site.arm_az_deg:
+        A = math.radians(az)
+        arms.append(north * math.cos(A) + east * math.sin(A))
+    u, v = arms
+    D = 0.5 * (u[:, :, None] * u[:, None, :] - v[:, :, None] * v[:, None, :])
+    return np.stack([D[:, 0, 0], D[:, 0, 1], D[:, 0, 2], D[:, 1, 1], D[:, 1, 2], D[:, 2, 2]], axis=1)
+
+
 def max_v_over_c() -> float:
     return (V_ORBIT + V_ROT) / C_LIGHT
 

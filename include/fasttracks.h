@@ -205,6 +205,59 @@ FT_API int ft_topk_per_band(ft_ctx *ctx, const ft_band *band, const ft_bank *ban
 FT_API int ft_topk_per_band_noalloc(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int k,
                                     ft_candidate *out, int out_on_device, void *stream);
 
+/* ----------------------------------------------------------------------------- injections --
+ * Injection-recovery runs: the Monte-Carlo estimate of the detection probability
+ * (Sec. V, Eq. (sampling)).  Each run simulates one signal in Gaussian noise and returns
+ * the loudest critical ratio z of a local bank around it; the caller applies the
+ * detection rule z > tau (Sec. V.B) and fits p_det(h0).
+ *   Signal (Sec. II.B.2): in SFT alpha the normalised power
+ *     rho^2 = 4 |h~|^2 / (T_SFT S_n),  |h~| = 0.7737 (T_SFT/2) h0 |Q|,
+ *     |Q|^2 = (F+ (1 + cos^2 iota)/2)^2 + (Fx cos iota)^2   (polarisations in quadrature),
+ *     F+ = a cos 2psi + b sin 2psi, Fx = b cos 2psi - a sin 2psi, a = D : e+, b = D : ex,
+ *     with D the detector tensor at the SFT and e+, ex built on X = z x n/|z x n|, Y = n x X;
+ *   placed in the bin nearest (f0 T_SFT + f1 tau)(1 + v.n) (FP64, tau = (t_mid - t0) T_SFT).
+ *   Data: per SFT the bins k_sig - H .. k_sig + H, generated on the device and never
+ *   stored: complex unit Gaussian noise (scaled by noise_scale) plus sqrt(rho^2) in k_sig,
+ *   i.e. P = -2 ln u1, or |r e^{i 2 pi u2} + sqrt(rho^2)|^2 with r^2 = -2 ln u1 in k_sig;
+ *   u1, u2 = ((x >> 8) + 1) / 2^24 from Philox4x32-10 (Salmon et al., SC'11) with counter
+ *   (absolute bin, SFT index, run id low, run id high) and key (seed low, seed high).
+ *   Local bank: the k_sky bank sky points nearest to n, every bank f1, and the bank f0 bins
+ *   within half_f0 of round(f0 T_SFT); each template's statistic is that of
+ *   ft_eval_statistic (same track bins and weights), reads outside the generated window
+ *   contribute 0 and are counted.
+ * The band supplies times, velocities, weights and S_n (it must be loaded with s_n); its
+ * stored power is not used.  det_tensor: host [N_SFT][6] (xx, xy, xz, yy, yz, zz).
+ * inj/out: host arrays of n runs; run i uses run id desc->first_run_id + i.
+ * Limits: k_sky <= 128, half_f0 <= 7, 1 <= half_window <= 1024, n_f1 <= 64 and at most 4096
+ * local templates.  Allocates device memory for the call; synchronises `stream`. */
+typedef struct {
+    double h0;    /* amplitude, in the units of sqrt(S_n T_SFT) of the band's power       */
+    double cosi;  /* cos(inclination)                                                        */
+    double psi;   /* polarisation angle (rad)                                               */
+    double f0;    /* frequency at t0 (Hz)                                                    */
+    double f1;    /* spindown (Hz/s)                                                         */
+    double n[3];  /* source direction, unit vector (equatorial)                              */
+} ft_injection;
+
+typedef struct {
+    int k_sky;
+    int half_f0;
+    int half_window;
+    double noise_scale; /* 1: Gaussian noise; 0: noise-free data (checking)                  */
+    uint64_t seed;
+    uint64_t first_run_id;
+} ft_inj_desc;
+
+typedef struct {
+    double max_z;            /* loudest critical ratio over the local bank                   */
+    int64_t template_idx;    /* the template attaining it (ties: smaller index)              */
+    int64_t n_out_of_window; /* local-bank reads outside the generated window                */
+} ft_inj_result;
+
+FT_API int ft_run_injections(ft_ctx *ctx, const ft_band *band, const ft_bank *bank,
+                             const double *det_tensor, const ft_inj_desc *desc, int64_t n,
+                             const ft_injection *inj, ft_inj_result *out, void *stream);
+
 /* ----------------------------------------------------------------------------- tuning --
  * Launch shape of the evaluation kernels.  Zero fields keep the built-in choice.
  *   rows_per_stage  SFT rows per shared-memory stage (fast kernel: multiple of 4, <= 32)

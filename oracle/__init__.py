@@ -48,6 +48,30 @@ class _Problem(ctypes.Structure):
     ]
 
 
+class _InjProblem(ctypes.Structure):
+    _fields_ = [
+        ("n_sft", ctypes.c_int64),
+        ("k_lo", ctypes.c_int64),
+        ("t_mid", ctypes.c_void_p),
+        ("v", ctypes.c_void_p),
+        ("w", ctypes.c_void_p),
+        ("s_n", ctypes.c_void_p),
+        ("D", ctypes.c_void_p),
+        ("t0", ctypes.c_double),
+        ("t_sft", ctypes.c_double),
+        ("K0", ctypes.c_int64),
+        ("n_f0", ctypes.c_int64),
+        ("n_f1", ctypes.c_int64),
+        ("f1", ctypes.c_void_p),
+        ("n_sky", ctypes.c_int64),
+        ("sky", ctypes.c_void_p),
+    ]
+
+
+INJ_DTYPE = np.dtype([("h0", "<f8"), ("cosi", "<f8"), ("psi", "<f8"), ("f0", "<f8"),
+                      ("f1", "<f8"), ("n", "<f8", (3,))])
+
+
 def load_library(path):
     """Open an oracle shared library and declare its signatures."""
     L = ctypes.CDLL(path)
@@ -64,6 +88,22 @@ def load_library(path):
     L.or_bins.argtypes = [ctypes.POINTER(_Problem), ctypes.c_void_p, ctypes.c_int64,
                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     L.or_num_threads.restype = ctypes.c_int
+    L.or_philox4x32_10.restype = None
+    L.or_philox4x32_10.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.or_uniform24.restype = ctypes.c_double
+    L.or_uniform24.argtypes = [ctypes.c_uint32]
+    L.or_antenna_ab.restype = None
+    L.or_antenna_ab.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.or_rho2.restype = ctypes.c_double
+    L.or_rho2.argtypes = [ctypes.c_void_p, ctypes.c_void_p] + [ctypes.c_double] * 5
+    L.or_inj_power.restype = ctypes.c_double
+    L.or_inj_power.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64,
+                               ctypes.c_double, ctypes.c_double]
+    L.or_injections.restype = None
+    L.or_injections.argtypes = [ctypes.POINTER(_InjProblem), ctypes.c_void_p, ctypes.c_int64,
+                                ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_void_p]
     return L
 
 
@@ -178,3 +218,75 @@ def topk_per_subband(s, bank, k: int, templates=None):
         idx[b, : len(order)] = tb[order]
         val[b, : len(order)] = sb[order]
     return idx, val
+
+
+# ----------------------------------------------------------------------------- injections
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 block (Salmon et al., SC'11) of counter ctr[4], key key[2]."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    o = np.empty(4, np.uint32)
+    lib().or_philox4x32_10(c.ctypes.data, k.ctypes.data, o.ctypes.data)
+    return o
+
+
+def uniform24(x):
+    return lib().or_uniform24(int(x))
+
+
+def antenna_ab(D, n):
+    """a = D : e+, b = D : ex for detector tensor D (6 components) and source direction n."""
+    Dv = _c(D, np.float64)
+    nv = _c(n, np.float64)
+    a, b = ctypes.c_double(), ctypes.c_double()
+    lib().or_antenna_ab(Dv.ctypes.data, nv.ctypes.data, ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def rho2(D, n, h0, cosi, psi, t_sft, s_n):
+    """Normalised signal power of one SFT (Sec. II.B.2 signal model)."""
+    Dv = _c(D, np.float64)
+    nv = _c(n, np.float64)
+    return lib().or_rho2(Dv.ctypes.data, nv.ctypes.data, h0, cosi, psi, t_sft, s_n)
+
+
+def inj_power(kabs, alpha, run_id, seed, amp, noise_scale=1.0):
+    return lib().or_inj_power(int(kabs), int(alpha), int(run_id), int(seed), float(amp),
+                              float(noise_scale))
+
+
+def injections(sfts, bank, D, inj, first_id, seed, K=64, half_f0=2, H=160, noise_scale=1.0,
+               w=None):
+    """Independent injection-recovery runs (run r uses run id first_id + r): max z over the
+    local bank, argmax template and out-of-window reads.  inj: structured INJ_DTYPE array."""
+    keep = dict(t_mid=_c(sfts.t_mid, np.float64), v=_c(sfts.v, np.float64),
+                s_n=_c(sfts.s_n, np.float64), D=_c(D, np.float64), f1=_c(bank.f1, np.float64),
+                sky=_c(bank.sky, np.float64),
+                w=None if w is None else _c(w, np.float64))
+    p = _InjProblem()
+    p.n_sft = len(keep["t_mid"])
+    p.k_lo = int(sfts.k_lo)
+    p.t_mid = keep["t_mid"].ctypes.data
+    p.v = keep["v"].ctypes.data
+    p.w = None if keep["w"] is None else keep["w"].ctypes.data
+    p.s_n = keep["s_n"].ctypes.data
+    p.D = keep["D"].ctypes.data
+    p.t0 = float(sfts.t0)
+    p.t_sft = float(sfts.t_sft)
+    p.K0 = int(bank.k0)
+    p.n_f0 = int(bank.n_f0)
+    p.n_f1 = len(keep["f1"])
+    p.f1 = keep["f1"].ctypes.data
+    p.n_sky = len(keep["sky"])
+    p.sky = keep["sky"].ctypes.data
+    arr = np.ascontiguousarray(inj, dtype=INJ_DTYPE)
+    n = len(arr)
+    mz = np.empty(n, np.float64)
+    am = np.empty(n, np.int64)
+    oob = np.empty(n, np.int64)
+    lib().or_injections(ctypes.byref(p), arr.ctypes.data, n, int(first_id), int(seed), int(K),
+                        int(half_f0), int(H), float(noise_scale), mz.ctypes.data, am.ctypes.data,
+                        oob.ctypes.data)
+    return mz, am, oob

@@ -11,14 +11,16 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "ft_oracle.c")
+SRCS = [SRC, os.path.join(HERE, "ft_oracle_inj.c")]
 LIB = os.path.join(HERE, "libftoracle.so")
 
 
 def build(force: bool = False) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+    if not force and os.path.exists(LIB) and all(
+            os.path.getmtime(LIB) >= os.path.getmtime(s) for s in SRCS):
         return LIB
     cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-std=gnu11", SRC, "-o", LIB + ".tmp", "-lm"]
+           "-std=gnu11"] + SRCS + ["-o", LIB + ".tmp", "-lm"]
     subprocess.check_call(cmd)
     os.replace(LIB + ".tmp", LIB)
     return LIB

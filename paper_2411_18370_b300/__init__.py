@@ -44,6 +44,18 @@ class _BankDesc(ctypes.Structure):
                 ("subband_bins", ctypes.c_int)]
 
 
+class _InjDesc(ctypes.Structure):
+    _fields_ = [("k_sky", ctypes.c_int), ("half_f0", ctypes.c_int), ("half_window", ctypes.c_int),
+                ("noise_scale", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("first_run_id", ctypes.c_uint64)]
+
+
+# ft_injection {h0, cosi, psi, f0, f1, n[3]} and ft_inj_result {max_z, template_idx, n_oob}
+INJECTION_DTYPE = np.dtype([("h0", "<f8"), ("cosi", "<f8"), ("psi", "<f8"), ("f0", "<f8"),
+                            ("f1", "<f8"), ("n", "<f8", (3,))])
+INJ_RESULT_DTYPE = np.dtype([("max_z", "<f8"), ("template_idx", "<i8"),
+                             ("n_out_of_window", "<i8")])
+
 _lib = None
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -85,6 +97,7 @@ def lib():
                                    ctypes.POINTER(_I)]),
             "ft_batch_destroy": (None, [_P]),
             "ft_eval_batched": (_I, [_P, _I, _P, _P, _I, _P, _I, _P, _P]),
+            "ft_run_injections": (_I, [_P, _P, _P, _P, ctypes.POINTER(_InjDesc), _I64, _P, _P, _P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -245,6 +258,22 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def run_injections(ctx, band, bank, det_tensor, inj, seed, first_run_id=0, k_sky=64, half_f0=2,
+                   half_window=160, noise_scale=1.0, stream=None):
+    """ft_run_injections: one injection-recovery run per record of `inj` (INJECTION_DTYPE);
+    returns an INJ_RESULT_DTYPE array (max z over the local bank, its template, reads outside
+    the generated window)."""
+    arr = np.ascontiguousarray(inj, dtype=INJECTION_DTYPE)
+    D = _f64(det_tensor).reshape(-1, 6)
+    out = np.zeros(len(arr), dtype=INJ_RESULT_DTYPE)
+    d = _InjDesc(int(k_sky), int(half_f0), int(half_window), float(noise_scale), int(seed),
+                 int(first_run_id))
+    _check(lib().ft_run_injections(ctx.handle, band.handle, bank.handle, D.ctypes.data,
+                                   ctypes.byref(d), len(arr), arr.ctypes.data, out.ctypes.data,
+                                   _stream(stream, False)))
+    return out
 
 
 def abi_version() -> int:

@@ -20,8 +20,8 @@ LIB = os.path.join(HERE, "libfasttracks.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-         "-Xcompiler", "-fvisibility=hidden", "-cudart", "static", "-shared"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fopenmp",
+         "-Xcompiler", "-fvisibility=hidden", "-cudart", "static", "-shared", "-lgomp"]
 
 
 def sources():

@@ -1,0 +1,90 @@
+"""Injection-recovery runs on the GPU against the CPU oracle.
+
+Both sides draw the same Philox4x32-10 streams; the GPU forms -2 ln u and the Box-Muller
+cosine in FP32 (CUDA's logf, cospif), the oracle in FP64, so P agrees to ~1e-7 relative and
+the loudest z of a run to ~1e-5 absolute (tolerance 2e-4 here).
+"""
+import numpy as np
+import pytest
+
+import ftsynth
+import oracle
+import paper_2411_18370_b300 as ft
+from tests import helpers as H
+from tests.test_oracle_injection_pins import _short_band
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    ctx = ft.create(0)
+    sfts, bank, D = _short_band(n_slots=400, n_sky=200)
+    band = H.band_from(ctx, sfts)
+    bk = H.bank_from(ctx, band, bank)
+    yield ctx, sfts, bank, D, band, bk
+    bk.close()
+    band.close()
+    ctx.close()
+
+
+def _random_injections(n, bank, g, h0_max=0.08, t_sft=1800.0):
+    inj = np.zeros(n, ft.INJECTION_DTYPE)
+    inj["h0"] = np.where(g.random(n) < 0.3, 0.0, g.uniform(0.005, h0_max, n))
+    inj["cosi"] = g.uniform(-1, 1, n)
+    inj["psi"] = g.uniform(0, np.pi, n)
+    inj["f0"] = (bank.k0 + g.uniform(3, bank.n_f0 - 3, n)) / t_sft
+    inj["f1"] = g.uniform(-1e-9, 0, n)
+    m = g.standard_normal((n, 3))
+    inj["n"] = m / np.linalg.norm(m, axis=1)[:, None]
+    return inj
+
+
+def test_injections_match_oracle(setup):
+    ctx, sfts, bank, D, band, bk = setup
+    inj = _random_injections(40, bank, np.random.default_rng(8))
+    got = ft.run_injections(ctx, band, bk, D, inj, seed=2024, first_run_id=100, k_sky=32)
+    oz, oa, oo = oracle.injections(sfts, bank, D, inj.astype(oracle.INJ_DTYPE), 100, 2024, K=32)
+    assert np.array_equal(got["n_out_of_window"], oo) and np.all(oo == 0)
+    assert np.all(np.abs(got["max_z"] - oz) < 2e-4), np.max(np.abs(got["max_z"] - oz))
+    assert np.mean(got["template_idx"] == oa) >= 0.9
+
+
+def test_noise_free_grid_injection(setup):
+    ctx, sfts, bank, D, band, bk = setup
+    j, f1i, ski = 61, 7, 33
+    inj = np.zeros(1, ft.INJECTION_DTYPE)
+    inj["h0"], inj["cosi"], inj["psi"] = 0.05, -0.4, 2.0
+    inj["f0"] = (bank.k0 + j) / sfts.t_sft
+    inj["f1"] = bank.f1[f1i]
+    inj["n"] = bank.sky[ski]
+    got = ft.run_injections(ctx, band, bk, D, inj, seed=1, k_sky=16, noise_scale=0.0)
+    rho2 = np.array([oracle.rho2(D[a], bank.sky[ski], 0.05, -0.4, 2.0, 1800.0, sfts.s_n[a])
+                     for a in range(sfts.n_total)])
+    mu, sig = oracle.mu_sigma(sfts.n_total)
+    want = (rho2.sum() - mu) / sig
+    assert got["template_idx"][0] == (ski * bank.n_f1 + f1i) * bank.n_f0 + j
+    assert abs(got["max_z"][0] - want) < 1e-6 * abs(want) + 1e-5
+
+
+def test_run_ids_are_independent_and_repeatable(setup):
+    ctx, sfts, bank, D, band, bk = setup
+    inj = _random_injections(8, bank, np.random.default_rng(9))
+    a = ft.run_injections(ctx, band, bk, D, inj, seed=7, first_run_id=0, k_sky=16)
+    b = ft.run_injections(ctx, band, bk, D, inj, seed=7, first_run_id=0, k_sky=16)
+    c = ft.run_injections(ctx, band, bk, D, inj, seed=7, first_run_id=1000, k_sky=16)
+    assert np.array_equal(a, b)
+    assert not np.array_equal(a["max_z"], c["max_z"])
+
+
+def test_injection_argument_checks(setup):
+    ctx, sfts, bank, D, band, bk = setup
+    inj = _random_injections(2, bank, np.random.default_rng(10))
+    with pytest.raises(ft.FtError) as e:
+        ft.run_injections(ctx, band, bk, D, inj, seed=1, k_sky=500)
+    assert e.value.code == -5
+    bad = inj.copy()
+    bad["n"][0] = [1.0, 1.0, 0.0]
+    with pytest.raises(ft.FtError) as e:
+        ft.run_injections(ctx, band, bk, D, bad, seed=1, k_sky=16)
+    assert e.value.code == -1
