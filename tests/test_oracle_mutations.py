@@ -51,8 +51,9 @@ def _compile(src: str, out: str):
     cfile = out[:-3] + ".c"
     with open(cfile, "w") as f:
         f.write(src)
+    others = [s for s in obuild.SRCS if s != obuild.SRC]
     subprocess.check_call(["gcc", "-O1", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
-                           "-std=gnu11", cfile, "-o", out, "-lm"])
+                           "-std=gnu11", cfile] + others + ["-o", out, "-lm"])
 
 
 def _runs_clean(lib):
