@@ -258,6 +258,39 @@ FT_API int ft_run_injections(ft_ctx *ctx, const ft_band *band, const ft_bank *ba
                              const double *det_tensor, const ft_inj_desc *desc, int64_t n,
                              const ft_injection *inj, ft_inj_result *out, void *stream);
 
+/* ----------------------------------------------------------------------------- surrogate --
+ * A learned model of the detection probability p_det (Sec. V, Eqs. (pdet_abstract),
+ * (simple_eq)) trained on injection-recovery outcomes: a 4-layer perceptron
+ * d_in -> width -> width -> width -> 1 with ReLU and a sigmoid output, binary cross entropy
+ * (mean over the batch) and Adam, all in this library's CUDA kernels.  FP32 training;
+ * inference in FP32 or BF16 (weights and activations rounded to BF16, FP32 accumulation).
+ * Parameter vector (FP32, this order): W1[width][d_in] b1 W2[width][width] b2 W3 b3
+ * W4[1][width] b4[1].  Reductions run in a fixed order: training is bit-reproducible.
+ * The model is bound to the context's device; host arrays unless stated. */
+typedef struct ft_mlp ft_mlp;
+/* He-uniform weights (bound sqrt(6/fan_in)) and zero biases from `seed`; 1 <= d_in, width <= 256. */
+FT_API int ft_mlp_create(ft_ctx *ctx, int d_in, int width, uint64_t seed, ft_mlp **out);
+FT_API void ft_mlp_destroy(ft_mlp *mlp);
+FT_API int ft_mlp_n_params(const ft_mlp *mlp, int64_t *n);
+FT_API int ft_mlp_get_params(ft_mlp *mlp, float *params);
+/* Sets the parameters and resets the optimiser state. */
+FT_API int ft_mlp_set_params(ft_mlp *mlp, const float *params);
+/* Loss and gradient of one batch X [B][d_in], labels y [B] in {0, 1} (loss, grad nullable;
+ * grad [n_params]).  The gradient stays on the device for ft_mlp_adam_step. */
+FT_API int ft_mlp_loss_grad(ft_mlp *mlp, const float *X, const float *y, int B, float *loss,
+                            float *grad);
+/* One Adam update with the last gradient (bias-corrected moments). */
+FT_API int ft_mlp_adam_step(ft_mlp *mlp, float lr, float beta1, float beta2, float eps);
+/* Mini-batch training on n samples for `epochs` passes (shuffled by `seed`; Adam with
+ * beta1 0.9, beta2 0.999, eps 1e-8); loss_history [epochs] (nullable) gets each pass's mean
+ * batch loss. */
+FT_API int ft_mlp_train(ft_mlp *mlp, const float *X, const float *y, int64_t n, int batch,
+                        int epochs, float lr, uint64_t seed, float *loss_history);
+/* p = sigmoid(network(X)) for n samples; bf16 selects BF16 inference; X and p both host
+ * (on_device 0) or both device (1, asynchronous on `stream`). */
+FT_API int ft_mlp_predict(ft_mlp *mlp, const float *X, int64_t n, float *p, int bf16,
+                          int on_device, void *stream);
+
 /* ----------------------------------------------------------------------------- tuning --
  * Launch shape of the evaluation kernels.  Zero fields keep the built-in choice.
  *   rows_per_stage  SFT rows per shared-memory stage (fast kernel: multiple of 4, <= 32)

@@ -98,6 +98,16 @@ def lib():
             "ft_batch_destroy": (None, [_P]),
             "ft_eval_batched": (_I, [_P, _I, _P, _P, _I, _P, _I, _P, _P]),
             "ft_run_injections": (_I, [_P, _P, _P, _P, ctypes.POINTER(_InjDesc), _I64, _P, _P, _P]),
+            "ft_mlp_create": (_I, [_P, _I, _I, ctypes.c_uint64, ctypes.POINTER(_P)]),
+            "ft_mlp_destroy": (None, [_P]),
+            "ft_mlp_n_params": (_I, [_P, ctypes.POINTER(_I64)]),
+            "ft_mlp_get_params": (_I, [_P, _P]),
+            "ft_mlp_set_params": (_I, [_P, _P]),
+            "ft_mlp_loss_grad": (_I, [_P, _P, _P, _I, _P, _P]),
+            "ft_mlp_adam_step": (_I, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                      ctypes.c_float]),
+            "ft_mlp_train": (_I, [_P, _P, _P, _I64, _I, _I, ctypes.c_float, ctypes.c_uint64, _P]),
+            "ft_mlp_predict": (_I, [_P, _P, _I64, _P, _I, _I, _P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -274,6 +284,73 @@ def run_injections(ctx, band, bank, det_tensor, inj, seed, first_run_id=0, k_sky
                                    ctypes.byref(d), len(arr), arr.ctypes.data, out.ctypes.data,
                                    _stream(stream, False)))
     return out
+
+
+class MLP:
+    """ft_mlp: the p_det surrogate network (4 layers, ReLU, sigmoid output)."""
+
+    def __init__(self, ctx, d_in, width=128, seed=0):
+        h = _P()
+        _check(lib().ft_mlp_create(ctx.handle, int(d_in), int(width), int(seed), ctypes.byref(h)))
+        self.ctx, self.handle, self.d_in, self.width = ctx, h, int(d_in), int(width)
+        n = _I64()
+        _check(lib().ft_mlp_n_params(h, ctypes.byref(n)))
+        self.n_params = n.value
+
+    def get_params(self):
+        out = np.empty(self.n_params, np.float32)
+        _check(lib().ft_mlp_get_params(self.handle, out.ctypes.data))
+        return out
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        assert th.size == self.n_params
+        _check(lib().ft_mlp_set_params(self.handle, th.ctypes.data))
+
+    def loss_grad(self, X, y):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        loss = ctypes.c_float()
+        g = np.empty(self.n_params, np.float32)
+        _check(lib().ft_mlp_loss_grad(self.handle, X.ctypes.data, y.ctypes.data, len(y),
+                                      ctypes.byref(loss), g.ctypes.data))
+        return loss.value, g
+
+    def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(lib().ft_mlp_adam_step(self.handle, lr, beta1, beta2, eps))
+
+    def train(self, X, y, batch=1024, epochs=10, lr=1e-3, seed=0):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        hist = np.empty(max(epochs, 1), np.float32)
+        _check(lib().ft_mlp_train(self.handle, X.ctypes.data, y.ctypes.data, len(y), int(batch),
+                                  int(epochs), float(lr), int(seed), hist.ctypes.data))
+        return hist[:epochs]
+
+    def predict(self, X, bf16=True):
+        if _is_torch(X) and X.is_cuda:
+            import torch
+
+            p = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+            _check(lib().ft_mlp_predict(self.handle, X.data_ptr(), X.shape[0], p.data_ptr(),
+                                        int(bf16), 1, _stream(None, True)))
+            return p
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        p = np.empty(len(X), np.float32)
+        _check(lib().ft_mlp_predict(self.handle, X.ctypes.data, len(X), p.ctypes.data, int(bf16),
+                                    0, None))
+        return p
+
+    def close(self):
+        if self.handle:
+            lib().ft_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def abi_version() -> int:

@@ -1,0 +1,74 @@
+"""The surrogate network's CUDA kernels against the FP64 oracle: gradients (relative 1e-4),
+Adam updates, FP32 vs BF16 inference, determinism, and learning a separable problem."""
+import numpy as np
+import pytest
+
+import paper_2411_18370_b300 as ft
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+D, W = 9, 128
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = ft.create(0)
+    yield c
+    c.close()
+
+
+def _batch(B, seed):
+    g = np.random.default_rng(seed)
+    X = g.standard_normal((B, D)).astype(np.float32)
+    y = (X[:, 0] + 0.5 * X[:, 1] - 0.3 * X[:, 2] + 0.2 * g.standard_normal(B) > 0).astype(np.float32)
+    return X, y
+
+
+def test_gradient_matches_fp64_backprop(ctx):
+    net = ft.MLP(ctx, D, W, seed=3)
+    theta = net.get_params()
+    X, y = _batch(256, 1)
+    loss, g = net.loss_grad(X, y)
+    l_or, g_or = omlp.loss_and_grad(theta.astype(np.float64), X, y, D, W)
+    assert abs(loss - l_or) < 1e-5 * abs(l_or) + 1e-7
+    scale = np.abs(g_or).max()
+    err = np.abs(g.astype(np.float64) - g_or)
+    assert np.all(err <= 1e-4 * np.abs(g_or) + 1e-6 * scale), float((err / (np.abs(g_or) + 1e-6 * scale)).max())
+    net.close()
+
+
+def test_adam_step_matches_oracle(ctx):
+    net = ft.MLP(ctx, D, W, seed=4)
+    th0 = net.get_params().astype(np.float64)
+    X, y = _batch(128, 2)
+    m = np.zeros_like(th0)
+    v = np.zeros_like(th0)
+    th = th0.copy()
+    for t in (1, 2, 3):
+        _, g = net.loss_grad(X, y)
+        net.adam_step(1e-3)
+        th, m, v = omlp.adam_step(th, g.astype(np.float64), m, v, t, 1e-3)
+        got = net.get_params().astype(np.float64)
+        assert np.all(np.abs(got - th) <= 1e-6 + 1e-5 * np.abs(th))
+    net.close()
+
+
+def test_training_learns_and_is_deterministic(ctx):
+    X, y = _batch(8192, 5)
+    nets = []
+    for _ in range(2):
+        net = ft.MLP(ctx, D, W, seed=11)
+        hist = net.train(X, y, batch=512, epochs=8, lr=2e-3, seed=21)
+        nets.append(net)
+    assert hist[-1] < 0.5 * hist[0]
+    assert np.array_equal(nets[0].get_params(), nets[1].get_params())
+    Xt, yt = _batch(4096, 6)
+    p32 = nets[0].predict(Xt, bf16=False)
+    p16 = nets[0].predict(Xt, bf16=True)
+    assert np.mean((p32 > 0.5) == (yt > 0.5)) > 0.9
+    assert np.max(np.abs(p32 - p16)) < 0.05
+    p_or = omlp.predict(nets[0].get_params().astype(np.float64), Xt, D, W)
+    assert np.max(np.abs(p32 - p_or)) < 1e-5
+    for n in nets:
+        n.close()
