@@ -365,3 +365,33 @@ def config3(n_bands: int = 64, sky_scale: float = 1.0, n_slots: int = None, duty
                     sky=fibonacci_sky(max(n_sky, 1)), subband_bins=18)
         out.append((sfts, bank))
     return out
+
+
+def psd_level(f_hz: float) -> float:
+    """Smooth synthetic PSD shape used for the surrogate workload (arbitrary units):
+    a steep low-frequency wall, a flat bucket and a rising high-frequency tail."""
+    return 1.0 + (f_hz / 120.0) ** -4 + (f_hz / 600.0) ** 2
+
+
+def config4_bands(n_bands: int = 64, sky_scale: float = 1.0, n_slots: int = None, seed_stream=0):
+    """The surrogate workload's bands: the batching workload's bands, each with its own duty
+    cycle U[0.5, 0.9] (SFTs dropped independently) and PSD level psd_level(f_mid) times a
+    per-SFT U[0.8, 1.2] factor.  Returns dicts with the band spec, timeline, velocities,
+    detector tensors and PSD levels (no power: injection runs synthesise their own data)."""
+    if n_slots is None:
+        n_slots = int(round(YEAR_S / T_SFT))
+    g = rng(4, 200 + seed_stream)
+    specs = config3_bands(n_bands, sky_scale)
+    out = []
+    for b, sp in enumerate(specs):
+        duty = float(g.uniform(0.5, 0.9))
+        starts = timeline(2, n_slots, T_SFT, duty, rng(4, 1000 + b))
+        t_mid = np.concatenate([st + 0.5 * T_SFT for st in starts])
+        v = np.concatenate([detector_velocity(st + 0.5 * T_SFT, X) for X, st in enumerate(starts)])
+        D = np.concatenate([detector_tensor(st + 0.5 * T_SFT, X) for X, st in enumerate(starts)])
+        f_mid = (sp["k_band"] + 0.5 * sp["n_bins"]) / T_SFT
+        s_ref = psd_level(f_mid)
+        s_n = s_ref * rng(4, 2000 + b).uniform(0.8, 1.2, len(t_mid))
+        out.append(dict(spec=sp, duty=duty, t_mid=t_mid, v=v, D=D, s_n=s_n,
+                        s_ref=float(np.mean(s_n)), n_sft=[len(st) for st in starts]))
+    return out
