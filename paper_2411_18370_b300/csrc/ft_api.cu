@@ -19,9 +19,12 @@ struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev)
     {
-        cudaGetDevice(&prev);
+        if (cudaGetDevice(&prev) != cudaSuccess)
+            prev = -1;
         if (prev != dev)
             cudaSetDevice(dev);
+        // errors of earlier, unrelated runtime calls on this thread are not ours to report
+        (void)cudaGetLastError();
     }
     ~DeviceGuard()
     {
@@ -42,6 +45,8 @@ int read_status(ft_ctx *ctx, cudaStream_t st)
             FT_FAIL(FT_ERR_TIMEOUT, "a device-side bounded wait ran out (kernel abandoned its tile)");
         if (h & FT_STATUS_NONFINITE)
             FT_FAIL(FT_ERR_ARG, "non-finite value in the SFT power");
+        if (h & FT_STATUS_WINDOW)
+            FT_FAIL(FT_ERR_RANGE, "a track window exceeded its shared-memory bound");
         FT_FAIL(FT_ERR_CUDA, "unknown device status");
     }
     return FT_OK;
@@ -271,6 +276,7 @@ int ft_load_sfts(ft_ctx *ctx, const ft_band_desc *d, const void *power, int powe
     cudaStream_t st = as_stream(stream);
     ft_band *b = new ft_band;
     b->ctx = ctx;
+    b->device = ctx->device;
     b->n_det = d->n_det;
     b->n_sft.assign(d->n_sft, d->n_sft + d->n_det);
     b->N = N;
@@ -290,6 +296,7 @@ int ft_load_sfts(ft_ctx *ctx, const ft_band_desc *d, const void *power, int powe
         b->h_vabs[a] = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
         sw += wv[a];
         sw2 += static_cast<double>(wv[a]) * wv[a];
+        b->tau_absmax = std::max(b->tau_absmax, std::fabs(b->h_tau[a]));
     }
     b->mu = 2.0 * sw;
     b->sigma = std::sqrt(4.0 * sw2);
@@ -344,7 +351,7 @@ void ft_band_destroy(ft_band *b)
 {
     if (!b)
         return;
-    DeviceGuard g(b->ctx->device);
+    DeviceGuard g(b->device);
     cudaFree(b->d_power);
     cudaFree(b->d_tau);
     cudaFree(b->d_v);
@@ -389,6 +396,7 @@ int ft_make_bank(ft_ctx *ctx, const ft_band *band, const ft_bank_desc *d, void *
     cudaStream_t st = as_stream(stream);
     ft_bank *b = new ft_bank;
     b->ctx = ctx;
+    b->device = ctx->device;
     b->band = band;
     b->k0 = d->k0;
     b->n_f0 = d->n_f0;
@@ -397,6 +405,8 @@ int ft_make_bank(ft_ctx *ctx, const ft_band *band, const ft_bank_desc *d, void *
     b->sub = d->subband_bins;
     b->n_sub = (d->n_f0 + d->subband_bins - 1) / d->subband_bins;
     b->window_safe = kmin >= band->k_lo && kmax <= band->k_lo + band->W - 1;
+    b->f1_lo = *std::min_element(d->f1, d->f1 + d->n_f1);
+    b->f1_hi = *std::max_element(d->f1, d->f1 + d->n_f1);
     int rc;
     if ((rc = dev_upload(&b->d_f1, d->f1, d->n_f1, st)) != FT_OK ||
         (rc = dev_upload(&b->d_sky, d->sky, 3 * static_cast<size_t>(d->n_sky), st)) != FT_OK) {
@@ -420,7 +430,7 @@ void ft_bank_destroy(ft_bank *b)
 {
     if (!b)
         return;
-    DeviceGuard g(b->ctx->device);
+    DeviceGuard g(b->device);
     cudaFree(b->d_f1);
     cudaFree(b->d_sky);
     cudaFree(b->d_G);
@@ -476,6 +486,7 @@ static EvalParams base_params(const ft_band *band, const ft_bank *bank)
     p.w = band->d_w;
     p.sky = bank->d_sky;
     p.G = bank->d_G;
+    p.f1 = bank->d_f1;
     p.K0 = bank->k0;
     p.k_lo = band->k_lo;
     p.n_f0 = bank->n_f0;

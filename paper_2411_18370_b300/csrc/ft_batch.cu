@@ -20,6 +20,7 @@
 
 struct ft_batch {
     ft_ctx *ctx = nullptr;
+    int device = 0;
     int n_bands = 0, k = 0, dtype = FT_F32;
     bool weighted = false;
     int F = 1, J = 32, nst = 2;
@@ -45,9 +46,11 @@ struct DevGuard {
     int prev = -1;
     explicit DevGuard(int d)
     {
-        cudaGetDevice(&prev);
+        if (cudaGetDevice(&prev) != cudaSuccess)
+            prev = -1;
         if (prev != d)
             cudaSetDevice(d);
+        (void)cudaGetLastError();
     }
     ~DevGuard()
     {
@@ -95,10 +98,11 @@ int check_inputs(ft_ctx *ctx, int n, const ft_band *const *bands, const ft_bank 
     return FT_OK;
 }
 
-// Rows per stage for a band: the largest multiple of 4 (<= 32) whose nst stages fit 80 KB.
-int rows_for(const ft_band *band, int nst)
+// Rows per stage: the largest multiple of 4 (<= 32) whose nst stages of Ws-bin windows fit
+// 80 KB.
+int rows_for(int Ws, int nst)
 {
-    const int rb = ft_batch_row_bytes(band);
+    const int rb = Ws * 4;
     int S = (80 * 1024) / (nst * rb);
     S = std::min(S, 32);
     S &= ~3;
@@ -112,6 +116,7 @@ int build(ft_ctx *ctx, int n, const ft_band *const *bands, const ft_bank *const 
 {
     ft_batch *b = new ft_batch;
     b->ctx = ctx;
+    b->device = ctx->device;
     b->n_bands = n;
     b->k = k;
     b->dtype = bands[0]->dtype;
@@ -144,6 +149,7 @@ int build(ft_ctx *ctx, int n, const ft_band *const *bands, const ft_bank *const 
         p.w = bd->d_w;
         p.sky = bk->d_sky;
         p.G = bk->d_G;
+        p.f1 = bk->d_f1;
         p.K0 = bk->k0;
         p.k_lo = bd->k_lo;
         p.n_f0 = bk->n_f0;
@@ -154,11 +160,15 @@ int build(ft_ctx *ctx, int n, const ft_band *const *bands, const ft_bank *const 
         p.status = ctx->d_status;
         p.k = k;
         p.sub = bk->sub;
-        const int S = rows_for(bd, nst);
+        const int Ws = ft_window_bins(bd, bk, J);
+        const int S = rows_for(Ws, nst);
         b->S.push_back(S);
         p.S = S;
         p.nst = nst;
         p.row_bytes = ft_batch_row_bytes(bd);
+        p.Wp = bd->Wp;
+        p.Ws = Ws;
+        p.srow_bytes = Ws * 4;
         p.row_elems = bd->dtype == FT_F32 ? bd->Wp : 2 * bd->Wp;
         p.n_stages = static_cast<int>((bd->N + S - 1) / S);
         p.n_f0t = (bk->n_f0 + J - 1) / J;
@@ -176,7 +186,7 @@ int build(ft_ctx *ctx, int n, const ft_band *const *bands, const ft_bank *const 
         sub_prefix[i + 1] = sub_prefix[i] + bk->n_sub;
         b->n_sub_max = std::max(b->n_sub_max, bk->n_sub);
         b->lsub_max = std::max(b->lsub_max, p.lsub_max);
-        tile_smem = std::max(tile_smem, ft_batch_tile_smem(bd, S, F, J, nst));
+        tile_smem = std::max(tile_smem, ft_batch_tile_smem(Ws, S, F, J, nst));
     }
     b->n_sub_total = sub_prefix[n];
     b->sub_prefix_h.assign(sub_prefix.begin(), sub_prefix.end());
@@ -416,7 +426,7 @@ void ft_batch_destroy(ft_batch *b)
 {
     if (!b)
         return;
-    DevGuard g(b->ctx->device);
+    DevGuard g(b->device);
     free_batch(b);
 }
 

@@ -57,6 +57,13 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, u
         : "memory");
 }
 
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
 {
     asm volatile(
@@ -575,9 +582,11 @@ constexpr int kMaxStages = 4;
 constexpr int kFoldRows = 128;  // FP32 partials cover at most this many SFT rows
 
 struct RowRec {
+    long long C;
     int E;
     float w;
-    long long C;
+    int start;  // first bin of the row's window in shared memory (multiple of 16)
+    int pad;
 };
 
 struct FastLayout {
@@ -643,8 +652,8 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int S = p.S;
     const int nst = p.nst;
-    const int row_words = p.row_bytes >> 2;
-    const FastLayout L = fast_layout(S, F, p.row_bytes, J, p.cand != nullptr, nst);
+    const int row_words = p.srow_bytes >> 2;  // shared-memory row: Ws bins
+    const FastLayout L = fast_layout(S, F, p.srow_bytes, J, p.cand != nullptr, nst);
     unsigned long long *full = reinterpret_cast<unsigned long long *>(smem + L.full);
     unsigned long long *empty = reinterpret_cast<unsigned long long *>(smem + L.empty);
     RowRec *rec = reinterpret_cast<RowRec *>(smem + L.rec);
@@ -676,6 +685,14 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
 
     if (warp == F) {
         // ------------------------------------------------------------ producer warp
+        // members of this CTA's f1 group with the smallest and largest f1
+        int f_min = c.f1g * F, f_max = c.f1g * F;
+        for (int f = c.f1g * F + 1; f < min(c.f1g * F + F, p.n_f1); ++f) {
+            if (p.f1[f] < p.f1[f_min])
+                f_min = f;
+            if (p.f1[f] > p.f1[f_max])
+                f_max = f;
+        }
         int st = 0, slot = 0, use = 0;
         for (; st < n_stages; ++st) {
             if (use > 0 && !mbar_wait_bounded(&empty[slot], (use - 1) & 1)) {
@@ -683,23 +700,76 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
                 break;
             }
             const int nr = rows_in_stage(p, st);
+            long long alpha = 0;
+            int start = 0, len = 0;
             if (lane < nr) {
-                const long long alpha = static_cast<long long>(st) * S + lane;
+                alpha = static_cast<long long>(st) * S + lane;
                 RowRec r;
                 track_ec(p.v + 3 * alpha, c.n0, c.n1, c.n2, p.K0, p.k_lo, r.E, r.C);
                 r.w = p.w[alpha];
+                int s0 = 0;
+                len = p.Wp;
+                if (p.Ws < p.Wp) {
+                    // the bins this tile reads in this row: the track origin is linear in f1, so
+                    // the group's smallest and largest f1 bound it; plus the tile width and one
+                    // carry step on each side
+                    const long long G1 = p.G[static_cast<long long>(f_min) * p.N + alpha];
+                    const long long G2 = p.G[static_cast<long long>(f_max) * p.N + alpha];
+                    const long long gmin = min(G1, G2), gmax = max(G1, G2);
+                    const long long a0 = r.C + (1ll << 31) + static_cast<long long>(c.j0) * r.E;
+                    const int b_lo = c.j0 + static_cast<int>((a0 + gmin + cross_q32(gmin, r.E)) >> 32);
+                    const int b_hi = c.j0 + static_cast<int>((a0 + gmax + cross_q32(gmax, r.E)) >> 32);
+                    s0 = max(min(b_lo, b_hi) - 2, 0) & ~15;
+                    int e0 = min((max(b_lo, b_hi) + J + 2 + 15) & ~15, p.Wp);
+                    len = max(e0 - s0, 16);
+                    if (s0 + len > p.Wp)
+                        s0 = p.Wp - len;
+                    if (len > p.Ws) {
+                        atomicOr(p.status, FT_STATUS_WINDOW);
+                        len = p.Ws;
+                    }
+                }
+                start = s0;
+                r.start = s0;
+                r.pad = 0;
                 rec[slot * S + lane] = r;
             }
-            if (lane == 0) {
-                const unsigned bytes = static_cast<unsigned>(nr) * p.row_bytes;
-                mbar_arrive_expect_tx(&full[slot], bytes);
-                bulk_copy_g2s(buf + slot * L.stage_bytes,
-                              static_cast<const unsigned char *>(p.power) +
-                                  static_cast<size_t>(st) * L.stage_bytes,
-                              bytes, &full[slot]);
+            if (p.Ws == p.Wp) {
+                // whole rows: the stage's rows are contiguous in global and shared memory
+                if (lane == 0) {
+                    const unsigned bytes = static_cast<unsigned>(nr) * static_cast<unsigned>(p.row_bytes);
+                    mbar_expect_tx(&full[slot], bytes);
+                    bulk_copy_g2s(buf + slot * L.stage_bytes,
+                                  static_cast<const unsigned char *>(p.power) +
+                                      static_cast<size_t>(st) * S * p.row_bytes,
+                                  bytes, &full[slot]);
+                }
             } else {
-                mbar_arrive(&full[slot]);
+                unsigned tot = static_cast<unsigned>(len) * 4u;  // bytes of this row's copies
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1)
+                    tot += __shfl_xor_sync(0xffffffffu, tot, off);
+                if (lane == 0)
+                    mbar_expect_tx(&full[slot], tot);
+                __syncwarp();
+                if (lane < nr) {
+                    unsigned char *dst = buf + slot * L.stage_bytes + static_cast<size_t>(lane) * p.srow_bytes;
+                    const unsigned char *src =
+                        static_cast<const unsigned char *>(p.power) + static_cast<size_t>(alpha) * p.row_bytes;
+                    if (!PAIR) {
+                        bulk_copy_g2s(dst, src + static_cast<size_t>(start) * 4, static_cast<unsigned>(len) * 4,
+                                      &full[slot]);
+                    } else {
+                        // even copy then odd copy: words [start/2, (start+len)/2) of each
+                        bulk_copy_g2s(dst, src + static_cast<size_t>(start >> 1) * 4,
+                                      static_cast<unsigned>(len) * 2, &full[slot]);
+                        bulk_copy_g2s(dst + (p.srow_bytes >> 1),
+                                      src + (p.row_bytes >> 1) + static_cast<size_t>(start >> 1) * 4,
+                                      static_cast<unsigned>(len) * 2, &full[slot]);
+                    }
+                }
             }
+            mbar_arrive(&full[slot]);
             if (++slot == nst) {
                 slot = 0;
                 ++use;
@@ -746,7 +816,7 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
                 const RowRec r = rr[lane];
                 const long long X0p = r.C + g_cur + cross_q32(g_cur, r.E) + (1ll << 31);
                 const long long acc0 = X0p + static_cast<long long>(c.j0) * r.E;
-                const int base = c.j0 + static_cast<int>(acc0 >> 32);
+                const int base = c.j0 + static_cast<int>(acc0 >> 32) - r.start;  // within the window
                 const unsigned L0 = static_cast<unsigned>(acc0);
                 const unsigned span = static_cast<unsigned>(J - 1) * static_cast<unsigned>(abs(r.E));
                 ev = r.E > 0 ? (span != 0u && L0 >= 0u - span) : (L0 < span);
@@ -1386,10 +1456,21 @@ int row_bytes_of(const ft_band *band)
 
 // ------------------------------------------------------------------ host launchers
 
+int ft_window_bins(const ft_band *band, const ft_bank *bank, int J)
+{
+    const double spread = std::ceil((bank->f1_hi - bank->f1_lo) * band->tau_absmax * 1.001) + 2.0;
+    long long ws = (static_cast<long long>(J) + static_cast<long long>(spread) + 40 + 31) / 32 * 32;
+    // a window that saves under a quarter of the row is not worth one copy per row: the
+    // stage is then one contiguous copy of whole rows
+    if (4 * ws > 3 * static_cast<long long>(band->Wp))
+        return band->Wp;
+    return static_cast<int>(ws);
+}
+
 size_t ft_eval_smem_bytes(const ft_band *band, const EvalShape &sh, int k)
 {
     if (sh.fast)
-        return fast_layout(sh.S, sh.F, row_bytes_of(band), sh.J, k > 0, sh.nbuf).total;
+        return fast_layout(sh.S, sh.F, sh.Ws * 4, sh.J, k > 0, sh.nbuf).total;
     return smem_layout(sh.S, sh.F, row_bytes_of(band), sh.J, false, k > 0).total;
 }
 
@@ -1416,11 +1497,16 @@ EvalShape ft_default_shape(const ft_ctx *ctx, const ft_band *band, const ft_bank
         }
     }
     sh.J = best;
+    if (ctx->tune.tile_f0 > 0)
+        sh.J = ctx->tune.tile_f0;
     const size_t rb = row_bytes_of(band);
+    sh.Ws = 0;
     if (sh.fast) {
-        // two slots of up to 32 rows (a multiple of 4) in about 80 KB: two CTAs per SM
+        // two slots of up to 32 rows (a multiple of 4) of windowed rows in about 80 KB: two
+        // CTAs per SM
+        sh.Ws = ft_window_bins(band, bank, sh.J);
         sh.nbuf = 2;
-        int S = static_cast<int>((80 * 1024) / (sh.nbuf * rb));
+        int S = static_cast<int>((80 * 1024) / (sh.nbuf * static_cast<size_t>(sh.Ws) * 4));
         S = S > 32 ? 32 : S;
         S = S < 4 ? 4 : S & ~3;
         sh.S = S;
@@ -1433,8 +1519,6 @@ EvalShape ft_default_shape(const ft_ctx *ctx, const ft_band *band, const ft_bank
             S &= ~7;
         sh.S = S;
     }
-    if (ctx->tune.tile_f0 > 0)
-        sh.J = ctx->tune.tile_f0;
     if (ctx->tune.rows_per_stage > 0)
         sh.S = ctx->tune.rows_per_stage;
     if (ctx->tune.stages > 0 && sh.fast)
@@ -1450,6 +1534,9 @@ int ft_launch_eval(const ft_band *band, const ft_bank *bank, const EvalShape &sh
     p.S = sh.S;
     p.n_stages = static_cast<int>((band->N + sh.S - 1) / sh.S);
     p.row_bytes = row_bytes_of(band);
+    p.Wp = band->Wp;
+    p.Ws = sh.Ws;
+    p.srow_bytes = sh.Ws * 4;
     p.nst = sh.nbuf;
     p.row_elems = band->dtype == FT_F32 ? band->Wp : 2 * band->Wp;
     const long long n_cta = bank->n_sky * p.n_f1g * static_cast<long long>(p.n_f0t);
@@ -1575,9 +1662,9 @@ int batched_r(int R, const BatchParams &bp, int threads, size_t smem, int *grid,
 
 }  // namespace
 
-size_t ft_batch_tile_smem(const ft_band *band, int S, int F, int J, int nst)
+size_t ft_batch_tile_smem(int Ws, int S, int F, int J, int nst)
 {
-    return fast_layout(S, F, row_bytes_of(band), J, true, nst).total;
+    return fast_layout(S, F, Ws * 4, J, true, nst).total;
 }
 
 int ft_batch_row_bytes(const ft_band *band)

@@ -343,6 +343,7 @@ extern "C" int ft_run_injections(ft_ctx *ctx, const ft_band *band, const ft_bank
     FT_CUDA(cudaGetDevice(&prev));
     if (prev != ctx->device)
         FT_CUDA(cudaSetDevice(ctx->device));
+    (void)cudaGetLastError();  // drop errors left by earlier, unrelated runtime calls
     struct Restore {
         int d;
         ~Restore()

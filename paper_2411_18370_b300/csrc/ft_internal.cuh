@@ -40,6 +40,7 @@ void ft_set_error(const std::string &msg);
 // device status word bits
 #define FT_STATUS_TIMEOUT 1u
 #define FT_STATUS_NONFINITE 2u
+#define FT_STATUS_WINDOW 4u
 
 // ------------------------------------------------------------------ handles
 
@@ -57,6 +58,7 @@ struct ft_ctx {
 
 struct ft_band {
     ft_ctx *ctx = nullptr;
+    int device = 0;  // kept so that destruction never needs the context
     int n_det = 0;
     std::vector<int> n_sft;
     int64_t N = 0;        // total rows
@@ -73,10 +75,12 @@ struct ft_band {
     double mu = 0, sigma = 0;
     bool weighted = false;
     std::vector<double> h_tau, h_vabs;
+    double tau_absmax = 0;
 };
 
 struct ft_bank {
     ft_ctx *ctx = nullptr;
+    int device = 0;
     const ft_band *band = nullptr;
     int64_t k0 = 0;
     int n_f0 = 0, n_f1 = 0;
@@ -87,6 +91,7 @@ struct ft_bank {
     double *d_sky = nullptr;   // [n_sky][3]
     long long *d_G = nullptr;  // [n_f1][N] Q32 f1*tau
     bool window_safe = false;
+    double f1_lo = 0, f1_hi = 0;
 };
 
 int ft_ctx_scratch(ft_ctx *ctx, size_t bytes, void **p);
@@ -103,6 +108,9 @@ struct FtCand {
 struct EvalParams {
     const void *power;
     int row_bytes;  // bytes per stored row (FP32 row, or the two 16-bit copies)
+    int Wp;         // bins per stored row copy
+    int Ws;         // bins per shared-memory row window (fast kernels)
+    int srow_bytes; // bytes per shared-memory row (Ws bins, FP32 or the two 16-bit copies)
     int row_elems;  // storage elements per stored row
     int W;
     long long N;
@@ -111,6 +119,7 @@ struct EvalParams {
     const float *w;
     const double *sky;
     const long long *G;  // [n_f1][N]
+    const double *f1;    // [n_f1]
     long long K0, k_lo;
     int n_f0, n_f1;
     long long n_sky;
@@ -147,7 +156,12 @@ struct EvalShape {
     int S;       // SFT rows per stage
     int nbuf;    // stage buffers
     bool fast;   // shifted-row kernel (bank tracks provably inside the window)
+    int Ws;      // fast kernel: bins per shared-memory row window
 };
+
+// Bins per shared-memory row window of the fast kernels for tile width J: the tile, the
+// spread of the track origins over the bank's f1 range, carry and alignment slack.
+int ft_window_bins(const ft_band *band, const ft_bank *bank, int J);
 
 size_t ft_eval_smem_bytes(const ft_band *band, const EvalShape &sh, int k);
 EvalShape ft_default_shape(const ft_ctx *ctx, const ft_band *band, const ft_bank *bank);
@@ -163,7 +177,7 @@ int ft_launch_gtable(const double *f1, int n_f1, const double *tau, long long N,
 int ft_launch_track_bins(const ft_band *band, const ft_bank *bank, const long long *tmpl,
                          long long n, int *bins, cudaStream_t st);
 
-size_t ft_batch_tile_smem(const ft_band *band, int S, int F, int J, int nst);
+size_t ft_batch_tile_smem(int Ws, int S, int F, int J, int nst);
 int ft_batch_row_bytes(const ft_band *band);
 int ft_launch_batched(int dtype, bool weighted, int J, int F, const BatchParams &bp, size_t smem,
                       int *grid, bool launch, cudaStream_t st);

@@ -322,6 +322,7 @@ int ft_mlp_create(ft_ctx *ctx, int d_in, int width, uint64_t seed, ft_mlp **out)
         FT_FAIL(FT_ERR_RANGE, "mlp_create: d_in and width must be in [1, 256]");
     ft_mlp *m = new ft_mlp;
     m->ctx = ctx;
+    (void)cudaGetLastError();
     m->d_in = d_in;
     m->width = width;
     const Layout L = layout(d_in, width);

@@ -56,6 +56,7 @@ extern "C" int ft_topk_per_band_noalloc(ft_ctx *ctx, const ft_band *band, const 
     FT_CUDA(cudaGetDevice(&prev));
     if (prev != ctx->device)
         FT_CUDA(cudaSetDevice(ctx->device));
+    (void)cudaGetLastError();  // drop errors left by earlier, unrelated runtime calls
     struct Restore {
         int dev;
         ~Restore()
@@ -97,6 +98,7 @@ extern "C" int ft_topk_per_band_noalloc(ft_ctx *ctx, const ft_band *band, const 
     p.w = band->d_w;
     p.sky = bank->d_sky;
     p.G = bank->d_G;
+    p.f1 = bank->d_f1;
     p.K0 = bank->k0;
     p.k_lo = band->k_lo;
     p.n_f0 = bank->n_f0;

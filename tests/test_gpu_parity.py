@@ -299,6 +299,29 @@ def test_edge_shapes(ctx, shape):
         assert_topk(idx, val, s_or, bank, k, s_gpu=s)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+def test_wide_band_windowed_rows_exact(ctx, dtype):
+    """A band ~4x wider than one f0 tile plus the f1 spread: each CTA copies only the
+    window of every row that its tracks can reach (two f1 groups, so two windows per
+    row), and integer powers keep the comparison with the oracle bit-exact."""
+    sfts, bank = _small(n_sft=150, W=1160, n_f0=1000, n_f1=25, n_sky=3, sub=40, wings=40)
+    g = np.random.default_rng(77)
+    P = g.integers(0, 256, sfts.power.shape).astype(np.float64)
+    sx = _with_power(sfts, P)
+    # precondition: the window (tile + spread + margin) is under 3/4 of the padded row
+    spread = (bank.f1.max() - bank.f1.min()) * (sfts.t_mid.max() + 900.0) * sfts.t_sft
+    assert 256 + spread + 72 < 0.75 * 1152
+    band = H.band_from(ctx, sx, dtype=dtype)
+    bk = H.bank_from(ctx, band, bank)
+    assert bk.window_safe
+    s, _, o = H.eval_host(ctx, band, bk, bank.n_templates)
+    s_or, o_or = oracle.statistic(sx, bank)
+    assert np.array_equal(o, o_or) and o_or.sum() == 0
+    assert np.array_equal(s.astype(np.float64), s_or)
+    idx, val, _ = H.topk_host(ctx, band, bk, bank.n_subbands, 8)
+    assert_topk(idx, val, s_or, bank, 8, s_gpu=s)
+
+
 def test_weighted_statistic(ctx):
     sfts, bank = _small(n_sft=80, n_f0=40, n_f1=4, n_sky=6)
     w = np.random.default_rng(9).uniform(0.2, 3.0, sfts.n_total)
