@@ -285,121 +285,25 @@ def run_batch(args):
 
 def run_surrogate(args):
     """The learned-surrogate workload: injection campaigns across the batching workload's
-    bands (per-band duty and PSD), a noise-only threshold per band, a 4-layer MLP trained on
-    the pooled outcomes by the library's kernels, and h0 at 90% p_det on held-out bands from
-    (a) the surrogate, (b) per-band sigmoid fits with the same per-band budget, (c) a
-    high-statistics campaign (the reference)."""
+    bands (per-band duty and PSD), a noise-only threshold per band, an ensemble of 4-layer
+    MLPs trained on the pooled outcomes by the library's kernels, and h0 at 90% p_det on
+    held-out bands from (a) the surrogate, (b) per-band sigmoid fits with the same per-band
+    budget, (c) a high-statistics campaign (the reference)."""
     import torch
 
-    import ftsynth
     import paper_2411_18370_b300 as ft
-    from paper_2411_18370_b300 import campaign as C
-    from paper_2411_18370_b300 import surrogate as SG
+    from paper_2411_18370_b300 import study
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     ctx = ft.create(local)
-    T = ftsynth.T_SFT
-    bands = ftsynth.config4_bands(args.n_bands, args.sky_scale)
-    held = list(range(0, args.n_bands, max(1, args.n_bands // args.n_held)))[:args.n_held]
-    train_bands = [b for b in range(args.n_bands) if b not in held]
-    kw = dict(k_sky=args.k_sky, half_f0=2, half_window=160)
-    objs = []
-    t_setup = time.perf_counter()
-    for bd in bands:
-        sp = bd["spec"]
-        N = len(bd["t_mid"])
-        band = ft.load_sfts(ctx, np.zeros((N, 1), np.float32), bd["t_mid"], bd["v"], bd["n_sft"],
-                            sp["k_band"], T, 0.0, dtype="f32", s_n=bd["s_n"])
-        bank = ft.make_bank(ctx, band, sp["k_band"], sp["n_bins"], ftsynth.f1_grid(10, -1e-9, 0.0),
-                            ftsynth.fibonacci_sky(sp["n_sky"]), 18)
-        objs.append((band, bank))
-    t_setup = time.perf_counter() - t_setup
-    run_id = 0
-    timing = {}
-
-    def frange(b):
-        sp = bands[b]["spec"]
-        return sp["k_band"] / T, (sp["k_band"] + sp["n_bins"] - 1) / T
-
-    # 1. thresholds: 1% false alarm from noise-only local searches, per band
     t0 = time.perf_counter()
-    taus = []
-    for b, (band, bank) in enumerate(objs):
-        lo, hi = frange(b)
-        tau, _ = C.noise_threshold(ctx, band, bank, bands[b]["D"], args.n_noise, 1 + b, run_id,
-                                   lo, hi, **kw)
-        run_id += args.n_noise
-        taus.append(tau)
-    timing["thresholds_s"] = time.perf_counter() - t0
-
-    # 2. pooled training campaign over the training bands
-    t0 = time.perf_counter()
-    per_band = max(1, args.n_train // len(train_bands))
-    feats, labels = [], []
-    for b in train_bands:
-        band, bank = objs[b]
-        lo, hi = frange(b)
-        lc, det, _, inj = C.run_campaign(ctx, band, bank, bands[b]["D"], per_band, taus[b],
-                                         5000 + b, run_id, lo, hi, bands[b]["s_ref"], T, **kw)
-        run_id += per_band
-        f0f = (inj["f0"] - lo) / (hi - lo)
-        feats.append(SG.features(lc, np.full(per_band, math.log10(bands[b]["s_ref"])),
-                                 np.full(per_band, bands[b]["duty"]), inj["n"], f0f, inj["f1"]))
-        labels.append(det)
-    F = np.concatenate(feats)
-    y = np.concatenate(labels)
-    timing["training_campaign_s"] = time.perf_counter() - t0
-
-    # 3. surrogate training on the GPU
-    t0 = time.perf_counter()
-    sur = SG.Surrogate(ctx, width=128, seed=7)
-    hist, vhist, best_ep = sur.fit(F, y, epochs=args.epochs, batch=1024, lr=2e-3, seed=3)
-    timing["surrogate_training_s"] = time.perf_counter() - t0
-
-    # 4. held-out bands: reference (high statistics), equal-budget per-band fit, surrogate
-    rows = []
-    g = np.random.default_rng(99)
-    for b in held:
-        band, bank = objs[b]
-        lo, hi = frange(b)
-        t0 = time.perf_counter()
-        lc_r, det_r, _, _ = C.run_campaign(ctx, band, bank, bands[b]["D"], args.n_ref, taus[b],
-                                           7000 + b, run_id, lo, hi, bands[b]["s_ref"], T,
-                                           c_range=(0.2, 5.0), **kw)
-        run_id += args.n_ref
-        t_ref = time.perf_counter() - t0
-        ref = C.fit_sigmoid(lc_r, det_r)
-        lc_b, det_b, _, _ = C.run_campaign(ctx, band, bank, bands[b]["D"], per_band, taus[b],
-                                           8000 + b, run_id, lo, hi, bands[b]["s_ref"], T, **kw)
-        run_id += per_band
-        fit_b = C.fit_sigmoid(lc_b, det_b)
-        inj_pop, _ = C.draw_population(2000, lo, hi, g)
-        pop = dict(n=inj_pop["n"], f0_frac=(inj_pop["f0"] - lo) / (hi - lo), f1=inj_pop["f1"])
-        t0 = time.perf_counter()
-        x_sur = sur.log10_c_at(0.9, math.log10(bands[b]["s_ref"]), bands[b]["duty"], pop)
-        t_sur = time.perf_counter() - t0
-        x_ref, x_b = ref.x_at(0.9), fit_b.x_at(0.9)
-        rows.append({"band": b, "f_start_hz": bands[b]["spec"]["k_band"] / T,
-                     "duty": bands[b]["duty"], "log10_S": math.log10(bands[b]["s_ref"]),
-                     "tau": taus[b], "ref_c90": 10 ** x_ref,
-                     "ref_c90_rel_sigma": math.log(10) * ref.x_at_sigma(0.9),
-                     "surrogate_c90": 10 ** x_sur, "per_band_fit_c90": 10 ** x_b,
-                     "surrogate_err": 10 ** (x_sur - x_ref) - 1,
-                     "per_band_fit_err": 10 ** (x_b - x_ref) - 1,
-                     "ref_campaign_s": t_ref, "surrogate_query_s": t_sur})
-    line = {
-        "workload": "learned p_det surrogate across the batching workload's bands",
-        "bands": args.n_bands, "held_out": held, "n_noise_per_band": args.n_noise,
-        "n_train": int(len(y)), "n_ref_per_heldout": args.n_ref, "per_band_budget": per_band,
-        "train_detected_frac": float(y.mean()), "best_epoch": int(best_ep),
-        "train_loss_at_best": float(hist[best_ep]), "val_loss_at_best": float(vhist[best_ep]),
-        "timing": timing, "setup_s": t_setup, "held_out_results": rows,
-        "max_abs_surrogate_err": max(abs(r["surrogate_err"]) for r in rows),
-        "rms_surrogate_err": math.sqrt(np.mean([r["surrogate_err"] ** 2 for r in rows])),
-        "rms_per_band_fit_err": math.sqrt(np.mean([r["per_band_fit_err"] ** 2 for r in rows])),
-        "h0_unit": "sqrt(S_ref / T_SFT)",
-    }
+    res = study.run_study(ctx, n_bands=args.n_bands, sky_scale=args.sky_scale, n_held=args.n_held,
+                          n_noise=args.n_noise, n_train=args.n_train, n_ref=args.n_ref,
+                          members=args.members, epochs=args.epochs, k_sky=args.k_sky)
+    line = {"workload": "learned p_det surrogate across the batching workload's bands",
+            "wall_s": time.perf_counter() - t0}
+    line.update(res)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -423,7 +327,8 @@ def main():
     ap.add_argument("--n-held", type=int, default=4)
     ap.add_argument("--n-noise", type=int, default=2000)
     ap.add_argument("--n-train", type=int, default=20000)
-    ap.add_argument("--n-ref", type=int, default=4000)
+    ap.add_argument("--members", type=int, default=5)
+    ap.add_argument("--n-ref", type=int, default=8000)
     ap.add_argument("--k-sky", type=int, default=64)
     ap.add_argument("--epochs", type=int, default=200)
     args = ap.parse_args()

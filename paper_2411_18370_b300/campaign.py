@@ -92,6 +92,26 @@ class Sigmoid:
         return float(math.sqrt(grad @ self.cov @ grad))
 
 
+def local_x_at(x, det, p, x0, half=0.05, iters=5):
+    """Amplitude x at which the detection fraction is p, from sigmoid fits restricted to the
+    samples with |x - x_p| < half, re-centred on each fit's estimate (starting from x0).
+
+    Far above the transition the detection curve rises more slowly than a logistic (the
+    least favourable orientations keep p_det below 1), so one sigmoid over a wide range
+    places the 90% point too low; within a narrow window the curve is a sigmoid.  Returns
+    (x_p, its standard error, samples used)."""
+    x = np.asarray(x, np.float64)
+    det = np.asarray(det, np.float64)
+    xp, f, m = x0, None, None
+    for _ in range(iters):
+        m = np.abs(x - xp) < half
+        if m.sum() < 20:
+            raise ValueError("local_x_at: fewer than 20 samples in the window")
+        f = fit_sigmoid(x[m], det[m])
+        xp = f.x_at(p)
+    return xp, f.x_at_sigma(p), int(m.sum())
+
+
 def fit_sigmoid(x, det, iters=100):
     """Maximum-likelihood logistic fit of detections against x (Newton's method on the
     binomial log-likelihood); the covariance is the inverse observed information."""

@@ -1,12 +1,23 @@
 """Learned p_det surrogate: features, training on campaign outcomes, h0 at a target p_det.
 
 The network (ft_mlp, trained and evaluated by the library's CUDA kernels) maps
-    [log10 c, log10 S_ref, duty cycle, n_x, n_y, n_z, f0 position in the band, f1 / 1e-9]
+    [log10 c, log10 S_ref, duty cycle, n_x, n_y, n_z, f0 position in the band, f1 / 1e-9,
+     A+^2, Ax^2, cos 4psi, sin 4psi, tau]
 to the probability that the search detects the signal (Sec. V's p_det), where
-c = h0 / sqrt(S_ref / T_SFT).  The amplitude at which a band reaches p_det = p is the root
-in log10 c of the network's p_det averaged over the population's other parameters
-(sky, f0, f1, and implicitly the orientation the network marginalises), found by
-bisection with BF16 inference.
+c = h0 / sqrt(S_ref / T_SFT), A+ = (1 + cos^2 iota) / 2 and Ax = cos iota.  The signal power
+per SFT is (F+ A+)^2 + (Fx Ax)^2 (Sec. II), and psi enters F+ and Fx through 2 psi, so the
+squared amplitudes and the 4 psi harmonics are the orientation terms it depends on; given
+them, detection is close to a step in c and the network learns it from few injections.
+tau is the band's threshold (Sec. V.B's detection rule): it is estimated per band from
+noise-only searches, and its statistical scatter between bands moves the band's 90% point,
+so the network sees it rather than averaging over it.
+The amplitude at which a band reaches p_det = p is the root in log10 c of the network's
+p_det averaged over the signal population (sky, orientation, f0, f1) drawn as in the
+campaign (Eq. (sampling)), found by bisection with BF16 inference.
+
+Early stopping on noisy outcomes leaves a single network's 90% point a few per cent off in
+either direction depending on its initialisation and validation split; the surrogate is
+therefore a small ensemble whose members differ in both, and p_det is the members' mean.
 """
 from __future__ import annotations
 
@@ -16,12 +27,14 @@ import numpy as np
 
 from . import MLP
 
-N_FEATURES = 8
+N_FEATURES = 13
 
 
-def features(log10_c, log10_s, duty, n, f0_frac, f1):
-    """Feature matrix [n_samples, 8] (FP32)."""
+def features(log10_c, log10_s, duty, n, f0_frac, f1, cosi, psi, tau):
+    """Feature matrix [n_samples, 13] (FP64; standardised and cast to FP32 by Surrogate)."""
     m = len(log10_c)
+    cosi = np.asarray(cosi, np.float64)
+    psi = np.asarray(psi, np.float64)
     F = np.empty((m, N_FEATURES), np.float64)
     F[:, 0] = log10_c
     F[:, 1] = log10_s
@@ -29,12 +42,17 @@ def features(log10_c, log10_s, duty, n, f0_frac, f1):
     F[:, 3:6] = n
     F[:, 6] = f0_frac
     F[:, 7] = np.asarray(f1, np.float64) / 1e-9
+    F[:, 8] = (0.5 * (1.0 + cosi * cosi)) ** 2
+    F[:, 9] = cosi * cosi
+    F[:, 10] = np.cos(4.0 * psi)
+    F[:, 11] = np.sin(4.0 * psi)
+    F[:, 12] = tau
     return F
 
 
 class Surrogate:
-    def __init__(self, ctx, width=128, seed=0):
-        self.net = MLP(ctx, N_FEATURES, width, seed=seed)
+    def __init__(self, ctx, width=128, seed=0, members=5):
+        self.nets = [MLP(ctx, N_FEATURES, width, seed=seed * 7919 + i) for i in range(members)]
         self.mu = None
         self.sd = None
 
@@ -42,44 +60,51 @@ class Surrogate:
         return ((F - self.mu) / self.sd).astype(np.float32)
 
     def fit(self, F, y, epochs=200, batch=1024, lr=2e-3, seed=0, val_frac=0.1, patience=12):
-        """Train on the GPU one pass at a time, keeping the parameters of the pass with the
-        lowest binary cross entropy on a seeded validation split (early stopping: the
-        outcomes are noisy, so a long run memorises noise and over-states p_det).
-        Returns (training losses, validation losses, best pass)."""
+        """Train every member on the GPU one pass at a time on its own seeded split, keeping
+        the parameters of the pass with the lowest binary cross entropy on that member's
+        validation part (early stopping: the outcomes are noisy, so a long run memorises
+        noise and over-states p_det).  Returns per member (training losses, validation
+        losses, best pass)."""
         y = np.asarray(y, np.float32)
-        g = np.random.default_rng(seed)
-        perm = g.permutation(len(y))
-        n_val = max(1, int(round(val_frac * len(y))))
-        vi, ti = perm[:n_val], perm[n_val:]
-        self.mu = F[ti].mean(0)
-        self.sd = F[ti].std(0) + 1e-12
-        Xt, yt = self._std(F[ti]), y[ti]
-        Xv, yv = self._std(F[vi]), y[vi].astype(np.float64)
-        best, best_ep, best_theta = np.inf, -1, None
-        tr, va = [], []
-        for ep in range(epochs):
-            tr.append(float(self.net.train(Xt, yt, batch=batch, epochs=1, lr=lr,
-                                           seed=seed * 1000003 + ep)[0]))
-            p = np.clip(self.net.predict(Xv, bf16=False).astype(np.float64), 1e-7, 1 - 1e-7)
-            v = float(-np.mean(yv * np.log(p) + (1 - yv) * np.log(1 - p)))
-            va.append(v)
-            if v < best:
-                best, best_ep, best_theta = v, ep, self.net.get_params()
-            elif ep - best_ep >= patience:
-                break
-        self.net.set_params(best_theta)
-        return np.array(tr), np.array(va), best_ep
+        self.mu = F.mean(0)
+        self.sd = F.std(0) + 1e-12
+        X = self._std(F)
+        hist = []
+        for i, net in enumerate(self.nets):
+            g = np.random.default_rng(seed * 1000 + i)
+            perm = g.permutation(len(y))
+            n_val = max(1, int(round(val_frac * len(y))))
+            vi, ti = perm[:n_val], perm[n_val:]
+            Xt, yt = X[ti], y[ti]
+            Xv, yv = X[vi], y[vi].astype(np.float64)
+            best, best_ep, best_theta = np.inf, -1, None
+            tr, va = [], []
+            for ep in range(epochs):
+                tr.append(float(net.train(Xt, yt, batch=batch, epochs=1, lr=lr,
+                                          seed=(seed * 1000 + i) * 1000003 + ep)[0]))
+                p = np.clip(net.predict(Xv, bf16=False).astype(np.float64), 1e-7, 1 - 1e-7)
+                v = float(-np.mean(yv * np.log(p) + (1 - yv) * np.log(1 - p)))
+                va.append(v)
+                if v < best:
+                    best, best_ep, best_theta = v, ep, net.get_params()
+                elif ep - best_ep >= patience:
+                    break
+            net.set_params(best_theta)
+            hist.append((np.array(tr), np.array(va), best_ep))
+        return hist
 
     def p(self, F, bf16=True):
-        return self.net.predict(self._std(F), bf16=bf16)
+        X = self._std(F)
+        return np.mean([net.predict(X, bf16=bf16) for net in self.nets], axis=0)
 
-    def log10_c_at(self, p, log10_s, duty, pop, lo=-1.5, hi=2.5, bf16=True, iters=40):
-        """Root in log10 c of mean_pop p_det = p; pop = dict(n [m,3], f0_frac [m], f1 [m])."""
+    def log10_c_at(self, p, log10_s, duty, tau, pop, lo=-1.5, hi=2.5, bf16=True, iters=40):
+        """Root in log10 c of mean_pop p_det = p; pop = dict(n [m,3], f0_frac, f1, cosi, psi
+        [m])."""
         m = len(pop["f0_frac"])
 
         def mean_p(lc):
             F = features(np.full(m, lc), np.full(m, log10_s), np.full(m, duty), pop["n"],
-                         pop["f0_frac"], pop["f1"])
+                         pop["f0_frac"], pop["f1"], pop["cosi"], pop["psi"], np.full(m, tau))
             return float(np.mean(self.p(F, bf16=bf16)))
 
         a, b = lo, hi
@@ -96,4 +121,5 @@ class Surrogate:
         return 0.5 * (a + b)
 
     def close(self):
-        self.net.close()
+        for net in self.nets:
+            net.close()

@@ -32,3 +32,25 @@ def test_population_priors():
     assert inj["f0"].min() >= 100.0 and inj["f0"].max() <= 100.5
     assert lc.min() >= math.log10(0.3) and lc.max() <= math.log10(30)
     assert np.allclose(inj["h0"], 10 ** lc * math.sqrt(2.0 / 1800.0))
+
+
+def test_local_fit_recovers_90_percent_point_of_a_long_tailed_curve():
+    """A mixture of two logistics (a slow upper tail, as orientation averaging produces):
+    one sigmoid over a wide range misplaces the 90% point, local re-centred fits find it."""
+    g = np.random.default_rng(5)
+
+    def p_true(x):
+        return 0.8 / (1 + np.exp(-12 * x)) + 0.2 / (1 + np.exp(-4 * (x - 0.3)))
+
+    # the 90% point by bisection on the known curve
+    a, b = -1.0, 2.0
+    for _ in range(60):
+        m = 0.5 * (a + b)
+        a, b = (m, b) if p_true(m) < 0.9 else (a, m)
+    x90 = 0.5 * (a + b)
+    x = g.uniform(-1.0, 1.5, 400_000)
+    det = (g.uniform(size=x.size) < p_true(x)).astype(float)
+    wide = C.fit_sigmoid(x, det).x_at(0.9)
+    loc, sig, n = C.local_x_at(x, det, 0.9, wide, half=0.05)
+    assert abs(wide - x90) > 0.02
+    assert abs(loc - x90) < max(4 * sig, 0.01) and n > 1000
