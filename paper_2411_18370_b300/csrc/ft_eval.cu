@@ -57,13 +57,6 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, u
         : "memory");
 }
 
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
-{
-    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
 __device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
 {
     asm volatile(
@@ -103,7 +96,7 @@ __device__ __forceinline__ unsigned long long global_ns()
 }
 
 // Wait for an mbarrier phase, giving up after about one second of wall time.
-__device__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity)
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity)
 {
     if (mbar_try_wait(bar, parity))
         return true;
@@ -565,6 +558,31 @@ __device__ __forceinline__ void acc_pair(float &a0, float &a1, unsigned u)
     }
 }
 
+// a += sg (hi(u) - lo(u)), sg = +-1, with 16-bit inputs and an FP32 accumulator.
+template <int MODE>
+__device__ __forceinline__ void acc_diff(float &a, unsigned u, int sg)
+{
+    const unsigned short one = MODE == MODE_F16 ? 0x3C00 : 0x3F80;  // +1 in the storage type
+    const unsigned short sign = 0x8000;
+    const unsigned short mh = sg < 0 ? static_cast<unsigned short>(one | sign) : one;
+    const unsigned short ml = static_cast<unsigned short>(mh ^ sign);
+    if (MODE == MODE_F16) {
+        asm("{\n\t.reg .b16 l, h;\n\t"
+            "mov.b32 {l, h}, %1;\n\t"
+            "fma.rn.f32.f16 %0, h, %2, %0;\n\t"
+            "fma.rn.f32.f16 %0, l, %3, %0;\n\t}"
+            : "+f"(a)
+            : "r"(u), "h"(mh), "h"(ml));
+    } else {
+        asm("{\n\t.reg .b16 l, h;\n\t"
+            "mov.b32 {l, h}, %1;\n\t"
+            "fma.rn.f32.bf16 %0, h, %2, %0;\n\t"
+            "fma.rn.f32.bf16 %0, l, %3, %0;\n\t}"
+            : "+f"(a)
+            : "r"(u), "h"(mh), "h"(ml));
+    }
+}
+
 template <int MODE>
 __device__ __forceinline__ float read_bin(const unsigned char *rows, int row_words, int a, int k)
 {
@@ -576,17 +594,18 @@ __device__ __forceinline__ float read_bin(const unsigned char *rows, int row_wor
 }
 
 // Shared-memory layout of the fast kernel: nst pipeline slots, each with S <= 32 rows of
-// power and one 16-byte record per row (the per-SFT track terms E, C and the weight);
+// power and one 24-byte record per row (the track terms C, E and span, the weight and
+// the window start);
 // per evaluating warp its own row offsets and correction list for the slot it works on.
 constexpr int kMaxStages = 4;
 constexpr int kFoldRows = 128;  // FP32 partials cover at most this many SFT rows
 
 struct RowRec {
-    long long C;
+    long long C;     // C + 2^31 + j0 E: the track's Q32 origin at the tile's first f0, before G
     int E;
+    unsigned span;   // (J - 1) |E|: how far the fraction moves across the tile
     float w;
-    int start;  // first bin of the row's window in shared memory (multiple of 16)
-    int pad;
+    int start;       // first bin of the row's window in shared memory (multiple of 16)
 };
 
 struct FastLayout {
@@ -663,8 +682,8 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
 
     if (threadIdx.x == 0) {
         for (int b = 0; b < nst; ++b) {
-            mbar_init(&full[b], 32);
-            mbar_init(&empty[b], 32 * F);
+            mbar_init(&full[b], 1);   // the producer's lane 0, with the stage's bytes
+            mbar_init(&empty[b], F);  // one elected lane per evaluating warp
         }
         fence_mbar_init();
     }
@@ -706,6 +725,8 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
                 alpha = static_cast<long long>(st) * S + lane;
                 RowRec r;
                 track_ec(p.v + 3 * alpha, c.n0, c.n1, c.n2, p.K0, p.k_lo, r.E, r.C);
+                r.C += (1ll << 31) + static_cast<long long>(c.j0) * r.E;
+                r.span = static_cast<unsigned>(J - 1) * static_cast<unsigned>(abs(r.E));
                 r.w = p.w[alpha];
                 int s0 = 0;
                 len = p.Wp;
@@ -716,7 +737,7 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
                     const long long G1 = p.G[static_cast<long long>(f_min) * p.N + alpha];
                     const long long G2 = p.G[static_cast<long long>(f_max) * p.N + alpha];
                     const long long gmin = min(G1, G2), gmax = max(G1, G2);
-                    const long long a0 = r.C + (1ll << 31) + static_cast<long long>(c.j0) * r.E;
+                    const long long a0 = r.C;
                     const int b_lo = c.j0 + static_cast<int>((a0 + gmin + cross_q32(gmin, r.E)) >> 32);
                     const int b_hi = c.j0 + static_cast<int>((a0 + gmax + cross_q32(gmax, r.E)) >> 32);
                     s0 = max(min(b_lo, b_hi) - 2, 0) & ~15;
@@ -731,45 +752,44 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
                 }
                 start = s0;
                 r.start = s0;
-                r.pad = 0;
                 rec[slot * S + lane] = r;
             }
+            unsigned row_tot;  // bytes of the stage's copies
+            if (p.Ws == p.Wp) {
+                row_tot = static_cast<unsigned>(nr) * static_cast<unsigned>(p.row_bytes);
+            } else {
+                row_tot = static_cast<unsigned>(len) * 4u;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1)
+                    row_tot += __shfl_xor_sync(0xffffffffu, row_tot, off);
+            }
+            // every lane's record is written before lane 0's arrival releases the slot
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive_expect_tx(&full[slot], row_tot);
             if (p.Ws == p.Wp) {
                 // whole rows: the stage's rows are contiguous in global and shared memory
-                if (lane == 0) {
-                    const unsigned bytes = static_cast<unsigned>(nr) * static_cast<unsigned>(p.row_bytes);
-                    mbar_expect_tx(&full[slot], bytes);
+                if (lane == 0)
                     bulk_copy_g2s(buf + slot * L.stage_bytes,
                                   static_cast<const unsigned char *>(p.power) +
                                       static_cast<size_t>(st) * S * p.row_bytes,
-                                  bytes, &full[slot]);
-                }
-            } else {
-                unsigned tot = static_cast<unsigned>(len) * 4u;  // bytes of this row's copies
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1)
-                    tot += __shfl_xor_sync(0xffffffffu, tot, off);
-                if (lane == 0)
-                    mbar_expect_tx(&full[slot], tot);
-                __syncwarp();
-                if (lane < nr) {
-                    unsigned char *dst = buf + slot * L.stage_bytes + static_cast<size_t>(lane) * p.srow_bytes;
-                    const unsigned char *src =
-                        static_cast<const unsigned char *>(p.power) + static_cast<size_t>(alpha) * p.row_bytes;
-                    if (!PAIR) {
-                        bulk_copy_g2s(dst, src + static_cast<size_t>(start) * 4, static_cast<unsigned>(len) * 4,
-                                      &full[slot]);
-                    } else {
-                        // even copy then odd copy: words [start/2, (start+len)/2) of each
-                        bulk_copy_g2s(dst, src + static_cast<size_t>(start >> 1) * 4,
-                                      static_cast<unsigned>(len) * 2, &full[slot]);
-                        bulk_copy_g2s(dst + (p.srow_bytes >> 1),
-                                      src + (p.row_bytes >> 1) + static_cast<size_t>(start >> 1) * 4,
-                                      static_cast<unsigned>(len) * 2, &full[slot]);
-                    }
+                                  row_tot, &full[slot]);
+            } else if (lane < nr) {
+                unsigned char *dst = buf + slot * L.stage_bytes + static_cast<size_t>(lane) * p.srow_bytes;
+                const unsigned char *src =
+                    static_cast<const unsigned char *>(p.power) + static_cast<size_t>(alpha) * p.row_bytes;
+                if (!PAIR) {
+                    bulk_copy_g2s(dst, src + static_cast<size_t>(start) * 4, static_cast<unsigned>(len) * 4,
+                                  &full[slot]);
+                } else {
+                    // even copy then odd copy: words [start/2, (start+len)/2) of each
+                    bulk_copy_g2s(dst, src + static_cast<size_t>(start >> 1) * 4,
+                                  static_cast<unsigned>(len) * 2, &full[slot]);
+                    bulk_copy_g2s(dst + (p.srow_bytes >> 1),
+                                  src + (p.row_bytes >> 1) + static_cast<size_t>(start >> 1) * 4,
+                                  static_cast<unsigned>(len) * 2, &full[slot]);
                 }
             }
-            mbar_arrive(&full[slot]);
             if (++slot == nst) {
                 slot = 0;
                 ++use;
@@ -784,7 +804,6 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
         }
     } else {
         // ------------------------------------------------------------ evaluating warps
-        const int fg = min(c.f1g * F + warp, p.n_f1 - 1);
         int *tabB = reinterpret_cast<int *>(smem + L.tabB) + warp * S;
         int *evA = reinterpret_cast<int *>(smem + L.evA) + warp * S;
         int *evK = reinterpret_cast<int *>(smem + L.evK) + warp * S;
@@ -794,7 +813,7 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
             part[i] = 0.f;
         int rows_since_fold = 0;
         // G of this lane's row, loaded one stage ahead
-        const long long *Gf = p.G + static_cast<long long>(fg) * p.N;
+        const long long *Gf = p.G + static_cast<long long>(min(c.f1g * F + warp, p.n_f1 - 1)) * p.N;
         long long g_cur = lane < rows_in_stage(p, 0) ? Gf[lane] : 0;
         int slot = 0, use = 0;
         for (int st = 0; st < n_stages; ++st) {
@@ -814,11 +833,10 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
             int packed = 0, basev = 0;
             if (lane < nr) {
                 const RowRec r = rr[lane];
-                const long long X0p = r.C + g_cur + cross_q32(g_cur, r.E) + (1ll << 31);
-                const long long acc0 = X0p + static_cast<long long>(c.j0) * r.E;
+                const long long acc0 = r.C + g_cur + cross_q32(g_cur, r.E);
                 const int base = c.j0 + static_cast<int>(acc0 >> 32) - r.start;  // within the window
                 const unsigned L0 = static_cast<unsigned>(acc0);
-                const unsigned span = static_cast<unsigned>(J - 1) * static_cast<unsigned>(abs(r.E));
+                const unsigned span = r.span;
                 ev = r.E > 0 ? (span != 0u && L0 >= 0u - span) : (L0 < span);
                 tabB[lane] = PAIR ? lane * row_words + (base & 1) * (row_words >> 1) + (base >> 1)
                                   : lane * row_words + base;
@@ -826,8 +844,9 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
                 basev = base;
                 if (ev) {
                     // first tile offset at which the bin steps (rare: one division)
-                    const int jc = r.E > 0 ? static_cast<int>((0x100000000ull - L0 + static_cast<unsigned>(r.E) - 1) /
-                                                              static_cast<unsigned>(r.E))
+                    // (E > 0: the first j with L0 + j E >= 2^32 is ceil((2^32 - L0) / E),
+                    // written with a 32-bit numerator)
+                    const int jc = r.E > 0 ? static_cast<int>((0xffffffffu - L0) / static_cast<unsigned>(r.E)) + 1
                                            : static_cast<int>(L0 / static_cast<unsigned>(-r.E)) + 1;
                     packed |= jc << 8;
                 }
@@ -879,25 +898,49 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
             }
             for (int a = nr4; a < nr; ++a)
                 row_sum(tabB[a], WEIGHTED ? rr[a].w : 1.f);
-            // corrections for the rows whose bin steps by sign(E) inside the tile
+            // corrections for the rows whose bin steps by sign(E) inside the tile: from
+            // slot jc on the track reads bin k + sg instead of k (slots past n_f0 are
+            // computed and discarded, like in the main loop; their bins stay in the window)
             for (int e = 0; e < ne; ++e) {
                 const int pk = evA[e];
                 const int a = pk & 0xff;
                 const int jc = (pk >> 8) & 0xfff;
                 const int sg = (pk >> 20) ? -1 : 1;
                 const int base = evK[e];
-                const float wa = rr[a].w;
+                const float wa = WEIGHTED ? rr[a].w : 1.f;
+                if (MODE == MODE_F32) {
 #pragma unroll
-                for (int i = 0; i < NS; ++i) {
-                    if (jrel[i] >= jc && c.j0 + jrel[i] < p.n_f0) {
-                        const int k = base + jrel[i];
-                        const float d = __fsub_rn(read_bin<MODE>(rows, row_words, a, k + sg),
-                                                  read_bin<MODE>(rows, row_words, a, k));
-                        part[i] = WEIGHTED ? __fmaf_rn(wa, d, part[i]) : __fadd_rn(part[i], d);
+                    for (int i = 0; i < NS; ++i) {
+                        if (jrel[i] >= jc) {
+                            const int k = base + jrel[i];
+                            const float d = __fsub_rn(read_bin<MODE>(rows, row_words, a, k + sg),
+                                                      read_bin<MODE>(rows, row_words, a, k));
+                            part[i] = WEIGHTED ? __fmaf_rn(wa, d, part[i]) : __fadd_rn(part[i], d);
+                        }
+                    }
+                } else {
+                    // one 32-bit word of the pair layout holds (P[k'], P[k'+1]) for any k';
+                    // with k' = k + min(sg, 0) the change is sg (P[k'+1] - P[k'])
+                    const unsigned *row = reinterpret_cast<const unsigned *>(rows) + a * row_words;
+#pragma unroll
+                    for (int i = 0; i < NS; ++i) {
+                        if (jrel[i] >= jc) {
+                            const int kp = base + jrel[i] + (sg < 0 ? -1 : 0);
+                            const unsigned u = row[(kp & 1) * (row_words >> 1) + (kp >> 1)];
+                            if (WEIGHTED) {
+                                const float d = __fsub_rn(hi_to_float<MODE>(u), lo_to_float<MODE>(u));
+                                part[i] = __fmaf_rn(sg < 0 ? -wa : wa, d, part[i]);
+                            } else {
+                                acc_diff<MODE>(part[i], u, sg);
+                            }
+                        }
                     }
                 }
             }
-            mbar_arrive(&empty[slot]);
+            // the warp's reads of this slot are done before its elected lane releases it
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&empty[slot]);
             if (++slot == nst) {
                 slot = 0;
                 ++use;
