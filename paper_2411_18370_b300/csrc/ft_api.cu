@@ -297,6 +297,7 @@ int ft_load_sfts(ft_ctx *ctx, const ft_band_desc *d, const void *power, int powe
         sw += wv[a];
         sw2 += static_cast<double>(wv[a]) * wv[a];
         b->tau_absmax = std::max(b->tau_absmax, std::fabs(b->h_tau[a]));
+        b->vmax = std::max(b->vmax, b->h_vabs[a]);
     }
     b->mu = 2.0 * sw;
     b->sigma = std::sqrt(4.0 * sw2);
@@ -380,6 +381,41 @@ int ft_band_info(const ft_band *b, int64_t *n, int *n_bins, int *stride, int *dt
     return FT_OK;
 }
 
+// Sky points ordered so that runs of a few consecutive points are close on the sky:
+// bands of equal area in z (about 2 points per band per row of the run), longitude
+// ascending in even bands and descending in odd ones.  dmax[P] is the largest distance
+// between two points of one run g*P .. g*P + P - 1 of the order.
+static void sky_proximity_order(const double *sky, int64_t n, std::vector<int> &order,
+                                double dmax[kMaxSkyGroup + 1])
+{
+    const int nz = std::max<int>(1, static_cast<int>(std::lround(std::sqrt(n / 2.0))));
+    std::vector<std::pair<std::pair<int, double>, int>> key(n);
+    for (int64_t i = 0; i < n; ++i) {
+        const double x = sky[3 * i], y = sky[3 * i + 1], z = sky[3 * i + 2];
+        int zone = static_cast<int>(std::floor((z + 1.0) * 0.5 * nz));
+        zone = std::min(std::max(zone, 0), nz - 1);
+        const double phi = std::atan2(y, x);
+        key[i] = {{zone, (zone & 1) ? -phi : phi}, static_cast<int>(i)};
+    }
+    std::sort(key.begin(), key.end());
+    order.resize(n);
+    for (int64_t i = 0; i < n; ++i)
+        order[i] = key[i].second;
+    dmax[0] = dmax[1] = 0.0;
+    for (int P = 2; P <= kMaxSkyGroup; ++P) {
+        double m = 0.0;
+        for (int64_t g0 = 0; g0 < n; g0 += P)
+            for (int64_t a = g0; a < std::min<int64_t>(g0 + P, n); ++a)
+                for (int64_t b = a + 1; b < std::min<int64_t>(g0 + P, n); ++b) {
+                    const double *u = sky + 3 * static_cast<int64_t>(order[a]);
+                    const double *w = sky + 3 * static_cast<int64_t>(order[b]);
+                    const double dx = u[0] - w[0], dy = u[1] - w[1], dz = u[2] - w[2];
+                    m = std::max(m, std::sqrt(dx * dx + dy * dy + dz * dz));
+                }
+        dmax[P] = m;
+    }
+}
+
 int ft_make_bank(ft_ctx *ctx, const ft_band *band, const ft_bank_desc *d, void *stream,
                  ft_bank **out)
 {
@@ -407,9 +443,12 @@ int ft_make_bank(ft_ctx *ctx, const ft_band *band, const ft_bank_desc *d, void *
     b->window_safe = kmin >= band->k_lo && kmax <= band->k_lo + band->W - 1;
     b->f1_lo = *std::min_element(d->f1, d->f1 + d->n_f1);
     b->f1_hi = *std::max_element(d->f1, d->f1 + d->n_f1);
+    std::vector<int> order;
+    sky_proximity_order(d->sky, d->n_sky, order, b->sky_dmax);
     int rc;
     if ((rc = dev_upload(&b->d_f1, d->f1, d->n_f1, st)) != FT_OK ||
-        (rc = dev_upload(&b->d_sky, d->sky, 3 * static_cast<size_t>(d->n_sky), st)) != FT_OK) {
+        (rc = dev_upload(&b->d_sky, d->sky, 3 * static_cast<size_t>(d->n_sky), st)) != FT_OK ||
+        (rc = dev_upload(&b->d_sky_order, order.data(), order.size(), st)) != FT_OK) {
         ft_bank_destroy(b);
         return rc;
     }
@@ -433,6 +472,7 @@ void ft_bank_destroy(ft_bank *b)
     DeviceGuard g(b->device);
     cudaFree(b->d_f1);
     cudaFree(b->d_sky);
+    cudaFree(b->d_sky_order);
     cudaFree(b->d_G);
     delete b;
 }
@@ -560,9 +600,7 @@ int ft_topk_per_band(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int 
     cudaStream_t st = as_stream(stream);
     const EvalShape sh = ft_default_shape(ctx, band, bank);
     const int J = sh.J;
-    const long long n_f0t = (bank->n_f0 + J - 1) / J;
-    const long long n_f1g = (bank->n_f1 + sh.F - 1) / sh.F;
-    const long long n_cta = bank->n_sky * n_f1g * n_f0t;
+    const long long n_cta = ft_grid_ctas(bank, sh);
     const int lsub_max = std::min(bank->n_sub, (J + bank->sub - 1) / bank->sub + 1);
     const size_t cand_bytes = static_cast<size_t>(n_cta) * lsub_max * k * sizeof(ft_candidate);
     const size_t out_bytes = static_cast<size_t>(bank->n_sub) * k * sizeof(ft_candidate);

@@ -123,9 +123,14 @@ int build(ft_ctx *ctx, int n, const ft_band *const *bands, const ft_bank *const 
     b->weighted = bands[0]->weighted;
     b->J = J;
     b->nst = nst;
+    // per band: P sky points x F1 f1 values per CTA; the CTA has the most warps any band
+    // uses (a band with fewer leaves the rest idle)
+    std::vector<int> bP(n), bF1(n);
     int F = 1;
-    for (int i = 0; i < n; ++i)
-        F = std::max(F, std::min(banks[i]->n_f1, 20));
+    for (int i = 0; i < n; ++i) {
+        ft_sky_grouping(banks[i], 20, &bP[i], &bF1[i]);
+        F = std::max(F, bP[i] * bF1[i]);
+    }
     b->F = F;
     const bool pair = b->dtype != FT_F32;
     if (J % (pair ? 64 : 32) != 0 || J < 32 || J > 256 || nst < 2 || nst > 4) {
@@ -148,6 +153,10 @@ int build(ft_ctx *ctx, int n, const ft_band *const *bands, const ft_bank *const 
         p.v = bd->d_v;
         p.w = bd->d_w;
         p.sky = bk->d_sky;
+        p.P = bP[i];
+        p.F1 = bF1[i];
+        p.n_skyg = (bk->n_sky + bP[i] - 1) / bP[i];
+        p.sky_order = bP[i] > 1 ? bk->d_sky_order : nullptr;
         p.G = bk->d_G;
         p.f1 = bk->d_f1;
         p.K0 = bk->k0;
@@ -160,7 +169,7 @@ int build(ft_ctx *ctx, int n, const ft_band *const *bands, const ft_bank *const 
         p.status = ctx->d_status;
         p.k = k;
         p.sub = bk->sub;
-        const int Ws = ft_window_bins(bd, bk, J);
+        const int Ws = ft_window_bins(bd, bk, J, bP[i]);
         const int S = rows_for(Ws, nst);
         b->S.push_back(S);
         p.S = S;
@@ -172,9 +181,9 @@ int build(ft_ctx *ctx, int n, const ft_band *const *bands, const ft_bank *const 
         p.row_elems = bd->dtype == FT_F32 ? bd->Wp : 2 * bd->Wp;
         p.n_stages = static_cast<int>((bd->N + S - 1) / S);
         p.n_f0t = (bk->n_f0 + J - 1) / J;
-        p.n_f1g = (bk->n_f1 + F - 1) / F;
+        p.n_f1g = (bk->n_f1 + bF1[i] - 1) / bF1[i];
         p.lsub_max = std::min(bk->n_sub, (J + bk->sub - 1) / bk->sub + 1);
-        const long long T = bk->n_sky * p.n_f1g * static_cast<long long>(p.n_f0t);
+        const long long T = p.n_skyg * p.n_f1g * static_cast<long long>(p.n_f0t);
         long long Tc = T;
         if (cap_frac < 1.0)
             Tc = std::max<long long>(1, static_cast<long long>(std::ceil(T * cap_frac)));
@@ -186,7 +195,7 @@ int build(ft_ctx *ctx, int n, const ft_band *const *bands, const ft_bank *const 
         sub_prefix[i + 1] = sub_prefix[i] + bk->n_sub;
         b->n_sub_max = std::max(b->n_sub_max, bk->n_sub);
         b->lsub_max = std::max(b->lsub_max, p.lsub_max);
-        tile_smem = std::max(tile_smem, ft_batch_tile_smem(Ws, S, F, J, nst));
+        tile_smem = std::max(tile_smem, ft_batch_tile_smem(Ws, S, F, bP[i], J, nst));
     }
     b->n_sub_total = sub_prefix[n];
     b->sub_prefix_h.assign(sub_prefix.begin(), sub_prefix.end());

@@ -195,7 +195,7 @@ __host__ __device__ inline SmemLayout smem_layout(int S, int F, int row_bytes, i
     L.buf = o;
     L.stage_bytes = (size_t)S * row_bytes;
     const size_t pipe = kNbuf * L.stage_bytes + (size_t)(J + 64) * 4;
-    const size_t tk = topk ? (size_t)F * J * 2 * sizeof(float) : 0;
+    const size_t tk = topk ? (size_t)F * J * 2 * sizeof(float) + (size_t)F * sizeof(long long) : 0;
     o += pipe > tk ? pipe : tk;
     L.total = o;
     return L;
@@ -204,10 +204,32 @@ __host__ __device__ inline SmemLayout smem_layout(int S, int F, int row_bytes, i
 // ------------------------------------------------------------------ pieces shared by kernels
 
 struct CtaTile {
-    long long cta, sky;
+    long long cta, skyg, sky;  // sky group, and its first sky point
     int f0t, f1g, j0;
-    double n0, n1, n2;
+    double n0, n1, n2;         // unit vector of that sky point
 };
+
+// Sky index of member q of sky group g (P consecutive points of the bank's sky order), or
+// -1 past the last sky point.
+__device__ __forceinline__ long long sky_of(const EvalParams &p, long long g, int q)
+{
+    const long long i = g * p.P + q;
+    if (i >= p.n_sky)
+        return -1;
+    return p.sky_order != nullptr ? static_cast<long long>(p.sky_order[i]) : i;
+}
+
+// Template index base (sky, f1) * n_f0 of evaluating warp w of the tile, or -1 when the
+// warp has no template (past the last sky point or f1 value, or beyond P * F1 warps).
+__device__ __forceinline__ long long warp_template_base(const EvalParams &p, long long skyg,
+                                                        int f1g, int w)
+{
+    const int q = w / p.F1, f = f1g * p.F1 + (w - q * p.F1);
+    if (q >= p.P || f >= p.n_f1)
+        return -1;
+    const long long sk = sky_of(p, skyg, q);
+    return sk < 0 ? -1 : (sk * p.n_f1 + f) * static_cast<long long>(p.n_f0);
+}
 
 __device__ __forceinline__ CtaTile decode_tile(const EvalParams &p, int J, long long tile)
 {
@@ -216,7 +238,8 @@ __device__ __forceinline__ CtaTile decode_tile(const EvalParams &p, int J, long 
     c.f0t = static_cast<int>(c.cta % p.n_f0t);
     const long long rest = c.cta / p.n_f0t;
     c.f1g = static_cast<int>(rest % p.n_f1g);
-    c.sky = rest / p.n_f1g;
+    c.skyg = rest / p.n_f1g;
+    c.sky = sky_of(p, c.skyg, 0);
     c.j0 = c.f0t * J;
     c.n0 = p.sky[3 * c.sky];
     c.n1 = p.sky[3 * c.sky + 1];
@@ -271,19 +294,19 @@ __device__ void abandon_tile(const EvalParams &p, unsigned long long *bars, int 
 }
 
 // Fused candidate selection: vs/vz hold [F][J] values of this CTA's templates (index
-// = f1 slot * J + j - j0).  Per sub-band, one warp extracts the k best by (s desc, t asc)
-// in k rounds of a warp arg-max restricted to keys ranked after the previous pick.
+// = warp * J + j - j0) and wt[w] the template base of warp w (-1: no templates).  Per
+// sub-band, one warp extracts the k best by (s desc, t asc) in k rounds of a warp arg-max
+// restricted to keys ranked after the previous pick.
 __device__ void cta_topk(const EvalParams &p, const CtaTile &c, int F, int J, const float *vs,
-                         const float *vz, ft_candidate *dst)
+                         const float *vz, const long long *wt, ft_candidate *dst)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int jhi = min(c.j0 + J, p.n_f0);
     const int lb0 = c.j0 / p.sub, lb1 = (jhi - 1) / p.sub;
-    const int nf = min(F, p.n_f1 - c.f1g * F);
     for (int lb = lb0 + warp; lb <= lb1; lb += F) {
         const int ja = max(c.j0, lb * p.sub), jb = min(jhi, (lb + 1) * p.sub);
         const int width = jb - ja;
-        const int count = nf * width;
+        const int count = F * width;
         float last_s = INFINITY;
         long long last_t = -1;
         ft_candidate *out = dst + (lb - lb0) * p.k;
@@ -293,9 +316,11 @@ __device__ void cta_topk(const EvalParams &p, const CtaTile &c, int F, int J, co
             long long bt = LLONG_MAX;
             for (int q = lane; q < count; q += 32) {
                 const int fl = q / width, jj = ja + (q - fl * width);
+                const long long tb = wt[fl];
+                if (tb < 0)
+                    continue;
                 const float s = vs[fl * J + (jj - c.j0)];
-                const long long t =
-                    (c.sky * p.n_f1 + c.f1g * F + fl) * static_cast<long long>(p.n_f0) + jj;
+                const long long t = tb + jj;
                 const bool elig = (s < last_s) || (s == last_s && t > last_t);
                 const bool better = !have || (s > bs) || (s == bs && t < bt);
                 if (elig && better) {
@@ -352,9 +377,8 @@ __device__ __forceinline__ void finish_tile(const EvalParams &p, const CtaTile &
 {
     const int warp = threadIdx.x >> 5;
     const bool active = warp < F;
-    const int f = c.f1g * F + warp;
-    const bool f_ok = active && f < p.n_f1;
-    const long long trow = (c.sky * p.n_f1 + f) * static_cast<long long>(p.n_f0);
+    const long long trow = active ? warp_template_base(p, c.skyg, c.f1g, warp) : -1;
+    const bool f_ok = trow >= 0;
     float sv[NS], zv[NS];
 #pragma unroll
     for (int r = 0; r < NS; ++r) {
@@ -379,18 +403,21 @@ __device__ __forceinline__ void finish_tile(const EvalParams &p, const CtaTile &
         return;
     float *vs = reinterpret_cast<float *>(buf);
     float *vz = vs + F * J;
+    long long *wt = reinterpret_cast<long long *>(vz + F * J);
     if (active) {
 #pragma unroll
         for (int r = 0; r < NS; ++r) {
             vs[warp * J + jrel[r]] = sv[r];
             vz[warp * J + jrel[r]] = zv[r];
         }
+        if ((threadIdx.x & 31) == 0)
+            wt[warp] = trow;
     }
     __syncthreads();
     if (active) {
         if (dst == nullptr)
             dst = reinterpret_cast<ft_candidate *>(p.cand) + c.cta * p.lsub_max * p.k;
-        cta_topk(p, c, F, J, vs, vz, dst);
+        cta_topk(p, c, F, J, vs, vz, wt, dst);
     }
 }
 
@@ -600,6 +627,79 @@ __device__ __forceinline__ float read_bin(const unsigned char *rows, int row_wor
 constexpr int kMaxStages = 4;
 constexpr int kFoldRows = 128;  // FP32 partials cover at most this many SFT rows
 
+// ------------------------------------------------------------------ tensor memory
+//
+// Between folds the compensated sums (hi, lo) of every evaluating warp are parked in the
+// SM's tensor memory instead of registers: 16 columns per warp in the warp's lane quarter
+// (warp w reaches lanes 32 (w mod 4) .. + 31), hi in the first 8 columns and lo in the
+// next 8, column base 16 (w div 4).  Warp 0 allocates the columns for the CTA and frees
+// them when the CTA ends.
+
+__host__ __device__ constexpr unsigned tm_cols_for(int F)
+{
+    return ((F + 3) / 4) * 16 <= 32 ? 32u : ((F + 3) / 4) * 16 <= 64 ? 64u : 128u;
+}
+
+__device__ __forceinline__ void tm_alloc(unsigned *dst, unsigned ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tm_dealloc(unsigned taddr, unsigned ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tm_fence_before()
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tm_fence_after()
+{
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Eight consecutive columns of this thread's lane into v (valid after tm_wait_ld).
+__device__ __forceinline__ void tm_ld8(unsigned taddr, float (&v)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]),
+                   "=f"(v[6]), "=f"(v[7])
+                 : "r"(taddr)
+                 : "memory");
+}
+
+// Wait for this thread's tensor-memory loads; a and b are the registers they fill, tied to
+// the wait so that no use moves above it.
+__device__ __forceinline__ void tm_wait_ld(float (&a)[8], float (&b)[8])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+f"(a[0]), "+f"(a[1]), "+f"(a[2]), "+f"(a[3]), "+f"(a[4]), "+f"(a[5]),
+                   "+f"(a[6]), "+f"(a[7]), "+f"(b[0]), "+f"(b[1]), "+f"(b[2]), "+f"(b[3]),
+                   "+f"(b[4]), "+f"(b[5]), "+f"(b[6]), "+f"(b[7])
+                 :
+                 : "memory");
+}
+
+__device__ __forceinline__ void tm_st8(unsigned taddr, const float (&v)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(
+                     taddr),
+                 "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]),
+                 "f"(v[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tm_wait_st()
+{
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 struct RowRec {
     long long C;     // C + 2^31 + j0 E: the track's Q32 origin at the tile's first f0, before G
     int E;
@@ -609,11 +709,11 @@ struct RowRec {
 };
 
 struct FastLayout {
-    size_t full, empty, rec, tabB, evA, evK, buf, total, stage_bytes;
+    size_t full, empty, skyn, rec, tabB, evA, evK, buf, total, stage_bytes;
 };
 
-__host__ __device__ inline FastLayout fast_layout(int S, int F, int row_bytes, int J, bool topk,
-                                                  int nst)
+__host__ __device__ inline FastLayout fast_layout(int S, int F, int P, int row_bytes, int J,
+                                                  bool topk, int nst)
 {
     FastLayout L;
     size_t o = 0;
@@ -621,8 +721,10 @@ __host__ __device__ inline FastLayout fast_layout(int S, int F, int row_bytes, i
     o += kMaxStages * 8;
     L.empty = o;
     o = align_up(o + kMaxStages * 8, 16);
-    L.rec = o;
-    o = align_up(o + (size_t)nst * S * sizeof(RowRec), 16);
+    L.skyn = o;  // unit vectors of the tile's sky points
+    o = align_up(o + (size_t)kMaxSkyGroup * 3 * sizeof(double), 16);
+    L.rec = o;   // per slot, sky point and row
+    o = align_up(o + (size_t)nst * P * S * sizeof(RowRec), 16);
     L.tabB = o;
     o = align_up(o + (size_t)F * S * sizeof(int), 16);
     L.evA = o;
@@ -632,7 +734,7 @@ __host__ __device__ inline FastLayout fast_layout(int S, int F, int row_bytes, i
     L.buf = o;
     L.stage_bytes = (size_t)S * row_bytes;
     const size_t pipe = (size_t)nst * L.stage_bytes + (size_t)(J + 64) * 4;
-    const size_t tk = topk ? (size_t)F * J * 2 * sizeof(float) : 0;
+    const size_t tk = topk ? (size_t)F * J * 2 * sizeof(float) + (size_t)F * sizeof(long long) : 0;
     o += pipe > tk ? pipe : tk;
     L.total = o;
     return L;
@@ -662,7 +764,7 @@ __device__ __forceinline__ long long cross_q32(long long G, int E)
 #endif
 template <int MODE, int R, bool WEIGHTED>
 __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, unsigned char *smem,
-                                          ft_candidate *dst)
+                                          ft_candidate *dst, unsigned tm)
 {
     constexpr bool PAIR = MODE != MODE_F32;
     constexpr int NS = PAIR ? 2 * R : R;  // accumulator slots per thread
@@ -672,7 +774,8 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
     const int S = p.S;
     const int nst = p.nst;
     const int row_words = p.srow_bytes >> 2;  // shared-memory row: Ws bins
-    const FastLayout L = fast_layout(S, F, p.srow_bytes, J, p.cand != nullptr, nst);
+    const FastLayout L = fast_layout(S, F, p.P, p.srow_bytes, J, p.cand != nullptr, nst);
+    double *skyn = reinterpret_cast<double *>(smem + L.skyn);
     unsigned long long *full = reinterpret_cast<unsigned long long *>(smem + L.full);
     unsigned long long *empty = reinterpret_cast<unsigned long long *>(smem + L.empty);
     RowRec *rec = reinterpret_cast<RowRec *>(smem + L.rec);
@@ -686,6 +789,13 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
             mbar_init(&empty[b], F);  // one elected lane per evaluating warp
         }
         fence_mbar_init();
+    }
+    if (threadIdx.x < 3 * p.P) {
+        // sky points of the group; a ragged last group repeats its first point (those
+        // warps' templates do not exist and are never written)
+        const int q = threadIdx.x / 3;
+        const long long sk = sky_of(p, c.skyg, q);
+        skyn[threadIdx.x] = p.sky[3 * (sk < 0 ? c.sky : sk) + (threadIdx.x - 3 * q)];
     }
     __syncthreads();
 
@@ -705,8 +815,9 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
     if (warp == F) {
         // ------------------------------------------------------------ producer warp
         // members of this CTA's f1 group with the smallest and largest f1
-        int f_min = c.f1g * F, f_max = c.f1g * F;
-        for (int f = c.f1g * F + 1; f < min(c.f1g * F + F, p.n_f1); ++f) {
+        const int F1 = p.F1;
+        int f_min = c.f1g * F1, f_max = c.f1g * F1;
+        for (int f = c.f1g * F1 + 1; f < min(c.f1g * F1 + F1, p.n_f1); ++f) {
             if (p.f1[f] < p.f1[f_min])
                 f_min = f;
             if (p.f1[f] > p.f1[f_max])
@@ -723,25 +834,38 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
             int start = 0, len = 0;
             if (lane < nr) {
                 alpha = static_cast<long long>(st) * S + lane;
-                RowRec r;
-                track_ec(p.v + 3 * alpha, c.n0, c.n1, c.n2, p.K0, p.k_lo, r.E, r.C);
-                r.C += (1ll << 31) + static_cast<long long>(c.j0) * r.E;
-                r.span = static_cast<unsigned>(J - 1) * static_cast<unsigned>(abs(r.E));
-                r.w = p.w[alpha];
+                const double va[3] = {p.v[3 * alpha], p.v[3 * alpha + 1], p.v[3 * alpha + 2]};
+                const float wa = p.w[alpha];
+                RowRec *rq = rec + static_cast<size_t>(slot) * p.P * S + lane;
+                // track terms per sky point, and the bins the tile reads in this row: the
+                // track origin is linear in f1, so per sky point the group's smallest and
+                // largest f1 bound it; plus the tile width and one carry step on each side
+                int b_lo = INT_MAX, b_hi = INT_MIN;
+                long long G1 = 0, G2 = 0;
+                if (p.Ws < p.Wp) {
+                    G1 = p.G[static_cast<long long>(f_min) * p.N + alpha];
+                    G2 = p.G[static_cast<long long>(f_max) * p.N + alpha];
+                }
+                for (int q = 0; q < p.P; ++q) {
+                    RowRec r;
+                    track_ec(va, skyn[3 * q], skyn[3 * q + 1], skyn[3 * q + 2], p.K0, p.k_lo, r.E, r.C);
+                    r.C += (1ll << 31) + static_cast<long long>(c.j0) * r.E;
+                    r.span = static_cast<unsigned>(J - 1) * static_cast<unsigned>(abs(r.E));
+                    r.w = wa;
+                    r.start = 0;
+                    rq[q * S] = r;
+                    if (p.Ws < p.Wp) {
+                        const int x1 = c.j0 + static_cast<int>((r.C + G1 + cross_q32(G1, r.E)) >> 32);
+                        const int x2 = c.j0 + static_cast<int>((r.C + G2 + cross_q32(G2, r.E)) >> 32);
+                        b_lo = min(b_lo, min(x1, x2));
+                        b_hi = max(b_hi, max(x1, x2));
+                    }
+                }
                 int s0 = 0;
                 len = p.Wp;
                 if (p.Ws < p.Wp) {
-                    // the bins this tile reads in this row: the track origin is linear in f1, so
-                    // the group's smallest and largest f1 bound it; plus the tile width and one
-                    // carry step on each side
-                    const long long G1 = p.G[static_cast<long long>(f_min) * p.N + alpha];
-                    const long long G2 = p.G[static_cast<long long>(f_max) * p.N + alpha];
-                    const long long gmin = min(G1, G2), gmax = max(G1, G2);
-                    const long long a0 = r.C;
-                    const int b_lo = c.j0 + static_cast<int>((a0 + gmin + cross_q32(gmin, r.E)) >> 32);
-                    const int b_hi = c.j0 + static_cast<int>((a0 + gmax + cross_q32(gmax, r.E)) >> 32);
-                    s0 = max(min(b_lo, b_hi) - 2, 0) & ~15;
-                    int e0 = min((max(b_lo, b_hi) + J + 2 + 15) & ~15, p.Wp);
+                    s0 = max(b_lo - 2, 0) & ~15;
+                    int e0 = min((b_hi + J + 2 + 15) & ~15, p.Wp);
                     len = max(e0 - s0, 16);
                     if (s0 + len > p.Wp)
                         s0 = p.Wp - len;
@@ -749,10 +873,10 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
                         atomicOr(p.status, FT_STATUS_WINDOW);
                         len = p.Ws;
                     }
+                    for (int q = 0; q < p.P; ++q)
+                        rq[q * S].start = s0;
                 }
                 start = s0;
-                r.start = s0;
-                rec[slot * S + lane] = r;
             }
             unsigned row_tot;  // bytes of the stage's copies
             if (p.Ws == p.Wp) {
@@ -812,8 +936,25 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
         for (int i = 0; i < NS; ++i)
             part[i] = 0.f;
         int rows_since_fold = 0;
+        // this warp's sky point (q) and f1 value; warps past P * F1 (a batch whose bands
+        // use fewer warps) only keep the pipeline's barriers
+        const int wq = warp / p.F1;
+        const int rows_max = wq < p.P ? S : 0;  // idle warps see empty stages
+        // this warp's compensated sums in tensor memory, cleared for the tile
+        const unsigned tq = tm + (static_cast<unsigned>((warp & 3) * 32) << 16) +
+                            static_cast<unsigned>((warp >> 2) * 16);
+        {
+            float z[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                z[i] = 0.f;
+            tm_st8(tq, z);
+            tm_st8(tq + 8, z);
+            tm_wait_st();
+        }
         // G of this lane's row, loaded one stage ahead
-        const long long *Gf = p.G + static_cast<long long>(min(c.f1g * F + warp, p.n_f1 - 1)) * p.N;
+        const long long *Gf =
+            p.G + static_cast<long long>(min(c.f1g * p.F1 + (warp - wq * p.F1), p.n_f1 - 1)) * p.N;
         long long g_cur = lane < rows_in_stage(p, 0) ? Gf[lane] : 0;
         int slot = 0, use = 0;
         for (int st = 0; st < n_stages; ++st) {
@@ -824,9 +965,9 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
                 ok = false;
                 break;
             }
-            const int nr = rows_in_stage(p, st);
+            const int nr = min(rows_in_stage(p, st), rows_max);
             const unsigned char *rows = buf + slot * L.stage_bytes;
-            const RowRec *rr = rec + slot * S;
+            const RowRec *rr = rec + (slot * p.P + wq) * S;
             // row offset of this warp's track origin and, if the track steps by sign(E)
             // inside the tile, a correction entry (lane = row)
             bool ev = false;
@@ -948,14 +1089,32 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
             g_cur = g_next;
             rows_since_fold += nr;
             if (rows_since_fold >= kFoldRows || st == n_stages - 1) {
+                float h[8], l[8];
+                tm_ld8(tq, h);
+                tm_ld8(tq + 8, l);
+                tm_wait_ld(h, l);
 #pragma unroll
                 for (int i = 0; i < NS; ++i)
-                    fold2sum(hi[i], lo[i], part[i]);
+                    fold2sum(h[i], l[i], part[i]);
+                tm_st8(tq, h);
+                tm_st8(tq + 8, l);
+                tm_wait_st();
                 rows_since_fold = 0;
             }
         }
         if (!ok && lane == 0)
             atomicOr(p.status, FT_STATUS_TIMEOUT);
+        {
+            float h[8], l[8];
+            tm_ld8(tq, h);
+            tm_ld8(tq + 8, l);
+            tm_wait_ld(h, l);
+#pragma unroll
+            for (int i = 0; i < NS; ++i) {
+                hi[i] = h[i];
+                lo[i] = l[i];
+            }
+        }
     }
     // every copy has landed: its slot was consumed, or the producer waited for it above
     if (!__syncthreads_and(ok))
@@ -969,7 +1128,21 @@ template <int MODE, int R, bool WEIGHTED>
 __global__ void __maxnreg__(FT_FAST_MAXNREG) k_eval_fast(const EvalParams p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    fast_tile<MODE, R, WEIGHTED>(p, blockIdx.x, smem, nullptr);
+    __shared__ unsigned s_tm;
+    const unsigned ncols = tm_cols_for((blockDim.x >> 5) - 1);
+    if ((threadIdx.x >> 5) == 0)
+        tm_alloc(&s_tm, ncols);
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    const unsigned tm = s_tm;
+    fast_tile<MODE, R, WEIGHTED>(p, blockIdx.x, smem, nullptr, tm);
+    tm_fence_before();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) {
+        tm_fence_after();
+        tm_dealloc(tm, ncols);
+    }
 }
 
 // Persistent form for many bands: each CTA takes tiles from a global ticket counter over
@@ -1028,10 +1201,18 @@ __global__ void __maxnreg__(FT_FAST_MAXNREG) k_eval_batched(const BatchParams bp
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ long long s_tile;
     __shared__ int s_band;
+    __shared__ unsigned s_tm;
     ft_candidate *tl = reinterpret_cast<ft_candidate *>(smem + bp.list_off);
     ft_candidate *run = tl + bp.lsub_max * bp.k;
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5;
     const long long total = bp.tile_prefix[bp.n_bands];
+    const unsigned ncols = tm_cols_for(nw - 1);
+    if (warp == 0)
+        tm_alloc(&s_tm, ncols);
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    const unsigned tm = s_tm;
     int cur = -1;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -1076,7 +1257,7 @@ __global__ void __maxnreg__(FT_FAST_MAXNREG) k_eval_batched(const BatchParams bp
         if (b < 0)
             break;
         const EvalParams &p = bp.params[b];
-        const bool done = fast_tile<MODE, R, WEIGHTED>(p, tile, smem, tl);
+        const bool done = fast_tile<MODE, R, WEIGHTED>(p, tile, smem, tl, tm);
         __syncthreads();
         if (!done)
             break;  // a bounded wait ran out (status already set): stop taking tiles
@@ -1086,6 +1267,12 @@ __global__ void __maxnreg__(FT_FAST_MAXNREG) k_eval_batched(const BatchParams bp
         for (int lb = lb0 + warp; lb <= lb1; lb += nw)
             warp_merge_lists(run + lb * bp.k, tl + (lb - lb0) * bp.k, bp.k);
         __syncthreads();
+    }
+    tm_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tm_fence_after();
+        tm_dealloc(tm, ncols);
     }
 }
 
@@ -1102,7 +1289,7 @@ constexpr int kMergeThreads = 256;
 // One CTA per sub-band b: gathers the per-CTA lists of every evaluation CTA whose f0 tile
 // meets the sub-band and keeps the k best by (s desc, template index asc).
 __device__ __forceinline__ void merge_subband(const ft_candidate *cand, int k, int lsub_max,
-                                              long long n_sky, int n_f1g, int n_f0t, int J,
+                                              long long n_skyg, int n_f1g, int n_f0t, int J,
                                               int sub, int n_f0, int b, ft_candidate *out)
 {
     __shared__ ft_candidate wl[kMergeThreads / 32][kKmax];
@@ -1110,7 +1297,7 @@ __device__ __forceinline__ void merge_subband(const ft_candidate *cand, int k, i
     const int ft_lo = (b * sub) / J;
     const int ft_hi = (min((b + 1) * sub, n_f0) - 1) / J;
     const int nft = ft_hi - ft_lo + 1;
-    const long long total = n_sky * n_f1g * static_cast<long long>(nft) * k;
+    const long long total = n_skyg * n_f1g * static_cast<long long>(nft) * k;
 
     ft_candidate Lst[kKmax];
     int n = 0;
@@ -1218,11 +1405,11 @@ __device__ __forceinline__ void merge_subband(const ft_candidate *cand, int k, i
 }
 
 __global__ void __launch_bounds__(kMergeThreads) k_topk_merge(const ft_candidate *cand, int k,
-                                                              int lsub_max, long long n_sky,
+                                                              int lsub_max, long long n_skyg,
                                                               int n_f1g, int n_f0t, int J, int sub,
                                                               int n_f0, ft_candidate *out)
 {
-    merge_subband(cand, k, lsub_max, n_sky, n_f1g, n_f0t, J, sub, n_f0, blockIdx.x, out);
+    merge_subband(cand, k, lsub_max, n_skyg, n_f1g, n_f0t, J, sub, n_f0, blockIdx.x, out);
 }
 
 // Merge for the persistent batch: block i handles sub-band j = i - sub_prefix[b] of band b
@@ -1499,10 +1686,17 @@ int row_bytes_of(const ft_band *band)
 
 // ------------------------------------------------------------------ host launchers
 
-int ft_window_bins(const ft_band *band, const ft_bank *bank, int J)
+int ft_window_bins(const ft_band *band, const ft_bank *bank, int J, int P)
 {
     const double spread = std::ceil((bank->f1_hi - bank->f1_lo) * band->tau_absmax * 1.001) + 2.0;
-    long long ws = (static_cast<long long>(J) + static_cast<long long>(spread) + 40 + 31) / 32 * 32;
+    // a sky group moves the track origin by at most (K0 + j) |v| |n_a - n_b| bins between
+    // its points (j < n_f0 + J covers the tile's padding)
+    double sky_spread = 0.0;
+    if (P > 1)
+        sky_spread = std::ceil((static_cast<double>(bank->k0) + bank->n_f0 + J) * band->vmax *
+                               bank->sky_dmax[P] * 1.001) + 2.0;
+    long long ws = (static_cast<long long>(J) + static_cast<long long>(spread) +
+                    static_cast<long long>(sky_spread) + 40 + 31) / 32 * 32;
     // a window that saves under a quarter of the row is not worth one copy per row: the
     // stage is then one contiguous copy of whole rows
     if (4 * ws > 3 * static_cast<long long>(band->Wp))
@@ -1513,17 +1707,40 @@ int ft_window_bins(const ft_band *band, const ft_bank *bank, int J)
 size_t ft_eval_smem_bytes(const ft_band *band, const EvalShape &sh, int k)
 {
     if (sh.fast)
-        return fast_layout(sh.S, sh.F, sh.Ws * 4, sh.J, k > 0, sh.nbuf).total;
+        return fast_layout(sh.S, sh.F, sh.P, sh.Ws * 4, sh.J, k > 0, sh.nbuf).total;
     return smem_layout(sh.S, sh.F, row_bytes_of(band), sh.J, false, k > 0).total;
+}
+
+void ft_sky_grouping(const ft_bank *bank, int max_warps, int *P, int *F1)
+{
+    const int groups = (bank->n_f1 + max_warps - 1) / max_warps;
+    *F1 = (bank->n_f1 + groups - 1) / groups;
+    int q = std::max(1, std::min(kMaxSkyGroup, max_warps / *F1));
+    *P = static_cast<int>(std::min<long long>(q, bank->n_sky));
+}
+
+long long ft_grid_ctas(const ft_bank *bank, const EvalShape &sh)
+{
+    const long long n_skyg = (bank->n_sky + sh.P - 1) / sh.P;
+    const long long n_f1g = (bank->n_f1 + sh.F1 - 1) / sh.F1;
+    const long long n_f0t = (bank->n_f0 + sh.J - 1) / sh.J;
+    return n_skyg * n_f1g * n_f0t;
 }
 
 EvalShape ft_default_shape(const ft_ctx *ctx, const ft_band *band, const ft_bank *bank)
 {
     EvalShape sh;
     sh.fast = bank->window_safe;
-    const int maxw = sh.fast ? kFastMaxWarps : 32;
-    const int groups = (bank->n_f1 + maxw - 1) / maxw;
-    sh.F = (bank->n_f1 + groups - 1) / groups;
+    if (sh.fast) {
+        // up to kFastMaxWarps evaluating warps: the f1 values of one group for P sky
+        // points that share the shared-memory rows
+        ft_sky_grouping(bank, kFastMaxWarps, &sh.P, &sh.F1);
+    } else {
+        const int groups = (bank->n_f1 + 31) / 32;
+        sh.F1 = (bank->n_f1 + groups - 1) / groups;
+        sh.P = 1;
+    }
+    sh.F = sh.P * sh.F1;
     // tile width J = 32 x slots per lane (pairs of slots for 16-bit storage): fewest idle
     // lanes, then the widest tile
     const bool pair = sh.fast && band->dtype != FT_F32;
@@ -1547,7 +1764,7 @@ EvalShape ft_default_shape(const ft_ctx *ctx, const ft_band *band, const ft_bank
     if (sh.fast) {
         // two slots of up to 32 rows (a multiple of 4) of windowed rows in about 80 KB: two
         // CTAs per SM
-        sh.Ws = ft_window_bins(band, bank, sh.J);
+        sh.Ws = ft_window_bins(band, bank, sh.J, sh.P);
         sh.nbuf = 2;
         int S = static_cast<int>((80 * 1024) / (sh.nbuf * static_cast<size_t>(sh.Ws) * 4));
         S = S > 32 ? 32 : S;
@@ -1573,7 +1790,11 @@ int ft_launch_eval(const ft_band *band, const ft_bank *bank, const EvalShape &sh
                    cudaStream_t st)
 {
     p.n_f0t = (bank->n_f0 + sh.J - 1) / sh.J;
-    p.n_f1g = (bank->n_f1 + sh.F - 1) / sh.F;
+    p.n_f1g = (bank->n_f1 + sh.F1 - 1) / sh.F1;
+    p.P = sh.P;
+    p.F1 = sh.F1;
+    p.n_skyg = (bank->n_sky + sh.P - 1) / sh.P;
+    p.sky_order = sh.P > 1 ? bank->d_sky_order : nullptr;
     p.S = sh.S;
     p.n_stages = static_cast<int>((band->N + sh.S - 1) / sh.S);
     p.row_bytes = row_bytes_of(band);
@@ -1582,9 +1803,11 @@ int ft_launch_eval(const ft_band *band, const ft_bank *bank, const EvalShape &sh
     p.srow_bytes = sh.Ws * 4;
     p.nst = sh.nbuf;
     p.row_elems = band->dtype == FT_F32 ? band->Wp : 2 * band->Wp;
-    const long long n_cta = bank->n_sky * p.n_f1g * static_cast<long long>(p.n_f0t);
+    const long long n_cta = ft_grid_ctas(bank, sh);
     if (n_cta <= 0 || n_cta > INT_MAX)
-        FT_FAIL(FT_ERR_RANGE, "eval: grid too large (n_sky * f1 groups * f0 tiles >= 2^31)");
+        FT_FAIL(FT_ERR_RANGE, "eval: grid too large (sky groups * f1 groups * f0 tiles >= 2^31)");
+    if (sh.P > 1 && bank->d_sky_order == nullptr)
+        FT_FAIL(FT_ERR_ARG, "eval: sky groups need the bank's sky order");
     if (sh.fast && !bank->window_safe)
         FT_FAIL(FT_ERR_ARG, "eval: the unchecked kernel needs a bank whose tracks stay in the window");
     const size_t smem = ft_eval_smem_bytes(band, sh, p.cand ? p.k : 0);
@@ -1618,9 +1841,10 @@ int ft_launch_merge(const ft_bank *bank, const EvalShape &sh, const FtCand *cand
                     int lsub_max, ft_candidate *out, cudaStream_t st)
 {
     const int n_f0t = (bank->n_f0 + sh.J - 1) / sh.J;
-    const int n_f1g = (bank->n_f1 + sh.F - 1) / sh.F;
+    const int n_f1g = (bank->n_f1 + sh.F1 - 1) / sh.F1;
+    const long long n_skyg = (bank->n_sky + sh.P - 1) / sh.P;
     k_topk_merge<<<bank->n_sub, kMergeThreads, 0, st>>>(
-        reinterpret_cast<const ft_candidate *>(cand), k, lsub_max, bank->n_sky, n_f1g, n_f0t, sh.J,
+        reinterpret_cast<const ft_candidate *>(cand), k, lsub_max, n_skyg, n_f1g, n_f0t, sh.J,
         bank->sub, bank->n_f0, out);
     FT_CUDA(cudaGetLastError());
     return FT_OK;
@@ -1673,13 +1897,27 @@ int batched_t(const BatchParams &bp, int threads, size_t smem, int *grid_out, bo
                                      cudaSharedmemCarveoutMaxShared));
         configured = smem;
     }
-    int per_sm = 0;
-    FT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
-    if (per_sm < 1)
-        FT_FAIL(FT_ERR_RANGE, "batch: the persistent kernel does not fit on an SM with this shape");
-    int dev = 0, sms = 0;
+    // resident CTAs per SM from the kernel's registers and shared memory and its tensor-
+    // memory columns (the occupancy query does not count the latter and treats a kernel
+    // that allocates tensor memory as one CTA per SM); extra CTAs would only queue
+    int dev = 0, sms = 0, smem_sm = 0, reserved = 0, threads_sm = 0;
     FT_CUDA(cudaGetDevice(&dev));
     FT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    FT_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    FT_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+    FT_CUDA(cudaDeviceGetAttribute(&threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev));
+    cudaFuncAttributes fa;
+    FT_CUDA(cudaFuncGetAttributes(&fa, fn));
+    const int warps = threads / 32;
+    const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;  // allocated per warp
+    const int by_regs = 4 * (16384 / warp_regs) / warps;         // four 16K-register partitions
+    const int by_smem =
+        static_cast<int>(smem_sm / (smem + fa.sharedSizeBytes + static_cast<size_t>(reserved)));
+    const int by_warps = threads_sm / threads;
+    const int by_tmem = 512 / static_cast<int>(tm_cols_for(warps - 1));
+    const int per_sm = std::min(std::min(std::min(by_regs, by_smem), std::min(by_warps, by_tmem)), 32);
+    if (per_sm < 1)
+        FT_FAIL(FT_ERR_RANGE, "batch: the persistent kernel does not fit on an SM with this shape");
     *grid_out = per_sm * sms;
     if (launch) {
         fn<<<*grid_out, threads, smem, st>>>(bp);
@@ -1705,9 +1943,9 @@ int batched_r(int R, const BatchParams &bp, int threads, size_t smem, int *grid,
 
 }  // namespace
 
-size_t ft_batch_tile_smem(int Ws, int S, int F, int J, int nst)
+size_t ft_batch_tile_smem(int Ws, int S, int F, int P, int J, int nst)
 {
-    return fast_layout(S, F, Ws * 4, J, true, nst).total;
+    return fast_layout(S, F, P, Ws * 4, J, true, nst).total;
 }
 
 int ft_batch_row_bytes(const ft_band *band)

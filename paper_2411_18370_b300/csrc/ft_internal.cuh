@@ -76,6 +76,7 @@ struct ft_band {
     bool weighted = false;
     std::vector<double> h_tau, h_vabs;
     double tau_absmax = 0;
+    double vmax = 0;  // largest |v| / c over the SFTs
 };
 
 struct ft_bank {
@@ -89,6 +90,11 @@ struct ft_bank {
     int n_sub = 0;
     double *d_f1 = nullptr;    // [n_f1]
     double *d_sky = nullptr;   // [n_sky][3]
+    // the sky points in an order that keeps neighbours on the sky together, so that a CTA
+    // can search P consecutive ones over the same shared-memory rows; sky_dmax[P] is the
+    // largest distance between two points of one such group of P (P <= kMaxSkyGroup)
+    int *d_sky_order = nullptr;
+    double sky_dmax[5] = {};
     long long *d_G = nullptr;  // [n_f1][N] Q32 f1*tau
     bool window_safe = false;
     double f1_lo = 0, f1_hi = 0;
@@ -118,12 +124,15 @@ struct EvalParams {
     const double *v;
     const float *w;
     const double *sky;
+    const int *sky_order;  // [n_sky] CTA sky groups are runs of P in this order (null: identity)
     const long long *G;  // [n_f1][N]
     const double *f1;    // [n_f1]
     long long K0, k_lo;
     int n_f0, n_f1;
     long long n_sky;
-    int n_f1g, n_f0t;  // f1 groups (warps per CTA = F) and f0 tiles (32*R each)
+    int n_f1g, n_f0t;  // f1 groups (F1 f1 values each) and f0 tiles (32*R each)
+    int P, F1;         // sky points per CTA and f1 values per sky point: warps = P * F1
+    long long n_skyg;  // sky groups: ceil(n_sky / P)
     int S, n_stages;   // SFT rows per stage
     int nst;           // pipeline slots (fast kernel)
     double mu, sigma;
@@ -152,16 +161,27 @@ struct BatchParams {
 // launch helpers implemented in ft_eval.cu
 struct EvalShape {
     int J;       // f0 values per CTA tile (32 x slots per lane)
-    int F;       // warps (f1 values) per CTA
+    int F;       // evaluating warps per CTA: P sky points x F1 f1 values
+    int P;       // sky points per CTA
+    int F1;      // f1 values per CTA
     int S;       // SFT rows per stage
     int nbuf;    // stage buffers
     bool fast;   // shifted-row kernel (bank tracks provably inside the window)
     int Ws;      // fast kernel: bins per shared-memory row window
 };
 
-// Bins per shared-memory row window of the fast kernels for tile width J: the tile, the
-// spread of the track origins over the bank's f1 range, carry and alignment slack.
-int ft_window_bins(const ft_band *band, const ft_bank *bank, int J);
+// Bins per shared-memory row window of the fast kernels for tile width J and P sky points
+// per CTA: the tile, the spread of the track origins over the bank's f1 range and over a
+// sky group, carry and alignment slack.
+int ft_window_bins(const ft_band *band, const ft_bank *bank, int J, int P);
+
+// Sky points per CTA and f1 values per CTA for a bank whose f1 values are split into groups
+// of at most max_warps: P * F1 <= max_warps, P <= kMaxSkyGroup.
+void ft_sky_grouping(const ft_bank *bank, int max_warps, int *P, int *F1);
+constexpr int kMaxSkyGroup = 4;
+
+// CTAs of the evaluation grid: sky groups x f1 groups x f0 tiles.
+long long ft_grid_ctas(const ft_bank *bank, const EvalShape &sh);
 
 size_t ft_eval_smem_bytes(const ft_band *band, const EvalShape &sh, int k);
 EvalShape ft_default_shape(const ft_ctx *ctx, const ft_band *band, const ft_bank *bank);
@@ -177,7 +197,7 @@ int ft_launch_gtable(const double *f1, int n_f1, const double *tau, long long N,
 int ft_launch_track_bins(const ft_band *band, const ft_bank *bank, const long long *tmpl,
                          long long n, int *bins, cudaStream_t st);
 
-size_t ft_batch_tile_smem(int Ws, int S, int F, int J, int nst);
+size_t ft_batch_tile_smem(int Ws, int S, int F, int P, int J, int nst);
 int ft_batch_row_bytes(const ft_band *band);
 int ft_launch_batched(int dtype, bool weighted, int J, int F, const BatchParams &bp, size_t smem,
                       int *grid, bool launch, cudaStream_t st);

@@ -68,9 +68,7 @@ extern "C" int ft_topk_per_band_noalloc(ft_ctx *ctx, const ft_band *band, const 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
     const EvalShape sh = ft_default_shape(ctx, band, bank);
-    const long long n_f0t = (bank->n_f0 + sh.J - 1) / sh.J;
-    const long long n_f1g = (bank->n_f1 + sh.F - 1) / sh.F;
-    const long long n_cta = bank->n_sky * n_f1g * n_f0t;
+    const long long n_cta = ft_grid_ctas(bank, sh);
     const int lsub_max = std::min(bank->n_sub, (sh.J + bank->sub - 1) / bank->sub + 1);
     const size_t cand_bytes = static_cast<size_t>(n_cta) * lsub_max * k * sizeof(ft_candidate);
     const size_t out_bytes = static_cast<size_t>(bank->n_sub) * k * sizeof(ft_candidate);
