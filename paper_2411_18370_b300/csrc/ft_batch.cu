@@ -178,6 +178,7 @@ int build(ft_ctx *ctx, int n, const ft_band *const *bands, const ft_bank *const 
         p.Wp = bd->Wp;
         p.Ws = Ws;
         p.srow_bytes = Ws * 4;
+        ft_encode_rows_map(bd, Ws, S, &p.rows_map, &p.rows_map_ok);  // (never fails: ok = 0 instead)
         p.row_elems = bd->dtype == FT_F32 ? bd->Wp : 2 * bd->Wp;
         p.n_stages = static_cast<int>((bd->N + S - 1) / S);
         p.n_f0t = (bk->n_f0 + J - 1) / J;

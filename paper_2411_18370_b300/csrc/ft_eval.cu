@@ -22,6 +22,10 @@
 // templates of the CTA into a candidate list that k_topk_merge reduces.
 #include "ft_internal.cuh"
 
+#include <cudaTypedefs.h>
+#include <cstring>
+#include <mutex>
+
 #include <climits>
 #include <cmath>
 
@@ -62,6 +66,27 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
     asm volatile(
         "{\n\t.reg .b64 st;\n\t"
         "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
+        : "memory");
+}
+
+// One box of a tiled tensor map (3 or 4 coordinates, innermost first) into shared memory.
+__device__ __forceinline__ void tensor_copy_3d(void *dst, const CUtensorMap *map, int c0, int c1,
+                                               int c2, unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(smem_addr(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tensor_copy_4d(void *dst, const CUtensorMap *map, int c0, int c1,
+                                               int c2, int c3, unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::
+            "r"(smem_addr(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
         : "memory");
 }
 
@@ -832,15 +857,14 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
             const int nr = rows_in_stage(p, st);
             long long alpha = 0;
             int start = 0, len = 0;
+            int b_lo = INT_MAX, b_hi = INT_MIN;  // bins this tile reads in the row (windowed)
+            RowRec *rq = rec + static_cast<size_t>(slot) * p.P * S + lane;
             if (lane < nr) {
                 alpha = static_cast<long long>(st) * S + lane;
                 const double va[3] = {p.v[3 * alpha], p.v[3 * alpha + 1], p.v[3 * alpha + 2]};
                 const float wa = p.w[alpha];
-                RowRec *rq = rec + static_cast<size_t>(slot) * p.P * S + lane;
-                // track terms per sky point, and the bins the tile reads in this row: the
-                // track origin is linear in f1, so per sky point the group's smallest and
-                // largest f1 bound it; plus the tile width and one carry step on each side
-                int b_lo = INT_MAX, b_hi = INT_MIN;
+                // track terms per sky point and, per sky point, the track origins of the
+                // group's smallest and largest f1 (the origin is linear in f1)
                 long long G1 = 0, G2 = 0;
                 if (p.Ws < p.Wp) {
                     G1 = p.G[static_cast<long long>(f_min) * p.N + alpha];
@@ -861,26 +885,45 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
                         b_hi = max(b_hi, max(x1, x2));
                     }
                 }
-                int s0 = 0;
                 len = p.Wp;
-                if (p.Ws < p.Wp) {
-                    s0 = max(b_lo - 2, 0) & ~15;
-                    int e0 = min((b_hi + J + 2 + 15) & ~15, p.Wp);
-                    len = max(e0 - s0, 16);
-                    if (s0 + len > p.Wp)
-                        s0 = p.Wp - len;
-                    if (len > p.Ws) {
-                        atomicOr(p.status, FT_STATUS_WINDOW);
-                        len = p.Ws;
+            }
+            // windowed rows: one window for the whole stage when it covers every row (one
+            // tensor copy of S rows x Ws bins, kept inside the row), else one per row
+            bool whole = false;
+            if (p.Ws < p.Wp) {
+                int wlo = b_lo, whi = b_hi;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    wlo = min(wlo, __shfl_xor_sync(0xffffffffu, wlo, off));
+                    whi = max(whi, __shfl_xor_sync(0xffffffffu, whi, off));
+                }
+                int ts = max(wlo - 2, 0) & ~15;
+                whole = p.rows_map_ok && nr == S && whi + J + 2 - ts <= p.Ws;
+                ts = min(ts, p.Wp - p.Ws);
+                if (lane < nr) {
+                    int s0 = ts;
+                    if (!whole) {
+                        // the row's own window: tile width plus one carry step each side
+                        s0 = max(b_lo - 2, 0) & ~15;
+                        const int e0 = min((b_hi + J + 2 + 15) & ~15, p.Wp);
+                        len = max(e0 - s0, 16);
+                        if (s0 + len > p.Wp)
+                            s0 = p.Wp - len;
+                        if (len > p.Ws) {
+                            atomicOr(p.status, FT_STATUS_WINDOW);
+                            len = p.Ws;
+                        }
                     }
                     for (int q = 0; q < p.P; ++q)
                         rq[q * S].start = s0;
+                    start = s0;
                 }
-                start = s0;
             }
             unsigned row_tot;  // bytes of the stage's copies
             if (p.Ws == p.Wp) {
                 row_tot = static_cast<unsigned>(nr) * static_cast<unsigned>(p.row_bytes);
+            } else if (whole) {
+                row_tot = static_cast<unsigned>(S) * static_cast<unsigned>(p.srow_bytes);
             } else {
                 row_tot = static_cast<unsigned>(len) * 4u;
 #pragma unroll
@@ -891,15 +934,23 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
             __syncwarp();
             if (lane == 0)
                 mbar_arrive_expect_tx(&full[slot], row_tot);
+            unsigned char *stage_buf = buf + slot * L.stage_bytes;
             if (p.Ws == p.Wp) {
                 // whole rows: the stage's rows are contiguous in global and shared memory
                 if (lane == 0)
-                    bulk_copy_g2s(buf + slot * L.stage_bytes,
+                    bulk_copy_g2s(stage_buf,
                                   static_cast<const unsigned char *>(p.power) +
                                       static_cast<size_t>(st) * S * p.row_bytes,
                                   row_tot, &full[slot]);
+            } else if (whole) {
+                if (lane == 0) {
+                    if (PAIR)  // (16-byte group, group, copy, row): both copies of each row
+                        tensor_copy_4d(stage_buf, &p.rows_map, 0, start >> 3, 0, st * S, &full[slot]);
+                    else
+                        tensor_copy_3d(stage_buf, &p.rows_map, 0, start >> 2, st * S, &full[slot]);
+                }
             } else if (lane < nr) {
-                unsigned char *dst = buf + slot * L.stage_bytes + static_cast<size_t>(lane) * p.srow_bytes;
+                unsigned char *dst = stage_buf + static_cast<size_t>(lane) * p.srow_bytes;
                 const unsigned char *src =
                     static_cast<const unsigned char *>(p.power) + static_cast<size_t>(alpha) * p.row_bytes;
                 if (!PAIR) {
@@ -1125,7 +1176,7 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
 
 // One CTA per tile of the (sky, f1 group, f0 tile) grid.
 template <int MODE, int R, bool WEIGHTED>
-__global__ void __maxnreg__(FT_FAST_MAXNREG) k_eval_fast(const EvalParams p)
+__global__ void __maxnreg__(FT_FAST_MAXNREG) k_eval_fast(const __grid_constant__ EvalParams p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned s_tm;
@@ -1686,6 +1737,61 @@ int row_bytes_of(const ft_band *band)
 
 // ------------------------------------------------------------------ host launchers
 
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled_fn()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+}  // namespace
+
+int ft_encode_rows_map(const ft_band *band, int Ws, int S, CUtensorMap *map, int *ok)
+{
+    *ok = 0;
+    std::memset(map, 0, sizeof(*map));
+    const bool pair = band->dtype != FT_F32;
+    // 16-byte groups of four 32-bit words: a window start (a multiple of 16 bins) is a
+    // whole group, so the innermost coordinate is always 0
+    const int groups = pair ? Ws / 8 : Ws / 4;
+    if (Ws >= band->Wp || Ws % 32 != 0 || groups > 256 || S < 1 || S > 256)
+        return FT_OK;
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled_fn();
+    if (fn == nullptr)
+        return FT_OK;
+    const cuuint64_t Wp = static_cast<cuuint64_t>(band->Wp), N = static_cast<cuuint64_t>(band->N);
+    cuuint64_t dims[4], strides[3];
+    cuuint32_t box[4], es[4] = {1, 1, 1, 1};
+    cuuint32_t rank;
+    if (pair) {  // (group, group in copy, copy, row); a row is the even copy then the odd one
+        rank = 4;
+        dims[0] = 4; dims[1] = Wp / 8; dims[2] = 2; dims[3] = N;
+        strides[0] = 16; strides[1] = 2 * Wp; strides[2] = 4 * Wp;
+        box[0] = 4; box[1] = static_cast<cuuint32_t>(groups); box[2] = 2; box[3] = static_cast<cuuint32_t>(S);
+    } else {     // (group, group in row, row)
+        rank = 3;
+        dims[0] = 4; dims[1] = Wp / 4; dims[2] = N;
+        strides[0] = 16; strides[1] = 4 * Wp;
+        box[0] = 4; box[1] = static_cast<cuuint32_t>(groups); box[2] = static_cast<cuuint32_t>(S);
+    }
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, rank, band->d_power, dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r == CUDA_SUCCESS)
+        *ok = 1;
+    return FT_OK;
+}
+
 int ft_window_bins(const ft_band *band, const ft_bank *bank, int J, int P)
 {
     const double spread = std::ceil((bank->f1_hi - bank->f1_lo) * band->tau_absmax * 1.001) + 2.0;
@@ -1803,6 +1909,9 @@ int ft_launch_eval(const ft_band *band, const ft_bank *bank, const EvalShape &sh
     p.srow_bytes = sh.Ws * 4;
     p.nst = sh.nbuf;
     p.row_elems = band->dtype == FT_F32 ? band->Wp : 2 * band->Wp;
+    p.rows_map_ok = 0;
+    if (sh.fast)
+        FT_TRY(ft_encode_rows_map(band, sh.Ws, sh.S, &p.rows_map, &p.rows_map_ok));
     const long long n_cta = ft_grid_ctas(bank, sh);
     if (n_cta <= 0 || n_cta > INT_MAX)
         FT_FAIL(FT_ERR_RANGE, "eval: grid too large (sky groups * f1 groups * f0 tiles >= 2^31)");

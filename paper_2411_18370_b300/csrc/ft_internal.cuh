@@ -1,6 +1,7 @@
 // ft_internal.cuh -- shared internals of the fasttracks CUDA library (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -112,6 +113,11 @@ struct FtCand {
 };
 
 struct EvalParams {
+    // tiled view of the power rows for one-instruction window copies of a whole stage:
+    // 16-byte groups x groups per row copy (x 2 copies for 16-bit storage) x rows, box
+    // (S rows, Ws bins); rows_map_ok = 0 when the launch shape has no such view
+    CUtensorMap rows_map;
+    int rows_map_ok;
     const void *power;
     int row_bytes;  // bytes per stored row (FP32 row, or the two 16-bit copies)
     int Wp;         // bins per stored row copy
@@ -179,6 +185,10 @@ int ft_window_bins(const ft_band *band, const ft_bank *bank, int J, int P);
 // of at most max_warps: P * F1 <= max_warps, P <= kMaxSkyGroup.
 void ft_sky_grouping(const ft_bank *bank, int max_warps, int *P, int *F1);
 constexpr int kMaxSkyGroup = 4;
+
+// Tiled tensor-map view of the band's power rows with a (S rows, Ws bins) box; returns 0
+// and sets *ok = 0 when the shape cannot be expressed (box larger than the hardware allows).
+int ft_encode_rows_map(const ft_band *band, int Ws, int S, CUtensorMap *map, int *ok);
 
 // CTAs of the evaluation grid: sky groups x f1 groups x f0 tiles.
 long long ft_grid_ctas(const ft_bank *bank, const EvalShape &sh);
