@@ -787,7 +787,68 @@ __device__ __forceinline__ long long cross_q32(long long G, int E)
 #ifndef FT_FAST_MAXNREG
 #define FT_FAST_MAXNREG 40
 #endif
-template <int MODE, int R, bool WEIGHTED>
+// Shifted-row sums of one stage for the first RA slot units of each lane (RA <= R; the
+// others belong to f0 values past the band): per row, RA loads of the word holding the
+// lane's bins and their accumulation; the row offsets come four at a time from tabB.
+template <int MODE, int RA, bool WEIGHTED, int NS>
+__device__ __forceinline__ void stage_rows(const unsigned char *lane_rows, const int *tabB,
+                                           const RowRec *rr, int nr, float (&part)[NS])
+{
+    auto row_sum = [&](int off, float wa) {
+        if (MODE == MODE_F32) {
+            const float *q = reinterpret_cast<const float *>(lane_rows) + off;
+#pragma unroll
+            for (int r = 0; r < RA; ++r)
+                part[r] = WEIGHTED ? __fmaf_rn(wa, q[32 * r], part[r]) : __fadd_rn(part[r], q[32 * r]);
+        } else {
+            const unsigned *q = reinterpret_cast<const unsigned *>(lane_rows) + off;
+#pragma unroll
+            for (int r = 0; r < RA; ++r) {
+                const unsigned u = q[32 * r];
+                if (WEIGHTED) {
+                    part[2 * r] = __fmaf_rn(wa, lo_to_float<MODE>(u), part[2 * r]);
+                    part[2 * r + 1] = __fmaf_rn(wa, hi_to_float<MODE>(u), part[2 * r + 1]);
+                } else {
+                    acc_pair<MODE>(part[2 * r], part[2 * r + 1], u);
+                }
+            }
+        }
+    };
+    const int nr4 = nr & ~3;
+    for (int a = 0; a < nr4; a += 4) {
+        const int4 o4 = *reinterpret_cast<const int4 *>(tabB + a);
+        if (WEIGHTED) {
+            row_sum(o4.x, rr[a].w);
+            row_sum(o4.y, rr[a + 1].w);
+            row_sum(o4.z, rr[a + 2].w);
+            row_sum(o4.w, rr[a + 3].w);
+        } else {
+            row_sum(o4.x, 1.f);
+            row_sum(o4.y, 1.f);
+            row_sum(o4.z, 1.f);
+            row_sum(o4.w, 1.f);
+        }
+    }
+    for (int a = nr4; a < nr; ++a)
+        row_sum(tabB[a], WEIGHTED ? rr[a].w : 1.f);
+}
+
+// stage_rows with the slot count ract chosen at run time (uniform over the CTA).
+template <int MODE, int RA, bool WEIGHTED, int NS>
+__device__ __forceinline__ void stage_rows_upto(int ract, const unsigned char *lane_rows,
+                                                const int *tabB, const RowRec *rr, int nr,
+                                                float (&part)[NS])
+{
+    if constexpr (RA > 1) {
+        if (ract < RA) {
+            stage_rows_upto<MODE, RA - 1, WEIGHTED>(ract, lane_rows, tabB, rr, nr, part);
+            return;
+        }
+    }
+    stage_rows<MODE, RA, WEIGHTED>(lane_rows, tabB, rr, nr, part);
+}
+
+template <int MODE, int R, bool WEIGHTED, bool RAGGED>
 __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, unsigned char *smem,
                                           ft_candidate *dst, unsigned tm)
 {
@@ -991,6 +1052,9 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
         // use fewer warps) only keep the pipeline's barriers
         const int wq = warp / p.F1;
         const int rows_max = wq < p.P ? S : 0;  // idle warps see empty stages
+        // slot units (32 f0 values, or 64 for 16-bit pairs) that hold f0 values of the band
+        // (the persistent batch skips the others; one launch per band keeps the full loop)
+        const int ract = RAGGED ? min(R, (min(J, p.n_f0 - c.j0) + (PAIR ? 63 : 31)) / (PAIR ? 64 : 32)) : R;
         // this warp's compensated sums in tensor memory, cleared for the tile
         const unsigned tq = tm + (static_cast<unsigned>((warp & 3) * 32) << 16) +
                             static_cast<unsigned>((warp >> 2) * 16);
@@ -1051,45 +1115,12 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
             }
             const int ne = __popc(m);
             __syncwarp();
-            // main loop: shifted-row sums, four rows' offsets per vector load
-            const unsigned char *lane_rows = rows + 4 * lane;
-            auto row_sum = [&](int off, float wa) {
-                if (MODE == MODE_F32) {
-                    const float *q = reinterpret_cast<const float *>(lane_rows) + off;
-#pragma unroll
-                    for (int r = 0; r < R; ++r)
-                        part[r] = WEIGHTED ? __fmaf_rn(wa, q[32 * r], part[r]) : __fadd_rn(part[r], q[32 * r]);
-                } else {
-                    const unsigned *q = reinterpret_cast<const unsigned *>(lane_rows) + off;
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const unsigned u = q[32 * r];
-                        if (WEIGHTED) {
-                            part[2 * r] = __fmaf_rn(wa, lo_to_float<MODE>(u), part[2 * r]);
-                            part[2 * r + 1] = __fmaf_rn(wa, hi_to_float<MODE>(u), part[2 * r + 1]);
-                        } else {
-                            acc_pair<MODE>(part[2 * r], part[2 * r + 1], u);
-                        }
-                    }
-                }
-            };
-            const int nr4 = nr & ~3;
-            for (int a = 0; a < nr4; a += 4) {
-                const int4 o4 = *reinterpret_cast<const int4 *>(tabB + a);
-                if (WEIGHTED) {
-                    row_sum(o4.x, rr[a].w);
-                    row_sum(o4.y, rr[a + 1].w);
-                    row_sum(o4.z, rr[a + 2].w);
-                    row_sum(o4.w, rr[a + 3].w);
-                } else {
-                    row_sum(o4.x, 1.f);
-                    row_sum(o4.y, 1.f);
-                    row_sum(o4.z, 1.f);
-                    row_sum(o4.w, 1.f);
-                }
-            }
-            for (int a = nr4; a < nr; ++a)
-                row_sum(tabB[a], WEIGHTED ? rr[a].w : 1.f);
+            // main loop over the stage's rows, with as many slots per lane as the tile has
+            // f0 values (a ragged last tile skips the rest)
+            if (RAGGED)
+                stage_rows_upto<MODE, R, WEIGHTED>(ract, rows + 4 * lane, tabB, rr, nr, part);
+            else
+                stage_rows<MODE, R, WEIGHTED>(rows + 4 * lane, tabB, rr, nr, part);
             // corrections for the rows whose bin steps by sign(E) inside the tile: from
             // slot jc on the track reads bin k + sg instead of k (slots past n_f0 are
             // computed and discarded, like in the main loop; their bins stay in the window)
@@ -1103,7 +1134,7 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
                 if (MODE == MODE_F32) {
 #pragma unroll
                     for (int i = 0; i < NS; ++i) {
-                        if (jrel[i] >= jc) {
+                        if (jrel[i] >= jc && i < ract) {
                             const int k = base + jrel[i];
                             const float d = __fsub_rn(read_bin<MODE>(rows, row_words, a, k + sg),
                                                       read_bin<MODE>(rows, row_words, a, k));
@@ -1116,7 +1147,7 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
                     const unsigned *row = reinterpret_cast<const unsigned *>(rows) + a * row_words;
 #pragma unroll
                     for (int i = 0; i < NS; ++i) {
-                        if (jrel[i] >= jc) {
+                        if (jrel[i] >= jc && (i >> 1) < ract) {
                             const int kp = base + jrel[i] + (sg < 0 ? -1 : 0);
                             const unsigned u = row[(kp & 1) * (row_words >> 1) + (kp >> 1)];
                             if (WEIGHTED) {
@@ -1187,7 +1218,7 @@ __global__ void __maxnreg__(FT_FAST_MAXNREG) k_eval_fast(const __grid_constant__
     __syncthreads();
     tm_fence_after();
     const unsigned tm = s_tm;
-    fast_tile<MODE, R, WEIGHTED>(p, blockIdx.x, smem, nullptr, tm);
+    fast_tile<MODE, R, WEIGHTED, false>(p, blockIdx.x, smem, nullptr, tm);
     tm_fence_before();
     __syncthreads();
     if ((threadIdx.x >> 5) == 0) {
@@ -1308,7 +1339,7 @@ __global__ void __maxnreg__(FT_FAST_MAXNREG) k_eval_batched(const BatchParams bp
         if (b < 0)
             break;
         const EvalParams &p = bp.params[b];
-        const bool done = fast_tile<MODE, R, WEIGHTED>(p, tile, smem, tl, tm);
+        const bool done = fast_tile<MODE, R, WEIGHTED, true>(p, tile, smem, tl, tm);
         __syncthreads();
         if (!done)
             break;  // a bounded wait ran out (status already set): stop taking tiles
