@@ -130,26 +130,49 @@ def time_steps(fn, steps, warmup, stream, flush):
 
 
 def cpu_baseline(sfts, bank, target_s, seed=7):
-    """The CPU FP64 oracle, as it stands, on a bounded template sample of the same workload."""
+    """The CPU FP64 oracle, as it stands, on a bounded template sample of the same workload,
+    sized to run about target_s seconds."""
     import oracle
 
     g = np.random.default_rng(seed)
-    n = 256
-    t0 = time.perf_counter()
-    samp = g.choice(bank.n_templates, n, replace=False)
-    s_or, _ = oracle.statistic(sfts, bank, samp)
-    dt = time.perf_counter() - t0
-    if dt < target_s:
-        n2 = int(min(bank.n_templates, max(n, n * target_s / max(dt, 1e-3))))
-        samp = g.choice(bank.n_templates, n2, replace=False)
+    n = 4096
+    for _ in range(3):
+        samp = g.choice(bank.n_templates, min(n, bank.n_templates), replace=False)
         t0 = time.perf_counter()
         s_or, _ = oracle.statistic(sfts, bank, samp)
         dt = time.perf_counter() - t0
+        if dt >= 0.66 * target_s or len(samp) == bank.n_templates:
+            break
+        n = int(len(samp) * target_s / max(dt, 1e-3))
     evals = len(samp) * sfts.n_total
     return {"value": evals / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{len(samp)} random templates of the same bank x all {sfts.n_total} SFTs "
                       f"({evals:.3g} evals, {dt:.1f} s, FP64, OpenMP over templates)",
             "seconds": dt}, samp, s_or
+
+
+def profiled_traffic(dtype):
+    """DRAM bytes (read + write) per launch of the evaluation kernel from the committed ncu
+    capture of this workload, or None when there is none for this storage type or the
+    kernel source changed since it was taken."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", f"k_eval_fast_search_config1_{dtype}_dram.md")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line and not line.startswith((" ", "#", "`")):
+            k, v = line.split(":", 1)
+            fields[k.strip()] = v.strip()
+    src = os.path.join(ROOT, "paper_2411_18370_b300", "csrc", "ft_eval.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if fields.get("kernel source sha256 prefix") != sha:
+        return None
+    try:
+        return float(fields["dram bytes per launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def rel_error(s_gpu, s_or):
@@ -420,7 +443,7 @@ def main():
         "bytes_per_eval": esize,
         "frac_at_sampled_clock": (achieved_gbs / (148 * SMEM_BYTES_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e9)
                                   if sm_mhz else None),
-        "traffic": None,
+        "traffic": profiled_traffic(args.dtype),
     }
 
     out = {
