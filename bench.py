@@ -260,6 +260,7 @@ def run_batch(args):
         evals += bank.n_templates * N
     stream = torch.cuda.current_stream()
     k = args.k
+    roof_e, _ = ft.gather_roof(ctx, args.dtype)
     cands = [torch.empty(b.n_subbands * k * 16, dtype=torch.uint8, device="cuda") for b in banks]
 
     def loop_step():
@@ -300,6 +301,8 @@ def run_batch(args):
         "per_band_loop": {"value": evals / (ml / 1e3), "ms_per_step": ml,
                           "gpu_launches_per_step": 2 * len(bands)},
         "speedup_vs_loop": ml / mb, "subbands_with_different_sets": differ,
+        "measured_gather_roof": {"evals_per_s": roof_e, "frac": (evals / (mb / 1e3)) / roof_e,
+                                 "entry": "ft_gather_roof", "storage": args.dtype},
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -446,6 +449,8 @@ def main():
         "traffic": profiled_traffic(args.dtype),
     }
 
+    roof_e, roof_c = ft.gather_roof(ctx, args.dtype)
+    roof32_e, _ = ft.gather_roof(ctx, "f32")
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": chosen["mean_ms_max"], "higher_is_better": True,
@@ -455,7 +460,13 @@ def main():
         "gpu_launches": 2 * args.steps,
         "clocks": chosen["clocks"],
         "plain_fp32": {"value": ws * evals / (runs["f32"]["mean_ms_max"] / 1e3),
-                       "ms_per_step": runs["f32"]["mean_ms_max"], "clocks": runs["f32"]["clocks"]},
+                       "ms_per_step": runs["f32"]["mean_ms_max"], "clocks": runs["f32"]["clocks"],
+                       "frac_of_measured_gather_roof": (evals / (runs["f32"]["mean_ms_max"] / 1e3)) / roof32_e},
+        # the bare inner loop (rows resident in shared memory, no tables or pipeline), run in
+        # the same process: the ceiling this kernel's design can reach on this GPU
+        "measured_gather_roof": {"evals_per_s": roof_e, "evals_per_clk_per_sm": roof_c,
+                                 "frac": (evals / (chosen["mean_ms"] / 1e3)) / roof_e,
+                                 "entry": "ft_gather_roof", "storage": args.dtype},
     }
 
     if rank == 0 and not args.no_cpu_baseline:

@@ -307,6 +307,15 @@ typedef struct {
 /* Set (tune != NULL) or clear (NULL) the context-wide launch-shape override. */
 FT_API int ft_set_tune(ft_ctx *ctx, const ft_tune *tune);
 
+/* Measured ceiling of the gather-accumulate (a benchmark aid, not part of the search): the
+ * evaluation kernel's inner loop alone, with rows resident in shared memory, four row
+ * offsets per vector load and one conflict-free 32-bit load per lane per 32 (FP32, dtype
+ * FT_F32) or 64 (16-bit pairs, FT_F16 / FT_BF16) f0 values, accumulated in FP32; 2 CTAs of
+ * 640 threads per SM, about 1.5e11 evaluations.  Writes evaluations per second (CUDA events)
+ * and per clock per SM (clock64 of the slowest CTA).  Synchronises the device.  Errors:
+ * FT_ERR_ARG (null pointer, bad dtype), FT_ERR_OOM, FT_ERR_CUDA. */
+FT_API int ft_gather_roof(ft_ctx *ctx, int dtype, double *evals_per_s, double *evals_per_clk_sm);
+
 /* ----------------------------------------------------------------------------- batches --
  * Many bands of uneven width and sky density searched by one persistent launch (the
  * batching pattern; each band's statistic and candidates are those of ft_topk_per_band).

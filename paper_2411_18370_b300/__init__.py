@@ -90,6 +90,7 @@ def lib():
             "ft_topk_per_band": (_I, [_P, _P, _P, _I, _P, _I, _P]),
             "ft_track_bins": (_I, [_P, _P, _P, _P, _I64, _P, _I, _P]),
             "ft_set_tune": (_I, [_P, _P]),
+            "ft_gather_roof": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
             "ft_topk_per_band_noalloc": (_I, [_P, _P, _P, _I, _P, _I, _P]),
             "ft_batch_create": (_I, [_P, _I, _P, _P, _I, _P, _P, ctypes.POINTER(_P)]),
             "ft_batch_run": (_I, [_P, _P, _I, _P]),
@@ -220,6 +221,15 @@ class Bank:
 
 class _Tune(ctypes.Structure):
     _fields_ = [("rows_per_stage", ctypes.c_int), ("stages", ctypes.c_int), ("tile_f0", ctypes.c_int)]
+
+
+def gather_roof(ctx, dtype="f16"):
+    """ft_gather_roof: measured evaluations/s and evaluations/clock/SM of the bare
+    gather-accumulate loop for a storage type."""
+    e = ctypes.c_double()
+    c = ctypes.c_double()
+    _check(lib().ft_gather_roof(ctx.handle, DTYPES[dtype], ctypes.byref(e), ctypes.byref(c)))
+    return e.value, c.value
 
 
 def set_tune(ctx, rows_per_stage=0, stages=0, tile_f0=0):

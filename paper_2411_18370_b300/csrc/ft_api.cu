@@ -220,6 +220,14 @@ int ft_set_tune(ft_ctx *ctx, const ft_tune *tune)
     return FT_OK;
 }
 
+int ft_gather_roof(ft_ctx *ctx, int dtype, double *evals_per_s, double *evals_per_clk_sm)
+{
+    if (!ctx || !evals_per_s || !evals_per_clk_sm)
+        FT_FAIL(FT_ERR_ARG, "gather_roof: null argument");
+    DeviceGuard g(ctx->device);
+    return ft_run_gather_roof(dtype, ctx->sm_count, evals_per_s, evals_per_clk_sm);
+}
+
 int ft_check_status(ft_ctx *ctx, void *stream)
 {
     if (!ctx)

@@ -26,6 +26,7 @@
 #include <cstring>
 #include <mutex>
 
+#include <algorithm>
 #include <climits>
 #include <cmath>
 
@@ -2119,4 +2120,131 @@ int ft_launch_merge_persist(const ft_candidate *scr, int n_ctas, int n_bands, in
                                                                 sub_prefix, out);
     FT_CUDA(cudaGetLastError());
     return FT_OK;
+}
+
+// ------------------------------------------------------------------ measured gather roof
+//
+// The evaluation kernel's inner loop with nothing around it: rows resident in shared memory,
+// four row offsets per vector load, one conflict-free 32-bit load per lane per slot unit and
+// its FP32 accumulation (FADD for FP32 rows, the mixed-precision FMA pair for 16-bit pairs),
+// 2 CTAs of 20 warps per SM.  No track tables, no pipeline, no corrections: the throughput
+// it reaches is the ceiling of the gather-accumulate on this GPU.
+
+namespace {
+
+constexpr int kRoofRowWords = 320;  // words per resident row
+constexpr int kRoofRows = 64;       // rows (and offsets) per pass
+constexpr int kRoofThreads = 640;
+constexpr int kRoofUnits = 3;       // slot units per lane: 3 x 64 bins (pairs), 6 x 32 (FP32)
+
+template <int MODE>
+__global__ void __launch_bounds__(kRoofThreads, 2)
+    k_gather_roof(int iters, float *out, long long *clk)
+{
+    constexpr bool PAIR = MODE != MODE_F32;
+    constexpr int WORDS = PAIR ? kRoofUnits : 2 * kRoofUnits;  // loads per lane per row
+    extern __shared__ __align__(16) unsigned roof_smem[];
+    unsigned *rows = roof_smem;
+    int *tab = reinterpret_cast<int *>(roof_smem + kRoofRows * kRoofRowWords);
+    const unsigned one = MODE == MODE_F32 ? 0x3F800000u : MODE == MODE_F16 ? 0x3C003C00u : 0x3F803F80u;
+    for (int i = threadIdx.x; i < kRoofRows * kRoofRowWords; i += blockDim.x)
+        rows[i] = one;
+    // row a starts at a word offset in [0, 128): the last word a lane reads is
+    // 127 + 31 + 32 (WORDS - 1) <= 318 < kRoofRowWords
+    for (int a = threadIdx.x; a < kRoofRows; a += blockDim.x)
+        tab[a] = a * kRoofRowWords + (a * 37) % 128;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    float acc[2 * kRoofUnits];
+#pragma unroll
+    for (int i = 0; i < 2 * kRoofUnits; ++i)
+        acc[i] = 0.f;
+    const unsigned *lr = rows + lane;
+    const long long t0 = clock64();
+    for (int it = 0; it < iters; ++it) {
+        for (int a = 0; a < kRoofRows; a += 4) {
+            const int4 o4 = *reinterpret_cast<const int4 *>(tab + a);
+            const int oo[4] = {o4.x, o4.y, o4.z, o4.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const unsigned *q = lr + oo[u];
+#pragma unroll
+                for (int r = 0; r < WORDS; ++r) {
+                    if (PAIR)
+                        acc_pair<MODE>(acc[2 * r], acc[2 * r + 1], q[32 * r]);
+                    else
+                        acc[r] = __fadd_rn(acc[r], __uint_as_float(q[32 * r]));
+                }
+            }
+        }
+    }
+    const long long t1 = clock64();
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < 2 * kRoofUnits; ++i)
+        s += acc[i];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+    if (threadIdx.x == 0)
+        clk[blockIdx.x] = t1 - t0;
+}
+
+}  // namespace
+
+int ft_run_gather_roof(int dtype, int sm_count, double *evals_per_s, double *evals_per_clk_sm)
+{
+    const int blocks = 2 * sm_count, iters = 2000;
+    const size_t smem = (kRoofRows * kRoofRowWords + kRoofRows) * sizeof(unsigned);
+    auto launch = [&](auto fn, float *out, long long *clk, int it) -> int {
+        FT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        FT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared));
+        fn<<<blocks, kRoofThreads, smem>>>(it, out, clk);
+        FT_CUDA(cudaGetLastError());
+        return FT_OK;
+    };
+    float *out = nullptr;
+    long long *clk = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = FT_OK;
+    if (cudaMalloc(&out, static_cast<size_t>(blocks) * kRoofThreads * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&clk, static_cast<size_t>(blocks) * sizeof(long long)) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        rc = FT_ERR_OOM;
+    } else {
+        auto run = [&](int it) -> int {
+            switch (dtype) {
+            case FT_F32: return launch(k_gather_roof<MODE_F32>, out, clk, it);
+            case FT_F16: return launch(k_gather_roof<MODE_F16>, out, clk, it);
+            case FT_BF16: return launch(k_gather_roof<MODE_BF16>, out, clk, it);
+            default: FT_FAIL(FT_ERR_ARG, "gather_roof: bad dtype");
+            }
+        };
+        float ms = 0.f;
+        if ((rc = run(20)) == FT_OK && cudaEventRecord(e0) == cudaSuccess && (rc = run(iters)) == FT_OK &&
+            cudaEventRecord(e1) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+            std::vector<long long> c(blocks);
+            if (cudaMemcpy(c.data(), clk, blocks * sizeof(long long), cudaMemcpyDeviceToHost) == cudaSuccess) {
+                const double per_thread = static_cast<double>(iters) * kRoofRows * 2 * kRoofUnits;
+                const long long mx = *std::max_element(c.begin(), c.end());
+                *evals_per_s = per_thread * kRoofThreads * blocks / (ms * 1e-3);
+                *evals_per_clk_sm = per_thread * kRoofThreads * 2 / static_cast<double>(mx);
+            } else {
+                rc = FT_ERR_CUDA;
+            }
+        } else if (rc == FT_OK) {
+            rc = FT_ERR_CUDA;
+        }
+    }
+    cudaFree(out);
+    cudaFree(clk);
+    if (e0)
+        cudaEventDestroy(e0);
+    if (e1)
+        cudaEventDestroy(e1);
+    if (rc == FT_ERR_OOM)
+        FT_FAIL(FT_ERR_OOM, "gather_roof: allocation failed");
+    if (rc == FT_ERR_CUDA)
+        FT_FAIL(FT_ERR_CUDA, "gather_roof: CUDA runtime error");
+    return rc;
 }

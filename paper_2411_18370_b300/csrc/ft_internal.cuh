@@ -190,6 +190,9 @@ constexpr int kMaxSkyGroup = 4;
 // and sets *ok = 0 when the shape cannot be expressed (box larger than the hardware allows).
 int ft_encode_rows_map(const ft_band *band, int Ws, int S, CUtensorMap *map, int *ok);
 
+// Runs the gather-roof microbenchmark on the current device (see ft_gather_roof).
+int ft_run_gather_roof(int dtype, int sm_count, double *evals_per_s, double *evals_per_clk_sm);
+
 // CTAs of the evaluation grid: sky groups x f1 groups x f0 tiles.
 long long ft_grid_ctas(const ft_bank *bank, const EvalShape &sh);
 

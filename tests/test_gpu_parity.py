@@ -375,3 +375,13 @@ def test_error_paths(ctx):
     # the context stays usable after errors
     s, _, _ = H.eval_host(ctx, band, bk, bank.n_templates)
     assert np.all(np.isfinite(s))
+
+
+def test_gather_roof_microbenchmark(ctx):
+    """The measured ceiling of the inner loop runs and is plausible: positive, 16-bit pairs
+    above FP32 per evaluation, and below the shared-memory bandwidth bound (128 B per clock
+    per SM = 32 FP32 or 64 16-bit evaluations)."""
+    e32, c32 = ft.gather_roof(ctx, "f32")
+    e16, c16 = ft.gather_roof(ctx, "f16")
+    assert 0 < c32 <= 32.5 and 0 < c16 <= 64.5
+    assert e16 > e32 > 0
