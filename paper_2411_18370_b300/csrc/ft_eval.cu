@@ -851,7 +851,7 @@ __device__ __forceinline__ void stage_rows_upto(int ract, const unsigned char *l
 
 template <int MODE, int R, bool WEIGHTED, bool RAGGED>
 __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, unsigned char *smem,
-                                          ft_candidate *dst, unsigned tm)
+                                          ft_candidate *dst, unsigned tm, const CUtensorMap *rows_map)
 {
     constexpr bool PAIR = MODE != MODE_F32;
     constexpr int NS = PAIR ? 2 * R : R;  // accumulator slots per thread
@@ -1007,9 +1007,9 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
             } else if (whole) {
                 if (lane == 0) {
                     if (PAIR)  // (16-byte group, group, copy, row): both copies of each row
-                        tensor_copy_4d(stage_buf, &p.rows_map, 0, start >> 3, 0, st * S, &full[slot]);
+                        tensor_copy_4d(stage_buf, rows_map, 0, start >> 3, 0, st * S, &full[slot]);
                     else
-                        tensor_copy_3d(stage_buf, &p.rows_map, 0, start >> 2, st * S, &full[slot]);
+                        tensor_copy_3d(stage_buf, rows_map, 0, start >> 2, st * S, &full[slot]);
                 }
             } else if (lane < nr) {
                 unsigned char *dst = stage_buf + static_cast<size_t>(lane) * p.srow_bytes;
@@ -1219,7 +1219,7 @@ __global__ void __maxnreg__(FT_FAST_MAXNREG) k_eval_fast(const __grid_constant__
     __syncthreads();
     tm_fence_after();
     const unsigned tm = s_tm;
-    fast_tile<MODE, R, WEIGHTED, false>(p, blockIdx.x, smem, nullptr, tm);
+    fast_tile<MODE, R, WEIGHTED, false>(p, blockIdx.x, smem, nullptr, tm, &p.rows_map);
     tm_fence_before();
     __syncthreads();
     if ((threadIdx.x >> 5) == 0) {
@@ -1285,6 +1285,7 @@ __global__ void __maxnreg__(FT_FAST_MAXNREG) k_eval_batched(const BatchParams bp
     __shared__ long long s_tile;
     __shared__ int s_band;
     __shared__ unsigned s_tm;
+    __shared__ EvalParams s_params;
     ft_candidate *tl = reinterpret_cast<ft_candidate *>(smem + bp.list_off);
     ft_candidate *run = tl + bp.lsub_max * bp.k;
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5;
@@ -1333,14 +1334,21 @@ __global__ void __maxnreg__(FT_FAST_MAXNREG) k_eval_batched(const BatchParams bp
                     run[i].s = -INFINITY;
                     run[i].z = 0.f;
                 }
+                // the band's parameters in shared memory: the tile code reads them all the
+                // time, and from global memory every read would go through the small L1
+                const unsigned *src = reinterpret_cast<const unsigned *>(bp.params + b);
+                unsigned *dstw = reinterpret_cast<unsigned *>(&s_params);
+                for (int i = threadIdx.x; i < static_cast<int>(sizeof(EvalParams) / 4); i += blockDim.x)
+                    dstw[i] = src[i];
             }
             __syncthreads();
             cur = b;
         }
         if (b < 0)
             break;
-        const EvalParams &p = bp.params[b];
-        const bool done = fast_tile<MODE, R, WEIGHTED, true>(p, tile, smem, tl, tm);
+        const EvalParams &p = s_params;
+        // (the tensor map is used from global memory, where a copy can be read from)
+        const bool done = fast_tile<MODE, R, WEIGHTED, true>(p, tile, smem, tl, tm, &bp.params[b].rows_map);
         __syncthreads();
         if (!done)
             break;  // a bounded wait ran out (status already set): stop taking tiles
