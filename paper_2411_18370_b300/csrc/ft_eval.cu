@@ -816,6 +816,7 @@ __device__ __forceinline__ void stage_rows(const unsigned char *lane_rows, const
         }
     };
     const int nr4 = nr & ~3;
+#pragma unroll 2
     for (int a = 0; a < nr4; a += 4) {
         const int4 o4 = *reinterpret_cast<const int4 *>(tabB + a);
         if (WEIGHTED) {
@@ -1071,17 +1072,21 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
         // G of this lane's row, loaded one stage ahead
         const long long *Gf =
             p.G + static_cast<long long>(min(c.f1g * p.F1 + (warp - wq * p.F1), p.n_f1 - 1)) * p.N;
-        long long g_cur = lane < rows_in_stage(p, 0) ? Gf[lane] : 0;
+        // rows of the last stage (every other stage has S)
+        const int last_nr = static_cast<int>(p.N - static_cast<long long>(n_stages - 1) * S);
+        long long g_cur = lane < (n_stages == 1 ? last_nr : S) ? Gf[lane] : 0;
+        const long long *gp = Gf + S + lane;  // this lane's G of the next stage
         int slot = 0, use = 0;
         for (int st = 0; st < n_stages; ++st) {
             long long g_next = 0;
-            if (st + 1 < n_stages && lane < rows_in_stage(p, st + 1))
-                g_next = Gf[static_cast<long long>(st + 1) * S + lane];
+            if (st + 1 < n_stages && lane < (st + 1 == n_stages - 1 ? last_nr : S))
+                g_next = *gp;
+            gp += S;
             if (!mbar_wait_bounded(&full[slot], use & 1)) {
                 ok = false;
                 break;
             }
-            const int nr = min(rows_in_stage(p, st), rows_max);
+            const int nr = min(st == n_stages - 1 ? last_nr : S, rows_max);
             const unsigned char *rows = buf + slot * L.stage_bytes;
             const RowRec *rr = rec + (slot * p.P + wq) * S;
             // row offset of this warp's track origin and, if the track steps by sign(E)
