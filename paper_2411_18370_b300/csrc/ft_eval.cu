@@ -651,7 +651,7 @@ __device__ __forceinline__ float read_bin(const unsigned char *rows, int row_wor
 // the window start);
 // per evaluating warp its own row offsets and correction list for the slot it works on.
 constexpr int kMaxStages = 4;
-constexpr int kFoldRows = 128;  // FP32 partials cover at most this many SFT rows
+constexpr int kFoldRows = 256;  // FP32 partials cover at most this many SFT rows
 
 // ------------------------------------------------------------------ tensor memory
 //
