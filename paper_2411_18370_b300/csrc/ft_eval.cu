@@ -749,8 +749,8 @@ __host__ __device__ inline FastLayout fast_layout(int S, int F, int P, int row_b
     o = align_up(o + kMaxStages * 8, 16);
     L.skyn = o;  // unit vectors of the tile's sky points
     o = align_up(o + (size_t)kMaxSkyGroup * 3 * sizeof(double), 16);
-    L.rec = o;   // per slot, sky point and row
-    o = align_up(o + (size_t)nst * P * S * sizeof(RowRec), 16);
+    L.rec = o;   // per stage (a ring of nst + 1), sky point and row
+    o = align_up(o + (size_t)(nst + 1) * P * S * sizeof(RowRec), 16);
     L.tabB = o;
     o = align_up(o + (size_t)F * S * sizeof(int), 16);
     L.evA = o;
@@ -911,17 +911,17 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
             if (p.f1[f] > p.f1[f_max])
                 f_max = f;
         }
-        int st = 0, slot = 0, use = 0;
-        for (; st < n_stages; ++st) {
-            if (use > 0 && !mbar_wait_bounded(&empty[slot], (use - 1) & 1)) {
-                ok = false;
-                break;
-            }
+        // The row records of stage st go to a ring of nst + 1 entries: the entry of stage
+        // st - nst - 1 is free once the slot of stage st - 1 was released, so the records
+        // (FP64 track terms, windows) are computed before waiting for the data slot, while
+        // the evaluating warps still work on earlier stages.
+        int st = 0, slot = 0, use = 0, rs = 0;  // rs = st mod (nst + 1)
+        for (; st < n_stages; ++st, rs = rs == nst ? 0 : rs + 1) {
             const int nr = rows_in_stage(p, st);
             long long alpha = 0;
             int start = 0, len = 0;
             int b_lo = INT_MAX, b_hi = INT_MIN;  // bins this tile reads in the row (windowed)
-            RowRec *rq = rec + static_cast<size_t>(slot) * p.P * S + lane;
+            RowRec *rq = rec + static_cast<size_t>(rs) * p.P * S + lane;
             if (lane < nr) {
                 alpha = static_cast<long long>(st) * S + lane;
                 const double va[3] = {p.v[3 * alpha], p.v[3 * alpha + 1], p.v[3 * alpha + 2]};
@@ -992,6 +992,10 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1)
                     row_tot += __shfl_xor_sync(0xffffffffu, row_tot, off);
+            }
+            if (use > 0 && !mbar_wait_bounded(&empty[slot], (use - 1) & 1)) {
+                ok = false;
+                break;
             }
             // every lane's record is written before lane 0's arrival releases the slot
             __syncwarp();
@@ -1076,8 +1080,8 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
         const int last_nr = static_cast<int>(p.N - static_cast<long long>(n_stages - 1) * S);
         long long g_cur = lane < (n_stages == 1 ? last_nr : S) ? Gf[lane] : 0;
         const long long *gp = Gf + S + lane;  // this lane's G of the next stage
-        int slot = 0, use = 0;
-        for (int st = 0; st < n_stages; ++st) {
+        int slot = 0, use = 0, rs = 0;  // rs = st mod (nst + 1): the stage's record entry
+        for (int st = 0; st < n_stages; ++st, rs = rs == nst ? 0 : rs + 1) {
             long long g_next = 0;
             if (st + 1 < n_stages && lane < (st + 1 == n_stages - 1 ? last_nr : S))
                 g_next = *gp;
@@ -1088,7 +1092,7 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
             }
             const int nr = min(st == n_stages - 1 ? last_nr : S, rows_max);
             const unsigned char *rows = buf + slot * L.stage_bytes;
-            const RowRec *rr = rec + (slot * p.P + wq) * S;
+            const RowRec *rr = rec + (rs * p.P + wq) * S;
             // row offset of this warp's track origin and, if the track steps by sign(E)
             // inside the tile, a correction entry (lane = row)
             bool ev = false;
