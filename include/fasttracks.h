@@ -258,6 +258,19 @@ FT_API int ft_run_injections(ft_ctx *ctx, const ft_band *band, const ft_bank *ba
                              const double *det_tensor, const ft_inj_desc *desc, int64_t n,
                              const ft_injection *inj, ft_inj_result *out, void *stream);
 
+/* Semi-analytic sensitivity inputs (Sec. V.A): the signal-dependent two of the four numbers
+ * q = {mu_G, sigma_G, rho^2_1, rho^2_2} that fix the distribution of s for a population
+ * draw.  For draw i of pop (direction n, cos iota, psi; h0 and f0, f1 ignored):
+ *   rho1[i] = sum_alpha w_alpha rho^2_alpha(h0 = 1),  rho2[i] = sum_alpha w_alpha^2 rho^2_alpha(h0 = 1),
+ * with rho^2_alpha the per-SFT normalised signal power of ft_run_injections (same antenna
+ * patterns, polarisations in quadrature, the band's S_n and weights); for amplitude h0 both
+ * scale by h0^2.  mu_G and sigma_G are the band's (ft_band_info).  det_tensor: host
+ * [N_SFT][6]; pop, rho1, rho2: host arrays of n.  Sums in FP64 in a fixed order (one CTA
+ * per draw).  Synchronises `stream`.  Errors: FT_ERR_ARG (null pointer, band without S_n,
+ * bad draw), FT_ERR_OOM, FT_ERR_CUDA. */
+FT_API int ft_pdet_q(ft_ctx *ctx, const ft_band *band, const double *det_tensor, int64_t n,
+                     const ft_injection *pop, double *rho1, double *rho2, void *stream);
+
 /* ----------------------------------------------------------------------------- surrogate --
  * A learned model of the detection probability p_det (Sec. V, Eqs. (pdet_abstract),
  * (simple_eq)) trained on injection-recovery outcomes: a 4-layer perceptron

@@ -99,6 +99,10 @@ def load_library(path):
     L.or_inj_power.restype = ctypes.c_double
     L.or_inj_power.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64,
                                ctypes.c_double, ctypes.c_double]
+    L.or_pdet_q.restype = None
+    L.or_pdet_q.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                            ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                            ctypes.c_void_p]
     L.or_injections.restype = None
     L.or_injections.argtypes = [ctypes.POINTER(_InjProblem), ctypes.c_void_p, ctypes.c_int64,
                                 ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
@@ -290,3 +294,18 @@ def injections(sfts, bank, D, inj, first_id, seed, K=64, half_f0=2, H=160, noise
                         int(half_f0), int(H), float(noise_scale), mz.ctypes.data, am.ctypes.data,
                         oob.ctypes.data)
     return mz, am, oob
+
+
+def pdet_q(s_n, t_sft, D, inj, w=None):
+    """Sec. V.A q numbers per population draw: (sum w rho^2, sum w^2 rho^2) at h0 = 1."""
+    sn = _c(s_n, np.float64)
+    Dv = _c(D, np.float64)
+    wv = None if w is None else _c(w, np.float64)
+    draws = np.ascontiguousarray(np.column_stack([inj["cosi"], inj["psi"], inj["n"]]), np.float64)
+    n = len(draws)
+    r1 = np.empty(n, np.float64)
+    r2 = np.empty(n, np.float64)
+    lib().or_pdet_q(len(sn), float(t_sft), sn.ctypes.data, Dv.ctypes.data,
+                    None if wv is None else wv.ctypes.data, n, draws.ctypes.data,
+                    r1.ctypes.data, r2.ctypes.data)
+    return r1, r2

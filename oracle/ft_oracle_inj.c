@@ -286,3 +286,26 @@ void or_injections(const or_inj_problem *p, const or_inj *inj, int64_t n, uint64
         or_injection(p, inj + r, first_id + (uint64_t)r, seed, K, half_f0, H, noise_scale,
                      max_z + r, argmax + r, oob + r);
 }
+
+/* ---------------------------------------------------------------- semi-analytic q */
+
+/* Sec. V.A ("Simulating detection statistics"): for each population draw the two
+ * signal-dependent numbers of q, rho1 = sum_alpha w_alpha rho^2_alpha and
+ * rho2 = sum_alpha w_alpha^2 rho^2_alpha, with rho^2 of one SFT at h0 = 1 (or_rho2).
+ * draws: [n][5] = (cos iota, psi, n_x, n_y, n_z); w may be NULL (all 1). */
+void or_pdet_q(int64_t n_sft, double t_sft, const double *s_n, const double *D, const double *w,
+               int64_t n, const double *draws, double *rho1, double *rho2)
+{
+    for (int64_t i = 0; i < n; i++) {
+        const double *d = draws + 5 * i;
+        double s1 = 0.0, s2 = 0.0;
+        for (int64_t a = 0; a < n_sft; a++) {
+            double r = or_rho2(D + 6 * a, d + 2, 1.0, d[0], d[1], t_sft, s_n[a]);
+            double wa = w ? w[a] : 1.0;
+            s1 += wa * r;
+            s2 += wa * wa * r;
+        }
+        rho1[i] = s1;
+        rho2[i] = s2;
+    }
+}

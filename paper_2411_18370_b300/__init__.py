@@ -91,6 +91,7 @@ def lib():
             "ft_track_bins": (_I, [_P, _P, _P, _P, _I64, _P, _I, _P]),
             "ft_set_tune": (_I, [_P, _P]),
             "ft_gather_roof": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+            "ft_pdet_q": (_I, [_P, _P, _P, _I64, _P, _P, _P, _P]),
             "ft_topk_per_band_noalloc": (_I, [_P, _P, _P, _I, _P, _I, _P]),
             "ft_batch_create": (_I, [_P, _I, _P, _P, _I, _P, _P, ctypes.POINTER(_P)]),
             "ft_batch_run": (_I, [_P, _P, _I, _P]),
@@ -221,6 +222,19 @@ class Bank:
 
 class _Tune(ctypes.Structure):
     _fields_ = [("rows_per_stage", ctypes.c_int), ("stages", ctypes.c_int), ("tile_f0", ctypes.c_int)]
+
+
+def pdet_q(ctx, band, det_tensor, pop, stream=None):
+    """ft_pdet_q: per population draw (INJECTION_DTYPE records; h0, f0, f1 unused) the sums
+    (w rho^2, w^2 rho^2) over the band's SFTs at h0 = 1 (Sec. V.A)."""
+    pop = np.ascontiguousarray(pop, dtype=INJECTION_DTYPE)
+    D = np.ascontiguousarray(det_tensor, np.float64)
+    n = len(pop)
+    r1 = np.empty(n, np.float64)
+    r2 = np.empty(n, np.float64)
+    _check(lib().ft_pdet_q(ctx.handle, band.handle, D.ctypes.data, n, pop.ctypes.data,
+                           r1.ctypes.data, r2.ctypes.data, _stream(stream, False)))
+    return r1, r2
 
 
 def gather_roof(ctx, dtype="f16"):

@@ -475,3 +475,118 @@ extern "C" int ft_run_injections(ft_ctx *ctx, const ft_band *band, const ft_bank
     }
     return FT_OK;
 }
+
+// ------------------------------------------------------------------ semi-analytic q (Sec. V.A)
+//
+// One CTA per population draw: every thread sums w rho^2 and w^2 rho^2 (h0 = 1) over a
+// strided set of SFTs in FP64, then a fixed-order tree over the CTA.
+
+namespace {
+
+constexpr int kQThreads = 256;
+
+__global__ void __launch_bounds__(kQThreads) k_pdet_q(long long N, double t_sft, const double *sn,
+                                                      const double *D, const float *w,
+                                                      const InjRun *pop, double *rho1, double *rho2)
+{
+    __shared__ double s1[kQThreads], s2[kQThreads];
+    const InjRun r = pop[blockIdx.x];
+    const double c2 = cos(2.0 * r.psi), sn2 = sin(2.0 * r.psi);
+    const double ap = 0.5 * (1.0 + r.cosi * r.cosi), ax = r.cosi;
+    const double h = 0.7737 * 0.5 * t_sft;  // |h~| per unit h0 and |Q|
+    double a1 = 0.0, a2 = 0.0;
+    for (long long a = threadIdx.x; a < N; a += kQThreads) {
+        double aa, bb;
+        antenna_ab(D + 6 * a, r.n, aa, bb);
+        const double fp = aa * c2 + bb * sn2, fx = bb * c2 - aa * sn2;
+        const double q2 = fp * fp * ap * ap + fx * fx * ax * ax;
+        const double rho = 4.0 * h * h * q2 / (t_sft * sn[a]);
+        const double wa = w != nullptr ? static_cast<double>(w[a]) : 1.0;
+        a1 += wa * rho;
+        a2 += wa * wa * rho;
+    }
+    s1[threadIdx.x] = a1;
+    s2[threadIdx.x] = a2;
+    __syncthreads();
+    for (int off = kQThreads / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) {
+            s1[threadIdx.x] += s1[threadIdx.x + off];
+            s2[threadIdx.x] += s2[threadIdx.x + off];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        rho1[blockIdx.x] = s1[0];
+        rho2[blockIdx.x] = s2[0];
+    }
+}
+
+}  // namespace
+
+extern "C" int ft_pdet_q(ft_ctx *ctx, const ft_band *band, const double *det_tensor, int64_t n,
+                         const ft_injection *pop, double *rho1, double *rho2, void *stream)
+{
+    if (!ctx || !band || !det_tensor || (n > 0 && (!pop || !rho1 || !rho2)))
+        FT_FAIL(FT_ERR_ARG, "pdet_q: null argument");
+    if (band->ctx != ctx)
+        FT_FAIL(FT_ERR_ARG, "pdet_q: band belongs to another context");
+    if (!band->d_sn)
+        FT_FAIL(FT_ERR_ARG, "pdet_q: the band was loaded without S_n");
+    if (n < 0)
+        FT_FAIL(FT_ERR_ARG, "pdet_q: negative count");
+    if (n == 0)
+        return FT_OK;
+    for (int64_t i = 0; i < n; ++i) {
+        const double *nn = pop[i].n;
+        const double r2 = nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2];
+        if (!(std::fabs(r2 - 1.0) < 1e-9) || !std::isfinite(pop[i].cosi) || !std::isfinite(pop[i].psi))
+            FT_FAIL(FT_ERR_ARG, "pdet_q: bad draw at index " + std::to_string(i));
+    }
+    int prev = -1;
+    FT_CUDA(cudaGetDevice(&prev));
+    if (prev != ctx->device)
+        FT_CUDA(cudaSetDevice(ctx->device));
+    (void)cudaGetLastError();  // drop errors left by earlier, unrelated runtime calls
+    struct Restore {
+        int d;
+        ~Restore()
+        {
+            if (d >= 0)
+                cudaSetDevice(d);
+        }
+    } restore{prev != ctx->device ? prev : -1};
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t N = band->N;
+    double *dD = nullptr, *d1 = nullptr, *d2 = nullptr;
+    InjRun *dpop = nullptr;
+    auto release = [&]() {
+        cudaFree(dD);
+        cudaFree(dpop);
+        cudaFree(d1);
+        cudaFree(d2);
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&dD, N * 6 * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&dpop, n * sizeof(InjRun))) != cudaSuccess ||
+        (e = cudaMalloc(&d1, n * 8)) != cudaSuccess || (e = cudaMalloc(&d2, n * 8)) != cudaSuccess) {
+        release();
+        FT_FAIL(FT_ERR_OOM, std::string("pdet_q: ") + cudaGetErrorString(e));
+    }
+    bool ok = cudaMemcpyAsync(dD, det_tensor, N * 6 * 8, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+              cudaMemcpyAsync(dpop, pop, n * sizeof(InjRun), cudaMemcpyHostToDevice, st) == cudaSuccess;
+    for (int64_t done = 0; ok && done < n;) {
+        const int64_t m = std::min<int64_t>(n - done, 1 << 30);
+        k_pdet_q<<<static_cast<unsigned>(m), kQThreads, 0, st>>>(static_cast<long long>(N), band->t_sft,
+                                                                 band->d_sn, dD, band->d_w, dpop + done,
+                                                                 d1 + done, d2 + done);
+        ok = cudaGetLastError() == cudaSuccess;
+        done += m;
+    }
+    ok = ok && cudaMemcpyAsync(rho1, d1, n * 8, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+         cudaMemcpyAsync(rho2, d2, n * 8, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+         cudaStreamSynchronize(st) == cudaSuccess;
+    release();
+    if (!ok)
+        FT_FAIL(FT_ERR_CUDA, "pdet_q: device work failed");
+    return FT_OK;
+}

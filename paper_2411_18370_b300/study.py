@@ -19,6 +19,7 @@ import time
 import numpy as np
 
 from . import campaign as C
+from . import semianalytic as SA
 from . import surrogate as SG
 
 # amplitudes of the training and per-band campaigns: log-uniform c = h0 / sqrt(S_ref/T_SFT)
@@ -42,7 +43,7 @@ def _load(ctx, bands, T):
 
 
 def run_study(ctx, n_bands=64, sky_scale=0.1, n_held=4, n_noise=2000, n_train=20000,
-              n_ref=8000, members=5, epochs=200, k_sky=64):
+              n_ref=8000, members=5, epochs=200, k_sky=64, n_semi=4000):
     import ftsynth
 
     T = ftsynth.T_SFT
@@ -128,6 +129,15 @@ def run_study(ctx, n_bands=64, sky_scale=0.1, n_held=4, n_noise=2000, n_train=20
         x_sur = sur.log10_c_at(0.9, math.log10(bands[b]["s_ref"]), bands[b]["duty"], taus[b],
                                pop)
         t_sur = time.perf_counter() - t0
+        # semi-analytic estimate (Sec. V.A-C) from its own population draws
+        t0 = time.perf_counter()
+        band, bank = objs[b]
+        sa_pop, _ = C.draw_population(n_semi, lo, hi, g)
+        est = SA.build(ctx, band, bank, bands[b]["D"], sa_pop, taus[b], bands[b]["s_ref"], T,
+                       seed=9000 + b, first_run_id=run_id, **kw)
+        run_id += n_semi
+        x_sa = est.log10_c_at(0.9)
+        t_sa = time.perf_counter() - t0
         rows.append({"band": b, "f_start_hz": bands[b]["spec"]["k_band"] / T,
                      "duty": bands[b]["duty"], "log10_S": math.log10(bands[b]["s_ref"]),
                      "tau": taus[b], "ref_c90": 10 ** x_ref,
@@ -135,7 +145,9 @@ def run_study(ctx, n_bands=64, sky_scale=0.1, n_held=4, n_noise=2000, n_train=20
                      "surrogate_c90": 10 ** x_sur, "per_band_fit_c90": 10 ** x_b,
                      "surrogate_err": 10 ** (x_sur - x_ref) - 1,
                      "per_band_fit_err": 10 ** (x_b - x_ref) - 1,
-                     "ref_campaign_s": t_ref, "surrogate_query_s": t_sur})
+                     "semi_analytic_c90": 10 ** x_sa, "semi_analytic_err": 10 ** (x_sa - x_ref) - 1,
+                     "semi_analytic_mean_mismatch": float(np.mean(est.m)),
+                     "ref_campaign_s": t_ref, "surrogate_query_s": t_sur, "semi_analytic_s": t_sa})
     sur.close()
     return {
         "bands": n_bands, "held_out": held, "n_noise_per_band": n_noise,
@@ -149,5 +161,8 @@ def run_study(ctx, n_bands=64, sky_scale=0.1, n_held=4, n_noise=2000, n_train=20
         "rms_surrogate_err": math.sqrt(np.mean([r["surrogate_err"] ** 2 for r in rows])),
         "max_abs_per_band_fit_err": max(abs(r["per_band_fit_err"]) for r in rows),
         "rms_per_band_fit_err": math.sqrt(np.mean([r["per_band_fit_err"] ** 2 for r in rows])),
+        "max_abs_semi_analytic_err": max(abs(r["semi_analytic_err"]) for r in rows),
+        "rms_semi_analytic_err": math.sqrt(np.mean([r["semi_analytic_err"] ** 2 for r in rows])),
+        "n_semi_analytic_draws": n_semi,
         "h0_unit": "sqrt(S_ref / T_SFT)",
     }

@@ -54,3 +54,27 @@ def test_local_fit_recovers_90_percent_point_of_a_long_tailed_curve():
     loc, sig, n = C.local_x_at(x, det, 0.9, wide, half=0.05)
     assert abs(wide - x90) > 0.02
     assert abs(loc - x90) < max(4 * sig, 0.01) and n > 1000
+
+
+def test_semi_analytic_closed_form_limit():
+    """With no mismatch and rho2 = 0 every draw's z is c^2 h rho1 / sigma_G + xi, so p_det(c)
+    = P(xi > tau - c^2 h rho1 / sigma_G) and the 90 % point is
+    c = sqrt((tau - Phi^-1(0.1)) sigma_G / (h rho1)); the bisection over 2e5 normal draws
+    must land on it within the sampling error of the 10 % quantile."""
+    import scipy.stats as st
+
+    from paper_2411_18370_b300 import semianalytic as SA
+
+    n = 200_000
+    g = np.random.default_rng(3)
+    est = SA.Estimate(rho1=np.full(n, 2.0), rho2=np.zeros(n), m=np.zeros(n),
+                      xi=g.standard_normal(n), mu=100.0, sigma=10.0, h2_per_c2=0.5, tau=4.5)
+    x = est.log10_c_at(0.9)
+    want = math.sqrt((4.5 - st.norm.ppf(0.1)) * 10.0 / (0.5 * 2.0))
+    assert abs(10 ** x / want - 1) < 2e-3
+    # monotone in c, 0 far below and 1 far above
+    ps = [est.pdet(c) for c in (0.1, 1.0, 3.0, 10.0, 100.0)]
+    assert ps == sorted(ps) and ps[0] == 0.0 and ps[-1] == 1.0
+    # mismatch m scales the signal power by (1 - m): the 90 % point moves by 1/sqrt(1 - m)
+    est.m = np.full(n, 0.36)
+    assert abs(10 ** (est.log10_c_at(0.9) - x) - 1 / 0.8) < 3e-3
