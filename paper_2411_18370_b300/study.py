@@ -106,6 +106,7 @@ def run_study(ctx, n_bands=64, sky_scale=0.1, n_held=4, n_noise=2000, n_train=20
     # 4. held-out bands
     rows = []
     g = np.random.default_rng(99)
+    g_sa = np.random.default_rng(199)  # the semi-analytic draws, apart from the others
     for b in held:
         lo, hi = frange(b)
         # reference: a rough fit over a wide range, then 3/4 of the budget within +-0.12 dex
@@ -132,7 +133,7 @@ def run_study(ctx, n_bands=64, sky_scale=0.1, n_held=4, n_noise=2000, n_train=20
         # semi-analytic estimate (Sec. V.A-C) from its own population draws
         t0 = time.perf_counter()
         band, bank = objs[b]
-        sa_pop, _ = C.draw_population(n_semi, lo, hi, g)
+        sa_pop, _ = C.draw_population(n_semi, lo, hi, g_sa)
         est = SA.build(ctx, band, bank, bands[b]["D"], sa_pop, taus[b], bands[b]["s_ref"], T,
                        seed=9000 + b, first_run_id=run_id, **kw)
         run_id += n_semi
