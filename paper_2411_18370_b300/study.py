@@ -134,9 +134,9 @@ def run_study(ctx, n_bands=64, sky_scale=0.1, n_held=4, n_noise=2000, n_train=20
         t0 = time.perf_counter()
         band, bank = objs[b]
         sa_pop, _ = C.draw_population(n_semi, lo, hi, g_sa)
+        # (noise-free runs: their run ids draw no noise; kept apart from the campaigns' ids)
         est = SA.build(ctx, band, bank, bands[b]["D"], sa_pop, taus[b], bands[b]["s_ref"], T,
-                       seed=9000 + b, first_run_id=run_id, **kw)
-        run_id += n_semi
+                       seed=9000 + b, first_run_id=(1 << 40) + b * n_semi, **kw)
         x_sa = est.log10_c_at(0.9)
         t_sa = time.perf_counter() - t0
         rows.append({"band": b, "f_start_hz": bands[b]["spec"]["k_band"] / T,
