@@ -45,6 +45,7 @@ class _Problem(ctypes.Structure):
         ("f1", ctypes.c_void_p),
         ("n_sky", ctypes.c_int64),
         ("sky", ctypes.c_void_p),
+        ("wsky", ctypes.c_void_p),
     ]
 
 
@@ -99,6 +100,9 @@ def load_library(path):
     L.or_inj_power.restype = ctypes.c_double
     L.or_inj_power.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64,
                                ctypes.c_double, ctypes.c_double]
+    L.or_sky_weights.restype = None
+    L.or_sky_weights.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                 ctypes.c_void_p, ctypes.c_void_p]
     L.or_pdet_q.restype = None
     L.or_pdet_q.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                             ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
@@ -129,7 +133,8 @@ def _c(a, dtype):
 class _Keep:
     """Holds the numpy arrays a _Problem points into."""
 
-    def __init__(self, sfts, bank, w):
+    def __init__(self, sfts, bank, w, wsky=None):
+        self.wsky = None if wsky is None else _c(wsky, np.float64)
         self.power = _c(sfts.power, np.float64)
         self.t_mid = _c(sfts.t_mid, np.float64)
         self.v = _c(sfts.v, np.float64)
@@ -152,12 +157,14 @@ class _Keep:
         p.f1 = self.f1.ctypes.data
         p.n_sky = len(self.sky)
         p.sky = self.sky.ctypes.data
+        p.wsky = None if self.wsky is None else self.wsky.ctypes.data
         self.p = p
 
 
-def statistic(sfts, bank, templates=None, w=None):
-    """FP64 s for the given template indices (all when None) and out-of-window counts."""
-    k = _Keep(sfts, bank, w)
+def statistic(sfts, bank, templates=None, w=None, wsky=None):
+    """FP64 s for the given template indices (all when None) and out-of-window counts.
+    wsky [n_sky][n_sft] (sky-dependent weights) replaces w when given."""
+    k = _Keep(sfts, bank, w, wsky)
     if templates is None:
         n = bank.n_templates
         tp = None
@@ -309,3 +316,20 @@ def pdet_q(s_n, t_sft, D, inj, w=None):
                     None if wv is None else wv.ctypes.data, n, draws.ctypes.data,
                     r1.ctypes.data, r2.ctypes.data)
     return r1, r2
+
+
+def sky_weights(D, s_n, sky):
+    """Sec. II.B all-sky weights w[i_sky][alpha] ~ (a^2 + b^2) / S_n, each row summing to 1."""
+    Dv = _c(D, np.float64)
+    sn = _c(s_n, np.float64)
+    sk = _c(sky, np.float64)
+    out = np.empty((len(sk), len(sn)), np.float64)
+    lib().or_sky_weights(len(sn), Dv.ctypes.data, sn.ctypes.data, len(sk), sk.ctypes.data,
+                         out.ctypes.data)
+    return out
+
+
+def mu_sigma_sky(wsky):
+    """Per sky point mu_G = 2 sum_alpha w and sigma_G = sqrt(4 sum_alpha w^2)."""
+    w = np.asarray(wsky, np.float64)
+    return 2.0 * w.sum(axis=1), np.sqrt(4.0 * (w * w).sum(axis=1))

@@ -97,6 +97,7 @@ typedef struct {
     const double *f1;  /* [n_f1] */
     int64_t n_sky;
     const double *sky; /* [n_sky][3] */
+    const double *wsky; /* [n_sky][n_sft] sky-dependent weights, or NULL (then w) */
 } or_problem;
 
 /* Offset of SFT alpha's mid-time from the reference time, times T_SFT: tau = (t - t0) T. */
@@ -135,7 +136,7 @@ void or_statistic(const or_problem *p, const int64_t *templates, int64_t n_out,
                 oob++;
                 continue;
             }
-            double w = p->w ? p->w[a] : 1.0;
+            double w = p->wsky ? p->wsky[isky * p->n_sft + a] : (p->w ? p->w[a] : 1.0);
             s += w * p->power[a * p->W + k];
         }
         s_out[i] = s;

@@ -309,3 +309,25 @@ void or_pdet_q(int64_t n_sft, double t_sft, const double *s_n, const double *D, 
         rho2[i] = s2;
     }
 }
+
+/* ---------------------------------------------------------------- sky-dependent weights */
+
+/* Sec. II.B: the all-sky weights w_alpha(n) proportional to (a^2 + b^2) / S_n, with a, b
+ * the detector response of SFT alpha to direction n (or_antenna_ab), normalised so that
+ * sum_alpha w_alpha(n) = 1 for every sky point.  wsky: [n_sky][n_sft]. */
+void or_sky_weights(int64_t n_sft, const double *D, const double *s_n, int64_t n_sky,
+                    const double *sky, double *wsky)
+{
+    for (int64_t i = 0; i < n_sky; i++) {
+        double *wi = wsky + i * n_sft;
+        double tot = 0.0;
+        for (int64_t a = 0; a < n_sft; a++) {
+            double aa, bb;
+            or_antenna_ab(D + 6 * a, sky + 3 * i, &aa, &bb);
+            wi[a] = (aa * aa + bb * bb) / s_n[a];
+            tot += wi[a];
+        }
+        for (int64_t a = 0; a < n_sft; a++)
+            wi[a] /= tot;
+    }
+}
