@@ -119,6 +119,21 @@ FT_API void ft_band_destroy(ft_band *band);
 FT_API int ft_band_info(const ft_band *band, int64_t *n_sft_total, int *n_bins, int *row_stride,
                  int *dtype, double *mu_g, double *sigma_g);
 
+/* All-sky weights (Sec. II.B): for a template at sky point n the weight of SFT alpha becomes
+ *     w_alpha(n) = r_alpha(n) / sum_beta r_beta(n),   r_alpha(n) = (a_alpha(n)^2 + b_alpha(n)^2) / S_n,alpha
+ * with a = D:e+, b = D:ex the antenna-pattern amplitudes of detector tensor D_alpha for
+ * direction n (the frame of ft_run_injections), so that each sky point's weights sum to 1;
+ * the statistic is then s = sum_alpha w_alpha(n) P_alpha(bin), and z uses that sky point's
+ * mu_G = 2 and sigma_G = sqrt(4 sum_alpha w_alpha(n)^2).  Candidates
+ * of a sub-band are still ranked by s (every sky point has the same noise mean).
+ *   det_tensor  host [N_SFT][6] (Dxx, Dxy, Dxz, Dyy, Dyz, Dzz), or NULL to turn the weights
+ *               off again (the per-SFT weights of ft_load_sfts apply once more).
+ * The per-sky sums are computed by ft_make_bank: banks made before this call keep none and
+ * are refused by the evaluation calls while the weights are on.  The injection and
+ * semi-analytic calls keep the per-SFT weights.  Errors: FT_ERR_ARG (null band, band loaded
+ * without S_n, non-finite tensor), FT_ERR_OOM.  Synchronises `stream`. */
+FT_API int ft_band_set_sky_weights(ft_band *band, const double *det_tensor, void *stream);
+
 /* ----------------------------------------------------------------------------- bank --
  * Regular bank: f0_j = (k0 + j)/T_SFT, j < n_f0 (delta f0 = 1/T_SFT, App. A); a list of
  * f1 values; a list of sky unit vectors n.  Template index

@@ -92,6 +92,7 @@ def lib():
             "ft_set_tune": (_I, [_P, _P]),
             "ft_gather_roof": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
             "ft_pdet_q": (_I, [_P, _P, _P, _I64, _P, _P, _P, _P]),
+            "ft_band_set_sky_weights": (_I, [_P, _P, _P]),
             "ft_topk_per_band_noalloc": (_I, [_P, _P, _P, _I, _P, _I, _P]),
             "ft_batch_create": (_I, [_P, _I, _P, _P, _I, _P, _P, ctypes.POINTER(_P)]),
             "ft_batch_run": (_I, [_P, _P, _I, _P]),
@@ -222,6 +223,18 @@ class Bank:
 
 class _Tune(ctypes.Structure):
     _fields_ = [("rows_per_stage", ctypes.c_int), ("stages", ctypes.c_int), ("tile_f0", ctypes.c_int)]
+
+
+def band_set_sky_weights(band, det_tensor, stream=None):
+    """ft_band_set_sky_weights: turn on the all-sky weights (a^2 + b^2) / S_n of Sec. II.B
+    for banks made from now on (det_tensor [N_SFT][6]), or off again with None."""
+    if det_tensor is None:
+        _check(lib().ft_band_set_sky_weights(band.handle, None, _stream(stream, False)))
+        return
+    D = np.ascontiguousarray(det_tensor, np.float64)
+    if D.shape != (band.n_sft, 6):
+        raise ValueError("det_tensor must be [N_SFT][6]")
+    _check(lib().ft_band_set_sky_weights(band.handle, D.ctypes.data, _stream(stream, False)))
 
 
 def pdet_q(ctx, band, det_tensor, pop, stream=None):

@@ -366,7 +366,31 @@ void ft_band_destroy(ft_band *b)
     cudaFree(b->d_v);
     cudaFree(b->d_w);
     cudaFree(b->d_sn);
+    cudaFree(b->d_D);
     delete b;
+}
+
+int ft_band_set_sky_weights(ft_band *band, const double *det_tensor, void *stream)
+{
+    if (!band)
+        FT_FAIL(FT_ERR_ARG, "band_set_sky_weights: null band");
+    DeviceGuard g(band->device);
+    cudaStream_t st = as_stream(stream);
+    if (!det_tensor) {
+        cudaFree(band->d_D);
+        band->d_D = nullptr;
+        return FT_OK;
+    }
+    if (!band->d_sn)
+        FT_FAIL(FT_ERR_ARG, "band_set_sky_weights: the band was loaded without S_n");
+    const size_t n6 = static_cast<size_t>(band->N) * 6;
+    if (!finite_all(det_tensor, n6))
+        FT_FAIL(FT_ERR_ARG, "band_set_sky_weights: non-finite detector tensor");
+    if (!band->d_D)
+        FT_CUDA(cudaMalloc(&band->d_D, n6 * sizeof(double)));
+    FT_CUDA(cudaMemcpyAsync(band->d_D, det_tensor, n6 * sizeof(double), cudaMemcpyHostToDevice, st));
+    FT_CUDA(cudaStreamSynchronize(st));
+    return FT_OK;
 }
 
 int ft_band_info(const ft_band *b, int64_t *n, int *n_bins, int *stride, int *dtype, double *mu,
@@ -469,6 +493,19 @@ int ft_make_bank(ft_ctx *ctx, const ft_band *band, const ft_bank_desc *d, void *
         ft_bank_destroy(b);
         return rc;
     }
+    if (band->d_D) {
+        // all-sky weights: per sky point the normalisation and mu_G, sigma_G
+        const size_t ns = static_cast<size_t>(b->n_sky) * sizeof(double);
+        if (cudaMalloc(&b->d_sky_inv, ns) != cudaSuccess || cudaMalloc(&b->d_sky_mu, ns) != cudaSuccess ||
+            cudaMalloc(&b->d_sky_sig, ns) != cudaSuccess) {
+            ft_bank_destroy(b);
+            FT_FAIL(FT_ERR_OOM, "make_bank: sky-weight table allocation failed");
+        }
+        if ((rc = ft_launch_sky_norms(band, b, st)) != FT_OK) {
+            ft_bank_destroy(b);
+            return rc;
+        }
+    }
     *out = b;
     return FT_OK;
 }
@@ -481,6 +518,9 @@ void ft_bank_destroy(ft_bank *b)
     cudaFree(b->d_f1);
     cudaFree(b->d_sky);
     cudaFree(b->d_sky_order);
+    cudaFree(b->d_sky_inv);
+    cudaFree(b->d_sky_mu);
+    cudaFree(b->d_sky_sig);
     cudaFree(b->d_G);
     delete b;
 }
@@ -532,6 +572,13 @@ static EvalParams base_params(const ft_band *band, const ft_bank *bank)
     p.tau = band->d_tau;
     p.v = band->d_v;
     p.w = band->d_w;
+    if (band->d_D) {
+        p.D = band->d_D;
+        p.sn = band->d_sn;
+        p.sky_inv = bank->d_sky_inv;
+        p.sky_mu = bank->d_sky_mu;
+        p.sky_sig = bank->d_sky_sig;
+    }
     p.sky = bank->d_sky;
     p.G = bank->d_G;
     p.f1 = bank->d_f1;

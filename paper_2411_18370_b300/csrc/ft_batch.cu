@@ -89,7 +89,9 @@ int check_inputs(ft_ctx *ctx, int n, const ft_band *const *bands, const ft_bank 
         if (!bands[i] || !banks[i] || bands[i]->ctx != ctx || banks[i]->ctx != ctx ||
             banks[i]->band != bands[i])
             FT_FAIL(FT_ERR_ARG, "batch: band/bank " + std::to_string(i) + " invalid or mismatched");
-        if (bands[i]->dtype != bands[0]->dtype || bands[i]->weighted != bands[0]->weighted)
+        if (bands[i]->dtype != bands[0]->dtype ||
+            ft_band_weighted(bands[i]) != ft_band_weighted(bands[0]) ||
+            (bands[i]->d_D && !banks[i]->d_sky_inv))
             FT_FAIL(FT_ERR_ARG, "batch: all bands must share storage type and weighting");
         if (!banks[i]->window_safe)
             FT_FAIL(FT_ERR_ARG, "batch: bank " + std::to_string(i) +
@@ -120,7 +122,7 @@ int build(ft_ctx *ctx, int n, const ft_band *const *bands, const ft_bank *const 
     b->n_bands = n;
     b->k = k;
     b->dtype = bands[0]->dtype;
-    b->weighted = bands[0]->weighted;
+    b->weighted = ft_band_weighted(bands[0]);
     b->J = J;
     b->nst = nst;
     // per band: P sky points x F1 f1 values per CTA; the CTA has the most warps any band
@@ -152,6 +154,13 @@ int build(ft_ctx *ctx, int n, const ft_band *const *bands, const ft_bank *const 
         p.tau = bd->d_tau;
         p.v = bd->d_v;
         p.w = bd->d_w;
+        if (bd->d_D) {
+            p.D = bd->d_D;
+            p.sn = bd->d_sn;
+            p.sky_inv = bk->d_sky_inv;
+            p.sky_mu = bk->d_sky_mu;
+            p.sky_sig = bk->d_sky_sig;
+        }
         p.sky = bk->d_sky;
         p.P = bP[i];
         p.F1 = bF1[i];
@@ -300,7 +309,7 @@ std::map<std::string, std::pair<int, int>> g_tune_cache;  // key -> (J, nst)
 std::string tune_key(int n, const ft_band *const *bands, const ft_bank *const *banks, int k)
 {
     // storage type, weighting, rows, the set of window widths (rounded) and f1 counts
-    std::string key = std::to_string(bands[0]->dtype) + (bands[0]->weighted ? "w" : "u") + "k" +
+    std::string key = std::to_string(bands[0]->dtype) + (ft_band_weighted(bands[0]) ? "w" : "u") + "k" +
                       std::to_string(k);
     std::vector<int> wb;
     long long nrows = 0;

@@ -304,7 +304,10 @@ __device__ __forceinline__ void stage_table_a(const EvalParams &p, const CtaTile
         track_ec(p.v + 3 * alpha, c.n0, c.n1, c.n2, p.K0, p.k_lo, E, C);
         tabE[tb * p.S + a] = E;
         tabC[tb * p.S + a] = C;
-        tabW[tb * p.S + a] = p.w[alpha];
+        tabW[tb * p.S + a] =
+            p.D != nullptr ? static_cast<float>(ft_response_a2b2(p.D + 6 * alpha, c.n0, c.n1, c.n2) /
+                                                p.sn[alpha] * p.sky_inv[c.sky])
+                           : p.w[alpha];
     }
 }
 
@@ -395,7 +398,7 @@ __device__ __forceinline__ void fold2sum(float &hi, float &lo, float &part)
 
 // Epilogue shared by both kernels: s = hi + lo, z in FP64; write and/or select.  F is
 // the number of evaluating warps (warps >= F only take part in the barrier).
-template <int NS>
+template <int NS, bool WEIGHTED>
 __device__ __forceinline__ void finish_tile(const EvalParams &p, const CtaTile &c, int F, int J,
                                             const int (&jrel)[NS], const float (&hi)[NS],
                                             const float (&lo)[NS], const int (&oob)[NS],
@@ -405,12 +408,18 @@ __device__ __forceinline__ void finish_tile(const EvalParams &p, const CtaTile &
     const bool active = warp < F;
     const long long trow = active ? warp_template_base(p, c.skyg, c.f1g, warp) : -1;
     const bool f_ok = trow >= 0;
+    double mu = p.mu, sigma = p.sigma;
+    if (WEIGHTED && p.sky_sig != nullptr && f_ok) {
+        const long long sk = trow / (static_cast<long long>(p.n_f1) * p.n_f0);
+        mu = p.sky_mu[sk];
+        sigma = p.sky_sig[sk];
+    }
     float sv[NS], zv[NS];
 #pragma unroll
     for (int r = 0; r < NS; ++r) {
         sv[r] = __fadd_rn(hi[r], lo[r]);
         zv[r] = static_cast<float>(
-            (static_cast<double>(hi[r]) + static_cast<double>(lo[r]) - p.mu) / p.sigma);
+            (static_cast<double>(hi[r]) + static_cast<double>(lo[r]) - mu) / sigma);
     }
     if (p.s_out != nullptr && f_ok) {
 #pragma unroll
@@ -549,7 +558,7 @@ __global__ void __launch_bounds__(1024, 1) k_eval_checked(const EvalParams p)
         if (threadIdx.x == 0 && st + kNbuf < p.n_stages)
             issue_stage(p, buf, bars, L.stage_bytes, st + kNbuf);
     }
-    finish_tile<R>(p, c, F, J, jrel, hi, lo, oob, buf, nullptr);
+    finish_tile<R, true>(p, c, F, J, jrel, hi, lo, oob, buf, nullptr);
 }
 
 // ------------------------------------------------------------------ fast kernel
@@ -925,7 +934,8 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
             if (lane < nr) {
                 alpha = static_cast<long long>(st) * S + lane;
                 const double va[3] = {p.v[3 * alpha], p.v[3 * alpha + 1], p.v[3 * alpha + 2]};
-                const float wa = p.w[alpha];
+                const bool sky_w = WEIGHTED && p.D != nullptr;
+                const float wa = sky_w ? 0.f : p.w[alpha];
                 // track terms per sky point and, per sky point, the track origins of the
                 // group's smallest and largest f1 (the origin is linear in f1)
                 long long G1 = 0, G2 = 0;
@@ -939,6 +949,13 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
                     r.C += (1ll << 31) + static_cast<long long>(c.j0) * r.E;
                     r.span = static_cast<unsigned>(J - 1) * static_cast<unsigned>(abs(r.E));
                     r.w = wa;
+                    if (sky_w) {
+                        // all-sky weight of this row for sky point q
+                        const long long sk = sky_of(p, c.skyg, q);
+                        r.w = static_cast<float>(ft_response_a2b2(p.D + 6 * alpha, skyn[3 * q], skyn[3 * q + 1],
+                                                                  skyn[3 * q + 2]) /
+                                                 p.sn[alpha] * p.sky_inv[sk < 0 ? c.sky : sk]);
+                    }
                     r.start = 0;
                     rq[q * S] = r;
                     if (p.Ws < p.Wp) {
@@ -1211,7 +1228,7 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
     // every copy has landed: its slot was consumed, or the producer waited for it above
     if (!__syncthreads_and(ok))
         return false;
-    finish_tile<NS>(p, c, F, J, jrel, hi, lo, oob, buf, dst);
+    finish_tile<NS, WEIGHTED>(p, c, F, J, jrel, hi, lo, oob, buf, dst);
     return true;
 }
 
@@ -1968,6 +1985,8 @@ int ft_launch_eval(const ft_band *band, const ft_bank *bank, const EvalShape &sh
         FT_FAIL(FT_ERR_ARG, "eval: sky groups need the bank's sky order");
     if (sh.fast && !bank->window_safe)
         FT_FAIL(FT_ERR_ARG, "eval: the unchecked kernel needs a bank whose tracks stay in the window");
+    if (band->d_D && !bank->d_sky_inv)
+        FT_FAIL(FT_ERR_ARG, "eval: the bank was made before the band's all-sky weights were set; make it again");
     const size_t smem = ft_eval_smem_bytes(band, sh, p.cand ? p.k : 0);
     if (smem > band->ctx->smem_optin)
         FT_FAIL(FT_ERR_RANGE, "eval: tile needs more shared memory than the device offers");
@@ -1988,9 +2007,9 @@ int ft_launch_eval(const ft_band *band, const ft_bank *bank, const EvalShape &sh
         FT_FAIL(FT_ERR_ARG, "eval: shape not supported by the unchecked kernel");
     const int tf = threads + 32;  // plus the producer warp
     switch (band->dtype) {
-    case FT_F32: return launch_fast<MODE_F32>(band->weighted, sh.J / 32, n_cta, tf, smem, p, st);
-    case FT_F16: return launch_fast<MODE_F16>(band->weighted, sh.J / 64, n_cta, tf, smem, p, st);
-    case FT_BF16: return launch_fast<MODE_BF16>(band->weighted, sh.J / 64, n_cta, tf, smem, p, st);
+    case FT_F32: return launch_fast<MODE_F32>(ft_band_weighted(band), sh.J / 32, n_cta, tf, smem, p, st);
+    case FT_F16: return launch_fast<MODE_F16>(ft_band_weighted(band), sh.J / 64, n_cta, tf, smem, p, st);
+    case FT_BF16: return launch_fast<MODE_BF16>(ft_band_weighted(band), sh.J / 64, n_cta, tf, smem, p, st);
     default: FT_FAIL(FT_ERR_ARG, "eval: bad dtype");
     }
 }
@@ -2264,4 +2283,53 @@ int ft_run_gather_roof(int dtype, int sm_count, double *evals_per_s, double *eva
     if (rc == FT_ERR_CUDA)
         FT_FAIL(FT_ERR_CUDA, "gather_roof: CUDA runtime error");
     return rc;
+}
+
+// ------------------------------------------------------------------ all-sky weight norms
+
+namespace {
+
+constexpr int kNormThreads = 256;
+
+__global__ void __launch_bounds__(kNormThreads)
+    k_sky_norms(long long N, const double *D, const double *sn, const double *sky, double *inv,
+                double *mu, double *sig)
+{
+    __shared__ double s1[kNormThreads], s2[kNormThreads];
+    const double *n = sky + 3 * blockIdx.x;
+    double a1 = 0.0, a2 = 0.0;
+    for (long long a = threadIdx.x; a < N; a += kNormThreads) {
+        const double r = ft_response_a2b2(D + 6 * a, n[0], n[1], n[2]) / sn[a];
+        a1 += r;
+        a2 += r * r;
+    }
+    s1[threadIdx.x] = a1;
+    s2[threadIdx.x] = a2;
+    __syncthreads();
+    for (int off = kNormThreads / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) {
+            s1[threadIdx.x] += s1[threadIdx.x + off];
+            s2[threadIdx.x] += s2[threadIdx.x + off];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        // w = r / sum r: sum w = 1, so mu_G = 2; sigma_G^2 = 4 sum w^2
+        inv[blockIdx.x] = 1.0 / s1[0];
+        mu[blockIdx.x] = 2.0;
+        sig[blockIdx.x] = 2.0 * sqrt(s2[0]) / s1[0];
+    }
+}
+
+}  // namespace
+
+int ft_launch_sky_norms(const ft_band *band, const ft_bank *bank, cudaStream_t st)
+{
+    if (bank->n_sky > INT_MAX)
+        FT_FAIL(FT_ERR_RANGE, "sky weights: too many sky points");
+    k_sky_norms<<<static_cast<unsigned>(bank->n_sky), kNormThreads, 0, st>>>(
+        static_cast<long long>(band->N), band->d_D, band->d_sn, bank->d_sky, bank->d_sky_inv, bank->d_sky_mu,
+        bank->d_sky_sig);
+    FT_CUDA(cudaGetLastError());
+    return FT_OK;
 }

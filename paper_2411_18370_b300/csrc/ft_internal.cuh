@@ -78,6 +78,7 @@ struct ft_band {
     std::vector<double> h_tau, h_vabs;
     double tau_absmax = 0;
     double vmax = 0;  // largest |v| / c over the SFTs
+    double *d_D = nullptr;  // [N][6] detector tensors when the all-sky weights are on
 };
 
 struct ft_bank {
@@ -96,12 +97,21 @@ struct ft_bank {
     // largest distance between two points of one such group of P (P <= kMaxSkyGroup)
     int *d_sky_order = nullptr;
     double sky_dmax[5] = {};
+    // all-sky weights (band with detector tensors): per sky point 1 / sum_alpha (a^2+b^2)/S_n,
+    // and mu_G, sigma_G of the normalised weights
+    double *d_sky_inv = nullptr, *d_sky_mu = nullptr, *d_sky_sig = nullptr;
     long long *d_G = nullptr;  // [n_f1][N] Q32 f1*tau
     bool window_safe = false;
     double f1_lo = 0, f1_hi = 0;
 };
 
 int ft_ctx_scratch(ft_ctx *ctx, size_t bytes, void **p);
+
+// The evaluation kernels weight the rows: per-SFT weights other than 1, or all-sky weights.
+inline bool ft_band_weighted(const ft_band *b)
+{
+    return b->weighted || b->d_D != nullptr;
+}
 int ft_ctx_outbuf(ft_ctx *ctx, size_t bytes, void **p);
 
 // ------------------------------------------------------------------ kernel parameters
@@ -129,6 +139,9 @@ struct EvalParams {
     const double *tau;
     const double *v;
     const float *w;
+    // all-sky weights (null: per-SFT w): w_alpha(n) = (a^2 + b^2)(D_alpha, n) / S_n,alpha
+    // times sky_inv[n]; z uses sky_mu[n], sky_sig[n]
+    const double *D, *sn, *sky_inv, *sky_mu, *sky_sig;
     const double *sky;
     const int *sky_order;  // [n_sky] CTA sky groups are runs of P in this order (null: identity)
     const long long *G;  // [n_f1][N]
@@ -189,6 +202,32 @@ constexpr int kMaxSkyGroup = 4;
 // Tiled tensor-map view of the band's power rows with a (S rows, Ws bins) box; returns 0
 // and sets *ok = 0 when the shape cannot be expressed (box larger than the hardware allows).
 int ft_encode_rows_map(const ft_band *band, int Ws, int S, CUtensorMap *map, int *ok);
+
+// a = D : e+, b = D : ex of detector tensor D (xx, xy, xz, yy, yz, zz) for direction n, with
+// the wave frame X = z x n / |z x n| (any X perpendicular to n at the poles), Y = n x X.
+__device__ __forceinline__ double ft_response_a2b2(const double *D, double n0, double n1, double n2)
+{
+    const double rho = sqrt(n0 * n0 + n1 * n1);
+    double X0 = 1.0, X1 = 0.0;
+    if (rho > 0) {
+        X0 = -n1 / rho;
+        X1 = n0 / rho;
+    }
+    const double Y0 = -n2 * X1, Y1 = n2 * X0, Y2 = n0 * X1 - n1 * X0;  // n x X (X2 = 0)
+    const double M00 = D[0], M01 = D[1], M02 = D[2], M11 = D[3], M12 = D[4], M22 = D[5];
+    // a = X^T M X - Y^T M Y, b = 2 X^T M Y
+    const double MX0 = M00 * X0 + M01 * X1, MX1 = M01 * X0 + M11 * X1, MX2 = M02 * X0 + M12 * X1;
+    const double MY0 = M00 * Y0 + M01 * Y1 + M02 * Y2, MY1 = M01 * Y0 + M11 * Y1 + M12 * Y2,
+                 MY2 = M02 * Y0 + M12 * Y1 + M22 * Y2;
+    const double a = (X0 * MX0 + X1 * MX1) - (Y0 * MY0 + Y1 * MY1 + Y2 * MY2);
+    const double b = 2.0 * (X0 * MY0 + X1 * MY1);
+    (void)MX2;
+    return a * a + b * b;
+}
+
+// Per sky point of the bank: 1 / sum (a^2+b^2)/S_n and mu_G, sigma_G of the normalised
+// all-sky weights (one CTA per sky point; the band must carry detector tensors).
+int ft_launch_sky_norms(const ft_band *band, const ft_bank *bank, cudaStream_t st);
 
 // Runs the gather-roof microbenchmark on the current device (see ft_gather_roof).
 int ft_run_gather_roof(int dtype, int sm_count, double *evals_per_s, double *evals_per_clk_sm);

@@ -94,6 +94,13 @@ extern "C" int ft_topk_per_band_noalloc(ft_ctx *ctx, const ft_band *band, const 
     p.tau = band->d_tau;
     p.v = band->d_v;
     p.w = band->d_w;
+    if (band->d_D) {
+        p.D = band->d_D;
+        p.sn = band->d_sn;
+        p.sky_inv = bank->d_sky_inv;
+        p.sky_mu = bank->d_sky_mu;
+        p.sky_sig = bank->d_sky_sig;
+    }
     p.sky = bank->d_sky;
     p.G = bank->d_G;
     p.f1 = bank->d_f1;
