@@ -15,10 +15,17 @@ Functions and the passages of arXiv 2411.18370 they follow:
 * topk_per_subband() Sec. IV.B (ahead-of-time clustering): the loudest templates of each
                      disjoint box, here the 1-D boxes "f0 bin j // subband_bins", ordered by
                      s descending, then template index ascending.
+* number_count()     Eq. (number_count) summed like Eq. (short_coh_general): the weighted
+                     count of SFTs whose normalised power on the track exceeds a threshold.
+* nc_moments()       its mean and deviation in Gaussian noise (P exponential with mean 2,
+                     so P(P > x) = exp(-x / 2); Bernoulli per SFT).
+* topk_gated()       Sec. VI.B: the loudest per box among templates whose second statistic
+                     (the weighted number count) reaches a minimum.
 """
 from __future__ import annotations
 
 import ctypes
+import dataclasses
 import math
 
 import numpy as np
@@ -333,3 +340,32 @@ def mu_sigma_sky(wsky):
     """Per sky point mu_G = 2 sum_alpha w and sigma_G = sqrt(4 sum_alpha w^2)."""
     w = np.asarray(wsky, np.float64)
     return 2.0 * w.sum(axis=1), np.sqrt(4.0 * (w * w).sum(axis=1))
+
+
+# ----------------------------------------------------------------------------- number count
+
+
+def number_count(sfts, bank, templates=None, threshold=3.2, w=None, wsky=None):
+    """Weighted number count sum_alpha w_alpha 1[P_alpha(track bin) > threshold] per template
+    (Eq. (number_count)): the statistic of the binarised spectrogram.  Out-of-window reads
+    count 0, as in statistic()."""
+    binar = (np.asarray(sfts.power, np.float64) > threshold).astype(np.float64)
+    return statistic(dataclasses.replace(sfts, power=binar), bank, templates, w=w, wsky=wsky)
+
+
+def nc_moments(threshold, n_sft=None, w=None):
+    """Gaussian-noise mean and deviation of the weighted number count: p sum w and
+    sqrt(p (1 - p) sum w^2) with p = exp(-threshold / 2)."""
+    p = math.exp(-0.5 * threshold)
+    if w is None:
+        return p * n_sft, math.sqrt(p * (1.0 - p) * n_sft)
+    w = np.asarray(w, np.float64)
+    return p * float(w.sum()), math.sqrt(p * (1.0 - p) * float((w * w).sum()))
+
+
+def topk_gated(s, gate, gate_min, bank, k, templates=None):
+    """topk_per_subband over the templates with gate >= gate_min only."""
+    s = np.asarray(s, np.float64)
+    t = np.arange(len(s), dtype=np.int64) if templates is None else np.asarray(templates, np.int64)
+    keep = np.asarray(gate) >= gate_min
+    return topk_per_subband(s[keep], bank, k, t[keep])
