@@ -134,6 +134,20 @@ FT_API int ft_band_info(const ft_band *band, int64_t *n_sft_total, int *n_bins, 
  * without S_n, non-finite tensor), FT_ERR_OOM.  Synchronises `stream`. */
 FT_API int ft_band_set_sky_weights(ft_band *band, const double *det_tensor, void *stream);
 
+/* Number count (Sec. II.B, Eq. (number_count)): a new band whose value in SFT alpha, bin k is
+ * nc = 1 if P > threshold else 0 (the paper's threshold is 3.2), with the source band's
+ * metadata, per-SFT weights, S_n and all-sky weights copied, so that ft_eval_statistic /
+ * ft_topk_per_band on it (with its own bank, same bank description) give the weighted
+ * number count sum_alpha w_alpha nc_alpha along each track.  The comparison takes the
+ * stored value (after the source band's FP16/BF16 rounding) in FP64.  Its mu_G and sigma_G
+ * (ft_band_info, and z) are the weighted count's Gaussian-noise mean and deviation:
+ * p sum w and sqrt(p (1 - p) sum w^2), p = exp(-threshold / 2) (P is exponential with mean
+ * 2); with all-sky weights p and sqrt(p (1 - p) sum w(n)^2) per sky point.  The source band
+ * is not changed.  Errors: FT_ERR_ARG (null, foreign or number-count band, threshold
+ * negative or not finite), FT_ERR_OOM.  Synchronises `stream`. */
+FT_API int ft_number_count_band(ft_ctx *ctx, const ft_band *band, double threshold, void *stream,
+                                ft_band **out);
+
 /* ----------------------------------------------------------------------------- bank --
  * Regular bank: f0_j = (k0 + j)/T_SFT, j < n_f0 (delta f0 = 1/T_SFT, App. A); a list of
  * f1 values; a list of sky unit vectors n.  Template index
@@ -195,6 +209,18 @@ typedef struct {
  * selection is fused into the evaluation kernel, followed by one merge kernel. */
 FT_API int ft_topk_per_band(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int k,
                      ft_candidate *out, int out_on_device, void *stream);
+
+/* ft_topk_per_band restricted to templates whose gate[t] >= gate_min: the loudest s among
+ * templates that also pass a second statistic (Sec. VI.B: the loudest normalised power
+ * whose weighted number count is at least its Gaussian-noise mean + 3 sigma; there gate is
+ * the s_out of ft_eval_statistic on the ft_number_count_band of the same data and bank
+ * shape, and gate_min = mu + 3 sigma of that band's ft_band_info).  A sub-band with fewer
+ * than k passing templates fills the rest with empty slots.
+ *   gate  device [n_templates] float (template index order of `bank`)
+ * Errors: FT_ERR_ARG (host or null gate, NaN gate_min), else as ft_topk_per_band. */
+FT_API int ft_topk_per_band_gated(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int k,
+                                  const float *gate, float gate_min, ft_candidate *out,
+                                  int out_on_device, void *stream);
 
 /* Same search and same output as ft_topk_per_band, for callers that cannot let the library
  * allocate device memory during the call: processes whose device memory is owned by another

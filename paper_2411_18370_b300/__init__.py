@@ -93,6 +93,8 @@ def lib():
             "ft_gather_roof": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
             "ft_pdet_q": (_I, [_P, _P, _P, _I64, _P, _P, _P, _P]),
             "ft_band_set_sky_weights": (_I, [_P, _P, _P]),
+            "ft_number_count_band": (_I, [_P, _P, ctypes.c_double, _P, ctypes.POINTER(_P)]),
+            "ft_topk_per_band_gated": (_I, [_P, _P, _P, _I, _P, ctypes.c_float, _P, _I, _P]),
             "ft_topk_per_band_noalloc": (_I, [_P, _P, _P, _I, _P, _I, _P]),
             "ft_batch_create": (_I, [_P, _I, _P, _P, _I, _P, _P, ctypes.POINTER(_P)]),
             "ft_batch_run": (_I, [_P, _P, _I, _P]),
@@ -235,6 +237,15 @@ def band_set_sky_weights(band, det_tensor, stream=None):
     if D.shape != (band.n_sft, 6):
         raise ValueError("det_tensor must be [N_SFT][6]")
     _check(lib().ft_band_set_sky_weights(band.handle, D.ctypes.data, _stream(stream, False)))
+
+
+def number_count_band(ctx, band, threshold=3.2, stream=None):
+    """ft_number_count_band: a band holding 1[P > threshold] (Eq. (number_count)) with the
+    source band's weights; its mu_g / sigma_g are the weighted count's noise moments."""
+    h = _P()
+    _check(lib().ft_number_count_band(ctx.handle, band.handle, float(threshold),
+                                      _stream(stream, False), ctypes.byref(h)))
+    return Band(ctx, h)
 
 
 def pdet_q(ctx, band, det_tensor, pop, stream=None):
@@ -474,6 +485,17 @@ def topk_per_band(ctx, band, bank, k, out, stream=None):
     po, dev = _ptr(out)
     _check(lib().ft_topk_per_band(ctx.handle, band.handle, bank.handle, int(k), po, int(dev),
                                   _stream(stream, dev)))
+
+
+def topk_per_band_gated(ctx, band, bank, k, gate, gate_min, out, stream=None):
+    """ft_topk_per_band_gated: as topk_per_band over the templates with gate[t] >= gate_min;
+    gate is a CUDA float32 tensor of n_templates values (e.g. the weighted number count)."""
+    pg, gdev = _ptr(gate)
+    if not gdev:
+        raise ValueError("gate must be a CUDA tensor")
+    po, dev = _ptr(out)
+    _check(lib().ft_topk_per_band_gated(ctx.handle, band.handle, bank.handle, int(k), pg,
+                                        float(gate_min), po, int(dev), _stream(stream, dev)))
 
 
 def topk_per_band_noalloc(ctx, band, bank, k, out, stream=None):

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <type_traits>
 
 namespace {
 
@@ -393,6 +394,79 @@ int ft_band_set_sky_weights(ft_band *band, const double *det_tensor, void *strea
     return FT_OK;
 }
 
+int ft_number_count_band(ft_ctx *ctx, const ft_band *band, double threshold, void *stream,
+                         ft_band **out)
+{
+    if (!ctx || !band || !out)
+        FT_FAIL(FT_ERR_ARG, "number_count_band: null argument");
+    if (band->ctx != ctx)
+        FT_FAIL(FT_ERR_ARG, "number_count_band: band belongs to another context");
+    if (band->number_count)
+        FT_FAIL(FT_ERR_ARG, "number_count_band: the band is already a number count");
+    if (!(threshold >= 0.0) || !std::isfinite(threshold))
+        FT_FAIL(FT_ERR_ARG, "number_count_band: threshold must be finite and >= 0");
+    *out = nullptr;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = as_stream(stream);
+    const size_t N = static_cast<size_t>(band->N);
+    ft_band *b = new ft_band(*band);  // metadata; device buffers are replaced below
+    b->d_power = nullptr;
+    b->d_tau = nullptr;
+    b->d_v = nullptr;
+    b->d_w = nullptr;
+    b->d_sn = nullptr;
+    b->d_D = nullptr;
+    auto fail = [&](int rc) {
+        ft_band_destroy(b);
+        return rc;
+    };
+    auto dup = [&](auto **dst, const auto *src, size_t n) -> int {
+        if (!src)
+            return FT_OK;
+        using T = std::remove_cv_t<std::remove_reference_t<decltype(*src)>>;
+        if (cudaMalloc(dst, n * sizeof(T)) != cudaSuccess) {
+            *dst = nullptr;
+            ft_set_error("number_count_band: allocation failed");
+            return FT_ERR_OOM;
+        }
+        if (cudaMemcpyAsync(*dst, src, n * sizeof(T), cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+            ft_set_error("number_count_band: device copy failed");
+            return FT_ERR_CUDA;
+        }
+        return FT_OK;
+    };
+    int rc;
+    if ((rc = dup(&b->d_tau, band->d_tau, N)) != FT_OK || (rc = dup(&b->d_v, band->d_v, 3 * N)) != FT_OK ||
+        (rc = dup(&b->d_w, band->d_w, N)) != FT_OK || (rc = dup(&b->d_sn, band->d_sn, N)) != FT_OK ||
+        (rc = dup(&b->d_D, band->d_D, 6 * N)) != FT_OK)
+        return fail(rc);
+    if (cudaMalloc(&b->d_power, N * band->Wp * 4) != cudaSuccess) {
+        b->d_power = nullptr;
+        ft_set_error("number_count_band: power allocation failed");
+        return fail(FT_ERR_OOM);
+    }
+    if ((rc = ft_launch_binarize(band, b, threshold, st)) != FT_OK)
+        return fail(rc);
+    // P is exponential with mean 2 in Gaussian noise: P(P > x) = exp(-x / 2)
+    const double pr = std::exp(-0.5 * threshold);
+    const double sw = band->mu / band->m1, sw2 = band->sigma * band->sigma / band->v1;
+    b->number_count = true;
+    b->m1 = pr;
+    b->v1 = pr * (1.0 - pr);
+    b->mu = pr * sw;
+    b->sigma = std::sqrt(b->v1 * sw2);
+    if (!(b->sigma > 0)) {
+        ft_set_error("number_count_band: threshold leaves no noise variance");
+        return fail(FT_ERR_ARG);
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        ft_set_error("number_count_band: stream failed");
+        return fail(FT_ERR_CUDA);
+    }
+    *out = b;
+    return FT_OK;
+}
+
 int ft_band_info(const ft_band *b, int64_t *n, int *n_bins, int *stride, int *dtype, double *mu,
                  double *sigma)
 {
@@ -643,8 +717,8 @@ int ft_eval_statistic(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, flo
     return FT_OK;
 }
 
-int ft_topk_per_band(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int k,
-                     ft_candidate *out, int out_on_device, void *stream)
+static int topk_impl(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int k, const float *gate,
+                     float gate_min, ft_candidate *out, int out_on_device, void *stream)
 {
     FT_TRY(check_pair(ctx, band, bank));
     if (!out)
@@ -668,6 +742,8 @@ int ft_topk_per_band(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int 
         dout = static_cast<ft_candidate *>(ob);
     }
     EvalParams p = base_params(band, bank);
+    p.gate = gate;
+    p.gate_min = gate_min;
     p.cand = static_cast<FtCand *>(scr);
     p.k = k;
     p.sub = bank->sub;
@@ -679,6 +755,28 @@ int ft_topk_per_band(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int 
         return read_status(ctx, st);
     }
     return FT_OK;
+}
+
+int ft_topk_per_band(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int k,
+                     ft_candidate *out, int out_on_device, void *stream)
+{
+    return topk_impl(ctx, band, bank, k, nullptr, 0.f, out, out_on_device, stream);
+}
+
+int ft_topk_per_band_gated(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int k,
+                           const float *gate, float gate_min, ft_candidate *out, int out_on_device,
+                           void *stream)
+{
+    if (!gate)
+        FT_FAIL(FT_ERR_ARG, "topk_per_band_gated: null gate");
+    if (std::isnan(gate_min))
+        FT_FAIL(FT_ERR_ARG, "topk_per_band_gated: gate_min is NaN");
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, gate) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        FT_FAIL(FT_ERR_ARG, "topk_per_band_gated: gate must be device memory");
+    }
+    return topk_impl(ctx, band, bank, k, gate, gate_min, out, out_on_device, stream);
 }
 
 int ft_track_bins(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, const int64_t *templates,

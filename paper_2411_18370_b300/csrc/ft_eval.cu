@@ -349,6 +349,8 @@ __device__ void cta_topk(const EvalParams &p, const CtaTile &c, int F, int J, co
                 if (tb < 0)
                     continue;
                 const float s = vs[fl * J + (jj - c.j0)];
+                if (s == -INFINITY)
+                    continue;  // gated out
                 const long long t = tb + jj;
                 const bool elig = (s < last_s) || (s == last_s && t > last_t);
                 const bool better = !have || (s > bs) || (s == bs && t < bt);
@@ -442,7 +444,14 @@ __device__ __forceinline__ void finish_tile(const EvalParams &p, const CtaTile &
     if (active) {
 #pragma unroll
         for (int r = 0; r < NS; ++r) {
-            vs[warp * J + jrel[r]] = sv[r];
+            float sel = sv[r];
+            if (p.gate != nullptr && f_ok) {
+                // gated out: -inf never enters the selection
+                const int j = c.j0 + jrel[r];
+                if (j < p.n_f0 && !(p.gate[trow + j] >= p.gate_min))
+                    sel = -INFINITY;
+            }
+            vs[warp * J + jrel[r]] = sel;
             vz[warp * J + jrel[r]] = zv[r];
         }
         if ((threadIdx.x & 31) == 0)
@@ -2292,8 +2301,8 @@ namespace {
 constexpr int kNormThreads = 256;
 
 __global__ void __launch_bounds__(kNormThreads)
-    k_sky_norms(long long N, const double *D, const double *sn, const double *sky, double *inv,
-                double *mu, double *sig)
+    k_sky_norms(long long N, const double *D, const double *sn, const double *sky, double m1,
+                double sd1, double *inv, double *mu, double *sig)
 {
     __shared__ double s1[kNormThreads], s2[kNormThreads];
     const double *n = sky + 3 * blockIdx.x;
@@ -2314,10 +2323,10 @@ __global__ void __launch_bounds__(kNormThreads)
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        // w = r / sum r: sum w = 1, so mu_G = 2; sigma_G^2 = 4 sum w^2
+        // w = r / sum r: sum w = 1, so the noise mean is m1 and the variance v1 sum w^2
         inv[blockIdx.x] = 1.0 / s1[0];
-        mu[blockIdx.x] = 2.0;
-        sig[blockIdx.x] = 2.0 * sqrt(s2[0]) / s1[0];
+        mu[blockIdx.x] = m1;
+        sig[blockIdx.x] = sd1 * sqrt(s2[0]) / s1[0];
     }
 }
 
@@ -2328,8 +2337,70 @@ int ft_launch_sky_norms(const ft_band *band, const ft_bank *bank, cudaStream_t s
     if (bank->n_sky > INT_MAX)
         FT_FAIL(FT_ERR_RANGE, "sky weights: too many sky points");
     k_sky_norms<<<static_cast<unsigned>(bank->n_sky), kNormThreads, 0, st>>>(
-        static_cast<long long>(band->N), band->d_D, band->d_sn, bank->d_sky, bank->d_sky_inv, bank->d_sky_mu,
-        bank->d_sky_sig);
+        static_cast<long long>(band->N), band->d_D, band->d_sn, bank->d_sky, band->m1, std::sqrt(band->v1),
+        bank->d_sky_inv, bank->d_sky_mu, bank->d_sky_sig);
+    FT_CUDA(cudaGetLastError());
+    return FT_OK;
+}
+
+// ------------------------------------------------------------------ number count
+//
+// The binarised spectrogram of Eq. (number_count): every stored element (both copies of a
+// 16-bit pair row, and the zero padding, which stays 0 for a threshold >= 0) becomes 1 when
+// its value exceeds the threshold.  Grid-stride over 16-byte vectors.
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T bin_of(T x, double thr);
+template <>
+__device__ __forceinline__ float bin_of<float>(float x, double thr)
+{
+    return static_cast<double>(x) > thr ? 1.f : 0.f;
+}
+template <>
+__device__ __forceinline__ __half bin_of<__half>(__half x, double thr)
+{
+    return __ushort_as_half(static_cast<double>(to_float<__half>(x)) > thr ? 0x3C00 : 0);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 bin_of<__nv_bfloat16>(__nv_bfloat16 x, double thr)
+{
+    return __ushort_as_bfloat16(static_cast<double>(to_float<__nv_bfloat16>(x)) > thr ? 0x3F80 : 0);
+}
+
+template <typename T>
+__global__ void k_binarize(const uint4 *src, uint4 *dst, long long n_vec, double thr)
+{
+    constexpr int E = 16 / sizeof(T);
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n_vec;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        uint4 u = src[i];
+        T *e = reinterpret_cast<T *>(&u);
+#pragma unroll
+        for (int q = 0; q < E; ++q)
+            e[q] = bin_of<T>(e[q], thr);
+        dst[i] = u;
+    }
+}
+
+}  // namespace
+
+int ft_launch_binarize(const ft_band *src, ft_band *dst, double threshold, cudaStream_t st)
+{
+    const long long bytes = static_cast<long long>(src->N) * src->Wp * 4;
+    const long long n_vec = bytes / 16;  // Wp is a multiple of 32 elements: rows are whole vectors
+    const int threads = 256;
+    const long long want = (n_vec + threads - 1) / threads;
+    const unsigned grid = static_cast<unsigned>(std::max(1ll, std::min(want, 148ll * 8)));
+    const uint4 *s = static_cast<const uint4 *>(src->d_power);
+    uint4 *d = static_cast<uint4 *>(dst->d_power);
+    switch (src->dtype) {
+    case FT_F32: k_binarize<float><<<grid, threads, 0, st>>>(s, d, n_vec, threshold); break;
+    case FT_F16: k_binarize<__half><<<grid, threads, 0, st>>>(s, d, n_vec, threshold); break;
+    case FT_BF16: k_binarize<__nv_bfloat16><<<grid, threads, 0, st>>>(s, d, n_vec, threshold); break;
+    default: FT_FAIL(FT_ERR_ARG, "number count: unknown storage type");
+    }
     FT_CUDA(cudaGetLastError());
     return FT_OK;
 }

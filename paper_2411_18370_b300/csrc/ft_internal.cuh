@@ -79,6 +79,10 @@ struct ft_band {
     double tau_absmax = 0;
     double vmax = 0;  // largest |v| / c over the SFTs
     double *d_D = nullptr;  // [N][6] detector tensors when the all-sky weights are on
+    // mean and variance of one SFT's value in Gaussian noise: 2 and 4 for normalised power
+    // (exponential with mean 2); p and p (1 - p) for a number-count band, p = exp(-threshold / 2)
+    double m1 = 2.0, v1 = 4.0;
+    bool number_count = false;
 };
 
 struct ft_bank {
@@ -142,6 +146,10 @@ struct EvalParams {
     // all-sky weights (null: per-SFT w): w_alpha(n) = (a^2 + b^2)(D_alpha, n) / S_n,alpha
     // times sky_inv[n]; z uses sky_mu[n], sky_sig[n]
     const double *D, *sn, *sky_inv, *sky_mu, *sky_sig;
+    // candidate gate (null: none): template t takes part in the selection only when
+    // gate[t] >= gate_min (e.g. its weighted number count)
+    const float *gate;
+    float gate_min;
     const double *sky;
     const int *sky_order;  // [n_sky] CTA sky groups are runs of P in this order (null: identity)
     const long long *G;  // [n_f1][N]
@@ -228,6 +236,9 @@ __device__ __forceinline__ double ft_response_a2b2(const double *D, double n0, d
 // Per sky point of the bank: 1 / sum (a^2+b^2)/S_n and mu_G, sigma_G of the normalised
 // all-sky weights (one CTA per sky point; the band must carry detector tensors).
 int ft_launch_sky_norms(const ft_band *band, const ft_bank *bank, cudaStream_t st);
+// dst power = 1[src power > threshold] element by element (same layout and storage type;
+// the stored value is compared in FP64)
+int ft_launch_binarize(const ft_band *src, ft_band *dst, double threshold, cudaStream_t st);
 
 // Runs the gather-roof microbenchmark on the current device (see ft_gather_roof).
 int ft_run_gather_roof(int dtype, int sm_count, double *evals_per_s, double *evals_per_clk_sm);
