@@ -157,7 +157,7 @@ def profiled_traffic(dtype):
     kernel source changed since it was taken."""
     import hashlib
 
-    path = os.path.join(ROOT, "profiles", f"k_eval_fast_search_config1_{dtype}_dram.md")
+    path = os.path.join(ROOT, "profiles", f"k_eval_fast_search_10000sky_{dtype}_dram.md")
     if not os.path.exists(path):
         return None
     fields = {}
@@ -188,7 +188,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    sfts, bank = ftsynth.config1(n_sky=args.n_sky)
+    sfts, bank = ftsynth.search_workload(n_sky=args.n_sky)
     g = np.random.default_rng(11)
     per_step = 128
     t0 = time.perf_counter()
@@ -241,7 +241,7 @@ def run_batch(args):
     v = np.concatenate([ftsynth.detector_velocity(st + 0.5 * T, X) for X, st in enumerate(starts)])
     n_sft = [len(st) for st in starts]
     N = len(t_mid)
-    specs = ftsynth.config3_bands(64, args.sky_scale)
+    specs = ftsynth.batch_bands(64, args.sky_scale)
     bands, banks, evals = [], [], 0
     for b, sp in enumerate(specs):
         wl, wh = ftsynth.wings_for(sp["f_hi"], -1e-9, n_slots * T, T)
@@ -393,7 +393,7 @@ def main():
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         return float(t.item())
 
-    sfts, bank = ftsynth.config1(n_sky=args.n_sky)
+    sfts, bank = ftsynth.search_workload(n_sky=args.n_sky)
     ctx = ft.create(local)
     stream = torch.cuda.current_stream()
     P32 = torch.from_numpy(sfts.power.astype(np.float32))

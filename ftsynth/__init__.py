@@ -293,7 +293,7 @@ class Bank:
 T_SFT = 1800.0
 
 
-def config0(wings: str = "literal") -> tuple:
+def tiny_workload(wings: str = "literal") -> tuple:
     """Plain, tiny: 1 detector, 48 SFTs 10 days, band 100.00-100.05 Hz, 4320 templates.
 
     wings="literal": 10 bins each side as stated; tracks near the band edges leave the
@@ -316,7 +316,7 @@ def config0(wings: str = "literal") -> tuple:
     return sfts, bank, inj
 
 
-def config1(n_sky: int = 10_000, duty: float = 0.7) -> tuple:
+def search_workload(n_sky: int = 10_000, duty: float = 0.7) -> tuple:
     """Plain, search-shaped: 2 detectors, 1 yr, 70% duty, band 200.0-200.1 Hz."""
     k_band = int(round(200.0 * T_SFT))
     n_bins = 180
@@ -328,7 +328,7 @@ def config1(n_sky: int = 10_000, duty: float = 0.7) -> tuple:
     return sfts, bank
 
 
-def config3_bands(n_bands: int = 64, sky_scale: float = 1.0, seed_stream: int = 0):
+def batch_bands(n_bands: int = 64, sky_scale: float = 1.0, seed_stream: int = 0):
     """The 64-band batching workload: widths log-uniform 0.05-0.5 Hz, starts U[50, 500] Hz,
     N_sky = round(1e3 (f_start/50)^2 * sky_scale) clamped to [1e3, 1e5] * sky_scale, 10 f1."""
     g = rng(3, 100 + seed_stream)
@@ -344,9 +344,9 @@ def config3_bands(n_bands: int = 64, sky_scale: float = 1.0, seed_stream: int = 
     return out
 
 
-def config3(n_bands: int = 64, sky_scale: float = 1.0, n_slots: int = None, duty: float = 0.7,
+def batch_workload(n_bands: int = 64, sky_scale: float = 1.0, n_slots: int = None, duty: float = 0.7,
             max_sky: int = None, bands=None):
-    """The batching workload: bands from config3_bands() sharing one 2-detector timeline of
+    """The batching workload: bands from batch_bands() sharing one 2-detector timeline of
     1800 s SFTs (70% duty), each with its own noise, wings sized for its top frequency,
     10 f1 values in [-1e-9, 0] and N_sky Fibonacci sky points (scaled by sky_scale, capped
     by max_sky).  Returns a list of (SFTSet, Bank)."""
@@ -354,7 +354,7 @@ def config3(n_bands: int = 64, sky_scale: float = 1.0, n_slots: int = None, duty
         n_slots = int(round(YEAR_S / T_SFT))
     t_obs = n_slots * T_SFT
     starts = timeline(2, n_slots, T_SFT, duty, rng(3, 1))
-    specs = config3_bands(n_bands, sky_scale)
+    specs = batch_bands(n_bands, sky_scale)
     out = []
     for b, spec in enumerate(specs if bands is None else [specs[i] for i in bands]):
         wl, wh = wings_for(spec["f_hi"], -1e-9, t_obs, T_SFT)
@@ -373,7 +373,7 @@ def psd_level(f_hz: float) -> float:
     return 1.0 + (f_hz / 120.0) ** -4 + (f_hz / 600.0) ** 2
 
 
-def config4_bands(n_bands: int = 64, sky_scale: float = 1.0, n_slots: int = None, seed_stream=0):
+def surrogate_bands(n_bands: int = 64, sky_scale: float = 1.0, n_slots: int = None, seed_stream=0):
     """The surrogate workload's bands: the batching workload's bands, each with its own duty
     cycle U[0.5, 0.9] (SFTs dropped independently) and PSD level psd_level(f_mid) times a
     per-SFT U[0.8, 1.2] factor.  Returns dicts with the band spec, timeline, velocities,
@@ -381,7 +381,7 @@ def config4_bands(n_bands: int = 64, sky_scale: float = 1.0, n_slots: int = None
     if n_slots is None:
         n_slots = int(round(YEAR_S / T_SFT))
     g = rng(4, 200 + seed_stream)
-    specs = config3_bands(n_bands, sky_scale)
+    specs = batch_bands(n_bands, sky_scale)
     out = []
     for b, sp in enumerate(specs):
         duty = float(g.uniform(0.5, 0.9))

@@ -47,7 +47,7 @@ def run_study(ctx, n_bands=64, sky_scale=0.1, n_held=4, n_noise=2000, n_train=20
     import ftsynth
 
     T = ftsynth.T_SFT
-    bands = ftsynth.config4_bands(n_bands, sky_scale)
+    bands = ftsynth.surrogate_bands(n_bands, sky_scale)
     held = list(range(0, n_bands, max(1, n_bands // n_held)))[:n_held]
     train_bands = [b for b in range(n_bands) if b not in held]
     kw = dict(k_sky=k_sky, half_f0=2, half_window=160)

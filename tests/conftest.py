@@ -14,21 +14,21 @@ def pytest_configure(config):
 
 
 @pytest.fixture(scope="session")
-def cfg0_literal():
+def tiny_literal():
     import ftsynth
 
-    return ftsynth.config0("literal")
+    return ftsynth.tiny_workload("literal")
 
 
 @pytest.fixture(scope="session")
-def cfg0_auto():
+def tiny_auto():
     import ftsynth
 
-    return ftsynth.config0("auto")
+    return ftsynth.tiny_workload("auto")
 
 
 @pytest.fixture(scope="session")
-def cfg1():
+def search_cfg():
     import ftsynth
 
-    return ftsynth.config1()
+    return ftsynth.search_workload()

@@ -55,23 +55,23 @@ def test_create_without_device_is_an_error_not_a_crash(built):
     assert ft.lib().ft_last_error().decode() != ""
 
 
-def test_required_wings_cover_config1_tracks(built):
+def test_required_wings_cover_search_tracks(built):
     """Host-only conservative extent: the config-1 wings sized from |v| <= v_max are enough."""
-    sfts, bank = ftsynth.config1(n_sky=16)
+    sfts, bank = ftsynth.search_workload(n_sky=16)
     lo, hi = ft.required_wings(sfts.n_sft, sfts.t_mid, sfts.v, sfts.t_sft, sfts.t0, bank.k0,
                                bank.n_f0, bank.f1, bank.sky, bank.subband_bins)
     wl = bank.k0 - sfts.k_lo
     wh = sfts.k_lo + sfts.n_bins - 1 - (bank.k0 + bank.n_f0 - 1)
     assert 0 < lo <= wl and 0 < hi <= wh
     # the literal 10-bin wings of the tiny workload are NOT enough
-    s0, b0, _ = ftsynth.config0("literal")
+    s0, b0, _ = ftsynth.tiny_workload("literal")
     lo0, hi0 = ft.required_wings(s0.n_sft, s0.t_mid, s0.v, s0.t_sft, s0.t0, b0.k0, b0.n_f0, b0.f1,
                                  b0.sky, b0.subband_bins)
     assert lo0 > 10 and hi0 > 10
 
 
 def test_required_wings_rejects_bad_bank(built):
-    sfts, bank = ftsynth.config1(n_sky=4)
+    sfts, bank = ftsynth.search_workload(n_sky=4)
     with pytest.raises(ft.FtError) as e:
         ft.required_wings(sfts.n_sft, sfts.t_mid, sfts.v, sfts.t_sft, sfts.t0, bank.k0, bank.n_f0,
                           bank.f1, bank.sky * 2.0, bank.subband_bins)

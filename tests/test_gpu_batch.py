@@ -29,7 +29,7 @@ def ctx():
 def bands_small():
     """Six bands of the batching workload (widths 90..900 bins, 100..500 Hz), a short
     timeline (1200 slots) and at most 60 sky points each, so the oracle finishes."""
-    return ftsynth.config3(n_bands=64, n_slots=1200, max_sky=60, bands=[0, 5, 17, 29, 42, 63])
+    return ftsynth.batch_workload(n_bands=64, n_slots=1200, max_sky=60, bands=[0, 5, 17, 29, 42, 63])
 
 
 def _split(cand, banks):

@@ -37,7 +37,7 @@ def fullsize():
     v = np.concatenate([ftsynth.detector_velocity(st + 0.5 * T, X) for X, st in enumerate(starts)])
     n_sft = [len(st) for st in starts]
     N = len(t_mid)
-    specs = ftsynth.config3_bands(64, SKY_SCALE)
+    specs = ftsynth.batch_bands(64, SKY_SCALE)
     # checked bands: the narrowest, the widest and the one with the most sky points
     widths = [sp["n_bins"] for sp in specs]
     skies = [sp["n_sky"] for sp in specs]

@@ -30,7 +30,7 @@ def _with_power(sfts, P):
                           k_lo=sfts.k_lo, t_sft=sfts.t_sft, t0=sfts.t0)
 
 
-def _injected_cfg0(cfg):
+def _injected_tiny(cfg):
     sfts, bank, inj = cfg
     t_inj = (inj["i_sky"] * bank.n_f1 + inj["i_f1"]) * bank.n_f0 + inj["j"]
     b = oracle.bins(sfts, bank, [t_inj])[0]
@@ -77,9 +77,9 @@ def assert_topk(idx, val, s_or, bank, k, s_gpu=None, templates=None):
 # ----------------------------------------------------------------------------- tiny workload
 
 
-def test_tiny_literal_wings_checked_kernel(ctx, cfg0_literal):
+def test_tiny_literal_wings_checked_kernel(ctx, tiny_literal):
     """4320 templates x 48 SFTs, 10-bin wings: edge tracks leave the window (checked kernel)."""
-    sfts, bank, t_inj = _injected_cfg0(cfg0_literal)
+    sfts, bank, t_inj = _injected_tiny(tiny_literal)
     band = H.band_from(ctx, sfts)
     bk = H.bank_from(ctx, band, bank)
     assert not bk.window_safe
@@ -93,8 +93,8 @@ def test_tiny_literal_wings_checked_kernel(ctx, cfg0_literal):
         assert_topk(idx, val, s_or, bank, k, s_gpu=s)
 
 
-def test_tiny_auto_wings_fast_kernel_and_injection(ctx, cfg0_auto):
-    sfts, bank, t_inj = _injected_cfg0(cfg0_auto)
+def test_tiny_auto_wings_fast_kernel_and_injection(ctx, tiny_auto):
+    sfts, bank, t_inj = _injected_tiny(tiny_auto)
     band = H.band_from(ctx, sfts)
     bk = H.bank_from(ctx, band, bank)
     assert bk.window_safe
@@ -110,9 +110,9 @@ def test_tiny_auto_wings_fast_kernel_and_injection(ctx, cfg0_auto):
     assert idx[b, 0] == t_inj
 
 
-def test_noise_free_injection_exact(ctx, cfg0_auto):
+def test_noise_free_injection_exact(ctx, tiny_auto):
     """P = 4 on the injected track and 0 elsewhere: s(lambda_inj) = 192 exactly in FP32."""
-    sfts, bank, inj = cfg0_auto
+    sfts, bank, inj = tiny_auto
     t_inj = (inj["i_sky"] * bank.n_f1 + inj["i_f1"]) * bank.n_f0 + inj["j"]
     b = oracle.bins(sfts, bank, [t_inj])[0]
     P = np.zeros_like(sfts.power)
@@ -128,7 +128,7 @@ def test_noise_free_injection_exact(ctx, cfg0_auto):
 def test_integer_power_bins_exact(ctx, wings, dtype):
     """Integer powers 0..255 are exact in every storage type and their sums < 2^24 are exact
     in FP32, so s must equal the oracle bit for bit: any wrong bin shows."""
-    sfts, bank, _ = ftsynth.config0(wings)
+    sfts, bank, _ = ftsynth.tiny_workload(wings)
     g = np.random.default_rng(31)
     P = g.integers(0, 256, sfts.power.shape).astype(np.float64)
     sx = _with_power(sfts, P)
@@ -140,8 +140,8 @@ def test_integer_power_bins_exact(ctx, wings, dtype):
     assert np.array_equal(o, o_or)
 
 
-def test_track_bins_tiny_all_pairs(ctx, cfg0_literal):
-    sfts, bank, _ = cfg0_literal
+def test_track_bins_tiny_all_pairs(ctx, tiny_literal):
+    sfts, bank, _ = tiny_literal
     band = H.band_from(ctx, sfts)
     bk = H.bank_from(ctx, band, bank)
     t = np.arange(bank.n_templates, dtype=np.int64)
@@ -154,17 +154,17 @@ def test_track_bins_tiny_all_pairs(ctx, cfg0_literal):
 
 
 @pytest.fixture(scope="module")
-def cfg1_slice(cfg1):
+def search_slice(search_cfg):
     """Search-shaped data (2 detectors, 1 yr, ~24.4k SFTs) with a 3-sky slice of the bank."""
-    sfts, bank = cfg1
+    sfts, bank = search_cfg
     sub = ftsynth.Bank(k0=bank.k0, n_f0=bank.n_f0, f1=bank.f1, sky=bank.sky[[0, 4321, 9999]],
                        subband_bins=bank.subband_bins)
     s_or, o_or = oracle.statistic(sfts, sub)
     return sfts, sub, s_or, o_or
 
 
-def test_search_shaped_slice_elementwise(ctx, cfg1_slice):
-    sfts, bank, s_or, o_or = cfg1_slice
+def test_search_shaped_slice_elementwise(ctx, search_slice):
+    sfts, bank, s_or, o_or = search_slice
     band = H.band_from(ctx, sfts, power_f32=True)
     bk = H.bank_from(ctx, band, bank)
     assert bk.window_safe and o_or.sum() == 0
@@ -176,10 +176,10 @@ def test_search_shaped_slice_elementwise(ctx, cfg1_slice):
 
 
 @pytest.mark.parametrize("dtype,max_rel,rms_rel", [("f16", 2e-5, 5e-6), ("bf16", 1.5e-4, 4e-5)])
-def test_search_shaped_reduced_precision_error(ctx, cfg1_slice, dtype, max_rel, rms_rel):
+def test_search_shaped_reduced_precision_error(ctx, search_slice, dtype, max_rel, rms_rel):
     """FP16/BF16 storage, FP32 accumulation: error against the FP64 oracle within the bound
     set by one rounding per stored value (2^-11, 2^-8), averaged over ~24k SFTs."""
-    sfts, bank, s_or, _ = cfg1_slice
+    sfts, bank, s_or, _ = search_slice
     band = H.band_from(ctx, sfts, dtype=dtype)
     bk = H.bank_from(ctx, band, bank)
     s, _, _ = H.eval_host(ctx, band, bk, bank.n_templates)
@@ -188,11 +188,11 @@ def test_search_shaped_reduced_precision_error(ctx, cfg1_slice, dtype, max_rel, 
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
-def test_search_shaped_integer_power_exact(ctx, cfg1_slice, dtype):
+def test_search_shaped_integer_power_exact(ctx, search_slice, dtype):
     """Integer powers on the search-shaped data: every bin of the shifted-row kernel, its
     per-row carry corrections and the 16-bit pair layout must reproduce the oracle's sum
     exactly (sums < 2^24 are exact in FP32)."""
-    sfts, bank, _, _ = cfg1_slice
+    sfts, bank, _, _ = search_slice
     P = np.random.default_rng(77).integers(0, 256, sfts.power.shape).astype(np.float64)
     sx = _with_power(sfts, P)
     band = H.band_from(ctx, sx, dtype=dtype)
@@ -204,9 +204,9 @@ def test_search_shaped_integer_power_exact(ctx, cfg1_slice, dtype):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
-def test_weighted_integer_power_exact(ctx, cfg0_auto, dtype):
+def test_weighted_integer_power_exact(ctx, tiny_auto, dtype):
     """Power-of-two weights and integer powers: the weighted kernels are exact too."""
-    sfts, bank, _ = cfg0_auto
+    sfts, bank, _ = tiny_auto
     g = np.random.default_rng(78)
     P = g.integers(0, 256, sfts.power.shape).astype(np.float64)
     w = 2.0 ** g.integers(-2, 3, sfts.n_total)
@@ -219,8 +219,8 @@ def test_weighted_integer_power_exact(ctx, cfg0_auto, dtype):
     assert_z_close(z, s_or, sfts.n_total, w)
 
 
-def test_track_bins_search_shaped_sample(ctx, cfg1):
-    sfts, bank = cfg1
+def test_track_bins_search_shaped_sample(ctx, search_cfg):
+    sfts, bank = search_cfg
     band = H.band_from(ctx, sfts, power_f32=True)
     bk = H.bank_from(ctx, band, bank)
     t = np.random.default_rng(5).choice(bank.n_templates, 64, replace=False).astype(np.int64)
@@ -229,13 +229,13 @@ def test_track_bins_search_shaped_sample(ctx, cfg1):
     assert np.array_equal(out.astype(np.int64), oracle.bins(sfts, bank, t))
 
 
-def test_search_shaped_full_bank_sampled(ctx, cfg1):
+def test_search_shaped_full_bank_sampled(ctx, search_cfg):
     """The full 3.6e7-template bank in the launch configuration the benchmark times, with
     device outputs: sampled templates against the oracle; candidates against the CPU
     selection over the GPU's own values, and each candidate's s against the oracle."""
     import torch
 
-    sfts, bank = cfg1
+    sfts, bank = search_cfg
     band = H.band_from(ctx, sfts, power_f32=True)
     bk = H.bank_from(ctx, band, bank)
     n = bank.n_templates

@@ -125,7 +125,7 @@ def test_band_without_psd_refused(ctx):
 
 
 def test_batch_with_sky_weights(ctx):
-    data = ftsynth.config3(n_bands=64, n_slots=1200, max_sky=40, bands=[3, 30, 60])
+    data = ftsynth.batch_workload(n_bands=64, n_slots=1200, max_sky=40, bands=[3, 30, 60])
     K = 8
     bands, banks = [], []
     for sfts, bank in data:

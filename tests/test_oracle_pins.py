@@ -121,9 +121,9 @@ def test_q32_bins_large_spindown_exact_rational():
                 assert b[r, a] == k, (r, a)
 
 
-def test_q32_bins_config0_full_exact():
+def test_q32_bins_tiny_workload_full_exact():
     """All 207,360 (template, SFT) pairs of the tiny workload: Q32 == exact rational."""
-    sfts, bank, _ = ftsynth.config0("literal")
+    sfts, bank, _ = ftsynth.tiny_workload("literal")
     t = np.arange(bank.n_templates)
     b, bf, d = oracle.bins(sfts, bank, t, with_fp64=True)
     # the direct FP64 form agrees everywhere it is not within 1e-7 of a tie
@@ -164,7 +164,7 @@ def test_doppler_direction_and_size():
 def test_noise_free_injection_recovers_summed_power():
     """Eq. (short_coh_general): with P = 4 on the injected track (placed by exact rational
     arithmetic) and 0 elsewhere, s(lambda_inj) = 4 * N_SFT exactly and no template exceeds it."""
-    sfts, bank, inj = ftsynth.config0("auto")
+    sfts, bank, inj = ftsynth.tiny_workload("auto")
     P = np.zeros_like(sfts.power)
     n = bank.sky[inj["i_sky"]]
     f1 = bank.f1[inj["i_f1"]]
@@ -253,9 +253,9 @@ def test_weighted_statistic_bruteforce():
         assert oob[r] == nb
 
 
-def test_out_of_window_counts_literal_wings(cfg0_literal):
+def test_out_of_window_counts_literal_wings(tiny_literal):
     """Tracks leaving the 10-bin literal wings contribute 0 and are counted."""
-    sfts, bank, _ = cfg0_literal
+    sfts, bank, _ = tiny_literal
     s, oob = oracle.statistic(sfts, bank)
     assert oob.sum() > 0
     tmpl = np.nonzero(oob)[0][:12]

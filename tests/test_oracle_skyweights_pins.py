@@ -54,7 +54,7 @@ def test_weights_normalise_and_scale_with_psd():
 
 
 def test_constant_response_reduces_to_plain_mean():
-    sfts, bank, _ = ftsynth.config0("auto")
+    sfts, bank, _ = ftsynth.tiny_workload("auto")
     N = sfts.n_total
     D = np.tile(ftsynth.detector_tensor(np.array([1234.5]), 0), (N, 1))
     wsky = oracle.sky_weights(D, np.ones(N), bank.sky)

@@ -19,7 +19,7 @@ REL = 1e-6
 @pytest.fixture(scope="module")
 def search():
     ctx = ft.create(0)
-    sfts, bank = ftsynth.config1()
+    sfts, bank = ftsynth.search_workload()
     band = ft.load_sfts(ctx, sfts.power.astype(np.float32), sfts.t_mid, sfts.v, sfts.n_sft,
                         sfts.k_lo, sfts.t_sft, sfts.t0, dtype="f32")
     bk = ft.make_bank(ctx, band, bank.k0, bank.n_f0, bank.f1, bank.sky, bank.subband_bins)
