@@ -288,6 +288,33 @@ class Bank:
         return r // self.n_f1, r % self.n_f1, j
 
 
+BINARY_DIMS = ("f0", "alpha", "sind", "ap", "omega", "phib")
+
+
+@dataclasses.dataclass
+class BinaryBank:
+    """Random bank for the binary-orbit track, cut into regular boxes in the uniform
+    coordinates.  lo / hi per dimension of BINARY_DIMS: f0 (Hz), right ascension alpha (turns,
+    within [0, 1]), sin(declination), projected semi-major axis a_p (light-seconds), orbital
+    angular frequency Omega (rad/s), orbital phase phi_b (turns, within [0, 1]).  n_div boxes
+    per dimension (f0 slowest, phi_b fastest), n_per_box templates each, drawn from `seed`.
+    Template i lies in box i // n_per_box."""
+
+    lo: tuple
+    hi: tuple
+    n_div: tuple
+    n_per_box: int
+    seed: int
+
+    @property
+    def n_boxes(self) -> int:
+        return int(np.prod(self.n_div))
+
+    @property
+    def n_templates(self) -> int:
+        return self.n_boxes * self.n_per_box
+
+
 # ----------------------------------------------------------------------------- configs
 
 T_SFT = 1800.0

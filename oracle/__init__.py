@@ -21,6 +21,10 @@ Functions and the passages of arXiv 2411.18370 they follow:
                      so P(P > x) = exp(-x / 2); Bernoulli per SFT).
 * topk_gated()       Sec. VI.B: the loudest per box among templates whose second statistic
                      (the weighted number count) reaches a minimum.
+* binary_*()         Eq. (track) with the binary-orbit term, the random bank in the uniform
+                     coordinates of Eq. (xi_of_lambda) / App. A and its hyperboxes (Sec. IV.B),
+                     and the statistic along those tracks (C source ft_oracle_bin.c).
+* topk_per_box()     the loudest templates of each hyperbox.
 """
 from __future__ import annotations
 
@@ -114,6 +118,22 @@ def load_library(path):
     L.or_pdet_q.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                             ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                             ctypes.c_void_p]
+    L.or_cos_q32.restype = ctypes.c_float
+    L.or_cos_q32.argtypes = [ctypes.c_uint32]
+    L.or_bt_tq.restype = ctypes.c_int64
+    L.or_bt_tq.argtypes = [ctypes.c_double, ctypes.c_double]
+    L.or_bt_templates.restype = None
+    L.or_bt_templates.argtypes = [ctypes.POINTER(_BDesc), ctypes.c_void_p, ctypes.c_int64,
+                                  ctypes.c_double, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+    L.or_bt_bins.restype = None
+    L.or_bt_bins.argtypes = [ctypes.POINTER(_BDesc), ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                             ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.or_bt_statistic.restype = None
+    L.or_bt_statistic.argtypes = [ctypes.POINTER(_BDesc), ctypes.c_void_p, ctypes.c_int64,
+                                  ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
     L.or_injections.restype = None
     L.or_injections.argtypes = [ctypes.POINTER(_InjProblem), ctypes.c_void_p, ctypes.c_int64,
                                 ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
@@ -369,3 +389,111 @@ def topk_gated(s, gate, gate_min, bank, k, templates=None):
     t = np.arange(len(s), dtype=np.int64) if templates is None else np.asarray(templates, np.int64)
     keep = np.asarray(gate) >= gate_min
     return topk_per_subband(s[keep], bank, k, t[keep])
+
+
+# ----------------------------------------------------------------------------- binary track
+
+
+class _BDesc(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double * 6), ("hi", ctypes.c_double * 6), ("n_div", ctypes.c_int32 * 6),
+                ("n_per_box", ctypes.c_int64), ("seed", ctypes.c_uint64)]
+
+
+class _BDer(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int64), ("phi", ctypes.c_float), ("F", ctypes.c_float),
+                ("nx", ctypes.c_float), ("ny", ctypes.c_float), ("nz", ctypes.c_float),
+                ("D", ctypes.c_float), ("nu_q", ctypes.c_uint64), ("psi_q", ctypes.c_uint64)]
+
+
+def _bdesc(bank):
+    d = _BDesc()
+    for k in range(6):
+        d.lo[k] = float(bank.lo[k])
+        d.hi[k] = float(bank.hi[k])
+        d.n_div[k] = int(bank.n_div[k])
+    d.n_per_box = int(bank.n_per_box)
+    d.seed = int(bank.seed) & ((1 << 64) - 1)
+    return d
+
+
+def _tmpl(bank, templates):
+    return _c(np.arange(bank.n_templates) if templates is None else templates, np.int64)
+
+
+def binary_templates(bank, templates=None, t_sft=1800.0, k_lo=0):
+    """lambda [n][6] (BINARY_DIMS order) and the per-template quantities of the canonical bin
+    rule (dict of arrays)."""
+    t = _tmpl(bank, templates)
+    n = len(t)
+    lam = np.empty((n, 6), np.float64)
+    der = (_BDer * max(n, 1))()
+    d = _bdesc(bank)
+    lib().or_bt_templates(ctypes.byref(d), t.ctypes.data, n, float(t_sft), int(k_lo),
+                           lam.ctypes.data, ctypes.cast(der, ctypes.c_void_p))
+    dt = {"K": np.int64, "nu_q": np.uint64, "psi_q": np.uint64}
+    out = {f: np.array([getattr(der[i], f) for i in range(n)], dtype=dt.get(f, np.float32))
+           for f, _ in _BDer._fields_}
+    return lam, out
+
+
+def cos_q32(theta):
+    """The canonical FP32 cosine of 2 pi theta / 2^32 (theta uint32)."""
+    return np.array([lib().or_cos_q32(int(x) & 0xFFFFFFFF) for x in np.atleast_1d(theta)], np.float32)
+
+
+def binary_tq(t_mid, t0):
+    return np.array([lib().or_bt_tq(float(x), float(t0)) for x in np.atleast_1d(t_mid)], np.int64)
+
+
+def binary_bins(sfts, bank, templates, with_fp64=False):
+    """Canonical bins [n, N_SFT] (band columns); with_fp64 also the FP64 bins of Eq. (track)
+    and the distance of the real-valued track from the rounding boundary."""
+    t = _tmpl(bank, templates)
+    n = len(t)
+    tm = _c(sfts.t_mid, np.float64)
+    v = _c(sfts.v, np.float64)
+    N = len(tm)
+    b = np.empty((n, N), np.int64)
+    b64 = np.empty((n, N), np.int64) if with_fp64 else None
+    dist = np.empty((n, N), np.float64) if with_fp64 else None
+    d = _bdesc(bank)
+    lib().or_bt_bins(ctypes.byref(d), t.ctypes.data, n, N, tm.ctypes.data, v.ctypes.data,
+                      float(sfts.t0), float(sfts.t_sft), int(sfts.k_lo), b.ctypes.data,
+                      None if b64 is None else b64.ctypes.data,
+                      None if dist is None else dist.ctypes.data)
+    return (b, b64, dist) if with_fp64 else b
+
+
+def binary_statistic(sfts, bank, templates=None, w=None):
+    """FP64 s along the canonical binary tracks and the out-of-window counts."""
+    t = None if templates is None else _c(templates, np.int64)
+    n = bank.n_templates if t is None else len(t)
+    P = _c(sfts.power, np.float64)
+    tm = _c(sfts.t_mid, np.float64)
+    v = _c(sfts.v, np.float64)
+    wv = None if w is None else _c(w, np.float64)
+    s = np.empty(n, np.float64)
+    oob = np.empty(n, np.int32)
+    d = _bdesc(bank)
+    lib().or_bt_statistic(ctypes.byref(d), None if t is None else t.ctypes.data, n, P.shape[0],
+                           P.shape[1], P.ctypes.data, None if wv is None else wv.ctypes.data,
+                           tm.ctypes.data, v.ctypes.data, float(sfts.t0), float(sfts.t_sft),
+                           int(sfts.k_lo), s.ctypes.data, oob.ctypes.data)
+    return s, oob
+
+
+def topk_per_box(s, n_per_box, n_boxes, k, templates=None):
+    """Per box b (templates i with i // n_per_box == b), the k largest s, ties by the smaller
+    index; idx -1 / val -inf beyond the box's population."""
+    s = np.asarray(s, np.float64)
+    t = np.arange(len(s), dtype=np.int64) if templates is None else np.asarray(templates, np.int64)
+    box = t // n_per_box
+    idx = np.full((n_boxes, k), -1, np.int64)
+    val = np.full((n_boxes, k), -np.inf)
+    for b in range(n_boxes):
+        m = box == b
+        tb, sb = t[m], s[m]
+        order = np.lexsort((tb, -sb))[:k]
+        idx[b, : len(order)] = tb[order]
+        val[b, : len(order)] = sb[order]
+    return idx, val

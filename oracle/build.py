@@ -11,7 +11,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "ft_oracle.c")
-SRCS = [SRC, os.path.join(HERE, "ft_oracle_inj.c")]
+SRCS = [SRC, os.path.join(HERE, "ft_oracle_inj.c"), os.path.join(HERE, "ft_oracle_bin.c")]
 LIB = os.path.join(HERE, "libftoracle.so")
 
 
