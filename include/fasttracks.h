@@ -312,6 +312,76 @@ FT_API int ft_run_injections(ft_ctx *ctx, const ft_band *band, const ft_bank *ba
 FT_API int ft_pdet_q(ft_ctx *ctx, const ft_band *band, const double *det_tensor, int64_t n,
                      const ft_injection *pop, double *rho1, double *rho2, void *stream);
 
+/* ----------------------------------------------------------------------------- binary --
+ * Sources in circular binary orbits (Eq. (track) with the orbit term, no spindown):
+ *     f(t) = f0 [1 + v(t).n - a_p Omega cos(Omega t - phi_b)],   t = t_mid - t0,
+ * searched with a random template bank (Sec. IV.A): templates uniform in the coordinates
+ * xi = {f0^6, alpha, sin(delta), a_p^3, Omega^4, phi_b} in which the template density of
+ * App. A (rho ~ f0^5 a_p^2 Omega^3) is constant (Eq. (xi_of_lambda), Eq. (unif_transform);
+ * constant factors dropped), cut ahead of time into regular hyperboxes of n_per_box templates
+ * each (Sec. IV.B).  Templates are pure functions of (seed, index) and are never stored: the
+ * kernels derive each one from a Philox4x32-10 counter.
+ *
+ * Canonical rule (evaluated identically on every path; the tests pin it to the FP64 track):
+ *   - template i is in box i / n_per_box (box index row-major over BINARY dims, f0 slowest);
+ *     u_0..u_5 are 53-bit uniforms ((a >> 5) 2^26 + (b >> 6)) / 2^53 from Philox4x32-10 at
+ *     counter (i lo, i hi, c, 0x62696e61), key (seed lo, seed hi), c = 0, 1, 2 (words 0,1 and
+ *     2,3 of each call); xi_d = xi_lo + (box_d + u_d) (xi_hi - xi_lo) / n_div_d; f0 =
+ *     sqrt(cbrt(xi_0)), a_p = cbrt(xi_3) (24 Newton steps y -= (y^3 - x) / (3 y^2) from the
+ *     range's top), Omega = sqrt(sqrt(xi_4)); alpha and phi_b stay below 1 turn;
+ *   - per template: F = f0 T_SFT, K = floor(F) - k_lo, phi = FP32(F - floor F); the sky vector
+ *     n = (cos delta cos alpha, cos delta sin alpha, sin delta) in FP32; D = FP32(F a_p Omega);
+ *     orbit frequency nu = Omega / 2 pi as round(nu 2^54) and phase phi_b as phi_b 2^64;
+ *   - per SFT: t_q = round((t_mid - t0) 2^10); orbit phase theta = top 32 bits of
+ *     (nu_q t_q - psi_q) mod 2^64; its cosine by Taylor polynomials (to x^10 / x^9) on the
+ *     nearest quadrant in FP32; X = (phi + F (v.n)) - D cos in FP32; bin = K + floor(X + 1/2).
+ *   Bins outside the band contribute 0 and are counted, as for the isolated bank.
+ */
+typedef struct ft_binary_bank ft_binary_bank;
+
+typedef struct {
+    /* ranges per dimension, order: f0 (Hz), alpha (right ascension, turns in [0, 1]),
+     * sin(delta) (in [-1, 1]), a_p (light-seconds), Omega (rad/s), phi_b (turns in [0, 1]).
+     * For f0, a_p and Omega: 0 < lo <= hi <= 16 lo, or (a_p only) lo = hi = 0 for an
+     * isolated source. */
+    double lo[6], hi[6];
+    int32_t n_div[6];    /* boxes per dimension (>= 1 each) */
+    int64_t n_per_box;   /* templates per box (>= 1); n_templates = prod(n_div) n_per_box < 2^40 */
+    uint64_t seed;
+} ft_binary_bank_desc;
+
+/* Set up a binary bank for `band` (uses its SFT times, velocities and weights).  Errors:
+ * FT_ERR_ARG (ranges, counts), FT_ERR_OOM. */
+FT_API int ft_make_binary_bank(ft_ctx *ctx, const ft_band *band, const ft_binary_bank_desc *desc,
+                               ft_binary_bank **out);
+FT_API void ft_binary_bank_destroy(ft_binary_bank *bank);
+FT_API int ft_binary_bank_info(const ft_binary_bank *bank, int64_t *n_templates, int64_t *n_boxes);
+
+/* lambda of templates first .. first + n - 1: host [n][6] in the order of ft_binary_bank_desc
+ * (alpha and phi_b in turns), as the kernels derive them. */
+FT_API int ft_binary_templates(ft_ctx *ctx, const ft_binary_bank *bank, int64_t first, int64_t n,
+                               double *lambda_out, void *stream);
+
+/* Canonical bins of templates[0..n) in every SFT: bins [n][N_SFT] int32 columns of the band
+ * (may lie outside [0, n_bins)).  templates / bins both host or both device (on_device). */
+FT_API int ft_binary_track_bins(ft_ctx *ctx, const ft_band *band, const ft_binary_bank *bank,
+                                const int64_t *templates, int64_t n, int32_t *bins, int on_device,
+                                void *stream);
+
+/* s (Eq. (short_coh_general) along the binary track), z = (s - mu_G) / sigma_G and the
+ * out-of-window count of templates first .. first + n - 1 into s_out[n] (required), z_out,
+ * n_oob_out (nullable).  FP32 partial sums per stage of SFTs folded into a compensated FP32
+ * pair.  Synchronises `stream` for host outputs. */
+FT_API int ft_binary_eval(ft_ctx *ctx, const ft_band *band, const ft_binary_bank *bank,
+                          int64_t first, int64_t n, float *s_out, float *z_out,
+                          int32_t *n_oob_out, int out_on_device, void *stream);
+
+/* The k loudest templates of every hyperbox (Sec. IV.B: the loudest per box), ordered by s
+ * descending, ties by smaller index: out [n_boxes][k] (empty slots: index -1, s = -inf).
+ * 1 <= k <= 32.  The statistic is not written to memory. */
+FT_API int ft_binary_topk_per_box(ft_ctx *ctx, const ft_band *band, const ft_binary_bank *bank,
+                                  int k, ft_candidate *out, int out_on_device, void *stream);
+
 /* ----------------------------------------------------------------------------- surrogate --
  * A learned model of the detection probability p_det (Sec. V, Eqs. (pdet_abstract),
  * (simple_eq)) trained on injection-recovery outcomes: a 4-layer perceptron

@@ -44,6 +44,11 @@ class _BankDesc(ctypes.Structure):
                 ("subband_bins", ctypes.c_int)]
 
 
+class _BinaryDesc(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double * 6), ("hi", ctypes.c_double * 6), ("n_div", ctypes.c_int32 * 6),
+                ("n_per_box", ctypes.c_int64), ("seed", ctypes.c_uint64)]
+
+
 class _InjDesc(ctypes.Structure):
     _fields_ = [("k_sky", ctypes.c_int), ("half_f0", ctypes.c_int), ("half_window", ctypes.c_int),
                 ("noise_scale", ctypes.c_double), ("seed", ctypes.c_uint64),
@@ -93,6 +98,13 @@ def lib():
             "ft_gather_roof": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
             "ft_pdet_q": (_I, [_P, _P, _P, _I64, _P, _P, _P, _P]),
             "ft_band_set_sky_weights": (_I, [_P, _P, _P]),
+            "ft_make_binary_bank": (_I, [_P, _P, ctypes.POINTER(_BinaryDesc), ctypes.POINTER(_P)]),
+            "ft_binary_bank_destroy": (None, [_P]),
+            "ft_binary_bank_info": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+            "ft_binary_templates": (_I, [_P, _P, _I64, _I64, _P, _P]),
+            "ft_binary_track_bins": (_I, [_P, _P, _P, _P, _I64, _P, _I, _P]),
+            "ft_binary_eval": (_I, [_P, _P, _P, _I64, _I64, _P, _P, _P, _I, _P]),
+            "ft_binary_topk_per_box": (_I, [_P, _P, _P, _I, _P, _I, _P]),
             "ft_number_count_band": (_I, [_P, _P, ctypes.c_double, _P, ctypes.POINTER(_P)]),
             "ft_topk_per_band_gated": (_I, [_P, _P, _P, _I, _P, ctypes.c_float, _P, _I, _P]),
             "ft_topk_per_band_noalloc": (_I, [_P, _P, _P, _I, _P, _I, _P]),
@@ -237,6 +249,79 @@ def band_set_sky_weights(band, det_tensor, stream=None):
     if D.shape != (band.n_sft, 6):
         raise ValueError("det_tensor must be [N_SFT][6]")
     _check(lib().ft_band_set_sky_weights(band.handle, D.ctypes.data, _stream(stream, False)))
+
+
+class BinaryBank:
+    """A random binary-orbit bank in hyperboxes (ft_make_binary_bank)."""
+
+    def __init__(self, band, handle):
+        self.band = band
+        self.handle = handle
+        nt, nb = _I64(), _I64()
+        _check(lib().ft_binary_bank_info(handle, ctypes.byref(nt), ctypes.byref(nb)))
+        self.n_templates, self.n_boxes = nt.value, nb.value
+
+    def close(self):
+        if self.handle:
+            lib().ft_binary_bank_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_binary_bank(ctx, band, lo, hi, n_div, n_per_box, seed) -> BinaryBank:
+    """ft_make_binary_bank: lo / hi per dimension (f0 Hz, alpha turns, sin(delta), a_p
+    light-seconds, Omega rad/s, phi_b turns), n_div boxes per dimension, n_per_box templates
+    per box, Philox seed."""
+    d = _BinaryDesc()
+    for k in range(6):
+        d.lo[k] = float(lo[k])
+        d.hi[k] = float(hi[k])
+        d.n_div[k] = int(n_div[k])
+    d.n_per_box = int(n_per_box)
+    d.seed = int(seed) & ((1 << 64) - 1)
+    h = _P()
+    _check(lib().ft_make_binary_bank(ctx.handle, band.handle, ctypes.byref(d), ctypes.byref(h)))
+    return BinaryBank(band, h)
+
+
+def binary_templates(ctx, bank, first, n, stream=None):
+    """lambda [n][6] of templates first .. first + n - 1 as the kernels derive them."""
+    out = np.empty((int(n), 6), np.float64)
+    _check(lib().ft_binary_templates(ctx.handle, bank.handle, int(first), int(n), out.ctypes.data,
+                                     _stream(stream, False)))
+    return out
+
+
+def binary_track_bins(ctx, band, bank, templates, out, stream=None):
+    """ft_binary_track_bins: templates int64 [n], out int32 [n, N_SFT]; both host or device."""
+    pt, dev = _ptr(templates)
+    pb, dev2 = _ptr(out)
+    if dev != dev2:
+        raise ValueError("templates and out must both be host or both device")
+    _check(lib().ft_binary_track_bins(ctx.handle, band.handle, bank.handle, pt, int(templates.shape[0]),
+                                      pb, int(dev), _stream(stream, dev)))
+
+
+def binary_eval(ctx, band, bank, first, n, s_out, z_out=None, n_oob_out=None, stream=None):
+    """ft_binary_eval: s (and z, out-of-window counts) of templates first .. first + n - 1."""
+    ps, dev = _ptr(s_out)
+    pz, _ = _ptr(z_out)
+    po, _ = _ptr(n_oob_out)
+    _check(lib().ft_binary_eval(ctx.handle, band.handle, bank.handle, int(first), int(n), ps, pz, po,
+                                int(dev), _stream(stream, dev)))
+
+
+def binary_topk_per_box(ctx, band, bank, k, out, stream=None):
+    """ft_binary_topk_per_box into a CANDIDATE_DTYPE [n_boxes, k] array or a device byte
+    tensor of n_boxes * k * 16 bytes."""
+    po, dev = _ptr(out)
+    _check(lib().ft_binary_topk_per_box(ctx.handle, band.handle, bank.handle, int(k), po, int(dev),
+                                        _stream(stream, dev)))
 
 
 def number_count_band(ctx, band, threshold=3.2, stream=None):

@@ -155,6 +155,11 @@ int ft_ctx_outbuf(ft_ctx *ctx, size_t bytes, void **p)
     return FT_OK;
 }
 
+int ft_read_status(ft_ctx *ctx, cudaStream_t st)
+{
+    return read_status(ctx, st);
+}
+
 extern "C" {
 
 const char *ft_last_error(void)
@@ -298,8 +303,10 @@ int ft_load_sfts(ft_ctx *ctx, const ft_band_desc *d, const void *power, int powe
     b->weighted = weighted;
     b->h_tau.resize(N);
     b->h_vabs.resize(N);
+    b->h_dt.resize(N);
     double sw = 0, sw2 = 0;
     for (int64_t a = 0; a < N; ++a) {
+        b->h_dt[a] = t_mid[a] - d->t0;
         b->h_tau[a] = (t_mid[a] - d->t0) * d->t_sft;
         const double *v = v_over_c + 3 * a;
         b->h_vabs[a] = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);

@@ -76,6 +76,7 @@ struct ft_band {
     double mu = 0, sigma = 0;
     bool weighted = false;
     std::vector<double> h_tau, h_vabs;
+    std::vector<double> h_dt;  // t_mid - t0 (s), FP64 as given
     double tau_absmax = 0;
     double vmax = 0;  // largest |v| / c over the SFTs
     double *d_D = nullptr;  // [N][6] detector tensors when the all-sky weights are on
@@ -117,6 +118,8 @@ inline bool ft_band_weighted(const ft_band *b)
     return b->weighted || b->d_D != nullptr;
 }
 int ft_ctx_outbuf(ft_ctx *ctx, size_t bytes, void **p);
+// Synchronise `st`, report and clear the device status word (FT_ERR_TIMEOUT etc.).
+int ft_read_status(ft_ctx *ctx, cudaStream_t st);
 
 // ------------------------------------------------------------------ kernel parameters
 

@@ -1,0 +1,205 @@
+"""The binary-orbit track over a random hyperbox bank on the GPU, against the oracle:
+
+* the templates the kernels derive from their Philox counters equal the oracle's, bit for bit;
+* the canonical bins of every (template, SFT) pair equal the oracle's, bit for bit;
+* s per template within the FP32 tolerance (FP32, FP16 and BF16 storage; the oracle reads the
+  same stored values), z and the out-of-window counts;
+* the loudest templates of every hyperbox: the oracle's sets (near-tie exemption) and exactly
+  the CPU selection over the GPU's own values;
+* ragged shapes: boxes that are not a multiple of the CTA, SFT counts that are not a multiple
+  of a stage, a single template, isolated sources (a_p = 0), k above the box population.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import ftsynth
+import oracle
+import paper_2411_18370_b300 as ft
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-6
+DAY = 86400.0
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = ft.create(0)
+    yield c
+    c.close()
+
+
+def _bank(n_div=(2, 2, 2, 2, 1, 2), n_per_box=300, seed=5, f0=(100.0, 100.05), ap=(5.0, 15.0)):
+    om = (2 * math.pi / (15 * DAY), 2 * math.pi / (7 * DAY))
+    return ftsynth.BinaryBank(lo=(f0[0], 0.0, -1.0, ap[0], om[0], 0.0),
+                              hi=(f0[1], 1.0, 1.0, ap[1], om[1], 1.0),
+                              n_div=n_div, n_per_box=n_per_box, seed=seed)
+
+
+def _sfts(n_sft=(150, 123), W=200, wings=55, seed=3, k_band=180_000):
+    g = np.random.default_rng(seed)
+    t_mid, v = [], []
+    for X, n in enumerate(n_sft):
+        t = np.sort(g.uniform(0, ftsynth.YEAR_S, n)) + 900
+        t_mid.append(t)
+        v.append(ftsynth.detector_velocity(t, X))
+    t_mid = np.concatenate(t_mid)
+    N = len(t_mid)
+    return ftsynth.SFTSet(power=g.exponential(2.0, (N, W)), t_mid=t_mid, v=np.concatenate(v),
+                          s_n=np.ones(N), n_sft=list(n_sft), k_lo=k_band - wings, t_sft=1800.0,
+                          t0=0.0)
+
+
+def _stored(sfts, dtype):
+    import torch
+
+    t = torch.from_numpy(sfts.power).to(torch.float32)
+    if dtype != "f32":
+        t = t.to(torch.float16 if dtype == "f16" else torch.bfloat16)
+    return ftsynth.SFTSet(**{**sfts.__dict__, "power": t.to(torch.float64).numpy()})
+
+
+def _gpu_bank(ctx, band, bank):
+    return ft.make_binary_bank(ctx, band, bank.lo, bank.hi, bank.n_div, bank.n_per_box, bank.seed)
+
+
+def test_templates_and_bins_bit_exact(ctx):
+    sfts = _sfts()
+    bank = _bank()
+    band = H.band_from(ctx, sfts, power_f32=True)
+    gb = _gpu_bank(ctx, band, bank)
+    assert gb.n_templates == bank.n_templates and gb.n_boxes == bank.n_boxes
+    lam = ft.binary_templates(ctx, gb, 0, gb.n_templates)
+    lam_or, _ = oracle.binary_templates(bank)
+    assert np.array_equal(lam, lam_or)
+    t = np.random.default_rng(1).choice(bank.n_templates, 400, replace=False).astype(np.int64)
+    out = np.empty((len(t), sfts.n_total), np.int32)
+    ft.binary_track_bins(ctx, band, gb, t, out)
+    assert np.array_equal(out.astype(np.int64), oracle.binary_bins(sfts, bank, t))
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+def test_statistic_and_z(ctx, dtype):
+    sfts = _sfts(seed=4)
+    bank = _bank(seed=6)
+    band = H.band_from(ctx, sfts, dtype=dtype, power_f32=True)
+    gb = _gpu_bank(ctx, band, bank)
+    n = bank.n_templates
+    s = np.empty(n, np.float32)
+    z = np.empty(n, np.float32)
+    o = np.empty(n, np.int32)
+    ft.binary_eval(ctx, band, gb, 0, n, s, z, o)
+    s_or, o_or = oracle.binary_statistic(_stored(sfts, dtype), bank)
+    assert np.array_equal(o, o_or)
+    assert np.all(np.abs(s - s_or) <= REL * np.abs(s_or))
+    mu, sig = oracle.mu_sigma(sfts.n_total)
+    assert np.all(np.abs(z - (s_or - mu) / sig) <= REL * np.abs(s_or) / sig + 1e-6)
+    # a sub-range equals the same slice of the full evaluation
+    s2 = np.empty(777, np.float32)
+    ft.binary_eval(ctx, band, gb, 1001, 777, s2)
+    assert np.array_equal(s2, s[1001:1778])
+
+
+def test_weighted_statistic(ctx):
+    sfts = _sfts(seed=7, n_sft=(100, 77))
+    bank = _bank(seed=8, n_per_box=100)
+    w = np.random.default_rng(3).uniform(0.3, 2.0, sfts.n_total)
+    band = H.band_from(ctx, sfts, w=w, power_f32=True)
+    gb = _gpu_bank(ctx, band, bank)
+    s = np.empty(bank.n_templates, np.float32)
+    ft.binary_eval(ctx, band, gb, 0, bank.n_templates, s)
+    s_or, _ = oracle.binary_statistic(_stored(sfts, "f32"), bank, w=w.astype(np.float32).astype(np.float64))
+    assert np.all(np.abs(s - s_or) <= REL * np.abs(s_or))
+
+
+def _check_topk(ctx, band, gb, sfts_stored, bank, k):
+    out = np.zeros((bank.n_boxes, k), dtype=ft.CANDIDATE_DTYPE)
+    ft.binary_topk_per_box(ctx, band, gb, k, out)
+    s = np.empty(bank.n_templates, np.float32)
+    ft.binary_eval(ctx, band, gb, 0, bank.n_templates, s)
+    s_or, _ = oracle.binary_statistic(sfts_stored, bank)
+    idx, val = out["template_idx"], out["s"]
+    # exactly the CPU selection over the GPU's own values
+    c_idx, c_val = oracle.topk_per_box(s.astype(np.float64), bank.n_per_box, bank.n_boxes, k)
+    assert np.array_equal(idx, c_idx)
+    ok = idx >= 0
+    assert np.array_equal(val[ok].astype(np.float64), c_val[ok])
+    assert np.all(val[~ok] == -np.inf)
+    # the oracle's sets, except where its k-th and (k+1)-th values nearly tie
+    o_idx, o_val = oracle.topk_per_box(s_or, bank.n_per_box, bank.n_boxes, k + 1)
+    for b in range(bank.n_boxes):
+        got = set(int(x) for x in idx[b] if x >= 0)
+        want = set(int(x) for x in o_idx[b, :k] if x >= 0)
+        if got != want:
+            kth, nxt = o_val[b, k - 1], o_val[b, k]
+            assert np.isfinite(nxt) and abs(kth - nxt) < 2e-6 * abs(kth), f"box {b}"
+    mu, sig = oracle.mu_sigma(sfts_stored.n_total)
+    assert np.all(np.abs(out["z"][ok] - (val[ok] - mu) / sig) <= 1e-5)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_topk_per_box(ctx, dtype):
+    sfts = _sfts(seed=9)
+    bank = _bank(seed=10, n_per_box=300)   # 2 tiles per box, the second ragged
+    band = H.band_from(ctx, sfts, dtype=dtype, power_f32=True)
+    gb = _gpu_bank(ctx, band, bank)
+    for k in (1, 5):
+        _check_topk(ctx, band, gb, _stored(sfts, dtype), bank, k)
+
+
+@pytest.mark.parametrize("shape", [
+    dict(n_sft=(5,), n_div=(1, 1, 1, 1, 1, 1), n_per_box=1, k=3),
+    dict(n_sft=(70, 1), n_div=(1, 2, 1, 1, 1, 3), n_per_box=257, k=2),
+    dict(n_sft=(33, 31), n_div=(3, 1, 1, 1, 1, 1), n_per_box=20, k=32, ap=(0.0, 0.0)),
+])
+def test_edge_shapes(ctx, shape):
+    sfts = _sfts(n_sft=shape["n_sft"], seed=11)
+    bank = _bank(n_div=shape["n_div"], n_per_box=shape["n_per_box"], seed=12,
+                 ap=shape.get("ap", (5.0, 15.0)))
+    band = H.band_from(ctx, sfts, power_f32=True)
+    gb = _gpu_bank(ctx, band, bank)
+    s = np.empty(bank.n_templates, np.float32)
+    o = np.empty(bank.n_templates, np.int32)
+    ft.binary_eval(ctx, band, gb, 0, bank.n_templates, s, None, o)
+    s_or, o_or = oracle.binary_statistic(_stored(sfts, "f32"), bank)
+    assert np.array_equal(o, o_or)
+    assert np.all(np.abs(s - s_or) <= REL * np.maximum(np.abs(s_or), 1.0))
+    _check_topk(ctx, band, gb, _stored(sfts, "f32"), bank, shape["k"])
+
+
+def test_bins_leaving_the_window_are_counted(ctx):
+    sfts = _sfts(W=80, wings=5, seed=13)   # narrow wings: many tracks leave the band
+    bank = _bank(seed=14, n_per_box=50)
+    band = H.band_from(ctx, sfts, power_f32=True)
+    gb = _gpu_bank(ctx, band, bank)
+    s = np.empty(bank.n_templates, np.float32)
+    o = np.empty(bank.n_templates, np.int32)
+    ft.binary_eval(ctx, band, gb, 0, bank.n_templates, s, None, o)
+    s_or, o_or = oracle.binary_statistic(_stored(sfts, "f32"), bank)
+    assert o_or.sum() > 0
+    assert np.array_equal(o, o_or)
+    assert np.all(np.abs(s - s_or) <= REL * np.maximum(np.abs(s_or), 1.0))
+
+
+def test_errors(ctx):
+    sfts = _sfts(n_sft=(20,), seed=15)
+    band = H.band_from(ctx, sfts)
+    b = _bank()
+    bad = [dict(lo=(100.0, 0, -1, 5, 1e-5, 0), hi=(99.0, 1, 1, 15, 2e-5, 1)),      # lo > hi
+           dict(lo=(100.0, 0, -1, 1, 1e-5, 0), hi=(100.1, 1, 1, 17, 2e-5, 1)),     # a_p ratio > 16
+           dict(lo=(100.0, 0, -2, 5, 1e-5, 0), hi=(100.1, 1, 1, 15, 2e-5, 1)),     # sin(delta) < -1
+           dict(lo=(100.0, 0, -1, 5, 1e-5, 0), hi=(100.1, 1.5, 1, 15, 2e-5, 1))]   # alpha > 1 turn
+    for d in bad:
+        with pytest.raises(ft.FtError):
+            ft.make_binary_bank(ctx, band, d["lo"], d["hi"], b.n_div, 10, 1)
+    with pytest.raises(ft.FtError):
+        ft.make_binary_bank(ctx, band, b.lo, b.hi, (1, 1, 1, 0, 1, 1), 10, 1)
+    gb = _gpu_bank(ctx, band, b)
+    out = np.zeros((gb.n_boxes, 40), dtype=ft.CANDIDATE_DTYPE)
+    with pytest.raises(ft.FtError):
+        ft.binary_topk_per_box(ctx, band, gb, 40, out)
+    with pytest.raises(ft.FtError):
+        ft.binary_eval(ctx, band, gb, gb.n_templates - 1, 5, np.empty(5, np.float32))
