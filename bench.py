@@ -309,6 +309,138 @@ def run_batch(args):
     return 0
 
 
+# per (template, SFT) operations of the binary track's canonical rule: orbit phase (64-bit
+# multiply, subtract, shift), the quadrant cosine (reduction 5, polynomials 10, select and
+# sign 2, scaling 3), v.n (3), the two products, X (2), the bin (4), bounds + gather + add (3)
+BT_OPS_PER_EVAL = 37
+ISSUE_LANES_PER_CLK_PER_SM = 128
+
+
+def profiled_traffic_binary(dtype):
+    """DRAM bytes per launch of k_bt_eval from the committed capture, or None when there is
+    none or ft_binary.cu changed since."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", f"k_bt_eval_binary_{dtype}_full.md")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line and not line.startswith((" ", "#", "`")):
+            k, v = line.split(":", 1)
+            fields[k.strip()] = v.strip()
+    src = os.path.join(ROOT, "paper_2411_18370_b300", "csrc", "ft_binary.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if fields.get("kernel source sha256 prefix") != sha:
+        return None
+    try:
+        return float(fields["dram bytes per launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def run_binary(args):
+    """The binary-orbit workload: a random hyperbox bank (2^20 templates in 32 boxes) for
+    0.125 Hz at 100 Hz, all sky, a_p 5-15 lt-s, P 7-15 d, over 2 detectors x 183 days of 1024 s
+    SFTs; one step = the loudest template of every box (evaluation + merge)."""
+    import torch
+
+    import ftsynth
+    import oracle
+    import paper_2411_18370_b300 as ft
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    ctx = ft.create(local)
+    sfts, bank = ftsynth.binary_workload()
+    stream = torch.cuda.current_stream()
+    P32 = torch.from_numpy(sfts.power.astype(np.float32))
+    band = ft.load_sfts(ctx, P32.cuda(), sfts.t_mid, sfts.v, sfts.n_sft, sfts.k_lo, sfts.t_sft,
+                        sfts.t0, dtype=args.dtype, s_n=sfts.s_n)
+    gb = ft.make_binary_bank(ctx, band, bank.lo, bank.hi, bank.n_div, bank.n_per_box, bank.seed)
+    k = 1
+    cand = torch.empty(gb.n_boxes * k * 16, dtype=torch.uint8, device="cuda")
+    step = lambda: ft.binary_topk_per_box(ctx, band, gb, k, cand, stream=stream)
+    flushbuf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush = lambda: flushbuf.fill_(1)
+    evals = bank.n_templates * sfts.n_total
+    with ClockSampler(local) as clk:
+        times = time_steps(step, args.steps, args.warmup, stream, flush)
+    ctx.check_status()
+    mean_ms = statistics.mean(times)
+    value = evals / (mean_ms / 1e3)
+    peak_ops = 148 * ISSUE_LANES_PER_CLK_PER_SM * 2032e6
+    achieved = BT_OPS_PER_EVAL * value
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"binary-orbit track, random hyperbox bank: f0 100-100.125 Hz, all sky, "
+                               f"a_p 5-15 lt-s, P 7-15 d, phi_b full orbit; {bank.n_templates} templates "
+                               f"in {bank.n_boxes} boxes; 2 det x 183 d of 1024 s SFTs at 70% duty "
+                               f"({sfts.n_total} SFTs, {sfts.power.shape[1]}-bin window); loudest per box",
+                   "n_sft": sfts.n_total, "n_templates": bank.n_templates, "n_boxes": bank.n_boxes,
+                   "evals_per_step": evals, "storage": args.dtype,
+                   "track_bins": "canonical split rule: exact integer f0 T, 64-bit fixed-point orbit "
+                                 "phase, FP32 Taylor cosine and sub-bin terms",
+                   "l2": "flushed between timed steps (256 MB write, outside the per-step events)"},
+        "roofline": {"bound": "alu", "kernel": "k_bt_eval (per-template track, gather, per-box top-k)",
+                     "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Top/s",
+                     "frac": achieved / peak_ops,
+                     "peak_basis": "derived: 148 SMs x 4 schedulers x 32 lanes x 2032 MHz max SM clock "
+                                   "(one operation per lane per clock)",
+                     "ops_per_eval": BT_OPS_PER_EVAL, "algorithmic_ops_per_launch": BT_OPS_PER_EVAL * evals,
+                     "traffic": profiled_traffic_binary(args.dtype)},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        g = np.random.default_rng(7)
+        n = 256
+        for _ in range(3):
+            samp = g.choice(bank.n_templates, n, replace=False).astype(np.int64)
+            t0 = time.perf_counter()
+            s_or, _ = oracle.binary_statistic(sfts, bank, samp)
+            dt = time.perf_counter() - t0
+            if dt >= 0.66 * args.cpu_seconds:
+                break
+            n = min(bank.n_templates, int(n * args.cpu_seconds / max(dt, 1e-3)))
+        ev = len(samp) * sfts.n_total
+        out["cpu_baseline"] = {"value": ev / dt, "unit": UNIT, "cores": oracle.num_threads(),
+                               "kind": "oracle",
+                               "sample": f"{len(samp)} random templates of the same bank x all "
+                                         f"{sfts.n_total} SFTs ({ev:.3g} evals, {dt:.1f} s, FP64 sums, "
+                                         f"OpenMP over templates)"}
+    if not args.no_e2e:
+        Ph = P32.pin_memory()
+        cand_h = np.zeros((bank.n_boxes, k), dtype=ft.CANDIDATE_DTYPE)
+
+        def e2e_step():
+            b2 = ft.load_sfts(ctx, Ph, sfts.t_mid, sfts.v, sfts.n_sft, sfts.k_lo, sfts.t_sft, sfts.t0,
+                              dtype=args.dtype, s_n=sfts.s_n)
+            g2 = ft.make_binary_bank(ctx, b2, bank.lo, bank.hi, bank.n_div, bank.n_per_box, bank.seed)
+            ft.binary_topk_per_box(ctx, b2, g2, k, cand_h)
+            g2.close()
+            b2.close()
+
+        for _ in range(2):
+            e2e_step()
+        wall = []
+        for _ in range(max(3, args.steps // 4)):
+            flush()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_step()
+            wall.append(time.perf_counter() - t0)
+        e2e_mean = statistics.mean(wall)
+        h2d = P32.numel() * 4 + sfts.t_mid.nbytes + sfts.v.nbytes + sfts.s_n.nbytes + 8 * len(sfts.n_sft)
+        out["e2e"] = {"value": evals / e2e_mean, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(cand_h.nbytes + 4), "ms_per_step": 1e3 * e2e_mean,
+                      "steps": len(wall), "gpu_launches_per_step": 4}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_surrogate(args):
     """The learned-surrogate workload: injection campaigns across the batching workload's
     bands (per-band duty and PSD), a noise-only threshold per band, an ensemble of 4-layer
@@ -347,7 +479,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-s", type=float, default=4.0)
-    ap.add_argument("--workload", default="search", choices=["search", "batch", "surrogate"])
+    ap.add_argument("--workload", default="search", choices=["search", "batch", "surrogate", "binary"])
     ap.add_argument("--sky-scale", type=float, default=0.1)
     ap.add_argument("--n-bands", type=int, default=64)
     ap.add_argument("--n-held", type=int, default=4)
@@ -366,6 +498,8 @@ def main():
         return run_batch(args)
     if args.workload == "surrogate":
         return run_surrogate(args)
+    if args.workload == "binary":
+        return run_binary(args)
 
     import torch
 

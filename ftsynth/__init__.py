@@ -394,6 +394,30 @@ def batch_workload(n_bands: int = 64, sky_scale: float = 1.0, n_slots: int = Non
     return out
 
 
+def binary_workload(days: float = 183.0, duty: float = 0.7, n_div=(2, 2, 2, 1, 1, 4),
+                    n_per_box: int = 32768, seed: int = 2024):
+    """Binary-orbit search slice shaped like the paper's all-sky binary search (Sec. VI.A):
+    2 detectors, `days` of 1024 s SFTs at `duty`, f0 in 100-100.125 Hz (0.125 Hz, the band of
+    the mismatch study in Sec. IV.A), the whole sky, a_p 5-15 light-seconds, orbital period
+    7-15 days, phi_b over the full orbit; a random bank of n_per_box templates in each of
+    prod(n_div) hyperboxes.  Wings cover the Doppler and orbit excursions.  Returns
+    (SFTSet, BinaryBank)."""
+    t_sft = 1024.0
+    n_slots = int(round(days * 86400.0 / t_sft))
+    f_lo, f_hi = 100.0, 100.125
+    ap_hi, om_hi = 15.0, 2 * math.pi / (7 * 86400.0)
+    orbit = math.ceil(f_hi * t_sft * ap_hi * om_hi * (1 + max_v_over_c()))
+    wl, wh = wings_for(f_hi, 0.0, n_slots * t_sft, t_sft)
+    k_band = int(round(f_lo * t_sft))
+    n_bins = int(round((f_hi - f_lo) * t_sft))
+    sfts = make_sfts(5, 2, n_slots, t_sft, duty, k_band, n_bins, wl + orbit + 1, wh + orbit + 1,
+                     psd_range=(0.8, 1.2))
+    bank = BinaryBank(lo=(f_lo, 0.0, -1.0, 5.0, 2 * math.pi / (15 * 86400.0), 0.0),
+                      hi=(f_hi, 1.0, 1.0, ap_hi, om_hi, 1.0), n_div=tuple(n_div),
+                      n_per_box=int(n_per_box), seed=int(seed))
+    return sfts, bank
+
+
 def psd_level(f_hz: float) -> float:
     """Smooth synthetic PSD shape used for the surrogate workload (arbitrary units):
     a steep low-frequency wall, a flat bucket and a rising high-frequency tail."""
