@@ -310,9 +310,10 @@ def run_batch(args):
 
 
 # per (template, SFT) operations of the binary track's canonical rule: orbit phase (64-bit
-# multiply, subtract, shift), the quadrant cosine (reduction 5, polynomials 10, select and
-# sign 2, scaling 3), v.n (3), the two products, X (2), the bin (4), bounds + gather + add (3)
-BT_OPS_PER_EVAL = 37
+# multiply, subtract, shift: 3), the table cosine (quadrant, mirror 2, index, fraction 3,
+# table read, interpolation, sign: 10), v.n (3), the two products (2), X (2), the bin (4),
+# bounds + gather + add (3)
+BT_OPS_PER_EVAL = 27
 ISSUE_LANES_PER_CLK_PER_SM = 128
 
 

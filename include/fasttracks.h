@@ -333,8 +333,11 @@ FT_API int ft_pdet_q(ft_ctx *ctx, const ft_band *band, const double *det_tensor,
  *     n = (cos delta cos alpha, cos delta sin alpha, sin delta) in FP32; D = FP32(F a_p Omega);
  *     orbit frequency nu = Omega / 2 pi as round(nu 2^54) and phase phi_b as phi_b 2^64;
  *   - per SFT: t_q = round((t_mid - t0) 2^10); orbit phase theta = top 32 bits of
- *     (nu_q t_q - psi_q) mod 2^64; its cosine by Taylor polynomials (to x^10 / x^9) on the
- *     nearest quadrant in FP32; X = (phi + F (v.n)) - D cos in FP32; bin = K + floor(X + 1/2).
+ *     (nu_q t_q - psi_q) mod 2^64; its cosine by linear interpolation in a quarter-wave table
+ *     (1024 intervals; entries cos(i pi / 2048) from the host's libm rounded to FP32, FP32
+ *     differences; odd quadrants mirrored, quadrants 1 and 2 negated); X = (phi + F (v.n)) -
+ *     D cos in FP32; bin = K + floor(X + 1/2).  The sky vector's cos / sin of alpha use the
+ *     same table.
  *   Bins outside the band contribute 0 and are counted, as for the isolated bank.
  */
 typedef struct ft_binary_bank ft_binary_bank;

@@ -21,7 +21,8 @@
  *     the sky vector and the orbit amplitude D = F a_p Omega in FP32; the orbit frequency and
  *     phase as 64-bit fixed point (turns);
  *   - per SFT: the orbit phase of (t_mid - t0) in exact 64-bit integer arithmetic, its cosine
- *     from a Taylor polynomial on the nearest quadrant in FP32, and
+ *     by linear interpolation in a quarter-wave table of 1024 intervals (entries: libm's
+ *     cos rounded to FP32, differences in FP32), and
  *         X = (phi + F v.n) - D cos,  bin = K + floor(X + 1/2)   (FP32, operations as written).
  *   or_bt_bins also returns the FP64 bin of Eq. (track) with libm's cos and its distance from
  *   the rounding boundary, which pins the canonical rule to the plain definition.
@@ -136,29 +137,37 @@ void or_bt_lambda(const or_bdesc *b, int64_t i, double lam[6])
         lam[2] = -1.0;
 }
 
-/* cos(2 pi theta / 2^32): nearest quadrant, Taylor polynomials of cos and sin in FP32 */
+/* quarter-wave table: C[i] = cos(i (pi/2) / 1024) (libm, FP64, rounded to FP32), D[i] =
+ * C[i+1] - C[i] in FP32, D[1024] = 0 */
+static float tab_c[1025], tab_d[1025];
+static int tab_ready;
+
+void or_bt_init(void)
+{
+    if (tab_ready)
+        return;
+    for (int i = 0; i <= 1024; i++)
+        tab_c[i] = (float)cos((double)i * 1.5339807878856412e-03);
+    for (int i = 0; i < 1024; i++)
+        tab_d[i] = tab_c[i + 1] - tab_c[i];
+    tab_d[1024] = 0.0f;
+    tab_ready = 1;
+}
+
+/* cos(2 pi theta / 2^32): quadrant q = theta >> 30, position u within it (mirrored in odd
+ * quadrants), linear interpolation between table entries u >> 20 and the next, negative in
+ * quadrants 1 and 2 */
 float or_cos_q32(uint32_t theta)
 {
-    uint32_t q = (theta + 0x20000000u) >> 30;
-    int32_t r = (int32_t)(theta - (q << 30));
-    float x = (float)r * 0x1.921fb6p-30f;
-    float x2 = x * x;
-    float c = fmaf(-0x1.27e4fcp-22f, x2, 0x1.a01a02p-16f);
-    c = fmaf(c, x2, -0x1.6c16c2p-10f);
-    c = fmaf(c, x2, 0x1.555556p-5f);
-    c = fmaf(c, x2, -0.5f);
-    c = fmaf(c, x2, 1.0f);
-    float s = fmaf(0x1.71de3ap-19f, x2, -0x1.a01a02p-13f);
-    s = fmaf(s, x2, 0x1.111112p-7f);
-    s = fmaf(s, x2, -0x1.555556p-3f);
-    s = fmaf(s, x2, 1.0f);
-    s = x * s;
-    switch (q & 3u) {
-    case 0: return c;
-    case 1: return -s;
-    case 2: return -c;
-    default: return s;
-    }
+    or_bt_init();
+    uint32_t q = theta >> 30;
+    uint32_t u = theta & 0x3FFFFFFFu;
+    if (q & 1u)
+        u = 0x40000000u - u;
+    uint32_t i = u >> 20;
+    float f = (float)(u & 0xFFFFFu) * 0x1p-20f;
+    float c = fmaf(f, tab_d[i], tab_c[i]);
+    return (q == 1u || q == 2u) ? -c : c;
 }
 
 void or_bt_derived(const double lam[6], double t_sft, int64_t k_lo, or_bder *o)
@@ -207,6 +216,7 @@ void or_bt_bins(const or_bdesc *b, const int64_t *tmpl, int64_t n, int64_t N, co
                  const double *v, double t0, double t_sft, int64_t k_lo, int64_t *bins,
                  int64_t *bins64, double *dist)
 {
+    or_bt_init();
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < n; i++) {
         double lam[6];
@@ -236,6 +246,7 @@ void or_bt_statistic(const or_bdesc *b, const int64_t *tmpl, int64_t n, int64_t 
                       const double *power, const double *w, const double *t_mid, const double *v,
                       double t0, double t_sft, int64_t k_lo, double *s, int32_t *oob)
 {
+    or_bt_init();
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < n; i++) {
         double lam[6];

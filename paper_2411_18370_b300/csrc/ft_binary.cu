@@ -28,12 +28,14 @@ struct ft_binary_bank {
     int n_pad = 0;                 // rows of d_rowv / d_tq (N rounded up to kBtRowPad)
     float4 *d_rowv = nullptr;      // [n_pad] (v/c as FP32, weight); zero beyond N
     long long *d_tq = nullptr;     // [n_pad] round((t_mid - t0) 2^10)
+    float2 *d_costab = nullptr;    // [kBtTab + 1] quarter-wave cosine table (value, difference)
 };
 
 namespace {
 
 constexpr int kBtThreads = 256;
 constexpr int kBtRowPad = 64;
+constexpr int kBtTab = 1024;  // intervals of the quarter-wave cosine table
 
 struct BtParams {
     double xlo[6], step[6];
@@ -49,6 +51,7 @@ struct BtParams {
     int W, N, S, n_stages;
     const float4 *rowv;
     const long long *tq;
+    const float2 *costab;          // (cos(i (pi/2) / 1024) in FP32, next minus this)
     double mu, sigma;
     // eval mode (box_mode == 0): templates [first, first + count), CTA c takes kBtThreads of them
     long long first, count;
@@ -61,6 +64,10 @@ struct BtParams {
 };
 
 // ------------------------------------------------------------------ canonical rule
+//
+// Every step below is the canonical bin rule (header: the binary section): the same
+// operations in the same precision and order as its statement, so that the bins are a
+// function of (seed, template, SFT) alone.
 
 __device__ __forceinline__ void bt_philox(unsigned c0, unsigned c1, unsigned c2, unsigned c3,
                                           unsigned k0, unsigned k1, unsigned o[4])
@@ -142,26 +149,19 @@ __device__ void bt_lambda(const BtParams &p, long long i, double lam[6])
     lam[2] = fmin(fmax(lam[2], -1.0), 1.0);
 }
 
-// cos(2 pi theta / 2^32): nearest quadrant, Taylor polynomials of cos (to x^10) and sin
-// (to x^9) in FP32, coefficients 1/n! rounded to FP32
-__device__ __forceinline__ float bt_cos_q32(unsigned theta)
+// cos(2 pi theta / 2^32): quadrant q = theta >> 30, position u within it (mirrored in odd
+// quadrants), linear interpolation between entries u >> 20 and the next of the quarter-wave
+// table, negative in quadrants 1 and 2
+__device__ __forceinline__ float bt_cos_q32(unsigned theta, const float2 *tab)
 {
-    const unsigned q = (theta + 0x20000000u) >> 30;
-    const int r = static_cast<int>(theta - (q << 30));
-    const float x = __fmul_rn(__int2float_rn(r), 0x1.921fb6p-30f);
-    const float x2 = __fmul_rn(x, x);
-    float c = __fmaf_rn(-0x1.27e4fcp-22f, x2, 0x1.a01a02p-16f);
-    c = __fmaf_rn(c, x2, -0x1.6c16c2p-10f);
-    c = __fmaf_rn(c, x2, 0x1.555556p-5f);
-    c = __fmaf_rn(c, x2, -0.5f);
-    c = __fmaf_rn(c, x2, 1.0f);
-    float s = __fmaf_rn(0x1.71de3ap-19f, x2, -0x1.a01a02p-13f);
-    s = __fmaf_rn(s, x2, 0x1.111112p-7f);
-    s = __fmaf_rn(s, x2, -0x1.555556p-3f);
-    s = __fmaf_rn(s, x2, 1.0f);
-    s = __fmul_rn(x, s);
-    const float v = (q & 1u) ? s : c;
-    return ((q + 1u) & 2u) ? -v : v;  // quadrants 1, 2 negative
+    const unsigned q = theta >> 30;
+    unsigned u = theta & 0x3FFFFFFFu;
+    if (q & 1u)
+        u = 0x40000000u - u;
+    const float f = __fmul_rn(__uint2float_rn(u & 0xFFFFFu), 0x1p-20f);
+    const float2 e = tab[u >> 20];
+    const float c = __fmaf_rn(f, e.y, e.x);
+    return (q == 1u || q == 2u) ? -c : c;
 }
 
 struct BtTmpl {
@@ -170,7 +170,7 @@ struct BtTmpl {
     unsigned long long nu_q, psi_q;
 };
 
-__device__ void bt_derive(const BtParams &p, const double lam[6], BtTmpl &t)
+__device__ void bt_derive(const BtParams &p, const double lam[6], const float2 *tab, BtTmpl &t)
 {
     const double F = __dmul_rn(lam[0], p.t_sft);
     const double Fl = floor(F);
@@ -180,8 +180,8 @@ __device__ void bt_derive(const BtParams &p, const double lam[6], BtTmpl &t)
     const double c2 = __dsub_rn(1.0, __dmul_rn(lam[2], lam[2]));
     const float cd = __double2float_rn(__dsqrt_rn(c2 > 0.0 ? c2 : 0.0));
     const unsigned ta = __double2uint_rz(__dmul_rn(lam[1], 4294967296.0));
-    t.nx = __fmul_rn(cd, bt_cos_q32(ta));
-    t.ny = __fmul_rn(cd, bt_cos_q32(ta - 0x40000000u));
+    t.nx = __fmul_rn(cd, bt_cos_q32(ta, tab));
+    t.ny = __fmul_rn(cd, bt_cos_q32(ta - 0x40000000u, tab));
     t.nz = __double2float_rn(lam[2]);
     t.D = __double2float_rn(__dmul_rn(__dmul_rn(F, lam[3]), lam[4]));
     const double nu = __ddiv_rn(lam[4], 6.283185307179586);
@@ -189,10 +189,10 @@ __device__ void bt_derive(const BtParams &p, const double lam[6], BtTmpl &t)
     t.psi_q = __double2ull_rz(__dmul_rn(lam[5], 18446744073709551616.0));
 }
 
-__device__ __forceinline__ int bt_bin(const BtTmpl &t, float4 v, long long tq)
+__device__ __forceinline__ int bt_bin(const BtTmpl &t, float4 v, long long tq, const float2 *tab)
 {
     const unsigned long long ph = t.nu_q * static_cast<unsigned long long>(tq) - t.psi_q;
-    const float c = bt_cos_q32(static_cast<unsigned>(ph >> 32));
+    const float c = bt_cos_q32(static_cast<unsigned>(ph >> 32), tab);
     const float a = __fmul_rn(v.z, t.nz);
     const float b = __fmaf_rn(v.y, t.ny, a);
     const float vn = __fmaf_rn(v.x, t.nx, b);
@@ -252,6 +252,7 @@ __global__ void __launch_bounds__(kBtThreads) k_bt_eval(const BtParams p)
     long long *stq[2] = {reinterpret_cast<long long *>(sv[1] + p.S),
                          reinterpret_cast<long long *>(sv[1] + p.S) + p.S};
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(stq[1] + p.S);
+    float2 *tab = reinterpret_cast<float2 *>(bars + 2);
 
     // this CTA's templates
     long long t_begin, t_end;
@@ -272,6 +273,8 @@ __global__ void __launch_bounds__(kBtThreads) k_bt_eval(const BtParams p)
         ftp::mbar_init(&bars[1], 1);
         ftp::fence_mbar_init();
     }
+    for (int i = threadIdx.x; i <= kBtTab; i += kBtThreads)
+        tab[i] = p.costab[i];
     __syncthreads();
     if (threadIdx.x < 32) {
         bt_issue(p, 0, rows[0], sv[0], stq[0], &bars[0]);
@@ -283,7 +286,7 @@ __global__ void __launch_bounds__(kBtThreads) k_bt_eval(const BtParams p)
     {
         double lam[6];
         bt_lambda(p, valid ? ti : t_begin, lam);
-        bt_derive(p, lam, t);
+        bt_derive(p, lam, tab, t);
     }
 
     float hi = 0.f, lo = 0.f;
@@ -299,7 +302,7 @@ __global__ void __launch_bounds__(kBtThreads) k_bt_eval(const BtParams p)
 #pragma unroll 4
             for (int r = 0; r < nr; ++r) {
                 const float4 v = sv[b][r];
-                const int k = bt_bin(t, v, stq[b][r]);
+                const int k = bt_bin(t, v, stq[b][r], tab);
                 const bool in = static_cast<unsigned>(k) < static_cast<unsigned>(p.W);
                 const float val = in ? bt_load<T>(rb + static_cast<size_t>(r) * p.row_bytes, k) : 0.f;
                 oob += in ? 0 : 1;
@@ -491,9 +494,9 @@ __global__ void k_bt_bins(const BtParams p, const long long *tmpl, long long n, 
     double lam[6];
     bt_lambda(p, tmpl[i], lam);
     BtTmpl t;
-    bt_derive(p, lam, t);
+    bt_derive(p, lam, p.costab, t);
     for (int a = threadIdx.x; a < p.N; a += blockDim.x)
-        bins[i * p.N + a] = bt_bin(t, p.rowv[a], p.tq[a]);
+        bins[i * p.N + a] = bt_bin(t, p.rowv[a], p.tq[a], p.costab);
 }
 
 __global__ void k_bt_rowv(const double *v, const float *w, int N, int n_pad, float4 *out)
@@ -577,6 +580,7 @@ BtParams base_params(const ft_band *band, const ft_binary_bank *bk)
     p.N = static_cast<int>(band->N);
     p.rowv = bk->d_rowv;
     p.tq = bk->d_tq;
+    p.costab = bk->d_costab;
     p.mu = band->mu;
     p.sigma = band->sigma;
     p.status = band->ctx->d_status;
@@ -585,17 +589,18 @@ BtParams base_params(const ft_band *band, const ft_binary_bank *bk)
 
 int stage_rows(const ft_band *band)
 {
-    // about 24 KB of rows per stage, 8..64 rows (a divisor of kBtRowPad)
+    // at most 16 KB of rows per stage, 8..64 rows (a divisor of kBtRowPad): two stages and
+    // the cosine table leave room for 4 CTAs of 256 threads per SM
     const int rb = band->Wp * elem_bytes(band->dtype);
     int S = 64;
-    while (S > 8 && S * rb > 24 * 1024)
+    while (S > 8 && S * rb > 16 * 1024)
         S >>= 1;
     return S;
 }
 
 size_t eval_smem(const BtParams &p)
 {
-    return 2 * (static_cast<size_t>(p.S) * p.row_bytes + p.S * 24) + 16;
+    return 2 * (static_cast<size_t>(p.S) * p.row_bytes + p.S * 24) + 16 + (kBtTab + 1) * sizeof(float2);
 }
 
 template <typename T, bool Wt>
@@ -711,12 +716,22 @@ int ft_make_binary_bank(ft_ctx *ctx, const ft_band *band, const ft_binary_bank_d
         ft_binary_bank_destroy(b);
         return rc;
     };
+    // quarter-wave cosine table: cos(i (pi/2) / 1024) from the host's libm in FP64, rounded
+    // to FP32, with the FP32 difference to the next entry (0 after the last)
+    float tc[kBtTab + 1];
+    for (int i = 0; i <= kBtTab; ++i)
+        tc[i] = static_cast<float>(std::cos(static_cast<double>(i) * 1.5339807878856412e-03));
+    std::vector<float2> tab(kBtTab + 1);
+    for (int i = 0; i <= kBtTab; ++i)
+        tab[i] = make_float2(tc[i], i < kBtTab ? tc[i + 1] - tc[i] : 0.0f);
     if (cudaMalloc(&b->d_rowv, static_cast<size_t>(b->n_pad) * sizeof(float4)) != cudaSuccess ||
-        cudaMalloc(&b->d_tq, static_cast<size_t>(b->n_pad) * sizeof(long long)) != cudaSuccess) {
+        cudaMalloc(&b->d_tq, static_cast<size_t>(b->n_pad) * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc(&b->d_costab, tab.size() * sizeof(float2)) != cudaSuccess) {
         ft_set_error("make_binary_bank: allocation failed");
         return fail(FT_ERR_OOM);
     }
-    if (cudaMemcpy(b->d_tq, tq.data(), tq.size() * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (cudaMemcpy(b->d_tq, tq.data(), tq.size() * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_costab, tab.data(), tab.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
         ft_set_error("make_binary_bank: copy failed");
         return fail(FT_ERR_CUDA);
     }
@@ -736,6 +751,7 @@ void ft_binary_bank_destroy(ft_binary_bank *b)
     Guard g(b->device);
     cudaFree(b->d_rowv);
     cudaFree(b->d_tq);
+    cudaFree(b->d_costab);
     delete b;
 }
 

@@ -1,7 +1,9 @@
 """Pins of the oracle's binary-orbit track (Eq. (track)) and random hyperbox bank
 (Eq. (xi_of_lambda), App. A Eq. (unif_transform), Sec. IV.B):
 
-* the canonical FP32 cosine of a 32-bit phase is within FP32 rounding of libm's cos;
+* the canonical cosine of a 32-bit phase (linear interpolation in a quarter-wave table of
+  1024 intervals) is within the interpolation bound (pi/2048)^2 / 8 = 2.9e-7 plus FP32
+  rounding of libm's cos, and exact at the table's nodes;
 * every template lies in its own box and is uniform in the uniform coordinates
   xi = {f0^6, alpha, sin(delta), a_p^3, Omega^4, phi_b} there (mean 1/2, variance 1/12 of the
   position within the box along each axis);
@@ -52,10 +54,16 @@ def test_canonical_cosine():
                                   np.uint64)])
     c = oracle.cos_q32(th).astype(np.float64)
     ref = np.cos(2 * np.pi * th.astype(np.float64) / 2 ** 32)
-    assert np.max(np.abs(c - ref)) < 3e-7
+    bound = (np.pi / 2048) ** 2 / 8 + 1.2e-7
+    assert np.max(np.abs(c - ref)) < bound
     s = oracle.cos_q32((th - (1 << 30)) % 2 ** 32).astype(np.float64)
-    assert np.max(np.abs(s - np.sin(2 * np.pi * th.astype(np.float64) / 2 ** 32))) < 3e-7
+    assert np.max(np.abs(s - np.sin(2 * np.pi * th.astype(np.float64) / 2 ** 32))) < bound
     assert oracle.cos_q32([0])[0] == 1.0
+    # nodes: the FP32 rounding of cos at multiples of (pi/2) / 1024, in every quadrant
+    nodes = np.arange(0, 4096, dtype=np.uint64) << np.uint64(20)
+    want = np.cos(np.arange(4096) * (np.pi / 2048)).astype(np.float32)
+    got = oracle.cos_q32(nodes)
+    assert np.max(np.abs(got.astype(np.float64) - want.astype(np.float64))) < 1.2e-7
 
 
 def _xi(lam):
