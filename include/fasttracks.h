@@ -443,6 +443,13 @@ FT_API int ft_set_tune(ft_ctx *ctx, const ft_tune *tune);
  * FT_ERR_ARG (null pointer, bad dtype), FT_ERR_OOM, FT_ERR_CUDA. */
 FT_API int ft_gather_roof(ft_ctx *ctx, int dtype, double *evals_per_s, double *evals_per_clk_sm);
 
+/* Failure-detection self-test: one CTA waits on an mbarrier that no thread ever arrives at,
+ * with the same bounded wait (about 1 s of %globaltimer) as the search kernels, records
+ * FT_STATUS_TIMEOUT in the context's status word and returns.  The call synchronises
+ * `stream` and returns FT_ERR_TIMEOUT as a search that ran out would; the status word is
+ * then clear and the context usable.  *waited_s (nullable) gets the device-measured wait. */
+FT_API int ft_selftest_bounded_wait(ft_ctx *ctx, double *waited_s, void *stream);
+
 /* ----------------------------------------------------------------------------- batches --
  * Many bands of uneven width and sky density searched by one persistent launch (the
  * batching pattern; each band's statistic and candidates are those of ft_topk_per_band).

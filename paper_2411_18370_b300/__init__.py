@@ -98,6 +98,7 @@ def lib():
             "ft_gather_roof": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
             "ft_pdet_q": (_I, [_P, _P, _P, _I64, _P, _P, _P, _P]),
             "ft_band_set_sky_weights": (_I, [_P, _P, _P]),
+            "ft_selftest_bounded_wait": (_I, [_P, ctypes.POINTER(ctypes.c_double), _P]),
             "ft_make_binary_bank": (_I, [_P, _P, ctypes.POINTER(_BinaryDesc), ctypes.POINTER(_P)]),
             "ft_binary_bank_destroy": (None, [_P]),
             "ft_binary_bank_info": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
@@ -344,6 +345,14 @@ def pdet_q(ctx, band, det_tensor, pop, stream=None):
     _check(lib().ft_pdet_q(ctx.handle, band.handle, D.ctypes.data, n, pop.ctypes.data,
                            r1.ctypes.data, r2.ctypes.data, _stream(stream, False)))
     return r1, r2
+
+
+def selftest_bounded_wait(ctx, stream=None):
+    """ft_selftest_bounded_wait: returns (return code, seconds waited on the device); the code
+    is FT_ERR_TIMEOUT when the bounded wait and the status plumbing work."""
+    w = ctypes.c_double()
+    rc = lib().ft_selftest_bounded_wait(ctx.handle, ctypes.byref(w), _stream(stream, False))
+    return rc, w.value
 
 
 def gather_roof(ctx, dtype="f16"):
