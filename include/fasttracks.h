@@ -385,6 +385,15 @@ FT_API int ft_binary_eval(ft_ctx *ctx, const ft_band *band, const ft_binary_bank
 FT_API int ft_binary_topk_per_box(ft_ctx *ctx, const ft_band *band, const ft_binary_bank *bank,
                                   int k, ft_candidate *out, int out_on_device, void *stream);
 
+/* ft_binary_topk_per_box among templates with gate[t] >= gate_min only (Sec. VI.B: the
+ * loudest normalised power whose weighted number count reaches its noise mean + 3 sigma;
+ * gate = s_out of ft_binary_eval on the ft_number_count_band of the same data, with a bank
+ * of the same description).  gate: device [n_templates] float.  Errors: FT_ERR_ARG (host or
+ * null gate, NaN gate_min), else as ft_binary_topk_per_box. */
+FT_API int ft_binary_topk_per_box_gated(ft_ctx *ctx, const ft_band *band, const ft_binary_bank *bank,
+                                        int k, const float *gate, float gate_min, ft_candidate *out,
+                                        int out_on_device, void *stream);
+
 /* ----------------------------------------------------------------------------- surrogate --
  * A learned model of the detection probability p_det (Sec. V, Eqs. (pdet_abstract),
  * (simple_eq)) trained on injection-recovery outcomes: a 4-layer perceptron

@@ -106,6 +106,7 @@ def lib():
             "ft_binary_track_bins": (_I, [_P, _P, _P, _P, _I64, _P, _I, _P]),
             "ft_binary_eval": (_I, [_P, _P, _P, _I64, _I64, _P, _P, _P, _I, _P]),
             "ft_binary_topk_per_box": (_I, [_P, _P, _P, _I, _P, _I, _P]),
+            "ft_binary_topk_per_box_gated": (_I, [_P, _P, _P, _I, _P, ctypes.c_float, _P, _I, _P]),
             "ft_number_count_band": (_I, [_P, _P, ctypes.c_double, _P, ctypes.POINTER(_P)]),
             "ft_topk_per_band_gated": (_I, [_P, _P, _P, _I, _P, ctypes.c_float, _P, _I, _P]),
             "ft_topk_per_band_noalloc": (_I, [_P, _P, _P, _I, _P, _I, _P]),
@@ -323,6 +324,16 @@ def binary_topk_per_box(ctx, band, bank, k, out, stream=None):
     po, dev = _ptr(out)
     _check(lib().ft_binary_topk_per_box(ctx.handle, band.handle, bank.handle, int(k), po, int(dev),
                                         _stream(stream, dev)))
+
+
+def binary_topk_per_box_gated(ctx, band, bank, k, gate, gate_min, out, stream=None):
+    """ft_binary_topk_per_box_gated: gate is a CUDA float32 tensor of n_templates values."""
+    pg, gdev = _ptr(gate)
+    if not gdev:
+        raise ValueError("gate must be a CUDA tensor")
+    po, dev = _ptr(out)
+    _check(lib().ft_binary_topk_per_box_gated(ctx.handle, band.handle, bank.handle, int(k), pg,
+                                              float(gate_min), po, int(dev), _stream(stream, dev)))
 
 
 def number_count_band(ctx, band, threshold=3.2, stream=None):

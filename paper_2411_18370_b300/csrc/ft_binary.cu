@@ -60,6 +60,8 @@ struct BtParams {
     // box mode: CTA c is tile c % tiles_per_box of box c / tiles_per_box
     int box_mode, tiles_per_box, k;
     ft_candidate *cand;            // [n_ctas][k]
+    const float *gate;             // null, or [n_templates]: only gate[t] >= gate_min compete
+    float gate_min;
     unsigned *status;
 };
 
@@ -350,7 +352,8 @@ __global__ void __launch_bounds__(kBtThreads) k_bt_eval(const BtParams p)
     // keys ranked after the previous pick
     float *vs = reinterpret_cast<float *>(smem);
     float *vz = vs + kBtThreads;
-    vs[threadIdx.x] = valid ? sv_ : -INFINITY;
+    const bool pass = valid && (p.gate == nullptr || p.gate[ti] >= p.gate_min);
+    vs[threadIdx.x] = pass ? sv_ : -INFINITY;  // -inf: not a candidate
     vz[threadIdx.x] = static_cast<float>((static_cast<double>(hi) + static_cast<double>(lo) - p.mu) / p.sigma);
     __syncthreads();
     if (threadIdx.x >= 32)
@@ -366,6 +369,8 @@ __global__ void __launch_bounds__(kBtThreads) k_bt_eval(const BtParams p)
         long long bt = LLONG_MAX;
         for (int q = lane; q < n_here; q += 32) {
             const float s = vs[q];
+            if (s == -INFINITY)
+                continue;
             const long long tt = t_begin + q;
             const bool elig = (s < last_s) || (s == last_s && tt > last_t);
             if (elig && (!have || s > bs || (s == bs && tt < bt))) {
@@ -862,8 +867,10 @@ int ft_binary_eval(ft_ctx *ctx, const ft_band *band, const ft_binary_bank *bank,
     return FT_OK;
 }
 
-int ft_binary_topk_per_box(ft_ctx *ctx, const ft_band *band, const ft_binary_bank *bank, int k,
-                           ft_candidate *out, int out_on_device, void *stream)
+namespace {
+
+int binary_topk(ft_ctx *ctx, const ft_band *band, const ft_binary_bank *bank, int k, const float *gate,
+                float gate_min, ft_candidate *out, int out_on_device, void *stream)
 {
     FT_TRY(check(ctx, band, bank));
     if (!out)
@@ -890,6 +897,8 @@ int ft_binary_topk_per_box(ft_ctx *ctx, const ft_band *band, const ft_binary_ban
     }
     BtParams p = base_params(band, bank);
     p.box_mode = 1;
+    p.gate = gate;
+    p.gate_min = gate_min;
     p.tiles_per_box = static_cast<int>(tiles);
     p.k = k;
     p.cand = static_cast<ft_candidate *>(scr);
@@ -901,4 +910,28 @@ int ft_binary_topk_per_box(ft_ctx *ctx, const ft_band *band, const ft_binary_ban
         return ft_read_status(ctx, st);
     }
     return FT_OK;
+}
+
+}  // namespace
+
+int ft_binary_topk_per_box(ft_ctx *ctx, const ft_band *band, const ft_binary_bank *bank, int k,
+                           ft_candidate *out, int out_on_device, void *stream)
+{
+    return binary_topk(ctx, band, bank, k, nullptr, 0.f, out, out_on_device, stream);
+}
+
+int ft_binary_topk_per_box_gated(ft_ctx *ctx, const ft_band *band, const ft_binary_bank *bank, int k,
+                                 const float *gate, float gate_min, ft_candidate *out,
+                                 int out_on_device, void *stream)
+{
+    if (!gate)
+        FT_FAIL(FT_ERR_ARG, "binary_topk_per_box_gated: null gate");
+    if (std::isnan(gate_min))
+        FT_FAIL(FT_ERR_ARG, "binary_topk_per_box_gated: gate_min is NaN");
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, gate) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        FT_FAIL(FT_ERR_ARG, "binary_topk_per_box_gated: gate must be device memory");
+    }
+    return binary_topk(ctx, band, bank, k, gate, gate_min, out, out_on_device, stream);
 }

@@ -7,7 +7,8 @@
 * the loudest templates of every hyperbox: the oracle's sets (near-tie exemption) and exactly
   the CPU selection over the GPU's own values;
 * ragged shapes: boxes that are not a multiple of the CTA, SFT counts that are not a multiple
-  of a stage, a single template, isolated sources (a_p = 0), k above the box population.
+  of a stage, a single template, isolated sources (a_p = 0), k above the box population;
+* the number count along binary tracks (exact) and the count-gated per-box selection.
 """
 import math
 
@@ -203,3 +204,39 @@ def test_errors(ctx):
         ft.binary_topk_per_box(ctx, band, gb, 40, out)
     with pytest.raises(ft.FtError):
         ft.binary_eval(ctx, band, gb, gb.n_templates - 1, 5, np.empty(5, np.float32))
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_number_count_gated_boxes(ctx, dtype):
+    """Sec. VI.B on the binary bank: the loudest s per box among templates whose number
+    count reaches its noise mean + sigma (a gate that keeps a few templates per box)."""
+    import dataclasses
+
+    import torch
+
+    sfts = _sfts(seed=16)
+    bank = _bank(seed=17, n_per_box=300)
+    band = H.band_from(ctx, sfts, dtype=dtype, power_f32=True)
+    gb = _gpu_bank(ctx, band, bank)
+    ncb = ft.number_count_band(ctx, band, 3.2)
+    gnc = _gpu_bank(ctx, ncb, bank)
+    n = bank.n_templates
+    gate = torch.empty(n, dtype=torch.float32, device="cuda")
+    ft.binary_eval(ctx, ncb, gnc, 0, n, gate)
+    torch.cuda.synchronize()
+    stored = _stored(sfts, dtype)
+    nc_or, _ = oracle.binary_statistic(dataclasses.replace(stored, power=(stored.power > 3.2) * 1.0), bank)
+    assert np.array_equal(gate.cpu().numpy().astype(np.float64), nc_or)
+    s = np.empty(n, np.float32)
+    ft.binary_eval(ctx, band, gb, 0, n, s)
+    for gmin in (ncb.mu_g + ncb.sigma_g, ncb.mu_g + 3 * ncb.sigma_g):
+        keep = nc_or >= np.float32(gmin)
+        k = 3
+        out = np.zeros((bank.n_boxes, k), dtype=ft.CANDIDATE_DTYPE)
+        ft.binary_topk_per_box_gated(ctx, band, gb, k, gate, gmin, out)
+        t = np.arange(n)[keep]
+        c_idx, c_val = oracle.topk_per_box(s[keep].astype(np.float64), bank.n_per_box, bank.n_boxes, k, t)
+        assert np.array_equal(out["template_idx"], c_idx)
+        ok = c_idx >= 0
+        assert np.array_equal(out["s"][ok].astype(np.float64), c_val[ok])
+        assert np.all(out["s"][~ok] == -np.inf)
