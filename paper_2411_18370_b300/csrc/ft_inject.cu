@@ -38,6 +38,12 @@ struct InjRun {
     double h0, cosi, psi, f0, f1, n[3];
 };
 
+// float count rounded up to a multiple of 4 (16 bytes)
+__host__ __device__ constexpr int align16f(int n)
+{
+    return (n + 3) & ~3;
+}
+
 struct InjParams {
     long long N, k_lo, K0;
     int n_f0, n_f1, K, half_f0, H;
@@ -46,7 +52,12 @@ struct InjParams {
     const float *w;
     const long long *G;          // [n_f1][N]
     const InjRun *runs;          // [n_runs]
-    const int *sky_idx;          // [n_runs][K]
+    const int *sky_idx;          // [n_runs][K] indices into the bank's sky points
+    const int *sky_cidx;         // [n_runs][K] indices into the E / C tables
+    const int *Etab;             // [n_used][N] E of the used sky points
+    const long long *Ctab;       // [n_used][N] C of the used sky points
+    const long long *ksig_rows;  // [n_runs][N] signal bin of each run and row (window centre)
+    const float *amp_rows;       // [n_runs][N] signal amplitude sqrt(rho^2)
     unsigned long long seed, first_id;
     double *max_z;
     long long *argmax, *oob;
@@ -123,18 +134,66 @@ __device__ __forceinline__ long long cross_q32_inj(long long G, int E)
     return static_cast<long long>(Gh) * E + (lo >> 32);
 }
 
-__global__ void __launch_bounds__(kInjThreads) k_injections(const InjParams p)
+// E and C (Q32 track terms, FP64 as in the search kernels) of the used sky points in every
+// row: [n_used][N].
+__global__ void k_inj_ec(long long N, int n_used, const int *used, const double *v, const double *sky,
+                         long long K0, long long k_lo, int *Etab, long long *Ctab)
+{
+    const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (i >= N * n_used)
+        return;
+    const long long u = i / N, a = i - u * N;
+    int E;
+    long long C;
+    track_ec_inj(v + 3 * a, sky + 3 * used[u], K0, k_lo, E, C);
+    Etab[i] = E;
+    Ctab[i] = C;
+}
+
+// The signal bin and amplitude of every (run, row): [n_runs][N].
+__global__ void k_inj_rows(const InjParams p, long long n_runs, long long *ksig_rows, float *amp_rows)
+{
+    const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (i >= n_runs * p.N)
+        return;
+    const long long run = i / p.N, a = i - run * p.N;
+    const InjRun inj = p.runs[run];
+    const double *v = p.v + 3 * a;
+    const double eps = __fma_rn(v[2], inj.n[2], __fma_rn(v[1], inj.n[1], __dmul_rn(v[0], inj.n[0])));
+    const double x = __dsub_rn(__dmul_rn(__fma_rn(inj.f0, p.t_sft, __dmul_rn(inj.f1, p.tau[a])),
+                                         __dadd_rn(1.0, eps)),
+                               static_cast<double>(p.k_lo));
+    ksig_rows[i] = __double2ll_rd(__dadd_rn(x, 0.5));
+    double amp = 0.0;
+    if (inj.h0 > 0.0) {
+        double aa, bb;
+        antenna_ab(p.D + 6 * a, inj.n, aa, bb);
+        const double c2 = cos(2.0 * inj.psi), s2 = sin(2.0 * inj.psi);
+        const double fp = aa * c2 + bb * s2, fx = bb * c2 - aa * s2;
+        const double ap = 0.5 * (1.0 + inj.cosi * inj.cosi), ax = inj.cosi;
+        const double q2 = fp * fp * ap * ap + fx * fx * ax * ax;
+        const double h = 0.7737 * 0.5 * p.t_sft * inj.h0;
+        amp = sqrt(4.0 * h * h * q2 / (p.t_sft * p.sn[a]));
+    }
+    amp_rows[i] = static_cast<float>(amp);
+}
+
+// One CTA per run.  Per row: E, C of the run's K sky points from the tables, the track
+// origins of every (sky, f1), the generated window, then each thread's local templates.
+// A template slot's (f1 row r, sky ks, f0 offset) is decoded once, before the row loop;
+// the compensated sums live in shared memory between folds.
+__global__ void __launch_bounds__(kInjThreads, 4) k_injections(const InjParams p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int K = p.K;
-    double *skyv = reinterpret_cast<double *>(smem);                       // [K][3]
+    double *skyv = reinterpret_cast<double *>(smem);                       // [K][3] (unused)
     long long *X0 = reinterpret_cast<long long *>(skyv + 3 * K);           // [K][n_f1]
     int *Et = reinterpret_cast<int *>(X0 + static_cast<size_t>(K) * p.n_f1);  // [K]
     long long *Ct = reinterpret_cast<long long *>(smem) +                   // [K] (8-aligned)
                     (3 * K + K * p.n_f1) + (K + 1) / 2;
     float *Pw = reinterpret_cast<float *>(Ct + K);                          // [2H + 1]
-    __shared__ long long s_ksig;
-    __shared__ float s_amp;
+    float *s_hi = Pw + align16f(2 * p.H + 1);                               // [kInjSlots][threads]
+    float *s_lo = s_hi + kInjSlots * kInjThreads;
     __shared__ double s_best_z[kInjThreads / 32];
     __shared__ long long s_best_t[kInjThreads / 32];
 
@@ -142,65 +201,61 @@ __global__ void __launch_bounds__(kInjThreads) k_injections(const InjParams p)
     const InjRun inj = p.runs[run];
     const unsigned long long rid = p.first_id + static_cast<unsigned long long>(run);
     const int tid = threadIdx.x;
-    for (int i = tid; i < K; i += blockDim.x) {
-        const int s = p.sky_idx[run * K + i];
-        skyv[3 * i] = p.sky[3 * s];
-        skyv[3 * i + 1] = p.sky[3 * s + 1];
-        skyv[3 * i + 2] = p.sky[3 * s + 2];
-    }
     const long long jc = __double2ll_rd(__dadd_rn(__dmul_rn(inj.f0, p.t_sft), 0.5)) - p.K0;
     const int j_lo = static_cast<int>(max(0ll, jc - p.half_f0));
     const int j_hi = static_cast<int>(min(static_cast<long long>(p.n_f0 - 1), jc + p.half_f0));
     const int nf0 = j_hi - j_lo + 1;
     const int nt = nf0 * p.n_f1 * K;
-    // local template slot i of this thread: t = tid + i * blockDim.x -> (sky, f1, f0)
-    float part[kInjSlots], hi[kInjSlots], lo[kInjSlots];
+    // local template slot i of this thread: t = tid + i * blockDim.x -> f1 row r = t / nf0
+    // (= ks n_f1 + f), sky ks, f0 offset t % nf0; packed as r | ks << 13 | offset << 20,
+    // or ~0 past the local bank
+    unsigned slot[kInjSlots];
+    float part[kInjSlots];
     int oobc = 0;
 #pragma unroll
-    for (int i = 0; i < kInjSlots; ++i)
-        part[i] = hi[i] = lo[i] = 0.f;
+    for (int i = 0; i < kInjSlots; ++i) {
+        const int t = tid + i * kInjThreads;
+        const int r = t / nf0;
+        slot[i] = t < nt ? static_cast<unsigned>(r) | static_cast<unsigned>(r / p.n_f1) << 13 |
+                               static_cast<unsigned>(t - r * nf0) << 20
+                         : ~0u;
+        part[i] = 0.f;
+        s_hi[i * kInjThreads + tid] = 0.f;
+        s_lo[i * kInjThreads + tid] = 0.f;
+    }
+    // (sky, f1) entries of this thread in the per-row origin loop, stepped without division
+    const int nkf = K * p.n_f1;
+    const int ks_first = tid / p.n_f1, f_first = tid - ks_first * p.n_f1;
+    const int dks = kInjThreads / p.n_f1, df = kInjThreads - dks * p.n_f1;
+    const int *cidx = p.sky_cidx + run * K;
+    const long long *ksig_row = p.ksig_rows + run * p.N;
+    const float *amp_row = p.amp_rows + run * p.N;
     const unsigned key0 = static_cast<unsigned>(p.seed), key1 = static_cast<unsigned>(p.seed >> 32);
     const int W = 2 * p.H + 1;
     int rows = 0;
     for (long long a = 0; a < p.N; ++a) {
         __syncthreads();  // previous row fully consumed
         if (tid < K) {
-            int E;
-            long long C;
-            track_ec_inj(p.v + 3 * a, skyv + 3 * tid, p.K0, p.k_lo, E, C);
-            Et[tid] = E;
-            Ct[tid] = C;
-        } else if (tid == kInjThreads - 1) {
-            const double *v = p.v + 3 * a;
-            const double eps = __fma_rn(v[2], inj.n[2], __fma_rn(v[1], inj.n[1], __dmul_rn(v[0], inj.n[0])));
-            const double x = __dsub_rn(__dmul_rn(__fma_rn(inj.f0, p.t_sft, __dmul_rn(inj.f1, p.tau[a])),
-                                                 __dadd_rn(1.0, eps)),
-                                       static_cast<double>(p.k_lo));
-            s_ksig = __double2ll_rd(__dadd_rn(x, 0.5));
-            double amp = 0.0;
-            if (inj.h0 > 0.0) {
-                double aa, bb;
-                antenna_ab(p.D + 6 * a, inj.n, aa, bb);
-                const double c2 = cos(2.0 * inj.psi), s2 = sin(2.0 * inj.psi);
-                const double fp = aa * c2 + bb * s2, fx = bb * c2 - aa * s2;
-                const double ap = 0.5 * (1.0 + inj.cosi * inj.cosi), ax = inj.cosi;
-                const double q2 = fp * fp * ap * ap + fx * fx * ax * ax;
-                const double h = 0.7737 * 0.5 * p.t_sft * inj.h0;
-                amp = sqrt(4.0 * h * h * q2 / (p.t_sft * p.sn[a]));
-            }
-            s_amp = static_cast<float>(amp);
+            const long long o = static_cast<long long>(cidx[tid]) * p.N + a;
+            Et[tid] = p.Etab[o];
+            Ct[tid] = p.Ctab[o];
         }
         __syncthreads();
         // track origins of (sky, f1) for this row
-        for (int i = tid; i < K * p.n_f1; i += blockDim.x) {
-            const int ks = i / p.n_f1, f = i - ks * p.n_f1;
+        for (int i = tid, ks = ks_first, f = f_first; i < nkf; i += kInjThreads) {
             const long long G = p.G[static_cast<long long>(f) * p.N + a];
             const int E = Et[ks];
             X0[i] = Ct[ks] + G + cross_q32_inj(G, E) + (1ll << 31);
+            ks += dks;
+            f += df;
+            if (f >= p.n_f1) {
+                f -= p.n_f1;
+                ++ks;
+            }
         }
         // the generated window of this row
-        const long long ksig = s_ksig;
-        const float amp = s_amp;
+        const long long ksig = ksig_row[a];
+        const float amp = amp_row[a];
         for (int q = tid; q < W; q += blockDim.x) {
             const long long kabs = ksig + (q - p.H) + p.k_lo;
             unsigned o0, o1;
@@ -221,11 +276,11 @@ __global__ void __launch_bounds__(kInjThreads) k_injections(const InjParams p)
         const float wa = p.w[a];
 #pragma unroll
         for (int i = 0; i < kInjSlots; ++i) {
-            const int t = tid + i * kInjThreads;
-            if (t < nt) {
-                const int jj = j_lo + t % nf0;
-                const int r = t / nf0;  // = ks * n_f1 + f
-                const long long acc = X0[r] + static_cast<long long>(jj) * Et[r / p.n_f1];
+            const unsigned sl = slot[i];
+            if (sl != ~0u) {
+                const int r = static_cast<int>(sl & 0x1FFFu);
+                const int jj = j_lo + static_cast<int>(sl >> 20);
+                const long long acc = X0[r] + static_cast<long long>(jj) * Et[(sl >> 13) & 0x7Fu];
                 const long long k = jj + (acc >> 32);
                 const long long q = k - ksig + p.H;
                 if (q >= 0 && q < W)
@@ -237,11 +292,13 @@ __global__ void __launch_bounds__(kInjThreads) k_injections(const InjParams p)
         if (++rows == 128 || a == p.N - 1) {
 #pragma unroll
             for (int i = 0; i < kInjSlots; ++i) {
-                const float s = __fadd_rn(hi[i], part[i]);
-                const float bp = __fsub_rn(s, hi[i]);
-                const float e = __fadd_rn(__fsub_rn(hi[i], __fsub_rn(s, bp)), __fsub_rn(part[i], bp));
-                lo[i] = __fadd_rn(lo[i], e);
-                hi[i] = s;
+                float &hi = s_hi[i * kInjThreads + tid];
+                float &lo = s_lo[i * kInjThreads + tid];
+                const float s = __fadd_rn(hi, part[i]);
+                const float bp = __fsub_rn(s, hi);
+                const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(part[i], bp));
+                lo = __fadd_rn(lo, e);
+                hi = s;
                 part[i] = 0.f;
             }
             rows = 0;
@@ -252,14 +309,16 @@ __global__ void __launch_bounds__(kInjThreads) k_injections(const InjParams p)
     long long bt = LLONG_MAX;
 #pragma unroll
     for (int i = 0; i < kInjSlots; ++i) {
-        const int t = tid + i * kInjThreads;
-        if (t < nt) {
-            const int jj = j_lo + t % nf0;
-            const int r = t / nf0;
-            const int ks = r / p.n_f1, f = r - ks * p.n_f1;
+        const unsigned sl = slot[i];
+        if (sl != ~0u) {
+            const int jj = j_lo + static_cast<int>(sl >> 20);
+            const int r = static_cast<int>(sl & 0x1FFFu);
+            const int ks = static_cast<int>((sl >> 13) & 0x7Fu), f = r - ks * p.n_f1;
             const long long tg =
                 (static_cast<long long>(p.sky_idx[run * K + ks]) * p.n_f1 + f) * p.n_f0 + jj;
-            const double z = (static_cast<double>(hi[i]) + static_cast<double>(lo[i]) - p.mu) / p.sigma;
+            const double z = (static_cast<double>(s_hi[i * kInjThreads + tid]) +
+                              static_cast<double>(s_lo[i * kInjThreads + tid]) - p.mu) /
+                             p.sigma;
             if (z > bz || (z == bz && tg < bt)) {
                 bz = z;
                 bt = tg;
@@ -302,7 +361,8 @@ __global__ void __launch_bounds__(kInjThreads) k_injections(const InjParams p)
 size_t inj_smem(int K, int n_f1, int H)
 {
     size_t words8 = 3 * K + static_cast<size_t>(K) * n_f1 + (K + 1) / 2 + K;  // 8-byte words
-    return words8 * 8 + static_cast<size_t>(2 * H + 1) * 4 + 16;
+    return words8 * 8 + static_cast<size_t>(align16f(2 * H + 1)) * 4 +
+           2 * static_cast<size_t>(kInjSlots) * kInjThreads * 4 + 16;
 }
 
 }  // namespace
@@ -374,16 +434,38 @@ extern "C" int ft_run_injections(ft_ctx *ctx, const ft_band *band, const ft_bank
             sidx[r * K + k] = d[k].second;
     }
 
+    // the sky points any run uses, compacted: their E / C tables are computed once
+    std::vector<int> cpos(static_cast<size_t>(bank->n_sky), -1), used, cidx(sidx.size());
+    for (size_t i = 0; i < sidx.size(); ++i) {
+        int &c = cpos[sidx[i]];
+        if (c < 0) {
+            c = static_cast<int>(used.size());
+            used.push_back(sidx[i]);
+        }
+        cidx[i] = c;
+    }
     const size_t N = band->N;
+    const size_t n_used = used.size();
+    // runs per launch: the per-(run, row) signal bins and amplitudes of one chunk take at
+    // most about 1 GB
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n, (1ll << 30) / (12 * static_cast<long long>(N))));
     double *dD = nullptr;
     InjRun *druns = nullptr;
-    int *dsidx = nullptr;
+    int *dsidx = nullptr, *dcidx = nullptr, *dused = nullptr, *dE = nullptr;
+    long long *dC = nullptr, *dks = nullptr;
+    float *damp = nullptr;
     double *dz = nullptr;
     long long *darg = nullptr, *doob = nullptr;
     auto release = [&]() {
         cudaFree(dD);
         cudaFree(druns);
         cudaFree(dsidx);
+        cudaFree(dcidx);
+        cudaFree(dused);
+        cudaFree(dE);
+        cudaFree(dC);
+        cudaFree(dks);
+        cudaFree(damp);
         cudaFree(dz);
         cudaFree(darg);
         cudaFree(doob);
@@ -392,6 +474,12 @@ extern "C" int ft_run_injections(ft_ctx *ctx, const ft_band *band, const ft_bank
     if ((e = cudaMalloc(&dD, N * 6 * 8)) != cudaSuccess ||
         (e = cudaMalloc(&druns, n * sizeof(InjRun))) != cudaSuccess ||
         (e = cudaMalloc(&dsidx, sidx.size() * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&dcidx, cidx.size() * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&dused, n_used * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&dE, n_used * N * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&dC, n_used * N * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&dks, static_cast<size_t>(chunk) * N * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&damp, static_cast<size_t>(chunk) * N * 4)) != cudaSuccess ||
         (e = cudaMalloc(&dz, n * 8)) != cudaSuccess || (e = cudaMalloc(&darg, n * 8)) != cudaSuccess ||
         (e = cudaMalloc(&doob, n * 8)) != cudaSuccess) {
         release();
@@ -400,7 +488,9 @@ extern "C" int ft_run_injections(ft_ctx *ctx, const ft_band *band, const ft_bank
     static_assert(sizeof(InjRun) == sizeof(ft_injection), "injection record layout");
     bool okc = cudaMemcpyAsync(dD, det_tensor, N * 6 * 8, cudaMemcpyHostToDevice, st) == cudaSuccess &&
                cudaMemcpyAsync(druns, inj, n * sizeof(InjRun), cudaMemcpyHostToDevice, st) == cudaSuccess &&
-               cudaMemcpyAsync(dsidx, sidx.data(), sidx.size() * 4, cudaMemcpyHostToDevice, st) == cudaSuccess;
+               cudaMemcpyAsync(dsidx, sidx.data(), sidx.size() * 4, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+               cudaMemcpyAsync(dcidx, cidx.data(), cidx.size() * 4, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+               cudaMemcpyAsync(dused, used.data(), n_used * 4, cudaMemcpyHostToDevice, st) == cudaSuccess;
     if (!okc) {
         release();
         FT_FAIL(FT_ERR_CUDA, "run_injections: upload failed");
@@ -429,6 +519,11 @@ extern "C" int ft_run_injections(ft_ctx *ctx, const ft_band *band, const ft_bank
     p.G = bank->d_G;
     p.runs = druns;
     p.sky_idx = dsidx;
+    p.sky_cidx = dcidx;
+    p.Etab = dE;
+    p.Ctab = dC;
+    p.ksig_rows = dks;
+    p.amp_rows = damp;
     p.seed = desc->seed;
     p.first_id = desc->first_run_id;
     p.max_z = dz;
@@ -442,16 +537,28 @@ extern "C" int ft_run_injections(ft_ctx *ctx, const ft_band *band, const ft_bank
             FT_FAIL(FT_ERR_RANGE, "run_injections: shared memory for this local bank too large");
         }
     }
-    // at most 2^31 - 1 runs per launch
+    {
+        const long long tot = static_cast<long long>(n_used) * static_cast<long long>(N);
+        k_inj_ec<<<static_cast<unsigned>((tot + 255) / 256), 256, 0, st>>>(
+            static_cast<long long>(N), static_cast<int>(n_used), dused, band->d_v, bank->d_sky, bank->k0,
+            band->k_lo, dE, dC);
+        if ((e = cudaGetLastError()) != cudaSuccess) {
+            release();
+            FT_FAIL(FT_ERR_CUDA, std::string("run_injections: launch: ") + cudaGetErrorString(e));
+        }
+    }
     for (int64_t done = 0; done < n;) {
-        const int64_t m = std::min<int64_t>(n - done, 1 << 30);
+        const int64_t m = std::min<int64_t>(n - done, chunk);
         InjParams q = p;
         q.runs = druns + done;
         q.sky_idx = dsidx + done * K;
+        q.sky_cidx = dcidx + done * K;
         q.first_id = desc->first_run_id + done;
         q.max_z = dz + done;
         q.argmax = darg + done;
         q.oob = doob + done;
+        const long long rows = static_cast<long long>(m) * static_cast<long long>(N);
+        k_inj_rows<<<static_cast<unsigned>((rows + 255) / 256), 256, 0, st>>>(q, m, dks, damp);
         k_injections<<<static_cast<unsigned>(m), kInjThreads, smem, st>>>(q);
         if ((e = cudaGetLastError()) != cudaSuccess) {
             release();
