@@ -129,6 +129,12 @@ def load_library(path):
     L.or_bt_bins.argtypes = [ctypes.POINTER(_BDesc), ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                              ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.or_bt_statistic_sky.restype = None
+    L.or_bt_statistic_sky.argtypes = [ctypes.POINTER(_BDesc), ctypes.c_void_p, ctypes.c_int64,
+                                      ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p]
     L.or_bt_statistic.restype = None
     L.or_bt_statistic.argtypes = [ctypes.POINTER(_BDesc), ctypes.c_void_p, ctypes.c_int64,
                                   ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
@@ -480,6 +486,28 @@ def binary_statistic(sfts, bank, templates=None, w=None):
                            tm.ctypes.data, v.ctypes.data, float(sfts.t0), float(sfts.t_sft),
                            int(sfts.k_lo), s.ctypes.data, oob.ctypes.data)
     return s, oob
+
+
+def binary_statistic_sky(sfts, bank, D, templates=None):
+    """s along the canonical binary tracks under the all-sky weights (a^2 + b^2)/S_n of each
+    template's sky direction (Sec. II.B), normalised per template; returns (s, sigma_G, oob)
+    with mu_G = 2."""
+    t = None if templates is None else _c(templates, np.int64)
+    n = bank.n_templates if t is None else len(t)
+    P = _c(sfts.power, np.float64)
+    Dv = _c(D, np.float64)
+    sn = _c(sfts.s_n, np.float64)
+    tm = _c(sfts.t_mid, np.float64)
+    v = _c(sfts.v, np.float64)
+    s = np.empty(n, np.float64)
+    sig = np.empty(n, np.float64)
+    oob = np.empty(n, np.int32)
+    d = _bdesc(bank)
+    lib().or_bt_statistic_sky(ctypes.byref(d), None if t is None else t.ctypes.data, n, P.shape[0],
+                              P.shape[1], P.ctypes.data, Dv.ctypes.data, sn.ctypes.data, tm.ctypes.data,
+                              v.ctypes.data, float(sfts.t0), float(sfts.t_sft), int(sfts.k_lo),
+                              s.ctypes.data, sig.ctypes.data, oob.ctypes.data)
+    return s, sig, oob
 
 
 def topk_per_box(s, n_per_box, n_boxes, k, templates=None):

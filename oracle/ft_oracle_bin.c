@@ -280,3 +280,46 @@ void or_bt_templates(const or_bdesc *b, const int64_t *tmpl, int64_t n, double t
             or_bt_derived(lam + 6 * i, t_sft, k_lo, der + i);
     }
 }
+
+void or_antenna_ab(const double *D, const double *n, double *a, double *b);
+
+/* The statistic under the all-sky weights of Sec. II.B for the binary bank: per template the
+ * weights are w_alpha = r_alpha / sum r, r_alpha = (a^2 + b^2)(D_alpha, n) / S_n,alpha, with
+ * n the template's unit sky vector (FP64, libm cos / sin of alpha); s = sum w P along the
+ * canonical bins, and sigma_G = 2 sqrt(sum w^2) (mu_G = 2). */
+void or_bt_statistic_sky(const or_bdesc *b, const int64_t *tmpl, int64_t n, int64_t N, int64_t W,
+                         const double *power, const double *D, const double *s_n, const double *t_mid,
+                         const double *v, double t0, double t_sft, int64_t k_lo, double *s,
+                         double *sigma, int32_t *oob)
+{
+    or_bt_init();
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; i++) {
+        double lam[6];
+        or_bdesc bd = *b;
+        or_bt_lambda(&bd, tmpl ? tmpl[i] : i, lam);
+        or_bder d;
+        or_bt_derived(lam, t_sft, k_lo, &d);
+        double cdl = sqrt(fmax(0.0, 1.0 - lam[2] * lam[2]));
+        double nn[3] = {cdl * cos(6.283185307179586 * lam[1]), cdl * sin(6.283185307179586 * lam[1]), lam[2]};
+        double acc = 0.0, sr = 0.0, sr2 = 0.0;
+        int32_t out = 0;
+        for (int64_t a = 0; a < N; a++) {
+            double aa, bb;
+            or_antenna_ab(D + 6 * a, nn, &aa, &bb);
+            double r = (aa * aa + bb * bb) / s_n[a];
+            sr += r;
+            sr2 += r * r;
+            float v32[3] = {(float)v[3 * a], (float)v[3 * a + 1], (float)v[3 * a + 2]};
+            int64_t k = canonical_bin(&d, or_bt_tq(t_mid[a], t0), v32);
+            if (k < 0 || k >= W) {
+                out++;
+                continue;
+            }
+            acc += r * power[a * W + k];
+        }
+        s[i] = acc / sr;
+        sigma[i] = 2.0 * sqrt(sr2) / sr;
+        oob[i] = out;
+    }
+}

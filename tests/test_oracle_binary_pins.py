@@ -172,3 +172,35 @@ def test_topk_per_box():
         assert np.array_equal(val[b], seg[order])
     idx, val = oracle.topk_per_box(s, bank.n_per_box, bank.n_boxes, 12)
     assert np.all(idx[:, 10:] == -1) and np.all(val[:, 10:] == -np.inf)
+
+
+def test_all_sky_weighted_statistic():
+    """Sec. II.B weights on the binary bank: with one detector tensor and one S_n for every
+    SFT the weights are 1/N (s = the plain sum / N, sigma_G = 2 / sqrt(N)); in general s is
+    the sum along the canonical bins with the normalised weights of the template's sky
+    direction (sky_weights of its unit vector)."""
+    bank = _bank(n_div=(1, 1, 1, 1, 2, 2), n_per_box=4)
+    sfts = _sfts(n_sft=(40, 33))
+    N = sfts.n_total
+    D1 = np.tile(ftsynth.detector_tensor(np.array([5000.0]), 0), (N, 1))
+    s_sky, sig, oob = oracle.binary_statistic_sky(sfts, bank, D1)
+    s_plain, oob2 = oracle.binary_statistic(sfts, bank)
+    assert np.array_equal(oob, oob2)
+    assert np.allclose(s_sky, s_plain / N, rtol=1e-12, atol=0)
+    assert np.allclose(sig, 2 / math.sqrt(N), rtol=1e-12, atol=0)
+    g = np.random.default_rng(9)
+    sx = ftsynth.SFTSet(**{**sfts.__dict__, "s_n": g.uniform(0.5, 2.0, N)})
+    D = np.concatenate([ftsynth.detector_tensor(sx.t_mid[:40], 0), ftsynth.detector_tensor(sx.t_mid[40:], 1)])
+    s_sky, sig, _ = oracle.binary_statistic_sky(sx, bank, D)
+    lam, _ = oracle.binary_templates(bank)
+    b = oracle.binary_bins(sx, bank, np.arange(bank.n_templates))
+    W = sx.power.shape[1]
+    for i in range(bank.n_templates):
+        cd = math.sqrt(1 - lam[i, 2] ** 2)
+        n = np.array([[cd * math.cos(2 * math.pi * lam[i, 1]), cd * math.sin(2 * math.pi * lam[i, 1]),
+                       lam[i, 2]]])
+        w = oracle.sky_weights(D, sx.s_n, n)[0]
+        ok = (b[i] >= 0) & (b[i] < W)
+        want = np.sum(w[ok] * sx.power[np.arange(N)[ok], b[i][ok]])
+        assert abs(s_sky[i] - want) <= 1e-12 * want
+        assert abs(sig[i] - 2 * math.sqrt(np.sum(w * w))) <= 1e-12 * sig[i]
