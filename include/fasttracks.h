@@ -129,7 +129,9 @@ FT_API int ft_band_info(const ft_band *band, int64_t *n_sft_total, int *n_bins, 
  *   det_tensor  host [N_SFT][6] (Dxx, Dxy, Dxz, Dyy, Dyz, Dzz), or NULL to turn the weights
  *               off again (the per-SFT weights of ft_load_sfts apply once more).
  * The per-sky sums are computed by ft_make_bank: banks made before this call keep none and
- * are refused by the evaluation calls while the weights are on.  The injection and
+ * are refused by the evaluation calls while the weights are on.  Binary banks made after this
+ * call weight every (template, SFT) by its template's own sky direction (the sums per
+ * template are formed in the evaluation kernel).  The injection and
  * semi-analytic calls keep the per-SFT weights.  Errors: FT_ERR_ARG (null band, band loaded
  * without S_n, non-finite tensor), FT_ERR_OOM.  Synchronises `stream`. */
 FT_API int ft_band_set_sky_weights(ft_band *band, const double *det_tensor, void *stream);
@@ -353,7 +355,10 @@ typedef struct {
     uint64_t seed;
 } ft_binary_bank_desc;
 
-/* Set up a binary bank for `band` (uses its SFT times, velocities and weights).  Errors:
+/* Set up a binary bank for `band` (uses its SFT times, velocities and weights: the per-SFT
+ * weights, or, when ft_band_set_sky_weights was called before, the all-sky weights
+ * (a^2 + b^2)/S_n of each template's own sky direction, normalised per template; then s =
+ * sum r P / sum r and z uses mu_G = 2, sigma_G = 2 sqrt(sum r^2) / sum r).  Errors:
  * FT_ERR_ARG (ranges, counts), FT_ERR_OOM. */
 FT_API int ft_make_binary_bank(ft_ctx *ctx, const ft_band *band, const ft_binary_bank_desc *desc,
                                ft_binary_bank **out);

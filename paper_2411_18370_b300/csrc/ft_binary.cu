@@ -29,6 +29,9 @@ struct ft_binary_bank {
     float4 *d_rowv = nullptr;      // [n_pad] (v/c as FP32, weight); zero beyond N
     long long *d_tq = nullptr;     // [n_pad] round((t_mid - t0) 2^10)
     float2 *d_costab = nullptr;    // [kBtTab + 1] quarter-wave cosine table (value, difference)
+    // all-sky weights (band with detector tensors): per SFT D / sqrt(S_n) in FP32 as
+    // (D00, D01, D02, D11), (D12, D22, |D|^2, tr D); zero beyond N
+    float4 *d_rowd = nullptr;      // [n_pad][2]
 };
 
 namespace {
@@ -52,6 +55,7 @@ struct BtParams {
     const float4 *rowv;
     const long long *tq;
     const float2 *costab;          // (cos(i (pi/2) / 1024) in FP32, next minus this)
+    const float4 *rowd;            // null, or the all-sky weight records [n_pad][2]
     double mu, sigma;
     // eval mode (box_mode == 0): templates [first, first + count), CTA c takes kBtThreads of them
     long long first, count;
@@ -226,12 +230,13 @@ __device__ __forceinline__ float bt_load<__nv_bfloat16>(const unsigned char *row
 
 // One stage: S power rows (each its own bulk copy), S velocity records, S times.
 __device__ __forceinline__ void bt_issue(const BtParams &p, int st, unsigned char *rows,
-                                         float4 *sv, long long *stq, unsigned long long *bar)
+                                         float4 *sv, long long *stq, float4 *sd, unsigned long long *bar)
 {
     const int lane = threadIdx.x & 31;
     const int nr = min(p.S, p.N - st * p.S);
     if (lane == 0)
-        ftp::mbar_arrive_expect_tx(bar, static_cast<unsigned>(nr * p.row_bytes + p.S * 24));
+        ftp::mbar_arrive_expect_tx(bar, static_cast<unsigned>(nr * p.row_bytes + p.S * 24 +
+                                                              (p.rowd != nullptr ? p.S * 32 : 0)));
     __syncwarp();
     for (int r = lane; r < nr; r += 32)
         ftp::bulk_g2s(rows + static_cast<size_t>(r) * p.row_bytes,
@@ -240,10 +245,34 @@ __device__ __forceinline__ void bt_issue(const BtParams &p, int st, unsigned cha
     if (lane == 0) {
         ftp::bulk_g2s(sv, p.rowv + static_cast<long long>(st) * p.S, static_cast<unsigned>(p.S * 16), bar);
         ftp::bulk_g2s(stq, p.tq + static_cast<long long>(st) * p.S, static_cast<unsigned>(p.S * 8), bar);
+        if (p.rowd != nullptr)
+            ftp::bulk_g2s(sd, p.rowd + 2ll * st * p.S, static_cast<unsigned>(p.S * 32), bar);
     }
 }
 
-template <typename T, bool WEIGHTED>
+// (a^2 + b^2)(D, n) / S_n for the FP32 record of D / sqrt(S_n): with u = D n and c = n.u,
+// a^2 + b^2 = 2 |TT(D)|^2 = 2 |D|^2 - 4 |u|^2 + 2 c^2 - (tr D - c)^2 for a unit n (the
+// transverse-traceless projection; no wave frame needed).
+__device__ __forceinline__ float bt_sky_r(float4 d0, float4 d1, float nx, float ny, float nz)
+{
+    const float u0 = d0.x * nx + d0.y * ny + d0.z * nz;
+    const float u1 = d0.y * nx + d0.w * ny + d1.x * nz;
+    const float u2 = d0.z * nx + d1.x * ny + d1.y * nz;
+    const float c = nx * u0 + ny * u1 + nz * u2;
+    const float uu = u0 * u0 + u1 * u1 + u2 * u2;
+    const float tc = d1.w - c;
+    return 2.f * d1.z - 4.f * uu + 2.f * c * c - tc * tc;
+}
+
+__device__ __forceinline__ void fold2(float &hi, float &lo, float part)
+{
+    const float s = __fadd_rn(hi, part);
+    const float bp = __fsub_rn(s, hi);
+    lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(part, bp)));
+    hi = s;
+}
+
+template <typename T, bool WEIGHTED, bool SKY>
 __global__ void __launch_bounds__(kBtThreads) k_bt_eval(const BtParams p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -255,6 +284,8 @@ __global__ void __launch_bounds__(kBtThreads) k_bt_eval(const BtParams p)
                          reinterpret_cast<long long *>(sv[1] + p.S) + p.S};
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(stq[1] + p.S);
     float2 *tab = reinterpret_cast<float2 *>(bars + 2);
+    float4 *sd[2] = {reinterpret_cast<float4 *>(tab + kBtTab + 1 + 1), nullptr};  // 16-byte aligned
+    sd[1] = sd[0] + 2 * p.S;
 
     // this CTA's templates
     long long t_begin, t_end;
@@ -279,9 +310,9 @@ __global__ void __launch_bounds__(kBtThreads) k_bt_eval(const BtParams p)
         tab[i] = p.costab[i];
     __syncthreads();
     if (threadIdx.x < 32) {
-        bt_issue(p, 0, rows[0], sv[0], stq[0], &bars[0]);
+        bt_issue(p, 0, rows[0], sv[0], stq[0], sd[0], &bars[0]);
         if (p.n_stages > 1)
-            bt_issue(p, 1, rows[1], sv[1], stq[1], &bars[1]);
+            bt_issue(p, 1, rows[1], sv[1], stq[1], sd[1], &bars[1]);
     }
 
     BtTmpl t;
@@ -292,13 +323,15 @@ __global__ void __launch_bounds__(kBtThreads) k_bt_eval(const BtParams p)
     }
 
     float hi = 0.f, lo = 0.f;
+    // all-sky weights: sum r, sum r^2 (r = (a^2 + b^2) / S_n), compensated like the sum
+    float hiB = 0.f, loB = 0.f, hiC = 0.f, loC = 0.f;
     int oob = 0;
     bool failed = false;
     for (int st = 0; st < p.n_stages; ++st) {
         const int b = st & 1;
         const bool ok = ftp::mbar_wait_bounded(&bars[b], (st >> 1) & 1);
         const int nr = min(p.S, p.N - st * p.S);
-        float part = 0.f;
+        float part = 0.f, partB = 0.f, partC = 0.f;
         if (ok) {
             const unsigned char *rb = rows[b];
 #pragma unroll 4
@@ -308,20 +341,28 @@ __global__ void __launch_bounds__(kBtThreads) k_bt_eval(const BtParams p)
                 const bool in = static_cast<unsigned>(k) < static_cast<unsigned>(p.W);
                 const float val = in ? bt_load<T>(rb + static_cast<size_t>(r) * p.row_bytes, k) : 0.f;
                 oob += in ? 0 : 1;
-                part = WEIGHTED ? __fmaf_rn(v.w, val, part) : __fadd_rn(part, val);
+                if (SKY) {
+                    const float rw = bt_sky_r(sd[b][2 * r], sd[b][2 * r + 1], t.nx, t.ny, t.nz);
+                    part = __fmaf_rn(rw, val, part);
+                    partB = __fadd_rn(partB, rw);
+                    partC = __fmaf_rn(rw, rw, partC);
+                } else {
+                    part = WEIGHTED ? __fmaf_rn(v.w, val, part) : __fadd_rn(part, val);
+                }
             }
         }
-        // compensated fold of the stage's partial (2Sum)
-        const float s = __fadd_rn(hi, part);
-        const float bp = __fsub_rn(s, hi);
-        lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(part, bp)));
-        hi = s;
+        // compensated folds of the stage's partials (2Sum)
+        fold2(hi, lo, part);
+        if (SKY) {
+            fold2(hiB, loB, partB);
+            fold2(hiC, loC, partC);
+        }
         if (__syncthreads_or(!ok)) {
             failed = true;
             break;
         }
         if (threadIdx.x < 32 && st + 2 < p.n_stages)
-            bt_issue(p, st + 2, rows[b], sv[b], stq[b], &bars[b]);
+            bt_issue(p, st + 2, rows[b], sv[b], stq[b], sd[b], &bars[b]);
     }
     if (failed) {
         if (threadIdx.x == 0) {
@@ -334,14 +375,23 @@ __global__ void __launch_bounds__(kBtThreads) k_bt_eval(const BtParams p)
         return;
     }
 
-    const float sv_ = __fadd_rn(hi, lo);
+    // s and z: the plain sum, or under all-sky weights sum r P / sum r with mu_G = 2 and
+    // sigma_G = 2 sqrt(sum r^2) / sum r of this template's sky direction
+    double s64 = static_cast<double>(hi) + static_cast<double>(lo);
+    double z64 = (s64 - p.mu) / p.sigma;
+    if (SKY) {
+        const double B = static_cast<double>(hiB) + static_cast<double>(loB);
+        const double C = static_cast<double>(hiC) + static_cast<double>(loC);
+        s64 /= B;
+        z64 = (s64 - 2.0) / (2.0 * sqrt(C) / B);
+    }
+    const float sv_ = SKY ? static_cast<float>(s64) : __fadd_rn(hi, lo);
     if (!p.box_mode) {
         if (valid) {
             const long long o = ti - p.first;
             p.s_out[o] = sv_;
             if (p.z_out)
-                p.z_out[o] = static_cast<float>(
-                    (static_cast<double>(hi) + static_cast<double>(lo) - p.mu) / p.sigma);
+                p.z_out[o] = static_cast<float>(z64);
             if (p.oob_out)
                 p.oob_out[o] = oob;
         }
@@ -354,7 +404,7 @@ __global__ void __launch_bounds__(kBtThreads) k_bt_eval(const BtParams p)
     float *vz = vs + kBtThreads;
     const bool pass = valid && (p.gate == nullptr || p.gate[ti] >= p.gate_min);
     vs[threadIdx.x] = pass ? sv_ : -INFINITY;  // -inf: not a candidate
-    vz[threadIdx.x] = static_cast<float>((static_cast<double>(hi) + static_cast<double>(lo) - p.mu) / p.sigma);
+    vz[threadIdx.x] = static_cast<float>(z64);
     __syncthreads();
     if (threadIdx.x >= 32)
         return;
@@ -516,6 +566,25 @@ __global__ void k_bt_rowv(const double *v, const float *w, int N, int n_pad, flo
     out[a] = r;
 }
 
+__global__ void k_bt_rowd(const double *D, const double *sn, int N, int n_pad, float4 *out)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n_pad)
+        return;
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+    if (a < N) {
+        const double g = 1.0 / sqrt(sn[a]);
+        const double *d = D + 6 * a;
+        const double e0 = d[0] * g, e1 = d[1] * g, e2 = d[2] * g, e3 = d[3] * g, e4 = d[4] * g, e5 = d[5] * g;
+        const double dd = e0 * e0 + e3 * e3 + e5 * e5 + 2.0 * (e1 * e1 + e2 * e2 + e4 * e4);
+        r0 = make_float4(static_cast<float>(e0), static_cast<float>(e1), static_cast<float>(e2), static_cast<float>(e3));
+        r1 = make_float4(static_cast<float>(e4), static_cast<float>(e5), static_cast<float>(dd),
+                         static_cast<float>(e0 + e3 + e5));
+    }
+    out[2 * a] = r0;
+    out[2 * a + 1] = r1;
+}
+
 // ------------------------------------------------------------------ host side
 
 struct Guard {
@@ -586,6 +655,7 @@ BtParams base_params(const ft_band *band, const ft_binary_bank *bk)
     p.rowv = bk->d_rowv;
     p.tq = bk->d_tq;
     p.costab = bk->d_costab;
+    p.rowd = band->d_D != nullptr ? bk->d_rowd : nullptr;
     p.mu = band->mu;
     p.sigma = band->sigma;
     p.status = band->ctx->d_status;
@@ -605,13 +675,14 @@ int stage_rows(const ft_band *band)
 
 size_t eval_smem(const BtParams &p)
 {
-    return 2 * (static_cast<size_t>(p.S) * p.row_bytes + p.S * 24) + 16 + (kBtTab + 1) * sizeof(float2);
+    return 2 * (static_cast<size_t>(p.S) * p.row_bytes + p.S * 24) + 16 + (kBtTab + 2) * sizeof(float2) +
+           (p.rowd != nullptr ? 2 * static_cast<size_t>(p.S) * 32 : 0);
 }
 
 template <typename T, bool Wt>
 int launch_t(long long n_cta, size_t smem, const BtParams &p, cudaStream_t st)
 {
-    auto fn = k_bt_eval<T, Wt>;
+    auto fn = p.rowd != nullptr ? k_bt_eval<T, false, true> : k_bt_eval<T, Wt, false>;
     FT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     fn<<<static_cast<unsigned>(n_cta), kBtThreads, smem, st>>>(p);
     FT_CUDA(cudaGetLastError());
@@ -648,8 +719,8 @@ int check(ft_ctx *ctx, const ft_band *band, const ft_binary_bank *bank)
         FT_FAIL(FT_ERR_ARG, "binary: band/bank belong to another context");
     if (bank->band != band)
         FT_FAIL(FT_ERR_ARG, "binary: bank was made for another band");
-    if (band->d_D)
-        FT_FAIL(FT_ERR_UNSUPPORTED, "binary: all-sky weights are not supported for the binary bank");
+    if (band->d_D && !bank->d_rowd)
+        FT_FAIL(FT_ERR_ARG, "binary: the bank was made before the band's all-sky weights were set; make it again");
     return FT_OK;
 }
 
@@ -741,6 +812,14 @@ int ft_make_binary_bank(ft_ctx *ctx, const ft_band *band, const ft_binary_bank_d
         return fail(FT_ERR_CUDA);
     }
     k_bt_rowv<<<(b->n_pad + 255) / 256, 256>>>(band->d_v, band->d_w, N, b->n_pad, b->d_rowv);
+    if (band->d_D) {
+        if (cudaMalloc(&b->d_rowd, static_cast<size_t>(b->n_pad) * 2 * sizeof(float4)) != cudaSuccess) {
+            b->d_rowd = nullptr;
+            ft_set_error("make_binary_bank: allocation failed");
+            return fail(FT_ERR_OOM);
+        }
+        k_bt_rowd<<<(b->n_pad + 255) / 256, 256>>>(band->d_D, band->d_sn, N, b->n_pad, b->d_rowd);
+    }
     if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
         ft_set_error("make_binary_bank: set-up kernel failed");
         return fail(FT_ERR_CUDA);
@@ -757,6 +836,7 @@ void ft_binary_bank_destroy(ft_binary_bank *b)
     cudaFree(b->d_rowv);
     cudaFree(b->d_tq);
     cudaFree(b->d_costab);
+    cudaFree(b->d_rowd);
     delete b;
 }
 

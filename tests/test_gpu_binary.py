@@ -240,3 +240,47 @@ def test_number_count_gated_boxes(ctx, dtype):
         ok = c_idx >= 0
         assert np.array_equal(out["s"][ok].astype(np.float64), c_val[ok])
         assert np.all(out["s"][~ok] == -np.inf)
+
+
+def _det_tensor(sfts):
+    parts, off = [], 0
+    for X, n in enumerate(sfts.n_sft):
+        parts.append(ftsynth.detector_tensor(sfts.t_mid[off:off + n], X))
+        off += n
+    return np.concatenate(parts)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_all_sky_weights(ctx, dtype):
+    """Sec. II.B weights on the binary bank: per (template, SFT) r = (a^2 + b^2)/S_n of the
+    template's own sky direction, computed in the kernel (FP32, frame-free form), s = sum r P /
+    sum r and z with sigma_G = 2 sqrt(sum r^2) / sum r.  Tolerance 2e-6 relative: the FP32
+    weights (error ~ 1e-7 of the largest r) enter every term."""
+    import dataclasses
+
+    sfts = _sfts(seed=18)
+    sfts = dataclasses.replace(sfts, s_n=np.random.default_rng(4).uniform(0.5, 2.0, sfts.n_total))
+    bank = _bank(seed=19, n_per_box=200)
+    band = H.band_from(ctx, sfts, dtype=dtype, power_f32=True)
+    stale = _gpu_bank(ctx, band, bank)
+    D = _det_tensor(sfts)
+    ft.band_set_sky_weights(band, D)
+    with pytest.raises(ft.FtError):
+        ft.binary_eval(ctx, band, stale, 0, 10, np.empty(10, np.float32))
+    gb = _gpu_bank(ctx, band, bank)
+    n = bank.n_templates
+    s = np.empty(n, np.float32)
+    z = np.empty(n, np.float32)
+    o = np.empty(n, np.int32)
+    ft.binary_eval(ctx, band, gb, 0, n, s, z, o)
+    s_or, sig_or, o_or = oracle.binary_statistic_sky(_stored(sfts, dtype), bank, D)
+    assert np.array_equal(o, o_or)
+    assert np.all(np.abs(s - s_or) <= 2e-6 * s_or)
+    z_or = (s_or - 2.0) / sig_or
+    assert np.all(np.abs(z - z_or) <= 2e-6 * s_or / sig_or + 1e-5)
+    k = 4
+    out = np.zeros((bank.n_boxes, k), dtype=ft.CANDIDATE_DTYPE)
+    ft.binary_topk_per_box(ctx, band, gb, k, out)
+    c_idx, c_val = oracle.topk_per_box(s.astype(np.float64), bank.n_per_box, bank.n_boxes, k)
+    assert np.array_equal(out["template_idx"], c_idx)
+    assert np.array_equal(out["s"].astype(np.float64), c_val)
