@@ -75,29 +75,6 @@ struct BtParams {
 // operations in the same precision and order as its statement, so that the bins are a
 // function of (seed, template, SFT) alone.
 
-__device__ __forceinline__ void bt_philox(unsigned c0, unsigned c1, unsigned c2, unsigned c3,
-                                          unsigned k0, unsigned k1, unsigned o[4])
-{
-    // Philox4x32-10 (Salmon et al., SC'11): multipliers 0xD2511F53 / 0xCD9E8D57, Weyl key
-    // increments 0x9E3779B9 / 0xBB67AE85
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const unsigned hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
-        const unsigned hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
-        const unsigned y0 = hi1 ^ c1 ^ k0, y2 = hi0 ^ c3 ^ k1;
-        c0 = y0;
-        c1 = lo1;
-        c2 = y2;
-        c3 = lo0;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    o[0] = c0;
-    o[1] = c1;
-    o[2] = c2;
-    o[3] = c3;
-}
-
 __device__ __forceinline__ double bt_u53(unsigned a, unsigned b)
 {
     const double hi = static_cast<double>(a >> 5), lo = static_cast<double>(b >> 6);
@@ -125,8 +102,8 @@ __device__ void bt_lambda(const BtParams &p, long long i, double lam[6])
 #pragma unroll
     for (unsigned c = 0; c < 3; ++c) {
         unsigned w[4];
-        bt_philox(static_cast<unsigned>(i), static_cast<unsigned>(static_cast<unsigned long long>(i) >> 32),
-                  c, 0x62696e61u, p.key0, p.key1, w);
+        ftp::philox4x32_10(static_cast<unsigned>(i), static_cast<unsigned>(static_cast<unsigned long long>(i) >> 32),
+                           c, 0x62696e61u, p.key0, p.key1, w);
         u[2 * c] = bt_u53(w[0], w[1]);
         u[2 * c + 1] = bt_u53(w[2], w[3]);
     }

@@ -21,6 +21,7 @@
 // epilogue writes s (and z, out-of-window counts) or selects, per sub-band, the k loudest
 // templates of the CTA into a candidate list that k_topk_merge reduces.
 #include "ft_internal.cuh"
+#include "ft_ptx.cuh"
 
 #include <cudaTypedefs.h>
 #include <cstring>
@@ -37,103 +38,17 @@ constexpr int kNbuf = 2;
 
 // ------------------------------------------------------------------ PTX helpers
 
-__device__ __forceinline__ unsigned smem_addr(const void *p)
-{
-    return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init()
-{
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes)
-{
-    asm volatile(
-        "{\n\t.reg .b64 st;\n\t"
-        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
-        "r"(bytes)
-        : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
-{
-    asm volatile(
-        "{\n\t.reg .b64 st;\n\t"
-        "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
-        : "memory");
-}
-
-// One box of a tiled tensor map (3 or 4 coordinates, innermost first) into shared memory.
-__device__ __forceinline__ void tensor_copy_3d(void *dst, const CUtensorMap *map, int c0, int c1,
-                                               int c2, unsigned long long *bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
-            "r"(smem_addr(dst)),
-        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void tensor_copy_4d(void *dst, const CUtensorMap *map, int c0, int c1,
-                                               int c2, int c3, unsigned long long *bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::
-            "r"(smem_addr(dst)),
-        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes,
-                                              unsigned long long *bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-            "r"(smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wait for an mbarrier phase, giving up after about one second of wall time.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity)
-{
-    if (mbar_try_wait(bar, parity))
-        return true;
-    const unsigned long long t0 = global_ns();
-    for (;;) {
-        if (mbar_try_wait(bar, parity))
-            return true;
-        if (global_ns() - t0 > 1000000000ull)
-            return false;
-    }
-}
+using ftp::bulk_g2s;
+using ftp::fence_mbar_init;
+using ftp::global_ns;
+using ftp::mbar_arrive;
+using ftp::mbar_arrive_expect_tx;
+using ftp::mbar_init;
+using ftp::mbar_try_wait;
+using ftp::mbar_wait_bounded;
+using ftp::smem_addr;
+using ftp::tensor_copy_3d;
+using ftp::tensor_copy_4d;
 
 // ------------------------------------------------------------------ track arithmetic
 
@@ -286,7 +201,7 @@ __device__ __forceinline__ void issue_stage(const EvalParams &p, unsigned char *
     const int nb = st % kNbuf;
     const unsigned bytes = static_cast<unsigned>(rows_in_stage(p, st)) * p.row_bytes;
     mbar_arrive_expect_tx(&bars[nb], bytes);
-    bulk_copy_g2s(buf + nb * stage_bytes,
+    bulk_g2s(buf + nb * stage_bytes,
                   static_cast<const unsigned char *>(p.power) + static_cast<size_t>(st) * stage_bytes,
                   bytes, &bars[nb]);
 }
@@ -1031,7 +946,7 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
             if (p.Ws == p.Wp) {
                 // whole rows: the stage's rows are contiguous in global and shared memory
                 if (lane == 0)
-                    bulk_copy_g2s(stage_buf,
+                    bulk_g2s(stage_buf,
                                   static_cast<const unsigned char *>(p.power) +
                                       static_cast<size_t>(st) * S * p.row_bytes,
                                   row_tot, &full[slot]);
@@ -1047,13 +962,13 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
                 const unsigned char *src =
                     static_cast<const unsigned char *>(p.power) + static_cast<size_t>(alpha) * p.row_bytes;
                 if (!PAIR) {
-                    bulk_copy_g2s(dst, src + static_cast<size_t>(start) * 4, static_cast<unsigned>(len) * 4,
+                    bulk_g2s(dst, src + static_cast<size_t>(start) * 4, static_cast<unsigned>(len) * 4,
                                   &full[slot]);
                 } else {
                     // even copy then odd copy: words [start/2, (start+len)/2) of each
-                    bulk_copy_g2s(dst, src + static_cast<size_t>(start >> 1) * 4,
+                    bulk_g2s(dst, src + static_cast<size_t>(start >> 1) * 4,
                                   static_cast<unsigned>(len) * 2, &full[slot]);
-                    bulk_copy_g2s(dst + (p.srow_bytes >> 1),
+                    bulk_g2s(dst + (p.srow_bytes >> 1),
                                   src + (p.row_bytes >> 1) + static_cast<size_t>(start >> 1) * 4,
                                   static_cast<unsigned>(len) * 2, &full[slot]);
                 }

@@ -19,6 +19,7 @@
 //   * output: max z over the local bank, its template, and the count of reads outside the
 //     generated window (0 when H covers the bank).
 #include "ft_internal.cuh"
+#include "ft_ptx.cuh"
 
 #include <algorithm>
 #include <climits>
@@ -63,25 +64,14 @@ struct InjParams {
     long long *argmax, *oob;
 };
 
+// The first two words of Philox4x32-10 at counter (c0..c3), key (k0, k1).
 __device__ __forceinline__ void philox4x32_10(unsigned c0, unsigned c1, unsigned c2, unsigned c3,
                                               unsigned k0, unsigned k1, unsigned &o0, unsigned &o1)
 {
-    // Philox4x32 with 10 rounds (multipliers 0xD2511F53, 0xCD9E8D57; Weyl key increments
-    // 0x9E3779B9, 0xBB67AE85), Salmon et al. SC'11.  Only the first two words are used.
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const unsigned hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
-        const unsigned hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
-        const unsigned y0 = hi1 ^ c1 ^ k0, y2 = hi0 ^ c3 ^ k1;
-        c0 = y0;
-        c1 = lo1;
-        c2 = y2;
-        c3 = lo0;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    o0 = c0;
-    o1 = c1;
+    unsigned o[4];
+    ftp::philox4x32_10(c0, c1, c2, c3, k0, k1, o);
+    o0 = o[0];
+    o1 = o[1];
 }
 
 __device__ __forceinline__ float uniform24(unsigned x)

@@ -1,7 +1,8 @@
-// ft_ptx.cuh -- small inline-PTX wrappers (mbarrier, bulk copies, bounded waits) for the
-// kernels of ft_binary.cu.  Internal; not part of the ABI.
+// ft_ptx.cuh -- small inline-PTX wrappers (mbarrier, bulk and tensor copies, bounded waits)
+// shared by the library's kernels.  Internal; not part of the ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace ftp {
@@ -28,6 +29,35 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, u
         "{\n\t.reg .b64 st;\n\t"
         "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
         "r"(bytes)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
+        : "memory");
+}
+
+// One box of a tiled tensor map (3 or 4 coordinates, innermost first) into shared memory.
+__device__ __forceinline__ void tensor_copy_3d(void *dst, const CUtensorMap *map, int c0, int c1,
+                                               int c2, unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(smem_addr(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tensor_copy_4d(void *dst, const CUtensorMap *map, int c0, int c1,
+                                               int c2, int c3, unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::
+            "r"(smem_addr(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
         : "memory");
 }
 
@@ -75,6 +105,29 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsig
         if (global_ns() - t0 > 1000000000ull)
             return false;
     }
+}
+
+// Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11): round multipliers
+// 0xD2511F53 and 0xCD9E8D57, key schedule Weyl increments 0x9E3779B9 and 0xBB67AE85.
+__device__ __forceinline__ void philox4x32_10(unsigned c0, unsigned c1, unsigned c2, unsigned c3,
+                                              unsigned k0, unsigned k1, unsigned o[4])
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const unsigned hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const unsigned y0 = hi1 ^ c1 ^ k0, y2 = hi0 ^ c3 ^ k1;
+        c0 = y0;
+        c1 = lo1;
+        c2 = y2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    o[0] = c0;
+    o[1] = c1;
+    o[2] = c2;
+    o[3] = c3;
 }
 
 }  // namespace ftp
