@@ -416,6 +416,11 @@ FT_API int ft_mlp_n_params(const ft_mlp *mlp, int64_t *n);
 FT_API int ft_mlp_get_params(ft_mlp *mlp, float *params);
 /* Sets the parameters and resets the optimiser state. */
 FT_API int ft_mlp_set_params(ft_mlp *mlp, const float *params);
+/* The whole training state, for checkpoints: state [3][n_params] = parameters, Adam's first
+ * and second moments; adam_t = the optimiser's step count (bias correction).  Setting it
+ * restores training exactly where it was taken. */
+FT_API int ft_mlp_get_state(ft_mlp *mlp, float *state, int64_t *adam_t);
+FT_API int ft_mlp_set_state(ft_mlp *mlp, const float *state, int64_t adam_t);
 /* Loss and gradient of one batch X [B][d_in], labels y [B] in {0, 1} (loss, grad nullable;
  * grad [n_params]).  The gradient stays on the device for ft_mlp_adam_step. */
 FT_API int ft_mlp_loss_grad(ft_mlp *mlp, const float *X, const float *y, int B, float *loss,

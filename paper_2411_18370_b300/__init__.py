@@ -122,6 +122,8 @@ def lib():
             "ft_mlp_n_params": (_I, [_P, ctypes.POINTER(_I64)]),
             "ft_mlp_get_params": (_I, [_P, _P]),
             "ft_mlp_set_params": (_I, [_P, _P]),
+            "ft_mlp_get_state": (_I, [_P, _P, ctypes.POINTER(_I64)]),
+            "ft_mlp_set_state": (_I, [_P, _P, _I64]),
             "ft_mlp_loss_grad": (_I, [_P, _P, _P, _I, _P, _P]),
             "ft_mlp_adam_step": (_I, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                       ctypes.c_float]),
@@ -459,6 +461,18 @@ class MLP:
         th = np.ascontiguousarray(theta, dtype=np.float32)
         assert th.size == self.n_params
         _check(lib().ft_mlp_set_params(self.handle, th.ctypes.data))
+
+    def get_state(self):
+        """(state [3, n_params]: parameters, Adam moments m and v; Adam step count)."""
+        st = np.empty((3, self.n_params), np.float32)
+        t = _I64()
+        _check(lib().ft_mlp_get_state(self.handle, st.ctypes.data, ctypes.byref(t)))
+        return st, t.value
+
+    def set_state(self, state, adam_t):
+        st = np.ascontiguousarray(state, dtype=np.float32)
+        assert st.shape == (3, self.n_params)
+        _check(lib().ft_mlp_set_state(self.handle, st.ctypes.data, int(adam_t)))
 
     def loss_grad(self, X, y):
         X = np.ascontiguousarray(X, dtype=np.float32)

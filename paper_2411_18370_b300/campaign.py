@@ -55,18 +55,54 @@ def noise_threshold(ctx, band, bank, det_tensor, n_runs, seed, first_run_id, f_l
     return float(np.quantile(z, 1.0 - false_alarm, method="higher")), z
 
 
+class CampaignInterrupted(RuntimeError):
+    """Raised by run_campaign(stop_after=...) once its batch budget is spent."""
+
+
 def run_campaign(ctx, band, bank, det_tensor, n, tau, seed, first_run_id, f_lo, f_hi, s_ref,
-                 t_sft, c_range=(0.3, 30.0), g=None, **kw):
+                 t_sft, c_range=(0.3, 30.0), g=None, checkpoint_dir=None, batch_runs=4096,
+                 stop_after=None, **kw):
     """n injections with log-uniform amplitude; returns log10 c, detected (0/1), max z and the
-    injection records."""
+    injection records.
+
+    checkpoint_dir: the runs go in batches of batch_runs (run ids first_run_id + index, so a
+    batch's outcomes equal the same slice of one launch); each finished batch is written to
+    batch_<seed>_<first_run_id>_<b>.npz there and skipped by a later call with the same
+    arguments.  stop_after: stop (raising CampaignInterrupted) after that many batches were
+    run by this call."""
     g = np.random.default_rng(seed) if g is None else g
     inj, lc = draw_population(n, f_lo, f_hi, g, c_range=c_range, s_ref=s_ref, t_sft=t_sft)
-    res = run_injections(ctx, band, bank, det_tensor, inj, seed=seed, first_run_id=first_run_id,
-                         **kw)
-    if np.any(res["n_out_of_window"] != 0):
+    if checkpoint_dir is None:
+        res = run_injections(ctx, band, bank, det_tensor, inj, seed=seed, first_run_id=first_run_id,
+                             **kw)
+        max_z, oob = res["max_z"], res["n_out_of_window"]
+    else:
+        import os
+
+        os.makedirs(checkpoint_dir, exist_ok=True)
+        max_z = np.empty(n, np.float64)
+        oob = np.empty(n, np.int64)
+        ran = 0
+        for b, lo in enumerate(range(0, n, batch_runs)):
+            hi = min(n, lo + batch_runs)
+            path = os.path.join(checkpoint_dir, f"batch_{seed}_{first_run_id}_{b}.npz")
+            if os.path.exists(path):
+                with np.load(path) as z:
+                    max_z[lo:hi], oob[lo:hi] = z["max_z"], z["n_out_of_window"]
+                continue
+            if stop_after is not None and ran >= stop_after:
+                raise CampaignInterrupted(f"stopped after {ran} batches")
+            res = run_injections(ctx, band, bank, det_tensor, inj[lo:hi], seed=seed,
+                                 first_run_id=first_run_id + lo, **kw)
+            max_z[lo:hi], oob[lo:hi] = res["max_z"], res["n_out_of_window"]
+            tmp = path + ".tmp.npz"
+            np.savez(tmp, max_z=res["max_z"], n_out_of_window=res["n_out_of_window"])
+            os.replace(tmp, path)
+            ran += 1
+    if np.any(oob != 0):
         raise RuntimeError("local bank reads outside the generated window; widen half_window")
-    det = (res["max_z"] > tau).astype(np.float64)
-    return lc, det, res["max_z"], inj
+    det = (max_z > tau).astype(np.float64)
+    return lc, det, max_z, inj
 
 
 @dataclasses.dataclass

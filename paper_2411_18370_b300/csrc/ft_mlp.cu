@@ -402,6 +402,31 @@ int ft_mlp_set_params(ft_mlp *m, const float *host)
     return FT_OK;
 }
 
+int ft_mlp_get_state(ft_mlp *m, float *state, int64_t *adam_t)
+{
+    if (!m || !state || !adam_t)
+        FT_FAIL(FT_ERR_ARG, "mlp_get_state: null argument");
+    const size_t nb = static_cast<size_t>(m->n_params) * 4;
+    FT_CUDA(cudaMemcpy(state, m->d_theta, nb, cudaMemcpyDeviceToHost));
+    FT_CUDA(cudaMemcpy(state + m->n_params, m->d_m, nb, cudaMemcpyDeviceToHost));
+    FT_CUDA(cudaMemcpy(state + 2 * m->n_params, m->d_v, nb, cudaMemcpyDeviceToHost));
+    *adam_t = m->adam_t;
+    return FT_OK;
+}
+
+int ft_mlp_set_state(ft_mlp *m, const float *state, int64_t adam_t)
+{
+    if (!m || !state || adam_t < 0)
+        FT_FAIL(FT_ERR_ARG, "mlp_set_state: bad arguments");
+    const size_t nb = static_cast<size_t>(m->n_params) * 4;
+    FT_CUDA(cudaMemcpy(m->d_theta, state, nb, cudaMemcpyHostToDevice));
+    FT_CUDA(cudaMemcpy(m->d_m, state + m->n_params, nb, cudaMemcpyHostToDevice));
+    FT_CUDA(cudaMemcpy(m->d_v, state + 2 * m->n_params, nb, cudaMemcpyHostToDevice));
+    m->adam_t = adam_t;
+    m->bf16_stale = true;
+    return FT_OK;
+}
+
 int ft_mlp_loss_grad(ft_mlp *m, const float *X, const float *y, int B, float *loss, float *grad)
 {
     if (!m || !X || !y || B < 1)

@@ -50,6 +50,38 @@ def features(log10_c, log10_s, duty, n, f0_frac, f1, cosi, psi, tau):
     return F
 
 
+class TrainingInterrupted(RuntimeError):
+    """Raised by Surrogate.fit(stop_after=...) once its pass budget is spent."""
+
+
+def _load_checkpoint(path):
+    import os
+
+    if path is None or not os.path.exists(path):
+        return None
+    with np.load(path, allow_pickle=False) as z:
+        return {k: z[k] for k in z.files}
+
+
+def _save_checkpoint(path, hist, done, cur, finals=None):
+    """Write the training state atomically: members 0 .. done-1 finished (their losses, best
+    pass and final parameters), and the current member's state if any."""
+    import os
+
+    d = {"done": np.int64(done)}
+    prev = _load_checkpoint(path) or {}
+    for i in range(done):
+        tr, va, be = hist[i]
+        d[f"tr_{i}"], d[f"va_{i}"], d[f"best_ep_{i}"] = tr, va, np.int64(be)
+        d[f"final_{i}"] = finals[i] if finals is not None else prev[f"final_{i}"]
+    if cur is not None:
+        for k, v in cur.items():
+            d[k] = np.asarray(v)
+    tmp = path + ".tmp.npz"
+    np.savez(tmp, **d)
+    os.replace(tmp, path)
+
+
 class Surrogate:
     def __init__(self, ctx, width=128, seed=0, members=5):
         self.nets = [MLP(ctx, N_FEATURES, width, seed=seed * 7919 + i) for i in range(members)]
@@ -59,18 +91,31 @@ class Surrogate:
     def _std(self, F):
         return ((F - self.mu) / self.sd).astype(np.float32)
 
-    def fit(self, F, y, epochs=200, batch=1024, lr=2e-3, seed=0, val_frac=0.1, patience=12):
+    def fit(self, F, y, epochs=200, batch=1024, lr=2e-3, seed=0, val_frac=0.1, patience=12,
+            checkpoint=None, every=10, stop_after=None):
         """Train every member on the GPU one pass at a time on its own seeded split, keeping
         the parameters of the pass with the lowest binary cross entropy on that member's
         validation part (early stopping: the outcomes are noisy, so a long run memorises
         noise and over-states p_det).  Returns per member (training losses, validation
-        losses, best pass)."""
+        losses, best pass).
+
+        checkpoint: a file path; the training state (finished members, the current member's
+        parameters, Adam moments and step count, losses and best pass) is written every
+        `every` passes and when a member finishes, and a call with the same arguments
+        resumes from it with results identical to an uninterrupted run.  stop_after: stop
+        (raising TrainingInterrupted) after that many passes of this call, for budgets."""
         y = np.asarray(y, np.float32)
         self.mu = F.mean(0)
         self.sd = F.std(0) + 1e-12
         X = self._std(F)
         hist = []
+        ck = _load_checkpoint(checkpoint)
+        passes = 0
         for i, net in enumerate(self.nets):
+            if ck is not None and i < ck["done"]:
+                net.set_params(ck[f"final_{i}"])
+                hist.append((ck[f"tr_{i}"], ck[f"va_{i}"], int(ck[f"best_ep_{i}"])))
+                continue
             g = np.random.default_rng(seed * 1000 + i)
             perm = g.permutation(len(y))
             n_val = max(1, int(round(val_frac * len(y))))
@@ -79,7 +124,14 @@ class Surrogate:
             Xv, yv = X[vi], y[vi].astype(np.float64)
             best, best_ep, best_theta = np.inf, -1, None
             tr, va = [], []
-            for ep in range(epochs):
+            ep0 = 0
+            if ck is not None and i == ck["done"] and "cur_state" in ck:
+                net.set_state(ck["cur_state"], int(ck["cur_t"]))
+                tr, va = list(ck["cur_tr"]), list(ck["cur_va"])
+                best, best_ep = float(ck["cur_best"]), int(ck["cur_best_ep"])
+                best_theta = ck["cur_best_theta"]
+                ep0 = len(tr)
+            for ep in range(ep0, epochs):
                 tr.append(float(net.train(Xt, yt, batch=batch, epochs=1, lr=lr,
                                           seed=(seed * 1000 + i) * 1000003 + ep)[0]))
                 p = np.clip(net.predict(Xv, bf16=False).astype(np.float64), 1e-7, 1 - 1e-7)
@@ -89,8 +141,18 @@ class Surrogate:
                     best, best_ep, best_theta = v, ep, net.get_params()
                 elif ep - best_ep >= patience:
                     break
+                passes += 1
+                if checkpoint is not None and ep + 1 < epochs and (ep + 1) % every == 0:
+                    st, t = net.get_state()
+                    _save_checkpoint(checkpoint, hist, i, dict(
+                        cur_state=st, cur_t=t, cur_tr=np.array(tr), cur_va=np.array(va),
+                        cur_best=best, cur_best_ep=best_ep, cur_best_theta=best_theta))
+                if stop_after is not None and passes >= stop_after and ep + 1 < epochs:
+                    raise TrainingInterrupted(f"stopped after {passes} passes")
             net.set_params(best_theta)
             hist.append((np.array(tr), np.array(va), best_ep))
+            if checkpoint is not None:
+                _save_checkpoint(checkpoint, hist, i + 1, None, [n.get_params() for n in self.nets[:i + 1]])
         return hist
 
     def p(self, F, bf16=True):
