@@ -105,7 +105,8 @@ typedef struct {
  *   v_over_c         host [N_SFT][3] detector velocity / c at t_mid (equatorial frame).
  *   w                host [N_SFT] per-SFT weights w_alpha >= 0, or NULL for w = 1
  *                    (Sec. II.B: weights are defined up to a constant).
- *   s_n              host [N_SFT] PSD levels, or NULL (kept for injections only).
+ *   s_n              host [N_SFT] PSD levels (finite, > 0), or NULL (needed by injections,
+ *                    the semi-analytic numbers and the all-sky weights).
  * Errors: FT_ERR_ARG on an inconsistent descriptor or non-finite power/metadata,
  * FT_ERR_RANGE beyond the size/velocity limits, FT_ERR_OOM.  Synchronises `stream`. */
 FT_API int ft_load_sfts(ft_ctx *ctx, const ft_band_desc *desc, const void *power, int power_dtype,

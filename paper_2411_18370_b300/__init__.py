@@ -351,7 +351,9 @@ def pdet_q(ctx, band, det_tensor, pop, stream=None):
     """ft_pdet_q: per population draw (INJECTION_DTYPE records; h0, f0, f1 unused) the sums
     (w rho^2, w^2 rho^2) over the band's SFTs at h0 = 1 (Sec. V.A)."""
     pop = np.ascontiguousarray(pop, dtype=INJECTION_DTYPE)
-    D = np.ascontiguousarray(det_tensor, np.float64)
+    D = np.ascontiguousarray(det_tensor, np.float64).reshape(-1, 6)
+    if len(D) != band.n_sft:
+        raise ValueError("det_tensor must be [N_SFT][6]")
     n = len(pop)
     r1 = np.empty(n, np.float64)
     r2 = np.empty(n, np.float64)
@@ -432,6 +434,8 @@ def run_injections(ctx, band, bank, det_tensor, inj, seed, first_run_id=0, k_sky
     the generated window)."""
     arr = np.ascontiguousarray(inj, dtype=INJECTION_DTYPE)
     D = _f64(det_tensor).reshape(-1, 6)
+    if len(D) != band.n_sft:
+        raise ValueError("det_tensor must be [N_SFT][6]")
     out = np.zeros(len(arr), dtype=INJ_RESULT_DTYPE)
     d = _InjDesc(int(k_sky), int(half_f0), int(half_window), float(noise_scale), int(seed),
                  int(first_run_id))
@@ -561,6 +565,11 @@ def load_sfts(ctx, power, t_mid, v_over_c, n_sft, k_lo, t_sft, t0, dtype="f32", 
     v = _f64(v_over_c).reshape(-1, 3)
     wv = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
     sn = None if s_n is None else _f64(s_n)
+    # the ABI takes arrays of N_SFT = sum(n_sft) entries: check the lengths here
+    N = int(np.sum(np.asarray(n_sft, np.int64)))
+    if (int(power.shape[0]) != N or len(t_mid) != N or len(v) != N or (wv is not None and len(wv) != N)
+            or (sn is not None and len(sn) != N)):
+        raise ValueError("power rows, t_mid, v_over_c, w and s_n must all have sum(n_sft) entries")
     h = _P()
     _check(lib().ft_load_sfts(ctx.handle, ctypes.byref(desc), pp, pdt, stride, int(on_dev),
                               t_mid.ctypes.data, v.ctypes.data,

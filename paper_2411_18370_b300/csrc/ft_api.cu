@@ -276,6 +276,9 @@ int ft_load_sfts(ft_ctx *ctx, const ft_band_desc *d, const void *power, int powe
         FT_FAIL(FT_ERR_ARG, "load_sfts: non-finite t_mid or velocity");
     if (s_n && !finite_all(s_n, N))
         FT_FAIL(FT_ERR_ARG, "load_sfts: non-finite S_n");
+    for (int64_t a = 0; s_n && a < N; ++a)
+        if (!(s_n[a] > 0.0))
+            FT_FAIL(FT_ERR_ARG, "load_sfts: S_n must be > 0");
     std::vector<float> wv(N, 1.0f);
     bool weighted = false;
     if (w) {
