@@ -1,9 +1,9 @@
 // ft_binary.cu -- the binary-orbit track (Eq. (track) with the orbit term) over a random
 // template bank in uniform coordinates (Sec. IV.A, App. A), cut into hyperboxes (Sec. IV.B).
 //
-// Templates are never stored: every thread derives its template from a Philox counter and
-// keeps the per-template terms of the canonical bin rule in registers.  Each CTA evaluates
-// up to kBtThreads templates of one box over all SFTs; stages of S SFT rows (power row,
+// Templates are never stored: every thread derives its templates (two, sharing each row's
+// records) from Philox counters and keeps the per-template terms of the canonical bin rule
+// in registers.  Each CTA evaluates up to kBtThreads templates of one box over all SFTs; stages of S SFT rows (power row,
 // FP32 velocity + weight, fixed-point time) are brought into shared memory by bulk copies on
 // two mbarrier-tracked buffers.  Per (template, SFT) the work is integer phase arithmetic, a
 // short FP32 polynomial, the bin, one shared-memory read and one add: the kernel is bound by
@@ -36,7 +36,9 @@ struct ft_binary_bank {
 
 namespace {
 
-constexpr int kBtThreads = 256;
+constexpr int kBtThreads = 256;              // templates per CTA
+constexpr int kBtTPT = 2;                    // templates per thread (they share each row's records)
+constexpr int kBtBlock = kBtThreads / kBtTPT;  // threads per CTA
 constexpr int kBtRowPad = 64;
 constexpr int kBtTab = 1024;  // intervals of the quarter-wave cosine table
 
@@ -250,7 +252,7 @@ __device__ __forceinline__ void fold2(float &hi, float &lo, float part)
 }
 
 template <typename T, bool WEIGHTED, bool SKY>
-__global__ void __launch_bounds__(kBtThreads) k_bt_eval(const BtParams p)
+__global__ void __launch_bounds__(kBtBlock) k_bt_eval(const BtParams p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const size_t rows_bytes = static_cast<size_t>(p.S) * p.row_bytes;
@@ -275,15 +277,21 @@ __global__ void __launch_bounds__(kBtThreads) k_bt_eval(const BtParams p)
         t_begin = p.first + static_cast<long long>(blockIdx.x) * kBtThreads;
         t_end = min(t_begin + kBtThreads, p.first + p.count);
     }
-    const long long ti = t_begin + threadIdx.x;
-    const bool valid = ti < t_end;
+    // this thread's templates: t_begin + threadIdx.x + u kBtBlock
+    long long ti[kBtTPT];
+    bool valid[kBtTPT];
+#pragma unroll
+    for (int u = 0; u < kBtTPT; ++u) {
+        ti[u] = t_begin + threadIdx.x + u * kBtBlock;
+        valid[u] = ti[u] < t_end;
+    }
 
     if (threadIdx.x == 0) {
         ftp::mbar_init(&bars[0], 1);
         ftp::mbar_init(&bars[1], 1);
         ftp::fence_mbar_init();
     }
-    for (int i = threadIdx.x; i <= kBtTab; i += kBtThreads)
+    for (int i = threadIdx.x; i <= kBtTab; i += kBtBlock)
         tab[i] = p.costab[i];
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -292,47 +300,64 @@ __global__ void __launch_bounds__(kBtThreads) k_bt_eval(const BtParams p)
             bt_issue(p, 1, rows[1], sv[1], stq[1], sd[1], &bars[1]);
     }
 
-    BtTmpl t;
-    {
+    BtTmpl t[kBtTPT];
+#pragma unroll
+    for (int u = 0; u < kBtTPT; ++u) {
         double lam[6];
-        bt_lambda(p, valid ? ti : t_begin, lam);
-        bt_derive(p, lam, tab, t);
+        bt_lambda(p, valid[u] ? ti[u] : t_begin, lam);
+        bt_derive(p, lam, tab, t[u]);
     }
 
-    float hi = 0.f, lo = 0.f;
+    float hi[kBtTPT], lo[kBtTPT];
     // all-sky weights: sum r, sum r^2 (r = (a^2 + b^2) / S_n), compensated like the sum
-    float hiB = 0.f, loB = 0.f, hiC = 0.f, loC = 0.f;
-    int oob = 0;
+    float hiB[kBtTPT], loB[kBtTPT], hiC[kBtTPT], loC[kBtTPT];
+    int oob[kBtTPT];
+#pragma unroll
+    for (int u = 0; u < kBtTPT; ++u) {
+        hi[u] = lo[u] = hiB[u] = loB[u] = hiC[u] = loC[u] = 0.f;
+        oob[u] = 0;
+    }
     bool failed = false;
     for (int st = 0; st < p.n_stages; ++st) {
         const int b = st & 1;
         const bool ok = ftp::mbar_wait_bounded(&bars[b], (st >> 1) & 1);
         const int nr = min(p.S, p.N - st * p.S);
-        float part = 0.f, partB = 0.f, partC = 0.f;
+        float part[kBtTPT], partB[kBtTPT], partC[kBtTPT];
+#pragma unroll
+        for (int u = 0; u < kBtTPT; ++u)
+            part[u] = partB[u] = partC[u] = 0.f;
         if (ok) {
             const unsigned char *rb = rows[b];
-#pragma unroll 4
+#pragma unroll 2
             for (int r = 0; r < nr; ++r) {
                 const float4 v = sv[b][r];
-                const int k = bt_bin(t, v, stq[b][r], tab);
-                const bool in = static_cast<unsigned>(k) < static_cast<unsigned>(p.W);
-                const float val = in ? bt_load<T>(rb + static_cast<size_t>(r) * p.row_bytes, k) : 0.f;
-                oob += in ? 0 : 1;
-                if (SKY) {
-                    const float rw = bt_sky_r(sd[b][2 * r], sd[b][2 * r + 1], t.nx, t.ny, t.nz);
-                    part = __fmaf_rn(rw, val, part);
-                    partB = __fadd_rn(partB, rw);
-                    partC = __fmaf_rn(rw, rw, partC);
-                } else {
-                    part = WEIGHTED ? __fmaf_rn(v.w, val, part) : __fadd_rn(part, val);
+                const long long tq = stq[b][r];
+                const unsigned char *row = rb + static_cast<size_t>(r) * p.row_bytes;
+#pragma unroll
+                for (int u = 0; u < kBtTPT; ++u) {
+                    const int k = bt_bin(t[u], v, tq, tab);
+                    const bool in = static_cast<unsigned>(k) < static_cast<unsigned>(p.W);
+                    const float val = in ? bt_load<T>(row, k) : 0.f;
+                    oob[u] += in ? 0 : 1;
+                    if (SKY) {
+                        const float rw = bt_sky_r(sd[b][2 * r], sd[b][2 * r + 1], t[u].nx, t[u].ny, t[u].nz);
+                        part[u] = __fmaf_rn(rw, val, part[u]);
+                        partB[u] = __fadd_rn(partB[u], rw);
+                        partC[u] = __fmaf_rn(rw, rw, partC[u]);
+                    } else {
+                        part[u] = WEIGHTED ? __fmaf_rn(v.w, val, part[u]) : __fadd_rn(part[u], val);
+                    }
                 }
             }
         }
         // compensated folds of the stage's partials (2Sum)
-        fold2(hi, lo, part);
-        if (SKY) {
-            fold2(hiB, loB, partB);
-            fold2(hiC, loC, partC);
+#pragma unroll
+        for (int u = 0; u < kBtTPT; ++u) {
+            fold2(hi[u], lo[u], part[u]);
+            if (SKY) {
+                fold2(hiB[u], loB[u], partB[u]);
+                fold2(hiC[u], loC[u], partC[u]);
+            }
         }
         if (__syncthreads_or(!ok)) {
             failed = true;
@@ -354,34 +379,40 @@ __global__ void __launch_bounds__(kBtThreads) k_bt_eval(const BtParams p)
 
     // s and z: the plain sum, or under all-sky weights sum r P / sum r with mu_G = 2 and
     // sigma_G = 2 sqrt(sum r^2) / sum r of this template's sky direction
-    double s64 = static_cast<double>(hi) + static_cast<double>(lo);
-    double z64 = (s64 - p.mu) / p.sigma;
-    if (SKY) {
-        const double B = static_cast<double>(hiB) + static_cast<double>(loB);
-        const double C = static_cast<double>(hiC) + static_cast<double>(loC);
-        s64 /= B;
-        z64 = (s64 - 2.0) / (2.0 * sqrt(C) / B);
-    }
-    const float sv_ = SKY ? static_cast<float>(s64) : __fadd_rn(hi, lo);
-    if (!p.box_mode) {
-        if (valid) {
-            const long long o = ti - p.first;
-            p.s_out[o] = sv_;
-            if (p.z_out)
-                p.z_out[o] = static_cast<float>(z64);
-            if (p.oob_out)
-                p.oob_out[o] = oob;
+    float *vs = reinterpret_cast<float *>(smem);
+    float *vz = vs + kBtThreads;
+#pragma unroll
+    for (int u = 0; u < kBtTPT; ++u) {
+        double s64 = static_cast<double>(hi[u]) + static_cast<double>(lo[u]);
+        double z64 = (s64 - p.mu) / p.sigma;
+        if (SKY) {
+            const double B = static_cast<double>(hiB[u]) + static_cast<double>(loB[u]);
+            const double C = static_cast<double>(hiC[u]) + static_cast<double>(loC[u]);
+            s64 /= B;
+            z64 = (s64 - 2.0) / (2.0 * sqrt(C) / B);
         }
-        return;
+        const float sv_ = SKY ? static_cast<float>(s64) : __fadd_rn(hi[u], lo[u]);
+        if (!p.box_mode) {
+            if (valid[u]) {
+                const long long o = ti[u] - p.first;
+                p.s_out[o] = sv_;
+                if (p.z_out)
+                    p.z_out[o] = static_cast<float>(z64);
+                if (p.oob_out)
+                    p.oob_out[o] = oob[u];
+            }
+            continue;
+        }
+        // candidates of the per-CTA selection; -inf: not a candidate
+        const bool pass = valid[u] && (p.gate == nullptr || p.gate[ti[u]] >= p.gate_min);
+        vs[threadIdx.x + u * kBtBlock] = pass ? sv_ : -INFINITY;
+        vz[threadIdx.x + u * kBtBlock] = static_cast<float>(z64);
     }
+    if (!p.box_mode)
+        return;
 
     // per-CTA top-k by (s desc, index asc): warp 0 extracts k rounds of the arg-max among
     // keys ranked after the previous pick
-    float *vs = reinterpret_cast<float *>(smem);
-    float *vz = vs + kBtThreads;
-    const bool pass = valid && (p.gate == nullptr || p.gate[ti] >= p.gate_min);
-    vs[threadIdx.x] = pass ? sv_ : -INFINITY;  // -inf: not a candidate
-    vz[threadIdx.x] = static_cast<float>(z64);
     __syncthreads();
     if (threadIdx.x >= 32)
         return;
@@ -661,7 +692,7 @@ int launch_t(long long n_cta, size_t smem, const BtParams &p, cudaStream_t st)
 {
     auto fn = p.rowd != nullptr ? k_bt_eval<T, false, true> : k_bt_eval<T, Wt, false>;
     FT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-    fn<<<static_cast<unsigned>(n_cta), kBtThreads, smem, st>>>(p);
+    fn<<<static_cast<unsigned>(n_cta), kBtBlock, smem, st>>>(p);
     FT_CUDA(cudaGetLastError());
     return FT_OK;
 }
