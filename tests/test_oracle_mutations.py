@@ -47,24 +47,48 @@ PINS = [
 ]
 
 
-def _compile(src: str, out: str):
-    cfile = out[:-3] + ".c"
+# the binary-orbit track and random bank (oracle/ft_oracle_bin.c), against its own pins
+BIN_SRC = os.path.join(os.path.dirname(obuild.SRC), "ft_oracle_bin.c")
+MUTATIONS_BIN = {
+    "orbit_sign": ("float X = (d->phi + dop) - m;", "float X = (d->phi + dop) + m;"),
+    "doppler_dropped": ("float dop = d->F * vn;", "float dop = 0.0f * vn;"),
+    "orbit_phase_sign": ("uint64_t ph = d->nu_q * (uint64_t)tq - d->psi_q;",
+                         "uint64_t ph = d->nu_q * (uint64_t)tq + d->psi_q;"),
+    "cos_quadrant_sign": ("return (q == 1u || q == 2u) ? -c : c;", "return (q == 1u) ? -c : c;"),
+    "cos_no_interpolation": ("float c = fmaf(f, tab_d[i], tab_c[i]);", "float c = tab_c[i] + 0.0f * f;"),
+    "box_order_reversed": ("for (int d = 5; d >= 0; d--) {", "for (int d = 0; d < 6; d++) {"),
+    "ap_root_wrong": ("case 3: return cbrt_newton(xi, b->hi[3]);", "case 3: return sqrt(xi);"),
+    "amplitude_without_omega": ("o->D = (float)((F * lam[3]) * lam[4]);", "o->D = (float)(F * lam[3]);"),
+    "sky_weight_times_psd": ("double r = (aa * aa + bb * bb) / s_n[a];",
+                             "double r = (aa * aa + bb * bb) * s_n[a];"),
+}
+
+
+def _bin_pins():
+    from tests import test_oracle_binary_pins as bp
+
+    return [getattr(bp, n) for n in sorted(dir(bp)) if n.startswith("test_")]
+
+
+def _compile(src: str, out: str, which=None):
+    which = obuild.SRC if which is None else which
+    cfile = os.path.join(os.path.dirname(out), os.path.basename(which))
     with open(cfile, "w") as f:
         f.write(src)
-    others = [s for s in obuild.SRCS if s != obuild.SRC]
+    others = [s for s in obuild.SRCS if s != which]
     subprocess.check_call(["gcc", "-O1", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
                            "-std=gnu11", cfile] + others + ["-o", out, "-lm"])
 
 
-def _runs_clean(lib):
+def _runs_clean(lib, pins_=None):
     saved = oracle._lib
     oracle._lib = lib
     try:
         failed = []
-        for p in PINS:
+        for p in (PINS if pins_ is None else pins_):
             try:
                 p()
-            except AssertionError:
+            except Exception:  # an assertion, or a mutated value breaking the pin outright
                 failed.append(p.__name__)
         return failed
     finally:
@@ -88,3 +112,22 @@ def test_unmutated_oracle_passes_all_pins():
         so = os.path.join(d, "clean.so")
         _compile(open(obuild.SRC).read(), so)
         assert _runs_clean(oracle.load_library(so)) == []
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS_BIN))
+def test_planted_mistake_in_binary_oracle_is_caught(name):
+    src = open(BIN_SRC).read()
+    old, new = MUTATIONS_BIN[name]
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    with tempfile.TemporaryDirectory() as d:
+        so = os.path.join(d, f"mut_{name}.so")
+        _compile(src.replace(old, new), so, BIN_SRC)
+        failed = _runs_clean(oracle.load_library(so), _bin_pins())
+    assert failed, f"no pin caught mutation {name}"
+
+
+def test_unmutated_binary_oracle_passes_its_pins():
+    with tempfile.TemporaryDirectory() as d:
+        so = os.path.join(d, "clean_bin.so")
+        _compile(open(BIN_SRC).read(), so, BIN_SRC)
+        assert _runs_clean(oracle.load_library(so), _bin_pins()) == []
