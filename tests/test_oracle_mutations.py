@@ -1,8 +1,10 @@
 """Planted mistakes: each plausible error in the oracle must make at least one pin fail.
 
-Each mutation edits a temporary copy of oracle/ft_oracle.c (the oracle itself is never
+Each mutation edits a temporary copy of one oracle source (the oracle itself is never
 touched), compiles it with the same flags, swaps it in for the duration of the check and
-runs the pins of tests/test_oracle_pins.py against it.
+runs that source's pins against it: tests/test_oracle_pins.py for ft_oracle.c,
+tests/test_oracle_binary_pins.py for ft_oracle_bin.c, and the injection and all-sky weight
+pins for ft_oracle_inj.c.
 """
 import os
 import subprocess
@@ -62,6 +64,34 @@ MUTATIONS_BIN = {
     "sky_weight_times_psd": ("double r = (aa * aa + bb * bb) / s_n[a];",
                              "double r = (aa * aa + bb * bb) * s_n[a];"),
 }
+
+
+# injections, antenna patterns and all-sky weights (oracle/ft_oracle_inj.c)
+INJ_SRC = os.path.join(os.path.dirname(obuild.SRC), "ft_oracle_inj.c")
+MUTATIONS_INJ = {
+    "sky_weight_times_psd": ("wi[a] = (aa * aa + bb * bb) / s_n[a];",
+                             "wi[a] = (aa * aa + bb * bb) * s_n[a];"),
+    "sky_weight_not_normalised": ("wi[a] /= tot;", "wi[a] /= 1.0;"),
+    "antenna_cross_sign": ("sx += M[i][j] * (X[i] * Y[j] + Y[i] * X[j]);",
+                           "sx += M[i][j] * (X[i] * Y[j] - Y[i] * X[j]);"),
+    "polarisations_in_phase": ("double q2 = fp * fp * ap * ap + fx * fx * ax * ax;",
+                               "double q2 = (fp * ap + fx * ax) * (fp * ap + fx * ax);"),
+}
+
+
+def _inj_pins():
+    import inspect
+
+    from tests import test_oracle_injection_pins as ip
+    from tests import test_oracle_skyweights_pins as sp
+
+    out = []
+    for mod in (ip, sp):
+        for n in sorted(dir(mod)):
+            f = getattr(mod, n)
+            if n.startswith("test_") and callable(f) and not inspect.signature(f).parameters:
+                out.append(f)
+    return out
 
 
 def _bin_pins():
@@ -131,3 +161,22 @@ def test_unmutated_binary_oracle_passes_its_pins():
         so = os.path.join(d, "clean_bin.so")
         _compile(open(BIN_SRC).read(), so, BIN_SRC)
         assert _runs_clean(oracle.load_library(so), _bin_pins()) == []
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS_INJ))
+def test_planted_mistake_in_injection_oracle_is_caught(name):
+    src = open(INJ_SRC).read()
+    old, new = MUTATIONS_INJ[name]
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    with tempfile.TemporaryDirectory() as d:
+        so = os.path.join(d, f"mut_{name}.so")
+        _compile(src.replace(old, new), so, INJ_SRC)
+        failed = _runs_clean(oracle.load_library(so), _inj_pins())
+    assert failed, f"no pin caught mutation {name}"
+
+
+def test_unmutated_injection_oracle_passes_its_pins():
+    with tempfile.TemporaryDirectory() as d:
+        so = os.path.join(d, "clean_inj.so")
+        _compile(open(INJ_SRC).read(), so, INJ_SRC)
+        assert _runs_clean(oracle.load_library(so), _inj_pins()) == []
