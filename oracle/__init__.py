@@ -510,6 +510,23 @@ def binary_statistic_sky(sfts, bank, D, templates=None):
     return s, sig, oob
 
 
+def topk_per_key(s, key, n_keys, k, templates=None):
+    """Per box id in 0 .. n_keys - 1 (key[i] is the box of template templates[i]), the k largest
+    s, ties by the smaller template index; idx -1 / val -inf beyond the box's population."""
+    s = np.asarray(s, np.float64)
+    key = np.asarray(key, np.int64)
+    t = np.arange(len(s), dtype=np.int64) if templates is None else np.asarray(templates, np.int64)
+    idx = np.full((n_keys, k), -1, np.int64)
+    val = np.full((n_keys, k), -np.inf)
+    order = np.lexsort((t, -s, key))
+    bounds = np.searchsorted(key[order], np.arange(n_keys + 1))
+    for b in range(n_keys):
+        sel = order[bounds[b]:bounds[b + 1]][:k]
+        idx[b, : len(sel)] = t[sel]
+        val[b, : len(sel)] = s[sel]
+    return idx, val
+
+
 def topk_per_box(s, n_per_box, n_boxes, k, templates=None):
     """Per box b (templates i with i // n_per_box == b), the k largest s, ties by the smaller
     index; idx -1 / val -inf beyond the box's population."""

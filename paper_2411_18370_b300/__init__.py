@@ -109,6 +109,8 @@ def lib():
             "ft_binary_topk_per_box_gated": (_I, [_P, _P, _P, _I, _P, ctypes.c_float, _P, _I, _P]),
             "ft_number_count_band": (_I, [_P, _P, ctypes.c_double, _P, ctypes.POINTER(_P)]),
             "ft_topk_per_band_gated": (_I, [_P, _P, _P, _I, _P, ctypes.c_float, _P, _I, _P]),
+            "ft_topk_per_skybox": (_I, [_P, _P, _P, _I, _I, _P, _I, _P]),
+            "ft_bank_sky_order": (_I, [_P, _P]),
             "ft_topk_per_band_noalloc": (_I, [_P, _P, _P, _I, _P, _I, _P]),
             "ft_batch_create": (_I, [_P, _I, _P, _P, _I, _P, _P, ctypes.POINTER(_P)]),
             "ft_batch_run": (_I, [_P, _P, _I, _P]),
@@ -624,6 +626,21 @@ def topk_per_band_gated(ctx, band, bank, k, gate, gate_min, out, stream=None):
     po, dev = _ptr(out)
     _check(lib().ft_topk_per_band_gated(ctx.handle, band.handle, bank.handle, int(k), pg,
                                         float(gate_min), po, int(dev), _stream(stream, dev)))
+
+
+def topk_per_skybox(ctx, band, bank, sky_box, k, out, stream=None):
+    """ft_topk_per_skybox into `out` (CANDIDATE_DTYPE [n_sky_boxes, n_sub, k] host array or a
+    device byte tensor)."""
+    po, dev = _ptr(out)
+    _check(lib().ft_topk_per_skybox(ctx.handle, band.handle, bank.handle, int(sky_box), int(k), po,
+                                    int(dev), _stream(stream, dev)))
+
+
+def bank_sky_order(bank, n_sky):
+    """ft_bank_sky_order: the bank's sky order (int32 [n_sky])."""
+    out = np.empty(int(n_sky), np.int32)
+    _check(lib().ft_bank_sky_order(bank.handle, out.ctypes.data))
+    return out
 
 
 def topk_per_band_noalloc(ctx, band, bank, k, out, stream=None):

@@ -2,6 +2,7 @@
 #include "ft_internal.cuh"
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <limits>
@@ -728,21 +729,24 @@ int ft_eval_statistic(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, flo
 }
 
 static int topk_impl(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int k, const float *gate,
-                     float gate_min, ft_candidate *out, int out_on_device, void *stream)
+                     float gate_min, ft_candidate *out, int out_on_device, void *stream, int sky_box = 0)
 {
     FT_TRY(check_pair(ctx, band, bank));
     if (!out)
         FT_FAIL(FT_ERR_ARG, "topk_per_band: null out");
     if (k < 1 || k > 32)
         FT_FAIL(FT_ERR_RANGE, "topk_per_band: k must be in [1, 32]");
+    if (sky_box < 0 || sky_box > INT_MAX / 2)
+        FT_FAIL(FT_ERR_ARG, "topk_per_skybox: bad sky box size");
     DeviceGuard g(ctx->device);
     cudaStream_t st = as_stream(stream);
-    const EvalShape sh = ft_default_shape(ctx, band, bank);
+    const EvalShape sh = ft_default_shape(ctx, band, bank, sky_box);
     const int J = sh.J;
     const long long n_cta = ft_grid_ctas(bank, sh);
     const int lsub_max = std::min(bank->n_sub, (J + bank->sub - 1) / bank->sub + 1);
     const size_t cand_bytes = static_cast<size_t>(n_cta) * lsub_max * k * sizeof(ft_candidate);
-    const size_t out_bytes = static_cast<size_t>(bank->n_sub) * k * sizeof(ft_candidate);
+    const long long n_boxes = sky_box > 0 ? (bank->n_sky + sky_box - 1) / sky_box : 1;
+    const size_t out_bytes = static_cast<size_t>(n_boxes) * bank->n_sub * k * sizeof(ft_candidate);
     void *scr = nullptr;
     FT_TRY(ft_ctx_scratch(ctx, cand_bytes, &scr));
     ft_candidate *dout = out;
@@ -759,11 +763,29 @@ static int topk_impl(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int 
     p.sub = bank->sub;
     p.lsub_max = lsub_max;
     FT_TRY(ft_launch_eval(band, bank, sh, p, st));
-    FT_TRY(ft_launch_merge(bank, sh, p.cand, k, lsub_max, dout, st));
+    FT_TRY(ft_launch_merge(bank, sh, p.cand, k, lsub_max, dout, st, sky_box));
     if (!out_on_device) {
         FT_CUDA(cudaMemcpyAsync(out, dout, out_bytes, cudaMemcpyDeviceToHost, st));
         return read_status(ctx, st);
     }
+    return FT_OK;
+}
+
+int ft_topk_per_skybox(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int sky_box, int k,
+                       ft_candidate *out, int out_on_device, void *stream)
+{
+    if (sky_box < 1)
+        FT_FAIL(FT_ERR_ARG, "topk_per_skybox: sky_box must be >= 1");
+    return topk_impl(ctx, band, bank, k, nullptr, 0.f, out, out_on_device, stream, sky_box);
+}
+
+int ft_bank_sky_order(const ft_bank *bank, int32_t *order)
+{
+    if (!bank || !order)
+        FT_FAIL(FT_ERR_ARG, "bank_sky_order: null argument");
+    DeviceGuard g(bank->device);
+    FT_CUDA(cudaMemcpy(order, bank->d_sky_order, static_cast<size_t>(bank->n_sky) * sizeof(int),
+                       cudaMemcpyDeviceToHost));
     return FT_OK;
 }
 

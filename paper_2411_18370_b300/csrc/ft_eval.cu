@@ -1329,9 +1329,10 @@ constexpr int kMergeThreads = 256;
 
 // One CTA per sub-band b: gathers the per-CTA lists of every evaluation CTA whose f0 tile
 // meets the sub-band and keeps the k best by (s desc, template index asc).
+// Sky groups [g0, g0 + n_skyg) (all f1 groups, the f0 tiles of sub-band b) into out.
 __device__ __forceinline__ void merge_subband(const ft_candidate *cand, int k, int lsub_max,
-                                              long long n_skyg, int n_f1g, int n_f0t, int J,
-                                              int sub, int n_f0, int b, ft_candidate *out)
+                                              long long g0, long long n_skyg, int n_f1g, int n_f0t,
+                                              int J, int sub, int n_f0, int b, ft_candidate *out)
 {
     __shared__ ft_candidate wl[kMergeThreads / 32][kKmax];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1339,6 +1340,7 @@ __device__ __forceinline__ void merge_subband(const ft_candidate *cand, int k, i
     const int ft_hi = (min((b + 1) * sub, n_f0) - 1) / J;
     const int nft = ft_hi - ft_lo + 1;
     const long long total = n_skyg * n_f1g * static_cast<long long>(nft) * k;
+    const long long sg0 = g0 * n_f1g;  // first combined (sky group, f1 group) index
 
     ft_candidate Lst[kKmax];
     int n = 0;
@@ -1346,7 +1348,7 @@ __device__ __forceinline__ void merge_subband(const ft_candidate *cand, int k, i
         const long long q = c / k;
         const int i = static_cast<int>(c - q * k);
         const int ftl = static_cast<int>(q % nft);
-        const long long sg = q / nft;
+        const long long sg = sg0 + q / nft;
         const int ft = ft_lo + ftl;
         const long long cta = sg * n_f0t + ft;
         const int lb = b - (ft * J) / sub;
@@ -1445,12 +1447,18 @@ __device__ __forceinline__ void merge_subband(const ft_candidate *cand, int k, i
     }
 }
 
+// Block (b, x): sub-band b of sky box x (sky groups [x gpb, (x + 1) gpb)) into
+// out[(x n_sub + b) k ..].
 __global__ void __launch_bounds__(kMergeThreads) k_topk_merge(const ft_candidate *cand, int k,
                                                               int lsub_max, long long n_skyg,
-                                                              int n_f1g, int n_f0t, int J, int sub,
-                                                              int n_f0, ft_candidate *out)
+                                                              long long gpb, int n_f1g, int n_f0t,
+                                                              int J, int sub, int n_f0, int n_sub,
+                                                              ft_candidate *out)
 {
-    merge_subband(cand, k, lsub_max, n_skyg, n_f1g, n_f0t, J, sub, n_f0, blockIdx.x, out);
+    const long long g0 = static_cast<long long>(blockIdx.y) * gpb;
+    const long long ng = min(gpb, n_skyg - g0);
+    merge_subband(cand, k, lsub_max, g0, ng, n_f1g, n_f0t, J, sub, n_f0, blockIdx.x,
+                  out + static_cast<long long>(blockIdx.y) * n_sub * k);
 }
 
 // Merge for the persistent batch: block i handles sub-band j = i - sub_prefix[b] of band b
@@ -1823,7 +1831,7 @@ long long ft_grid_ctas(const ft_bank *bank, const EvalShape &sh)
     return n_skyg * n_f1g * n_f0t;
 }
 
-EvalShape ft_default_shape(const ft_ctx *ctx, const ft_band *band, const ft_bank *bank)
+EvalShape ft_default_shape(const ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int sky_box)
 {
     EvalShape sh;
     sh.fast = bank->window_safe;
@@ -1831,6 +1839,8 @@ EvalShape ft_default_shape(const ft_ctx *ctx, const ft_band *band, const ft_bank
         // up to kFastMaxWarps evaluating warps: the f1 values of one group for P sky
         // points that share the shared-memory rows
         ft_sky_grouping(bank, kFastMaxWarps, &sh.P, &sh.F1);
+        while (sky_box > 0 && sky_box % sh.P != 0)
+            --sh.P;
     } else {
         const int groups = (bank->n_f1 + 31) / 32;
         sh.F1 = (bank->n_f1 + groups - 1) / groups;
@@ -1890,7 +1900,9 @@ int ft_launch_eval(const ft_band *band, const ft_bank *bank, const EvalShape &sh
     p.P = sh.P;
     p.F1 = sh.F1;
     p.n_skyg = (bank->n_sky + sh.P - 1) / sh.P;
-    p.sky_order = sh.P > 1 ? bank->d_sky_order : nullptr;
+    // CTAs walk the sky in the bank's proximity order (sky groups are runs of it, and so
+    // are the sky boxes of ft_topk_per_skybox)
+    p.sky_order = bank->d_sky_order;
     p.S = sh.S;
     p.n_stages = static_cast<int>((band->N + sh.S - 1) / sh.S);
     p.row_bytes = row_bytes_of(band);
@@ -1939,14 +1951,20 @@ int ft_launch_eval(const ft_band *band, const ft_bank *bank, const EvalShape &sh
 }
 
 int ft_launch_merge(const ft_bank *bank, const EvalShape &sh, const FtCand *cand, int k,
-                    int lsub_max, ft_candidate *out, cudaStream_t st)
+                    int lsub_max, ft_candidate *out, cudaStream_t st, int sky_box)
 {
     const int n_f0t = (bank->n_f0 + sh.J - 1) / sh.J;
     const int n_f1g = (bank->n_f1 + sh.F1 - 1) / sh.F1;
     const long long n_skyg = (bank->n_sky + sh.P - 1) / sh.P;
-    k_topk_merge<<<bank->n_sub, kMergeThreads, 0, st>>>(
-        reinterpret_cast<const ft_candidate *>(cand), k, lsub_max, n_skyg, n_f1g, n_f0t, sh.J,
-        bank->sub, bank->n_f0, out);
+    if (sky_box > 0 && sky_box % sh.P != 0)
+        FT_FAIL(FT_ERR_ARG, "merge: sky box not a multiple of the sky group size");
+    const long long gpb = sky_box > 0 ? sky_box / sh.P : n_skyg;
+    const long long n_boxes = (n_skyg + gpb - 1) / gpb;
+    if (n_boxes > 65535)
+        FT_FAIL(FT_ERR_RANGE, "merge: more than 65535 sky boxes");
+    k_topk_merge<<<dim3(static_cast<unsigned>(bank->n_sub), static_cast<unsigned>(n_boxes)), kMergeThreads, 0,
+                   st>>>(reinterpret_cast<const ft_candidate *>(cand), k, lsub_max, n_skyg, gpb, n_f1g, n_f0t,
+                         sh.J, bank->sub, bank->n_f0, bank->n_sub, out);
     FT_CUDA(cudaGetLastError());
     return FT_OK;
 }
