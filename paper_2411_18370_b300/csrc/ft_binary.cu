@@ -59,6 +59,7 @@ struct BtParams {
     const float2 *costab;          // (cos(i (pi/2) / 1024) in FP32, next minus this)
     const float4 *rowd;            // null, or the all-sky weight records [n_pad][2]
     double mu, sigma;
+    double m1, sd1;                // one SFT's noise mean and deviation (2, 2 for power)
     // eval mode (box_mode == 0): templates [first, first + count), CTA c takes kBtThreads of them
     long long first, count;
     float *s_out, *z_out;
@@ -377,8 +378,9 @@ __global__ void __launch_bounds__(kBtBlock) k_bt_eval(const BtParams p)
         return;
     }
 
-    // s and z: the plain sum, or under all-sky weights sum r P / sum r with mu_G = 2 and
-    // sigma_G = 2 sqrt(sum r^2) / sum r of this template's sky direction
+    // s and z: the plain sum, or under all-sky weights sum r P / sum r with mu_G = m1 and
+    // sigma_G = sd1 sqrt(sum r^2) / sum r of this template's sky direction (m1 = sd1 = 2 for
+    // normalised power; p and sqrt(p (1 - p)) for a number-count band)
     float *vs = reinterpret_cast<float *>(smem);
     float *vz = vs + kBtThreads;
 #pragma unroll
@@ -389,7 +391,7 @@ __global__ void __launch_bounds__(kBtBlock) k_bt_eval(const BtParams p)
             const double B = static_cast<double>(hiB[u]) + static_cast<double>(loB[u]);
             const double C = static_cast<double>(hiC[u]) + static_cast<double>(loC[u]);
             s64 /= B;
-            z64 = (s64 - 2.0) / (2.0 * sqrt(C) / B);
+            z64 = (s64 - p.m1) / (p.sd1 * sqrt(C) / B);
         }
         const float sv_ = SKY ? static_cast<float>(s64) : __fadd_rn(hi[u], lo[u]);
         if (!p.box_mode) {
@@ -665,6 +667,8 @@ BtParams base_params(const ft_band *band, const ft_binary_bank *bk)
     p.costab = bk->d_costab;
     p.rowd = band->d_D != nullptr ? bk->d_rowd : nullptr;
     p.mu = band->mu;
+    p.m1 = band->m1;
+    p.sd1 = std::sqrt(band->v1);
     p.sigma = band->sigma;
     p.status = band->ctx->d_status;
     return p;

@@ -284,3 +284,32 @@ def test_all_sky_weights(ctx, dtype):
     c_idx, c_val = oracle.topk_per_box(s.astype(np.float64), bank.n_per_box, bank.n_boxes, k)
     assert np.array_equal(out["template_idx"], c_idx)
     assert np.array_equal(out["s"].astype(np.float64), c_val)
+
+
+def test_sky_weighted_number_count(ctx):
+    """A number-count band inherits the all-sky weights: its binary statistic is the weighted
+    count with per-template weights, and z uses the count's noise moments (mu = p, sigma =
+    sqrt(p (1 - p) sum w^2))."""
+    import dataclasses
+    import math
+
+    sfts = _sfts(seed=20)
+    sfts = dataclasses.replace(sfts, s_n=np.random.default_rng(6).uniform(0.5, 2.0, sfts.n_total))
+    bank = _bank(seed=21, n_per_box=100)
+    band = H.band_from(ctx, sfts, power_f32=True)
+    D = _det_tensor(sfts)
+    ft.band_set_sky_weights(band, D)
+    ncb = ft.number_count_band(ctx, band, 3.2)
+    gb = _gpu_bank(ctx, ncb, bank)
+    n = bank.n_templates
+    s = np.empty(n, np.float32)
+    z = np.empty(n, np.float32)
+    ft.binary_eval(ctx, ncb, gb, 0, n, s, z)
+    stored = _stored(sfts, "f32")
+    bin_ = dataclasses.replace(stored, power=(stored.power > 3.2) * 1.0)
+    s_or, sig_pow, _ = oracle.binary_statistic_sky(bin_, bank, D)
+    assert np.all(np.abs(s - s_or) <= 2e-6 * np.maximum(s_or, 1e-3))
+    p = math.exp(-1.6)
+    sig = sig_pow / 2.0 * math.sqrt(p * (1 - p))  # sig_pow = 2 sqrt(sum w^2)
+    z_or = (s_or - p) / sig
+    assert np.all(np.abs(z - z_or) <= 2e-6 * np.maximum(s_or, 1e-3) / sig + 1e-5)
