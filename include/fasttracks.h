@@ -374,8 +374,9 @@ typedef struct {
 /* Set up a binary bank for `band` (uses its SFT times, velocities and weights: the per-SFT
  * weights, or, when ft_band_set_sky_weights was called before, the all-sky weights
  * (a^2 + b^2)/S_n of each template's own sky direction, normalised per template; then s =
- * sum r P / sum r and z uses mu_G = 2, sigma_G = 2 sqrt(sum r^2) / sum r).  Errors:
- * FT_ERR_ARG (ranges, counts), FT_ERR_OOM. */
+ * sum r P / sum r and z uses mu_G = m and sigma_G = d sqrt(sum r^2) / sum r, with one SFT's
+ * noise mean m and deviation d: 2 and 2 for normalised power, p and sqrt(p (1 - p)) for a
+ * number-count band).  Errors: FT_ERR_ARG (ranges, counts), FT_ERR_OOM. */
 FT_API int ft_make_binary_bank(ft_ctx *ctx, const ft_band *band, const ft_binary_bank_desc *desc,
                                ft_binary_bank **out);
 FT_API void ft_binary_bank_destroy(ft_binary_bank *bank);
