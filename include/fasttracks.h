@@ -236,6 +236,22 @@ FT_API int ft_topk_per_band_gated(ft_ctx *ctx, const ft_band *band, const ft_ban
 FT_API int ft_topk_per_skybox(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int sky_box,
                               int k, ft_candidate *out, int out_on_device, void *stream);
 
+/* Ahead-of-time boxes over all three dimensions of the regular bank (Sec. IV.B: disjoint
+ * boxes of neighbouring templates, the loudest kept per box): box (x, y, b) holds the templates
+ * of sub-band b whose sky point is at positions x sky_box .. (x + 1) sky_box - 1 of the bank's
+ * sky order (as in ft_topk_per_skybox) and whose f1 index is in y f1_box .. (y + 1) f1_box - 1
+ * of the bank's f1 list.  out: [n_sky_boxes][n_f1_boxes][n_subbands][k] ft_candidate with
+ * n_sky_boxes = ceil(n_sky / sky_box), n_f1_boxes = ceil(n_f1 / f1_box), each list as in
+ * ft_topk_per_band.  gate: NULL for the plain loudest, else as in ft_topk_per_band_gated (the
+ * count-gated loudest per box of Sec. VI.B).  The launch shape keeps every CTA's sky points and
+ * f1 values inside one box; small f1 boxes shrink the CTAs' f1 groups and cost speed.
+ * sky_box >= n_sky (f1_box >= n_f1) makes one box over that dimension.
+ * Errors: FT_ERR_ARG (sky_box or f1_box < 1; a gate as in ft_topk_per_band_gated),
+ * FT_ERR_RANGE (more than 65535 boxes along either dimension, k), else as ft_topk_per_band. */
+FT_API int ft_topk_per_box(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int sky_box,
+                           int f1_box, int k, const float *gate, float gate_min,
+                           ft_candidate *out, int out_on_device, void *stream);
+
 /* The bank's sky order: order[i] = index (in the bank's sky list) of the sky point at position
  * i; host [n_sky] int32. */
 FT_API int ft_bank_sky_order(const ft_bank *bank, int32_t *order);

@@ -110,6 +110,7 @@ def lib():
             "ft_number_count_band": (_I, [_P, _P, ctypes.c_double, _P, ctypes.POINTER(_P)]),
             "ft_topk_per_band_gated": (_I, [_P, _P, _P, _I, _P, ctypes.c_float, _P, _I, _P]),
             "ft_topk_per_skybox": (_I, [_P, _P, _P, _I, _I, _P, _I, _P]),
+            "ft_topk_per_box": (_I, [_P, _P, _P, _I, _I, _I, _P, ctypes.c_float, _P, _I, _P]),
             "ft_bank_sky_order": (_I, [_P, _P]),
             "ft_topk_per_band_noalloc": (_I, [_P, _P, _P, _I, _P, _I, _P]),
             "ft_batch_create": (_I, [_P, _I, _P, _P, _I, _P, _P, ctypes.POINTER(_P)]),
@@ -634,6 +635,20 @@ def topk_per_skybox(ctx, band, bank, sky_box, k, out, stream=None):
     po, dev = _ptr(out)
     _check(lib().ft_topk_per_skybox(ctx.handle, band.handle, bank.handle, int(sky_box), int(k), po,
                                     int(dev), _stream(stream, dev)))
+
+
+def topk_per_box(ctx, band, bank, sky_box, f1_box, k, out, gate=None, gate_min=0.0, stream=None):
+    """ft_topk_per_box into `out` (CANDIDATE_DTYPE [n_sky_boxes, n_f1_boxes, n_sub, k] host
+    array or a device byte tensor); gate: None, or a CUDA float32 tensor of n_templates values
+    as in topk_per_band_gated."""
+    pg = None
+    if gate is not None:
+        pg, gdev = _ptr(gate)
+        if not gdev:
+            raise ValueError("gate must be a CUDA tensor")
+    po, dev = _ptr(out)
+    _check(lib().ft_topk_per_box(ctx.handle, band.handle, bank.handle, int(sky_box), int(f1_box),
+                                 int(k), pg, float(gate_min), po, int(dev), _stream(stream, dev)))
 
 
 def bank_sky_order(bank, n_sky):

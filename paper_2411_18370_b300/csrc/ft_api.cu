@@ -729,7 +729,8 @@ int ft_eval_statistic(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, flo
 }
 
 static int topk_impl(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int k, const float *gate,
-                     float gate_min, ft_candidate *out, int out_on_device, void *stream, int sky_box = 0)
+                     float gate_min, ft_candidate *out, int out_on_device, void *stream, int sky_box = 0,
+                     int f1_box = 0)
 {
     FT_TRY(check_pair(ctx, band, bank));
     if (!out)
@@ -738,14 +739,17 @@ static int topk_impl(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int 
         FT_FAIL(FT_ERR_RANGE, "topk_per_band: k must be in [1, 32]");
     if (sky_box < 0 || sky_box > INT_MAX / 2)
         FT_FAIL(FT_ERR_ARG, "topk_per_skybox: bad sky box size");
+    if (f1_box < 0)
+        FT_FAIL(FT_ERR_ARG, "topk_per_box: bad f1 box size");
     DeviceGuard g(ctx->device);
     cudaStream_t st = as_stream(stream);
-    const EvalShape sh = ft_default_shape(ctx, band, bank, sky_box);
+    const EvalShape sh = ft_default_shape(ctx, band, bank, sky_box, f1_box);
     const int J = sh.J;
     const long long n_cta = ft_grid_ctas(bank, sh);
     const int lsub_max = std::min(bank->n_sub, (J + bank->sub - 1) / bank->sub + 1);
     const size_t cand_bytes = static_cast<size_t>(n_cta) * lsub_max * k * sizeof(ft_candidate);
-    const long long n_boxes = sky_box > 0 ? (bank->n_sky + sky_box - 1) / sky_box : 1;
+    const long long n_boxes = (sky_box > 0 ? (bank->n_sky + sky_box - 1) / sky_box : 1) *
+                              (f1_box > 0 ? (bank->n_f1 + f1_box - 1) / f1_box : 1);
     const size_t out_bytes = static_cast<size_t>(n_boxes) * bank->n_sub * k * sizeof(ft_candidate);
     void *scr = nullptr;
     FT_TRY(ft_ctx_scratch(ctx, cand_bytes, &scr));
@@ -763,7 +767,7 @@ static int topk_impl(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int 
     p.sub = bank->sub;
     p.lsub_max = lsub_max;
     FT_TRY(ft_launch_eval(band, bank, sh, p, st));
-    FT_TRY(ft_launch_merge(bank, sh, p.cand, k, lsub_max, dout, st, sky_box));
+    FT_TRY(ft_launch_merge(bank, sh, p.cand, k, lsub_max, dout, st, sky_box, f1_box));
     if (!out_on_device) {
         FT_CUDA(cudaMemcpyAsync(out, dout, out_bytes, cudaMemcpyDeviceToHost, st));
         return read_status(ctx, st);
@@ -777,6 +781,35 @@ int ft_topk_per_skybox(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, in
     if (sky_box < 1)
         FT_FAIL(FT_ERR_ARG, "topk_per_skybox: sky_box must be >= 1");
     return topk_impl(ctx, band, bank, k, nullptr, 0.f, out, out_on_device, stream, sky_box);
+}
+
+static int check_gate(const float *gate, float gate_min, const char *who)
+{
+    if (!gate)
+        FT_FAIL(FT_ERR_ARG, std::string(who) + ": null gate");
+    if (std::isnan(gate_min))
+        FT_FAIL(FT_ERR_ARG, std::string(who) + ": gate_min is NaN");
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, gate) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        FT_FAIL(FT_ERR_ARG, std::string(who) + ": gate must be device memory");
+    }
+    return FT_OK;
+}
+
+int ft_topk_per_box(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int sky_box, int f1_box,
+                    int k, const float *gate, float gate_min, ft_candidate *out, int out_on_device,
+                    void *stream)
+{
+    if (!bank)
+        FT_FAIL(FT_ERR_ARG, "topk_per_box: null bank");
+    if (sky_box < 1 || f1_box < 1)
+        FT_FAIL(FT_ERR_ARG, "topk_per_box: sky_box and f1_box must be >= 1");
+    if (gate)
+        FT_TRY(check_gate(gate, gate_min, "topk_per_box"));
+    // a box as wide as the dimension is the whole dimension (one box, the fastest shape)
+    return topk_impl(ctx, band, bank, k, gate, gate_min, out, out_on_device, stream,
+                     sky_box >= bank->n_sky ? 0 : sky_box, f1_box >= bank->n_f1 ? 0 : f1_box);
 }
 
 int ft_bank_sky_order(const ft_bank *bank, int32_t *order)
@@ -799,15 +832,7 @@ int ft_topk_per_band_gated(ft_ctx *ctx, const ft_band *band, const ft_bank *bank
                            const float *gate, float gate_min, ft_candidate *out, int out_on_device,
                            void *stream)
 {
-    if (!gate)
-        FT_FAIL(FT_ERR_ARG, "topk_per_band_gated: null gate");
-    if (std::isnan(gate_min))
-        FT_FAIL(FT_ERR_ARG, "topk_per_band_gated: gate_min is NaN");
-    cudaPointerAttributes at{};
-    if (cudaPointerGetAttributes(&at, gate) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
-        cudaGetLastError();
-        FT_FAIL(FT_ERR_ARG, "topk_per_band_gated: gate must be device memory");
-    }
+    FT_TRY(check_gate(gate, gate_min, "topk_per_band_gated"));
     return topk_impl(ctx, band, bank, k, gate, gate_min, out, out_on_device, stream);
 }
 

@@ -1329,18 +1329,19 @@ constexpr int kMergeThreads = 256;
 
 // One CTA per sub-band b: gathers the per-CTA lists of every evaluation CTA whose f0 tile
 // meets the sub-band and keeps the k best by (s desc, template index asc).
-// Sky groups [g0, g0 + n_skyg) (all f1 groups, the f0 tiles of sub-band b) into out.
+// Sky groups [g0, g0 + n_skyg) x f1 groups [h0, h0 + n_h) (the f0 tiles of sub-band b)
+// into out.
 __device__ __forceinline__ void merge_subband(const ft_candidate *cand, int k, int lsub_max,
-                                              long long g0, long long n_skyg, int n_f1g, int n_f0t,
-                                              int J, int sub, int n_f0, int b, ft_candidate *out)
+                                              long long g0, long long n_skyg, int h0, int n_h,
+                                              int n_f1g, int n_f0t, int J, int sub, int n_f0,
+                                              int b, ft_candidate *out)
 {
     __shared__ ft_candidate wl[kMergeThreads / 32][kKmax];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ft_lo = (b * sub) / J;
     const int ft_hi = (min((b + 1) * sub, n_f0) - 1) / J;
     const int nft = ft_hi - ft_lo + 1;
-    const long long total = n_skyg * n_f1g * static_cast<long long>(nft) * k;
-    const long long sg0 = g0 * n_f1g;  // first combined (sky group, f1 group) index
+    const long long total = n_skyg * n_h * static_cast<long long>(nft) * k;
 
     ft_candidate Lst[kKmax];
     int n = 0;
@@ -1348,7 +1349,9 @@ __device__ __forceinline__ void merge_subband(const ft_candidate *cand, int k, i
         const long long q = c / k;
         const int i = static_cast<int>(c - q * k);
         const int ftl = static_cast<int>(q % nft);
-        const long long sg = sg0 + q / nft;
+        const long long u = q / nft;  // (sky group, f1 group) of the box
+        const long long gi = u / n_h;
+        const long long sg = (g0 + gi) * n_f1g + h0 + (u - gi * n_h);
         const int ft = ft_lo + ftl;
         const long long cta = sg * n_f0t + ft;
         const int lb = b - (ft * J) / sub;
@@ -1447,18 +1450,21 @@ __device__ __forceinline__ void merge_subband(const ft_candidate *cand, int k, i
     }
 }
 
-// Block (b, x): sub-band b of sky box x (sky groups [x gpb, (x + 1) gpb)) into
-// out[(x n_sub + b) k ..].
+// Block (b, x, y): sub-band b of sky box x (sky groups [x gpb, (x + 1) gpb)) and f1 box y
+// (f1 groups [y hpb, (y + 1) hpb)) into out[((x n_f1b + y) n_sub + b) k ..].
 __global__ void __launch_bounds__(kMergeThreads) k_topk_merge(const ft_candidate *cand, int k,
                                                               int lsub_max, long long n_skyg,
-                                                              long long gpb, int n_f1g, int n_f0t,
-                                                              int J, int sub, int n_f0, int n_sub,
-                                                              ft_candidate *out)
+                                                              long long gpb, int n_f1g, int hpb,
+                                                              int n_f0t, int J, int sub, int n_f0,
+                                                              int n_sub, ft_candidate *out)
 {
     const long long g0 = static_cast<long long>(blockIdx.y) * gpb;
     const long long ng = min(gpb, n_skyg - g0);
-    merge_subband(cand, k, lsub_max, g0, ng, n_f1g, n_f0t, J, sub, n_f0, blockIdx.x,
-                  out + static_cast<long long>(blockIdx.y) * n_sub * k);
+    const int h0 = static_cast<int>(blockIdx.z) * hpb;
+    const int nh = min(hpb, n_f1g - h0);
+    const long long box = static_cast<long long>(blockIdx.y) * gridDim.z + blockIdx.z;
+    merge_subband(cand, k, lsub_max, g0, ng, h0, nh, n_f1g, n_f0t, J, sub, n_f0, blockIdx.x,
+                  out + box * n_sub * k);
 }
 
 // Merge for the persistent batch: block i handles sub-band j = i - sub_prefix[b] of band b
@@ -1831,7 +1837,8 @@ long long ft_grid_ctas(const ft_bank *bank, const EvalShape &sh)
     return n_skyg * n_f1g * n_f0t;
 }
 
-EvalShape ft_default_shape(const ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int sky_box)
+EvalShape ft_default_shape(const ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int sky_box,
+                           int f1_box)
 {
     EvalShape sh;
     sh.fast = bank->window_safe;
@@ -1839,11 +1846,19 @@ EvalShape ft_default_shape(const ft_ctx *ctx, const ft_band *band, const ft_bank
         // up to kFastMaxWarps evaluating warps: the f1 values of one group for P sky
         // points that share the shared-memory rows
         ft_sky_grouping(bank, kFastMaxWarps, &sh.P, &sh.F1);
+        if (f1_box > 0 && f1_box % sh.F1 != 0) {
+            while (f1_box % sh.F1 != 0)
+                --sh.F1;
+            sh.P = static_cast<int>(std::min<long long>(
+                std::min(kMaxSkyGroup, kFastMaxWarps / sh.F1), bank->n_sky));
+        }
         while (sky_box > 0 && sky_box % sh.P != 0)
             --sh.P;
     } else {
         const int groups = (bank->n_f1 + 31) / 32;
         sh.F1 = (bank->n_f1 + groups - 1) / groups;
+        while (f1_box > 0 && f1_box % sh.F1 != 0)
+            --sh.F1;
         sh.P = 1;
     }
     sh.F = sh.P * sh.F1;
@@ -1951,7 +1966,7 @@ int ft_launch_eval(const ft_band *band, const ft_bank *bank, const EvalShape &sh
 }
 
 int ft_launch_merge(const ft_bank *bank, const EvalShape &sh, const FtCand *cand, int k,
-                    int lsub_max, ft_candidate *out, cudaStream_t st, int sky_box)
+                    int lsub_max, ft_candidate *out, cudaStream_t st, int sky_box, int f1_box)
 {
     const int n_f0t = (bank->n_f0 + sh.J - 1) / sh.J;
     const int n_f1g = (bank->n_f1 + sh.F1 - 1) / sh.F1;
@@ -1962,9 +1977,17 @@ int ft_launch_merge(const ft_bank *bank, const EvalShape &sh, const FtCand *cand
     const long long n_boxes = (n_skyg + gpb - 1) / gpb;
     if (n_boxes > 65535)
         FT_FAIL(FT_ERR_RANGE, "merge: more than 65535 sky boxes");
-    k_topk_merge<<<dim3(static_cast<unsigned>(bank->n_sub), static_cast<unsigned>(n_boxes)), kMergeThreads, 0,
-                   st>>>(reinterpret_cast<const ft_candidate *>(cand), k, lsub_max, n_skyg, gpb, n_f1g, n_f0t,
-                         sh.J, bank->sub, bank->n_f0, bank->n_sub, out);
+    if (f1_box > 0 && f1_box % sh.F1 != 0)
+        FT_FAIL(FT_ERR_ARG, "merge: f1 box not a multiple of the f1 group size");
+    const int hpb = f1_box > 0 ? f1_box / sh.F1 : n_f1g;
+    const int n_f1b = (n_f1g + hpb - 1) / hpb;
+    if (n_f1b > 65535)
+        FT_FAIL(FT_ERR_RANGE, "merge: more than 65535 f1 boxes");
+    k_topk_merge<<<dim3(static_cast<unsigned>(bank->n_sub), static_cast<unsigned>(n_boxes),
+                        static_cast<unsigned>(n_f1b)),
+                   kMergeThreads, 0, st>>>(reinterpret_cast<const ft_candidate *>(cand), k, lsub_max,
+                                           n_skyg, gpb, n_f1g, hpb, n_f0t, sh.J, bank->sub,
+                                           bank->n_f0, bank->n_sub, out);
     FT_CUDA(cudaGetLastError());
     return FT_OK;
 }

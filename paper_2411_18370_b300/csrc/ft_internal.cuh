@@ -251,14 +251,18 @@ long long ft_grid_ctas(const ft_bank *bank, const EvalShape &sh);
 
 size_t ft_eval_smem_bytes(const ft_band *band, const EvalShape &sh, int k);
 // sky_box > 0: the sky group size P is reduced to a divisor of sky_box, so that no CTA's sky
-// points straddle two sky boxes (runs of sky_box points of the bank's sky order)
-EvalShape ft_default_shape(const ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int sky_box = 0);
+// points straddle two sky boxes (runs of sky_box points of the bank's sky order); f1_box > 0:
+// likewise the f1 group size F1 to a divisor of f1_box (runs of f1_box values of the f1 list)
+EvalShape ft_default_shape(const ft_ctx *ctx, const ft_band *band, const ft_bank *bank, int sky_box = 0,
+                           int f1_box = 0);
 int ft_launch_eval(const ft_band *band, const ft_bank *bank, const EvalShape &sh, EvalParams p,
                    cudaStream_t st);
-// Merge of the per-CTA lists: per sub-band (sky_box = 0), or per (sky box, sub-band) into
-// out [n_sky_boxes][n_sub][k] (sky_box a multiple of sh.P).
+// Merge of the per-CTA lists: per sub-band (sky_box = f1_box = 0), or per (sky box, f1 box,
+// sub-band) into out [n_sky_boxes][n_f1_boxes][n_sub][k] (sky_box a multiple of sh.P, f1_box
+// of sh.F1; 0 = one box over that dimension).
 int ft_launch_merge(const ft_bank *bank, const EvalShape &sh, const FtCand *cand, int k,
-                    int lsub_max, ft_candidate *out, cudaStream_t st, int sky_box = 0);
+                    int lsub_max, ft_candidate *out, cudaStream_t st, int sky_box = 0,
+                    int f1_box = 0);
 int ft_launch_convert(const void *src, int src_dtype, long long src_stride, void *dst,
                       int dst_dtype, long long N, int W, int Wp, unsigned int *status,
                       cudaStream_t st);
