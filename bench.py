@@ -383,7 +383,7 @@ def run_binary(args):
                    "n_sft": sfts.n_total, "n_templates": bank.n_templates, "n_boxes": bank.n_boxes,
                    "evals_per_step": evals, "storage": args.dtype,
                    "track_bins": "canonical split rule: exact integer f0 T, 64-bit fixed-point orbit "
-                                 "phase, FP32 Taylor cosine and sub-bin terms",
+                                 "phase, FP32 quarter-wave cosine table and sub-bin terms",
                    "l2": "flushed between timed steps (256 MB write, outside the per-step events)"},
         "roofline": {"bound": "alu", "kernel": "k_bt_eval (per-template track, gather, per-box top-k)",
                      "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Top/s",

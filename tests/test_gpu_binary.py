@@ -8,7 +8,8 @@
   the CPU selection over the GPU's own values;
 * ragged shapes: boxes that are not a multiple of the CTA, SFT counts that are not a multiple
   of a stage, a single template, isolated sources (a_p = 0), k above the box population;
-* the number count along binary tracks (exact) and the count-gated per-box selection.
+* the number count along binary tracks (exact) and the count-gated per-box selection;
+* the benchmark's full-size workload in its timed launch, on sampled templates.
 """
 import math
 
@@ -313,3 +314,27 @@ def test_sky_weighted_number_count(ctx):
     sig = sig_pow / 2.0 * math.sqrt(p * (1 - p))  # sig_pow = 2 sqrt(sum w^2)
     z_or = (s_or - p) / sig
     assert np.all(np.abs(z - z_or) <= 2e-6 * np.maximum(s_or, 1e-3) / sig + 1e-5)
+
+
+def test_full_workload_sampled(ctx):
+    """The benchmark's binary workload (2^20 templates in 32 boxes, 21 657 SFTs, FP16
+    storage) in the launch it times (loudest per box, k = 1): the selection is exactly the CPU
+    selection over the GPU's s of every template; s and the out-of-window counts of 192
+    sampled templates and of every box winner match the oracle."""
+    sfts, bank = ftsynth.binary_workload()
+    band = H.band_from(ctx, sfts, dtype="f16", power_f32=True, on_device=True)
+    gb = _gpu_bank(ctx, band, bank)
+    out = np.zeros((bank.n_boxes, 1), dtype=ft.CANDIDATE_DTYPE)
+    ft.binary_topk_per_box(ctx, band, gb, 1, out)
+    n = bank.n_templates
+    s = np.empty(n, np.float32)
+    o = np.empty(n, np.int32)
+    ft.binary_eval(ctx, band, gb, 0, n, s, None, o)
+    c_idx, c_val = oracle.topk_per_box(s.astype(np.float64), bank.n_per_box, bank.n_boxes, 1)
+    assert np.array_equal(out["template_idx"], c_idx)
+    assert np.array_equal(out["s"].astype(np.float64), c_val)
+    samp = np.concatenate([np.random.default_rng(12).choice(n, 192, replace=False),
+                           out["template_idx"][:, 0]]).astype(np.int64)
+    s_or, o_or = oracle.binary_statistic(_stored(sfts, "f16"), bank, samp)
+    assert np.array_equal(o[samp], o_or)
+    assert np.all(np.abs(s[samp] - s_or) <= REL * np.abs(s_or))
