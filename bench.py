@@ -242,14 +242,21 @@ def run_batch(args):
     n_sft = [len(st) for st in starts]
     N = len(t_mid)
     specs = ftsynth.batch_bands(64, args.sky_scale)
-    bands, banks, evals = [], [], 0
-    for b, sp in enumerate(specs):
+
+    def band_power(b):
+        """(power [N, W] on the device, first bin) of band b: chi^2_2 with a seeded generator."""
+        sp = specs[b]
         wl, wh = ftsynth.wings_for(sp["f_hi"], -1e-9, n_slots * T, T)
-        W = sp["n_bins"] + wl + wh
         g = torch.Generator(device="cuda")
         g.manual_seed(ftsynth.derive_seed(3, 1000 + b) & ((1 << 63) - 1))
-        P = torch.empty((N, W), dtype=torch.float32, device="cuda").exponential_(0.5, generator=g)
-        band = ft.load_sfts(ctx, P, t_mid, v, n_sft, sp["k_band"] - wl, T, 0.0, dtype=args.dtype)
+        P = torch.empty((N, sp["n_bins"] + wl + wh), dtype=torch.float32,
+                        device="cuda").exponential_(0.5, generator=g)
+        return P, sp["k_band"] - wl
+
+    bands, banks, evals = [], [], 0
+    for b, sp in enumerate(specs):
+        P, k_lo = band_power(b)
+        band = ft.load_sfts(ctx, P, t_mid, v, n_sft, k_lo, T, 0.0, dtype=args.dtype)
         del P
         sky = ftsynth.fibonacci_sky(sp["n_sky"])
         bank = ft.make_bank(ctx, band, sp["k_band"], sp["n_bins"], ftsynth.f1_grid(10, -1e-9, 0.0),
@@ -286,6 +293,9 @@ def run_batch(args):
     ref = np.concatenate([ft.decode_candidates(c, b.n_subbands, k)[0] for c, b in zip(cands, banks)])
     differ = int(np.sum(np.any(np.sort(got, 1) != np.sort(ref, 1), axis=1)))
     mb, ml = statistics.mean(t_batch), statistics.mean(t_loop)
+    esize = ESIZE[args.dtype]
+    achieved_gbs = evals * esize / (mb / 1e3) / 1e9
+    peak_max_clk = 148 * SMEM_BYTES_PER_CLK_PER_SM * 2032e6 / 1e9
     line = {
         "metric": METRIC, "value": evals / (mb / 1e3), "unit": UNIT, "n_gpus": 1,
         "steps": steps, "warmup": args.warmup, "ms_per_step": mb, "higher_is_better": True,
@@ -303,8 +313,32 @@ def run_batch(args):
         "speedup_vs_loop": ml / mb, "subbands_with_different_sets": differ,
         "measured_gather_roof": {"evals_per_s": roof_e, "frac": (evals / (mb / 1e3)) / roof_e,
                                  "entry": "ft_gather_roof", "storage": args.dtype},
+        # the timed step is the persistent evaluation plus its merge (under 0.1 % of the step)
+        "roofline": {"bound": "smem", "kernel": "k_eval_batched (all bands, fused top-k epilogue)",
+                     "achieved": achieved_gbs, "peak": peak_max_clk, "unit": "GB/s",
+                     "frac": achieved_gbs / peak_max_clk,
+                     "peak_basis": "derived: 148 SMs x 128 B/clk shared-memory load bandwidth x "
+                                   "2032 MHz max SM clock",
+                     "algorithmic_bytes_per_launch": evals * esize, "bytes_per_eval": esize,
+                     "traffic": None},
+        "gpu_launches": 2 * steps,
         "clocks": clk.summary(),
     }
+    if not args.no_cpu_baseline:
+        # the oracle on a template sample of the middle band (its power copied to the host)
+        b = len(specs) // 2
+        sp = specs[b]
+        P, k_lo = band_power(b)
+        sfts_b = ftsynth.SFTSet(power=P.double().cpu().numpy(), t_mid=t_mid, v=v, s_n=np.ones(N),
+                                n_sft=n_sft, k_lo=k_lo, t_sft=T, t0=0.0)
+        del P
+        bank_b = ftsynth.Bank(k0=sp["k_band"], n_f0=sp["n_bins"], f1=ftsynth.f1_grid(10, -1e-9, 0.0),
+                              sky=ftsynth.fibonacci_sky(sp["n_sky"]), subband_bins=18)
+        cb, _, _ = cpu_baseline(sfts_b, bank_b, args.cpu_seconds)
+        cb.pop("seconds")
+        cb["sample"] = (f"band {b} of the batch ({sp['n_bins']} f0 bins x 10 f1 x {sp['n_sky']} sky "
+                        f"points): " + cb["sample"])
+        line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)
     return 0
 
