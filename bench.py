@@ -344,10 +344,10 @@ def run_batch(args):
 
 
 # per (template, SFT) operations of the binary track's canonical rule: orbit phase (64-bit
-# multiply, subtract, shift: 3), the table cosine (quadrant, mirror 2, index, fraction 3,
-# table read, interpolation, sign: 10), v.n (3), the two products (2), X (2), the bin (4),
-# bounds + gather + add (3)
-BT_OPS_PER_EVAL = 27
+# multiply, subtract, shift: 3), the table cosine (index, fraction 3, table read,
+# interpolation: 6), v.n (3), the two products (2), X (2), the bin (4), bounds + gather +
+# add (3)
+BT_OPS_PER_EVAL = 23
 ISSUE_LANES_PER_CLK_PER_SM = 128
 
 
@@ -417,7 +417,7 @@ def run_binary(args):
                    "n_sft": sfts.n_total, "n_templates": bank.n_templates, "n_boxes": bank.n_boxes,
                    "evals_per_step": evals, "storage": args.dtype,
                    "track_bins": "canonical split rule: exact integer f0 T, 64-bit fixed-point orbit "
-                                 "phase, FP32 quarter-wave cosine table and sub-bin terms",
+                                 "phase, FP32 full-turn cosine table and sub-bin terms",
                    "l2": "flushed between timed steps (256 MB write, outside the per-step events)"},
         "roofline": {"bound": "alu", "kernel": "k_bt_eval (per-template track, gather, per-box top-k)",
                      "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Top/s",

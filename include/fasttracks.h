@@ -367,10 +367,10 @@ FT_API int ft_pdet_q(ft_ctx *ctx, const ft_band *band, const double *det_tensor,
  *     n = (cos delta cos alpha, cos delta sin alpha, sin delta) in FP32; D = FP32(F a_p Omega);
  *     orbit frequency nu = Omega / 2 pi as round(nu 2^54) and phase phi_b as phi_b 2^64;
  *   - per SFT: t_q = round((t_mid - t0) 2^10); orbit phase theta = top 32 bits of
- *     (nu_q t_q - psi_q) mod 2^64; its cosine by linear interpolation in a quarter-wave table
- *     (1024 intervals; entries cos(i pi / 2048) from the host's libm rounded to FP32, FP32
- *     differences; odd quadrants mirrored, quadrants 1 and 2 negated); X = (phi + F (v.n)) -
- *     D cos in FP32; bin = K + floor(X + 1/2).  The sky vector's cos / sin of alpha use the
+ *     (nu_q t_q - psi_q) mod 2^64; its cosine by linear interpolation in a full-turn table
+ *     (1024 intervals; entries cos(i 2 pi / 1024) from the host's libm rounded to FP32, FP32
+ *     differences; interval theta >> 22 at fraction (theta mod 2^22) 2^-22); X = (phi +
+ *     F (v.n)) - D cos in FP32; bin = K + floor(X + 1/2).  The sky vector's cos / sin of alpha use the
  *     same table.
  *   Bins outside the band contribute 0 and are counted, as for the isolated bank.
  */
@@ -389,7 +389,8 @@ typedef struct {
 
 /* Set up a binary bank for `band` (uses its SFT times, velocities and weights: the per-SFT
  * weights, or, when ft_band_set_sky_weights was called before, the all-sky weights
- * (a^2 + b^2)/S_n of each template's own sky direction, normalised per template; then s =
+ * (a^2 + b^2)/S_n of each template's own sky direction (to FP32 accuracy; the track's
+ * table cosine serves only the bin), normalised per template; then s =
  * sum r P / sum r and z uses mu_G = m and sigma_G = d sqrt(sum r^2) / sum r, with one SFT's
  * noise mean m and deviation d: 2 and 2 for normalised power, p and sqrt(p (1 - p)) for a
  * number-count band).  Errors: FT_ERR_ARG (ranges, counts), FT_ERR_OOM. */

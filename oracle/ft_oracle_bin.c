@@ -21,7 +21,7 @@
  *     the sky vector and the orbit amplitude D = F a_p Omega in FP32; the orbit frequency and
  *     phase as 64-bit fixed point (turns);
  *   - per SFT: the orbit phase of (t_mid - t0) in exact 64-bit integer arithmetic, its cosine
- *     by linear interpolation in a quarter-wave table of 1024 intervals (entries: libm's
+ *     by linear interpolation in a full-turn table of 1024 intervals (entries: libm's
  *     cos rounded to FP32, differences in FP32), and
  *         X = (phi + F v.n) - D cos,  bin = K + floor(X + 1/2)   (FP32, operations as written).
  *   or_bt_bins also returns the FP64 bin of Eq. (track) with libm's cos and its distance from
@@ -137,7 +137,7 @@ void or_bt_lambda(const or_bdesc *b, int64_t i, double lam[6])
         lam[2] = -1.0;
 }
 
-/* quarter-wave table: C[i] = cos(i (pi/2) / 1024) (libm, FP64, rounded to FP32), D[i] =
+/* full-turn table: C[i] = cos(i 2 pi / 1024) (libm, FP64, rounded to FP32), D[i] =
  * C[i+1] - C[i] in FP32, D[1024] = 0 */
 static float tab_c[1025], tab_d[1025];
 static int tab_ready;
@@ -147,27 +147,21 @@ void or_bt_init(void)
     if (tab_ready)
         return;
     for (int i = 0; i <= 1024; i++)
-        tab_c[i] = (float)cos((double)i * 1.5339807878856412e-03);
+        tab_c[i] = (float)cos((double)i * 6.135923151542565e-03);
     for (int i = 0; i < 1024; i++)
         tab_d[i] = tab_c[i + 1] - tab_c[i];
     tab_d[1024] = 0.0f;
     tab_ready = 1;
 }
 
-/* cos(2 pi theta / 2^32): quadrant q = theta >> 30, position u within it (mirrored in odd
- * quadrants), linear interpolation between table entries u >> 20 and the next, negative in
- * quadrants 1 and 2 */
+/* cos(2 pi theta / 2^32): the turn theta / 2^32 falls in table interval theta >> 22 at
+ * fraction (theta mod 2^22) / 2^22; linear interpolation between that entry and the next */
 float or_cos_q32(uint32_t theta)
 {
     or_bt_init();
-    uint32_t q = theta >> 30;
-    uint32_t u = theta & 0x3FFFFFFFu;
-    if (q & 1u)
-        u = 0x40000000u - u;
-    uint32_t i = u >> 20;
-    float f = (float)(u & 0xFFFFFu) * 0x1p-20f;
-    float c = fmaf(f, tab_d[i], tab_c[i]);
-    return (q == 1u || q == 2u) ? -c : c;
+    uint32_t i = theta >> 22;
+    float f = (float)(theta & 0x3FFFFFu) * 0x1p-22f;
+    return fmaf(f, tab_d[i], tab_c[i]);
 }
 
 void or_bt_derived(const double lam[6], double t_sft, int64_t k_lo, or_bder *o)

@@ -28,7 +28,7 @@ struct ft_binary_bank {
     int n_pad = 0;                 // rows of d_rowv / d_tq (N rounded up to kBtRowPad)
     float4 *d_rowv = nullptr;      // [n_pad] (v/c as FP32, weight); zero beyond N
     long long *d_tq = nullptr;     // [n_pad] round((t_mid - t0) 2^10)
-    float2 *d_costab = nullptr;    // [kBtTab + 1] quarter-wave cosine table (value, difference)
+    float2 *d_costab = nullptr;    // [kBtTab + 1] full-turn cosine table (value, difference)
     // all-sky weights (band with detector tensors): per SFT D / sqrt(S_n) in FP32 as
     // (D00, D01, D02, D11), (D12, D22, |D|^2, tr D); zero beyond N
     float4 *d_rowd = nullptr;      // [n_pad][2]
@@ -40,7 +40,7 @@ constexpr int kBtThreads = 256;              // templates per CTA
 constexpr int kBtTPT = 2;                    // templates per thread (they share each row's records)
 constexpr int kBtBlock = kBtThreads / kBtTPT;  // threads per CTA
 constexpr int kBtRowPad = 64;
-constexpr int kBtTab = 1024;  // intervals of the quarter-wave cosine table
+constexpr int kBtTab = 1024;  // intervals of the full-turn cosine table
 
 struct BtParams {
     double xlo[6], step[6];
@@ -135,24 +135,19 @@ __device__ void bt_lambda(const BtParams &p, long long i, double lam[6])
     lam[2] = fmin(fmax(lam[2], -1.0), 1.0);
 }
 
-// cos(2 pi theta / 2^32): quadrant q = theta >> 30, position u within it (mirrored in odd
-// quadrants), linear interpolation between entries u >> 20 and the next of the quarter-wave
-// table, negative in quadrants 1 and 2
+// cos(2 pi theta / 2^32): linear interpolation between entry theta >> 22 of the full-turn
+// table and the next, at the fraction given by the low 22 bits
 __device__ __forceinline__ float bt_cos_q32(unsigned theta, const float2 *tab)
 {
-    const unsigned q = theta >> 30;
-    unsigned u = theta & 0x3FFFFFFFu;
-    if (q & 1u)
-        u = 0x40000000u - u;
-    const float f = __fmul_rn(__uint2float_rn(u & 0xFFFFFu), 0x1p-20f);
-    const float2 e = tab[u >> 20];
-    const float c = __fmaf_rn(f, e.y, e.x);
-    return (q == 1u || q == 2u) ? -c : c;
+    const float f = __fmul_rn(__uint2float_rn(theta & 0x3FFFFFu), 0x1p-22f);
+    const float2 e = tab[theta >> 22];
+    return __fmaf_rn(f, e.y, e.x);
 }
 
 struct BtTmpl {
     int K;
     float phi, F, nx, ny, nz, D;
+    float wx, wy;  // the sky vector's x and y to FP32 accuracy, for the all-sky weights
     unsigned long long nu_q, psi_q;
 };
 
@@ -168,6 +163,12 @@ __device__ void bt_derive(const BtParams &p, const double lam[6], const float2 *
     const unsigned ta = __double2uint_rz(__dmul_rn(lam[1], 4294967296.0));
     t.nx = __fmul_rn(cd, bt_cos_q32(ta, tab));
     t.ny = __fmul_rn(cd, bt_cos_q32(ta - 0x40000000u, tab));
+    // the weights follow the template's true direction, not the track's table cosine
+    double sa, ca;
+    sincospi(__dmul_rn(2.0, lam[1]), &sa, &ca);
+    const double cd64 = sqrt(c2 > 0.0 ? c2 : 0.0);
+    t.wx = __double2float_rn(cd64 * ca);
+    t.wy = __double2float_rn(cd64 * sa);
     t.nz = __double2float_rn(lam[2]);
     t.D = __double2float_rn(__dmul_rn(__dmul_rn(F, lam[3]), lam[4]));
     const double nu = __ddiv_rn(lam[4], 6.283185307179586);
@@ -341,7 +342,7 @@ __global__ void __launch_bounds__(kBtBlock) k_bt_eval(const BtParams p)
                     const float val = in ? bt_load<T>(row, k) : 0.f;
                     oob[u] += in ? 0 : 1;
                     if (SKY) {
-                        const float rw = bt_sky_r(sd[b][2 * r], sd[b][2 * r + 1], t[u].nx, t[u].ny, t[u].nz);
+                        const float rw = bt_sky_r(sd[b][2 * r], sd[b][2 * r + 1], t[u].wx, t[u].wy, t[u].nz);
                         part[u] = __fmaf_rn(rw, val, part[u]);
                         partB[u] = __fadd_rn(partB[u], rw);
                         partC[u] = __fmaf_rn(rw, rw, partC[u]);
@@ -804,11 +805,11 @@ int ft_make_binary_bank(ft_ctx *ctx, const ft_band *band, const ft_binary_bank_d
         ft_binary_bank_destroy(b);
         return rc;
     };
-    // quarter-wave cosine table: cos(i (pi/2) / 1024) from the host's libm in FP64, rounded
+    // full-turn cosine table: cos(i 2 pi / 1024) from the host's libm in FP64, rounded
     // to FP32, with the FP32 difference to the next entry (0 after the last)
     float tc[kBtTab + 1];
     for (int i = 0; i <= kBtTab; ++i)
-        tc[i] = static_cast<float>(std::cos(static_cast<double>(i) * 1.5339807878856412e-03));
+        tc[i] = static_cast<float>(std::cos(static_cast<double>(i) * 6.135923151542565e-03));
     std::vector<float2> tab(kBtTab + 1);
     for (int i = 0; i <= kBtTab; ++i)
         tab[i] = make_float2(tc[i], i < kBtTab ? tc[i + 1] - tc[i] : 0.0f);

@@ -1,15 +1,17 @@
 """Pins of the oracle's binary-orbit track (Eq. (track)) and random hyperbox bank
 (Eq. (xi_of_lambda), App. A Eq. (unif_transform), Sec. IV.B):
 
-* the canonical cosine of a 32-bit phase (linear interpolation in a quarter-wave table of
-  1024 intervals) is within the interpolation bound (pi/2048)^2 / 8 = 2.9e-7 plus FP32
-  rounding of libm's cos, and exact at the table's nodes;
+* the canonical cosine of a 32-bit phase (linear interpolation in a full-turn table of 1024
+  intervals) is within the interpolation bound (2 pi/1024)^2 / 8 = 4.7e-6 plus FP32 rounding
+  of libm's cos, and exact at the table's nodes;
 * every template lies in its own box and is uniform in the uniform coordinates
   xi = {f0^6, alpha, sin(delta), a_p^3, Omega^4, phi_b} there (mean 1/2, variance 1/12 of the
   position within the box along each axis);
 * the fixed-point orbit phase equals (Omega t - phi_b) / 2 pi mod 1 to 1e-8 turns;
 * the canonical FP32 bin equals the FP64 bin of Eq. (track) (libm cos) wherever the track is
-  more than 1e-4 bins from the rounding boundary, and such cases are rare;
+  more than 5e-4 bins from the rounding boundary, and such cases are rare (the cosine's
+  error, under 4.9e-6, times the orbit amplitude, under 28 bins here, and times F (|v_x| +
+  |v_y|) in the sky vector, under 27 bins, plus FP32 rounding: about 2.8e-4 at most);
 * with a_p = 0 and no detector motion the bin is round(f0 T_SFT) (zero-Doppler tracks collapse
   to fixed bins);
 * the statistic equals a Python sum over SFTs along the canonical bins, and a noise-free track
@@ -54,14 +56,14 @@ def test_canonical_cosine():
                                   np.uint64)])
     c = oracle.cos_q32(th).astype(np.float64)
     ref = np.cos(2 * np.pi * th.astype(np.float64) / 2 ** 32)
-    bound = (np.pi / 2048) ** 2 / 8 + 1.2e-7
+    bound = (2 * np.pi / 1024) ** 2 / 8 + 1.2e-7
     assert np.max(np.abs(c - ref)) < bound
     s = oracle.cos_q32((th - (1 << 30)) % 2 ** 32).astype(np.float64)
     assert np.max(np.abs(s - np.sin(2 * np.pi * th.astype(np.float64) / 2 ** 32))) < bound
     assert oracle.cos_q32([0])[0] == 1.0
-    # nodes: the FP32 rounding of cos at multiples of (pi/2) / 1024, in every quadrant
-    nodes = np.arange(0, 4096, dtype=np.uint64) << np.uint64(20)
-    want = np.cos(np.arange(4096) * (np.pi / 2048)).astype(np.float32)
+    # nodes: the FP32 rounding of cos at multiples of 2 pi / 1024, exactly
+    nodes = np.arange(0, 1024, dtype=np.uint64) << np.uint64(22)
+    want = np.cos(np.arange(1024) * (2 * np.pi / 1024)).astype(np.float32)
     got = oracle.cos_q32(nodes)
     assert np.max(np.abs(got.astype(np.float64) - want.astype(np.float64))) < 1.2e-7
 
@@ -115,7 +117,7 @@ def test_canonical_bins_match_the_fp64_track():
     sfts = _sfts()
     b, b64, dist = oracle.binary_bins(sfts, bank, np.arange(bank.n_templates), with_fp64=True)
     differ = b != b64
-    assert np.all(dist[differ] < 1e-4)
+    assert np.all(dist[differ] < 5e-4)
     assert differ.mean() < 1e-3
     # the orbit really moves the track: several bins of spread within each template
     assert np.median(b.max(axis=1) - b.min(axis=1)) > 20
@@ -158,7 +160,7 @@ def test_statistic_brute_force_and_noise_free_track():
     sx = ftsynth.SFTSet(**{**sfts.__dict__, "power": P})
     s3, o3 = oracle.binary_statistic(sx, bank, [3])
     assert o3[0] == 0
-    assert s3[0] >= sfts.n_total - np.sum(dist[0] < 1e-4)
+    assert s3[0] >= sfts.n_total - np.sum(dist[0] < 5e-4)
 
 
 def test_topk_per_box():

@@ -56,8 +56,10 @@ MUTATIONS_BIN = {
     "doppler_dropped": ("float dop = d->F * vn;", "float dop = 0.0f * vn;"),
     "orbit_phase_sign": ("uint64_t ph = d->nu_q * (uint64_t)tq - d->psi_q;",
                          "uint64_t ph = d->nu_q * (uint64_t)tq + d->psi_q;"),
-    "cos_quadrant_sign": ("return (q == 1u || q == 2u) ? -c : c;", "return (q == 1u) ? -c : c;"),
-    "cos_no_interpolation": ("float c = fmaf(f, tab_d[i], tab_c[i]);", "float c = tab_c[i] + 0.0f * f;"),
+    "cos_half_turn_table": ("tab_c[i] = (float)cos((double)i * 6.135923151542565e-03);",
+                            "tab_c[i] = (float)cos((double)i * 3.0679615757712823e-03);"),
+    "cos_no_interpolation": ("return fmaf(f, tab_d[i], tab_c[i]);", "return tab_c[i] + 0.0f * f;"),
+    "cos_wrong_interval": ("uint32_t i = theta >> 22;", "uint32_t i = (theta >> 22) ^ 1u;"),
     "box_order_reversed": ("for (int d = 5; d >= 0; d--) {", "for (int d = 0; d < 6; d++) {"),
     "ap_root_wrong": ("case 3: return cbrt_newton(xi, b->hi[3]);", "case 3: return sqrt(xi);"),
     "amplitude_without_omega": ("o->D = (float)((F * lam[3]) * lam[4]);", "o->D = (float)(F * lam[3]);"),
