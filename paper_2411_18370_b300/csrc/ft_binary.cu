@@ -36,8 +36,8 @@ struct ft_binary_bank {
 
 namespace {
 
-constexpr int kBtThreads = 256;              // templates per CTA
-constexpr int kBtTPT = 2;                    // templates per thread (they share each row's records)
+constexpr int kBtThreads = 512;              // templates per CTA
+constexpr int kBtTPT = 4;                    // templates per thread (they share each row's records)
 constexpr int kBtBlock = kBtThreads / kBtTPT;  // threads per CTA
 constexpr int kBtRowPad = 64;
 constexpr int kBtTab = 1024;  // intervals of the full-turn cosine table

@@ -145,7 +145,7 @@ def _check_topk(ctx, band, gb, sfts_stored, bank, k):
 @pytest.mark.parametrize("dtype", ["f32", "f16"])
 def test_topk_per_box(ctx, dtype):
     sfts = _sfts(seed=9)
-    bank = _bank(seed=10, n_per_box=300)   # 2 tiles per box, the second ragged
+    bank = _bank(seed=10, n_per_box=700)   # 2 tiles of 512 per box, the second ragged
     band = H.band_from(ctx, sfts, dtype=dtype, power_f32=True)
     gb = _gpu_bank(ctx, band, bank)
     for k in (1, 5):
@@ -155,6 +155,7 @@ def test_topk_per_box(ctx, dtype):
 @pytest.mark.parametrize("shape", [
     dict(n_sft=(5,), n_div=(1, 1, 1, 1, 1, 1), n_per_box=1, k=3),
     dict(n_sft=(70, 1), n_div=(1, 2, 1, 1, 1, 3), n_per_box=257, k=2),
+    dict(n_sft=(40, 9), n_div=(1, 1, 1, 1, 1, 2), n_per_box=1537, k=4),
     dict(n_sft=(33, 31), n_div=(3, 1, 1, 1, 1, 1), n_per_box=20, k=32, ap=(0.0, 0.0)),
 ])
 def test_edge_shapes(ctx, shape):
