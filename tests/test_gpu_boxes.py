@@ -107,3 +107,44 @@ def test_box_arguments(ctx):
     # a gate nobody passes leaves every slot empty
     ft.topk_per_box(ctx, band, bk, 1, 1, K, out, gate=gate, gate_min=1.0)
     assert np.all(out["template_idx"] == -1) and np.all(np.isneginf(out["s"]))
+
+
+def test_full_bank_boxes(ctx, search_cfg):
+    """The full search-shaped bank (3.6e7 templates, 24 419 SFTs) in boxes of 100 sky points x
+    5 f1 values x one 0.01 Hz sub-band, plain and gated: the CPU selection over the GPU's s of
+    every template (from the default launch shape, whose stage lengths may differ from the
+    box launch's, so sets may differ only at near-ties and values by FP32 rounding), and every
+    candidate's s against the oracle."""
+    from tests.test_gpu_parity import assert_s_close
+
+    sfts, bank = search_cfg
+    band = H.band_from(ctx, sfts, power_f32=True)
+    bk = H.bank_from(ctx, band, bank)
+    n = bank.n_templates
+    s_d = torch.empty(n, dtype=torch.float32, device="cuda")
+    ft.eval_statistic(ctx, band, bk, s_d)
+    s = s_d.cpu().numpy().astype(np.float64)
+    del s_d
+    order = ft.bank_sky_order(bk, bank.n_sky)
+    sky_box, f1_box = 100, 5
+    n_skyb, n_f1b = -(-bank.n_sky // sky_box), -(-bank.n_f1 // f1_box)
+    n_keys = n_skyb * n_f1b * bank.n_subbands
+    key = _keys(bank, order, sky_box, f1_box)
+    gate = np.random.default_rng(5).uniform(0, 1, n).astype(np.float32)
+    gate_d = torch.from_numpy(gate).cuda()
+    for g in (None, gate_d):
+        out = np.zeros((n_skyb, n_f1b, bank.n_subbands, K), dtype=ft.CANDIDATE_DTYPE)
+        ft.topk_per_box(ctx, band, bk, sky_box, f1_box, K, out, gate=g, gate_min=0.5)
+        idx = out["template_idx"].reshape(n_keys, K)
+        val = out["s"].reshape(n_keys, K)
+        t = np.arange(n) if g is None else np.nonzero(gate >= np.float32(0.5))[0]
+        c_idx, c_val = oracle.topk_per_key(s[t], key[t], n_keys, K + 1, t)
+        for bx in range(n_keys):
+            if set(idx[bx].tolist()) != set(c_idx[bx, :K].tolist()):
+                kth, nxt = c_val[bx, K - 1], c_val[bx, K]
+                assert abs(kth - nxt) < 2e-6 * abs(kth), f"box {bx}"
+        flat = idx.ravel()
+        assert np.all(flat >= 0)
+        assert np.all(np.abs(val.ravel() - s[flat]) <= 2e-6 * np.abs(s[flat]))
+        s_or, _ = oracle.statistic(sfts, bank, flat)
+        assert_s_close(val.ravel(), s_or)
