@@ -1,13 +1,13 @@
 // ft_binary.cu -- the binary-orbit track (Eq. (track) with the orbit term) over a random
 // template bank in uniform coordinates (Sec. IV.A, App. A), cut into hyperboxes (Sec. IV.B).
 //
-// Templates are never stored: every thread derives its templates (two, sharing each row's
-// records) from Philox counters and keeps the per-template terms of the canonical bin rule
-// in registers.  Each CTA evaluates up to kBtThreads templates of one box over all SFTs; stages of S SFT rows (power row,
-// FP32 velocity + weight, fixed-point time) are brought into shared memory by bulk copies on
-// two mbarrier-tracked buffers.  Per (template, SFT) the work is integer phase arithmetic, a
-// short FP32 polynomial, the bin, one shared-memory read and one add: the kernel is bound by
-// instruction issue, not by memory.  Every floating-point operation of the rule is an
+// Templates are never stored: every thread derives its templates (kBtTPT of them, sharing
+// each row's records) from Philox counters and keeps the per-template terms of the canonical
+// bin rule in registers.  Each CTA evaluates up to kBtThreads templates of one box over all
+// SFTs; stages of S SFT rows (power row, FP32 velocity + weight, fixed-point time) are brought
+// into shared memory by bulk copies on two mbarrier-tracked buffers.  Per (template, SFT) the
+// work is integer phase arithmetic, a table cosine, the bin, one shared-memory read and one
+// add: the kernel is bound by instruction issue and shared-memory reads, not by HBM.  Every floating-point operation of the rule is an
 // explicit round-to-nearest intrinsic so that the compiler cannot contract or reorder it.
 
 #include "ft_internal.cuh"
@@ -678,7 +678,7 @@ BtParams base_params(const ft_band *band, const ft_binary_bank *bk)
 int stage_rows(const ft_band *band)
 {
     // at most 16 KB of rows per stage, 8..64 rows (a divisor of kBtRowPad): two stages and
-    // the cosine table leave room for 4 CTAs of 256 threads per SM
+    // the cosine table leave room for 4 CTAs per SM, as many as the registers allow
     const int rb = band->Wp * elem_bytes(band->dtype);
     int S = 64;
     while (S > 8 && S * rb > 16 * 1024)
