@@ -21,9 +21,11 @@ Functions and the passages of arXiv 2411.18370 they follow:
                      so P(P > x) = exp(-x / 2); Bernoulli per SFT).
 * topk_gated()       Sec. VI.B: the loudest per box among templates whose second statistic
                      (the weighted number count) reaches a minimum.
-* binary_*()         Eq. (track) with the binary-orbit term, the random bank in the uniform
-                     coordinates of Eq. (xi_of_lambda) / App. A and its hyperboxes (Sec. IV.B),
-                     and the statistic along those tracks (C source ft_oracle_bin.c).
+* binary_*()         Eq. (track) with the binary-orbit term, evaluated as written in FP64
+                     with libm's cos / sin and rounded half up to a bin; the random bank in
+                     the uniform coordinates of Eq. (xi_of_lambda) / App. A and its
+                     hyperboxes (Sec. IV.B); the statistic along those tracks (C source
+                     ft_oracle_bin.c).
 * topk_per_box()     the loudest templates of each hyperbox.
 """
 from __future__ import annotations
@@ -118,17 +120,18 @@ def load_library(path):
     L.or_pdet_q.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                             ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                             ctypes.c_void_p]
-    L.or_cos_q32.restype = ctypes.c_float
-    L.or_cos_q32.argtypes = [ctypes.c_uint32]
-    L.or_bt_tq.restype = ctypes.c_int64
-    L.or_bt_tq.argtypes = [ctypes.c_double, ctypes.c_double]
     L.or_bt_templates.restype = None
     L.or_bt_templates.argtypes = [ctypes.POINTER(_BDesc), ctypes.c_void_p, ctypes.c_int64,
-                                  ctypes.c_double, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+                                  ctypes.c_void_p]
+    L.or_bt_sky.restype = None
+    L.or_bt_sky.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.or_bt_position.restype = ctypes.c_double
+    L.or_bt_position.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_int64]
     L.or_bt_bins.restype = None
     L.or_bt_bins.argtypes = [ctypes.POINTER(_BDesc), ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
-                             ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+                             ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
     L.or_bt_statistic_sky.restype = None
     L.or_bt_statistic_sky.argtypes = [ctypes.POINTER(_BDesc), ctypes.c_void_p, ctypes.c_int64,
                                       ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
@@ -405,12 +408,6 @@ class _BDesc(ctypes.Structure):
                 ("n_per_box", ctypes.c_int64), ("seed", ctypes.c_uint64)]
 
 
-class _BDer(ctypes.Structure):
-    _fields_ = [("K", ctypes.c_int64), ("phi", ctypes.c_float), ("F", ctypes.c_float),
-                ("nx", ctypes.c_float), ("ny", ctypes.c_float), ("nz", ctypes.c_float),
-                ("D", ctypes.c_float), ("nu_q", ctypes.c_uint64), ("psi_q", ctypes.c_uint64)]
-
-
 def _bdesc(bank):
     d = _BDesc()
     for k in range(6):
@@ -426,52 +423,55 @@ def _tmpl(bank, templates):
     return _c(np.arange(bank.n_templates) if templates is None else templates, np.int64)
 
 
-def binary_templates(bank, templates=None, t_sft=1800.0, k_lo=0):
-    """lambda [n][6] (BINARY_DIMS order) and the per-template quantities of the canonical bin
-    rule (dict of arrays)."""
+def binary_templates(bank, templates=None):
+    """lambda [n][6] (BINARY_DIMS order: f0, alpha in turns, sin(delta), a_p, Omega, phi_b in
+    turns) of the given templates (default: all)."""
     t = _tmpl(bank, templates)
     n = len(t)
     lam = np.empty((n, 6), np.float64)
-    der = (_BDer * max(n, 1))()
     d = _bdesc(bank)
-    lib().or_bt_templates(ctypes.byref(d), t.ctypes.data, n, float(t_sft), int(k_lo),
-                           lam.ctypes.data, ctypes.cast(der, ctypes.c_void_p))
-    dt = {"K": np.int64, "nu_q": np.uint64, "psi_q": np.uint64}
-    out = {f: np.array([getattr(der[i], f) for i in range(n)], dtype=dt.get(f, np.float32))
-           for f, _ in _BDer._fields_}
-    return lam, out
+    lib().or_bt_templates(ctypes.byref(d), t.ctypes.data, n, lam.ctypes.data)
+    return lam
 
 
-def cos_q32(theta):
-    """The canonical FP32 cosine of 2 pi theta / 2^32 (theta uint32)."""
-    return np.array([lib().or_cos_q32(int(x) & 0xFFFFFFFF) for x in np.atleast_1d(theta)], np.float32)
+def binary_sky(lam):
+    """The unit sky vectors [n][3] of lambda rows (FP64, libm cos / sin of 2 pi alpha)."""
+    lam = _c(np.atleast_2d(lam), np.float64)
+    out = np.empty((len(lam), 3), np.float64)
+    for i in range(len(lam)):
+        lib().or_bt_sky(lam[i].ctypes.data, out[i].ctypes.data)
+    return out
 
 
-def binary_tq(t_mid, t0):
-    return np.array([lib().or_bt_tq(float(x), float(t0)) for x in np.atleast_1d(t_mid)], np.int64)
+def binary_position(lam, v, t, t_sft, k_lo):
+    """Eq. (track) times T_SFT as a band column, X = f(t) T_SFT - k_lo, for one template
+    (lambda row) and one SFT (v/c [3], t = t_mid - t0)."""
+    lam = _c(lam, np.float64)
+    n = binary_sky(lam)[0]
+    vv = _c(v, np.float64)
+    return float(lib().or_bt_position(lam.ctypes.data, n.ctypes.data, vv.ctypes.data, float(t),
+                                      float(t_sft), int(k_lo)))
 
 
-def binary_bins(sfts, bank, templates, with_fp64=False):
-    """Canonical bins [n, N_SFT] (band columns); with_fp64 also the FP64 bins of Eq. (track)
-    and the distance of the real-valued track from the rounding boundary."""
+def binary_bins(sfts, bank, templates, with_dist=False):
+    """Bins [n, N_SFT] (band columns) of Eq. (track), FP64, rounded half up; with_dist also the
+    distance of each real-valued position from its rounding boundary."""
     t = _tmpl(bank, templates)
     n = len(t)
     tm = _c(sfts.t_mid, np.float64)
     v = _c(sfts.v, np.float64)
     N = len(tm)
     b = np.empty((n, N), np.int64)
-    b64 = np.empty((n, N), np.int64) if with_fp64 else None
-    dist = np.empty((n, N), np.float64) if with_fp64 else None
+    dist = np.empty((n, N), np.float64) if with_dist else None
     d = _bdesc(bank)
     lib().or_bt_bins(ctypes.byref(d), t.ctypes.data, n, N, tm.ctypes.data, v.ctypes.data,
-                      float(sfts.t0), float(sfts.t_sft), int(sfts.k_lo), b.ctypes.data,
-                      None if b64 is None else b64.ctypes.data,
-                      None if dist is None else dist.ctypes.data)
-    return (b, b64, dist) if with_fp64 else b
+                     float(sfts.t0), float(sfts.t_sft), int(sfts.k_lo), b.ctypes.data,
+                     None if dist is None else dist.ctypes.data)
+    return (b, dist) if with_dist else b
 
 
 def binary_statistic(sfts, bank, templates=None, w=None):
-    """FP64 s along the canonical binary tracks and the out-of-window counts."""
+    """FP64 s along the binary tracks of Eq. (track) and the out-of-window counts."""
     t = None if templates is None else _c(templates, np.int64)
     n = bank.n_templates if t is None else len(t)
     P = _c(sfts.power, np.float64)
@@ -489,7 +489,7 @@ def binary_statistic(sfts, bank, templates=None, w=None):
 
 
 def binary_statistic_sky(sfts, bank, D, templates=None):
-    """s along the canonical binary tracks under the all-sky weights (a^2 + b^2)/S_n of each
+    """s along the binary tracks of Eq. (track) under the all-sky weights (a^2 + b^2)/S_n of each
     template's sky direction (Sec. II.B), normalised per template; returns (s, sigma_G, oob)
     with mu_G = 2."""
     t = None if templates is None else _c(templates, np.int64)

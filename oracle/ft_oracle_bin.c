@@ -12,20 +12,18 @@
  *   Sec. IV.B              the xi hyperbox is cut into regular boxes of n_per_box templates.
  *   Eq. (short_coh_general) the weighted sum of normalised power along the track.
  *
- * Canonical evaluation (the kernels evaluate the same rule in the same precision):
- *   - random numbers: Philox4x32-10 (or_philox4x32_10) at counter (i lo, i hi, c, 0x62696e61)
- *     with key (seed lo, seed hi), c = 0, 1, 2, two 53-bit uniforms per call;
- *   - template i lies in box i / n_per_box (f0 slowest, phi_b fastest); its xi is uniform in
- *     the box; the roots use sqrt (correctly rounded) and a fixed 24-step Newton cube root;
- *   - per template: F = f0 T_SFT split into K = floor(F) - k_lo and the FP32 fraction phi;
- *     the sky vector and the orbit amplitude D = F a_p Omega in FP32; the orbit frequency and
- *     phase as 64-bit fixed point (turns);
- *   - per SFT: the orbit phase of (t_mid - t0) in exact 64-bit integer arithmetic, its cosine
- *     by linear interpolation in a full-turn table of 1024 intervals (entries: libm's
- *     cos rounded to FP32, differences in FP32), and
- *         X = (phi + F v.n) - D cos,  bin = K + floor(X + 1/2)   (FP32, operations as written).
- *   or_bt_bins also returns the FP64 bin of Eq. (track) with libm's cos and its distance from
- *   the rounding boundary, which pins the canonical rule to the plain definition.
+ * The track is the plain definition, in FP64 with libm's trigonometric functions:
+ *   n  = (cos(delta) cos(2 pi alpha), cos(delta) sin(2 pi alpha), sin(delta)), alpha in turns;
+ *   t  = t_mid - t0 (the SFT's mid-time from the start of the observation, where f0 is
+ *        defined);
+ *   X  = f0 (1 + v.n - a_p Omega cos(Omega t - 2 pi phi_b)) T_SFT - k_lo, phi_b in turns;
+ *   bin = floor(X + 1/2)  (round half up to a column of the band).
+ * Random numbers are inputs of the method, drawn the same way on both sides:
+ *   Philox4x32-10 (or_philox4x32_10) at counter (i lo, i hi, c, 0x62696e61) with key
+ *   (seed lo, seed hi), c = 0, 1, 2, two 53-bit uniforms per call; template i lies in box
+ *   i / n_per_box (f0 slowest, phi_b fastest) and its xi is uniform in the box; the roots use
+ *   sqrt (correctly rounded) and a fixed 24-step Newton cube root, so lambda is a pure
+ *   function of (seed, i).
  */
 #include <math.h>
 #include <stdint.h>
@@ -40,15 +38,7 @@ typedef struct {
     uint64_t seed;
 } or_bdesc;
 
-typedef struct {
-    int64_t K;     /* floor(f0 T_SFT) - k_lo */
-    float phi;     /* f0 T_SFT - floor(f0 T_SFT) */
-    float F;       /* f0 T_SFT */
-    float nx, ny, nz;
-    float D;       /* f0 T_SFT a_p Omega */
-    uint64_t nu_q; /* Omega / 2 pi in turns per second, units of 2^-54 */
-    uint64_t psi_q; /* phi_b in turns, units of 2^-64 */
-} or_bder;
+static const double TWO_PI = 6.283185307179586476925286766559;
 
 static double u53(uint32_t a, uint32_t b)
 {
@@ -137,99 +127,56 @@ void or_bt_lambda(const or_bdesc *b, int64_t i, double lam[6])
         lam[2] = -1.0;
 }
 
-/* full-turn table: C[i] = cos(i 2 pi / 1024) (libm, FP64, rounded to FP32), D[i] =
- * C[i+1] - C[i] in FP32, D[1024] = 0 */
-static float tab_c[1025], tab_d[1025];
-static int tab_ready;
-
-void or_bt_init(void)
+/* the unit sky vector of (alpha in turns, sin(delta)) */
+void or_bt_sky(const double lam[6], double n[3])
 {
-    if (tab_ready)
-        return;
-    for (int i = 0; i <= 1024; i++)
-        tab_c[i] = (float)cos((double)i * 6.135923151542565e-03);
-    for (int i = 0; i < 1024; i++)
-        tab_d[i] = tab_c[i + 1] - tab_c[i];
-    tab_d[1024] = 0.0f;
-    tab_ready = 1;
+    double cd = sqrt(fmax(0.0, 1.0 - lam[2] * lam[2]));
+    n[0] = cd * cos(TWO_PI * lam[1]);
+    n[1] = cd * sin(TWO_PI * lam[1]);
+    n[2] = lam[2];
 }
 
-/* cos(2 pi theta / 2^32): the turn theta / 2^32 falls in table interval theta >> 22 at
- * fraction (theta mod 2^22) / 2^22; linear interpolation between that entry and the next */
-float or_cos_q32(uint32_t theta)
+/* Eq. (track) times T_SFT, as a column of the band: X = f(t) T_SFT - k_lo */
+double or_bt_position(const double lam[6], const double n[3], const double v[3], double t,
+                      double t_sft, int64_t k_lo)
 {
-    or_bt_init();
-    uint32_t i = theta >> 22;
-    float f = (float)(theta & 0x3FFFFFu) * 0x1p-22f;
-    return fmaf(f, tab_d[i], tab_c[i]);
+    double vn = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
+    double orbit = lam[3] * lam[4] * cos(lam[4] * t - TWO_PI * lam[5]);
+    double f = lam[0] * (1.0 + vn - orbit);
+    return f * t_sft - (double)k_lo;
 }
 
-void or_bt_derived(const double lam[6], double t_sft, int64_t k_lo, or_bder *o)
+/* t of SFT a: its mid-time from the start of the observation */
+static double sft_t(const double *t_mid, int64_t a, double t0)
 {
-    double F = lam[0] * t_sft;
-    double Fl = floor(F);
-    o->K = (int64_t)Fl - k_lo;
-    o->phi = (float)(F - Fl);
-    o->F = (float)F;
-    double s = lam[2];
-    double c2 = 1.0 - s * s;
-    float cd = (float)sqrt(c2 > 0.0 ? c2 : 0.0);
-    uint32_t ta = (uint32_t)(lam[1] * 4294967296.0);
-    float ca = or_cos_q32(ta), sa = or_cos_q32(ta - 0x40000000u);
-    o->nx = cd * ca;
-    o->ny = cd * sa;
-    o->nz = (float)s;
-    o->D = (float)((F * lam[3]) * lam[4]);
-    double nu = lam[4] / 6.283185307179586;
-    o->nu_q = (uint64_t)floor(nu * 18014398509481984.0 + 0.5);
-    o->psi_q = (uint64_t)(lam[5] * 18446744073709551616.0);
+    return t_mid[a] - t0;
 }
 
-int64_t or_bt_tq(double t_mid, double t0)
+/* round half up, and |X - the nearest rounding boundary (a half-integer)| */
+static int64_t bin_of(double X, double *dist)
 {
-    return (int64_t)floor((t_mid - t0) * 1024.0 + 0.5);
+    double k = floor(X + 0.5);
+    if (dist) {
+        double lo = X - (k - 0.5), hi = (k + 0.5) - X;
+        *dist = lo < hi ? lo : hi;
+    }
+    return (int64_t)k;
 }
 
-static int64_t canonical_bin(const or_bder *d, int64_t tq, const float v[3])
-{
-    uint64_t ph = d->nu_q * (uint64_t)tq - d->psi_q;
-    float c = or_cos_q32((uint32_t)(ph >> 32));
-    float a = v[2] * d->nz;
-    float b = fmaf(v[1], d->ny, a);
-    float vn = fmaf(v[0], d->nx, b);
-    float dop = d->F * vn;
-    float m = d->D * c;
-    float X = (d->phi + dop) - m;
-    return d->K + (int64_t)floorf(X + 0.5f);
-}
-
-/* bins[n][N] (columns of the band); optionally the FP64 bins of Eq. (track) with libm cos
- * for the same lambda and sky vector, and the distance of that real-valued track from the
- * rounding boundary. */
+/* bins[n][N] (columns of the band) of templates tmpl[0..n) over SFTs 0..N-1, and optionally
+ * the distance of each real-valued position from its rounding boundary */
 void or_bt_bins(const or_bdesc *b, const int64_t *tmpl, int64_t n, int64_t N, const double *t_mid,
-                 const double *v, double t0, double t_sft, int64_t k_lo, int64_t *bins,
-                 int64_t *bins64, double *dist)
+                const double *v, double t0, double t_sft, int64_t k_lo, int64_t *bins, double *dist)
 {
-    or_bt_init();
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < n; i++) {
-        double lam[6];
+        double lam[6], nn[3];
         or_bdesc bd = *b;
         or_bt_lambda(&bd, tmpl[i], lam);
-        or_bder d;
-        or_bt_derived(lam, t_sft, k_lo, &d);
+        or_bt_sky(lam, nn);
         for (int64_t a = 0; a < N; a++) {
-            float v32[3] = {(float)v[3 * a], (float)v[3 * a + 1], (float)v[3 * a + 2]};
-            bins[i * N + a] = canonical_bin(&d, or_bt_tq(t_mid[a], t0), v32);
-            if (bins64) {
-                double vn = v[3 * a] * (double)d.nx + v[3 * a + 1] * (double)d.ny + v[3 * a + 2] * (double)d.nz;
-                double t = t_mid[a] - t0;
-                double f = lam[0] * (1.0 + vn - lam[3] * lam[4] * cos(lam[4] * t - 6.283185307179586 * lam[5]));
-                double X = f * t_sft - (double)k_lo;
-                double k = floor(X + 0.5);
-                bins64[i * N + a] = (int64_t)k;
-                dist[i * N + a] = fabs(X - k - 0.5) < fabs(X - k + 0.5) ? fabs(X - k - 0.5) : fabs(X - k + 0.5);
-            }
+            double X = or_bt_position(lam, nn, v + 3 * a, sft_t(t_mid, a, t0), t_sft, k_lo);
+            bins[i * N + a] = bin_of(X, dist ? dist + i * N + a : NULL);
         }
     }
 }
@@ -237,22 +184,19 @@ void or_bt_bins(const or_bdesc *b, const int64_t *tmpl, int64_t n, int64_t N, co
 /* s = sum_alpha w_alpha P[alpha][bin] (FP64, alpha order); bins outside [0, W) add 0 and
  * are counted. */
 void or_bt_statistic(const or_bdesc *b, const int64_t *tmpl, int64_t n, int64_t N, int64_t W,
-                      const double *power, const double *w, const double *t_mid, const double *v,
-                      double t0, double t_sft, int64_t k_lo, double *s, int32_t *oob)
+                     const double *power, const double *w, const double *t_mid, const double *v,
+                     double t0, double t_sft, int64_t k_lo, double *s, int32_t *oob)
 {
-    or_bt_init();
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < n; i++) {
-        double lam[6];
+        double lam[6], nn[3];
         or_bdesc bd = *b;
         or_bt_lambda(&bd, tmpl ? tmpl[i] : i, lam);
-        or_bder d;
-        or_bt_derived(lam, t_sft, k_lo, &d);
+        or_bt_sky(lam, nn);
         double acc = 0.0;
         int32_t out = 0;
         for (int64_t a = 0; a < N; a++) {
-            float v32[3] = {(float)v[3 * a], (float)v[3 * a + 1], (float)v[3 * a + 2]};
-            int64_t k = canonical_bin(&d, or_bt_tq(t_mid[a], t0), v32);
+            int64_t k = bin_of(or_bt_position(lam, nn, v + 3 * a, sft_t(t_mid, a, t0), t_sft, k_lo), NULL);
             if (k < 0 || k >= W) {
                 out++;
                 continue;
@@ -264,38 +208,30 @@ void or_bt_statistic(const or_bdesc *b, const int64_t *tmpl, int64_t n, int64_t 
     }
 }
 
-/* lambda [n][6] and the derived per-template quantities of templates tmpl[0..n) */
-void or_bt_templates(const or_bdesc *b, const int64_t *tmpl, int64_t n, double t_sft, int64_t k_lo,
-                      double *lam, or_bder *der)
+/* lambda [n][6] of templates tmpl[0..n) */
+void or_bt_templates(const or_bdesc *b, const int64_t *tmpl, int64_t n, double *lam)
 {
-    for (int64_t i = 0; i < n; i++) {
+    for (int64_t i = 0; i < n; i++)
         or_bt_lambda(b, tmpl[i], lam + 6 * i);
-        if (der)
-            or_bt_derived(lam + 6 * i, t_sft, k_lo, der + i);
-    }
 }
 
 void or_antenna_ab(const double *D, const double *n, double *a, double *b);
 
 /* The statistic under the all-sky weights of Sec. II.B for the binary bank: per template the
  * weights are w_alpha = r_alpha / sum r, r_alpha = (a^2 + b^2)(D_alpha, n) / S_n,alpha, with
- * n the template's unit sky vector (FP64, libm cos / sin of alpha); s = sum w P along the
- * canonical bins, and sigma_G = 2 sqrt(sum w^2) (mu_G = 2). */
+ * n the template's unit sky vector; s = sum w P along the track's bins, and
+ * sigma_G = 2 sqrt(sum w^2) (mu_G = 2). */
 void or_bt_statistic_sky(const or_bdesc *b, const int64_t *tmpl, int64_t n, int64_t N, int64_t W,
                          const double *power, const double *D, const double *s_n, const double *t_mid,
                          const double *v, double t0, double t_sft, int64_t k_lo, double *s,
                          double *sigma, int32_t *oob)
 {
-    or_bt_init();
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < n; i++) {
-        double lam[6];
+        double lam[6], nn[3];
         or_bdesc bd = *b;
         or_bt_lambda(&bd, tmpl ? tmpl[i] : i, lam);
-        or_bder d;
-        or_bt_derived(lam, t_sft, k_lo, &d);
-        double cdl = sqrt(fmax(0.0, 1.0 - lam[2] * lam[2]));
-        double nn[3] = {cdl * cos(6.283185307179586 * lam[1]), cdl * sin(6.283185307179586 * lam[1]), lam[2]};
+        or_bt_sky(lam, nn);
         double acc = 0.0, sr = 0.0, sr2 = 0.0;
         int32_t out = 0;
         for (int64_t a = 0; a < N; a++) {
@@ -304,8 +240,7 @@ void or_bt_statistic_sky(const or_bdesc *b, const int64_t *tmpl, int64_t n, int6
             double r = (aa * aa + bb * bb) / s_n[a];
             sr += r;
             sr2 += r * r;
-            float v32[3] = {(float)v[3 * a], (float)v[3 * a + 1], (float)v[3 * a + 2]};
-            int64_t k = canonical_bin(&d, or_bt_tq(t_mid[a], t0), v32);
+            int64_t k = bin_of(or_bt_position(lam, nn, v + 3 * a, sft_t(t_mid, a, t0), t_sft, k_lo), NULL);
             if (k < 0 || k >= W) {
                 out++;
                 continue;

@@ -1,25 +1,27 @@
 """Pins of the oracle's binary-orbit track (Eq. (track)) and random hyperbox bank
 (Eq. (xi_of_lambda), App. A Eq. (unif_transform), Sec. IV.B):
 
-* the canonical cosine of a 32-bit phase (linear interpolation in a full-turn table of 1024
-  intervals) is within the interpolation bound (2 pi/1024)^2 / 8 = 4.7e-6 plus FP32 rounding
-  of libm's cos, and exact at the table's nodes;
 * every template lies in its own box and is uniform in the uniform coordinates
   xi = {f0^6, alpha, sin(delta), a_p^3, Omega^4, phi_b} there (mean 1/2, variance 1/12 of the
   position within the box along each axis);
-* the fixed-point orbit phase equals (Omega t - phi_b) / 2 pi mod 1 to 1e-8 turns;
-* the canonical FP32 bin equals the FP64 bin of Eq. (track) (libm cos) wherever the track is
-  more than 5e-4 bins from the rounding boundary, and such cases are rare (the cosine's
-  error, under 4.9e-6, times the orbit amplitude, under 28 bins here, and times F (|v_x| +
-  |v_y|) in the sky vector, under 27 bins, plus FP32 rounding: about 2.8e-4 at most);
-* with a_p = 0 and no detector motion the bin is round(f0 T_SFT) (zero-Doppler tracks collapse
-  to fixed bins);
-* the statistic equals a Python sum over SFTs along the canonical bins, and a noise-free track
-  of unit power recovers N_SFT;
+* the orbit term in closed form: with the detectors at rest, SFTs placed where the orbit phase
+  Omega t - phi_b is 0, pi/2, pi and 3 pi/2 put the track at f0 T_SFT (1 - a_p Omega),
+  f0 T_SFT, f0 T_SFT (1 + a_p Omega) and f0 T_SFT (a source receding at the ascending node
+  is redshifted by a_p Omega);
+* the Doppler term in closed form: an isolated source (a_p = 0) at n = x, y or z sits at
+  f0 T_SFT (1 + v_x), (1 + v_y) or (1 + v_z);
+* with a_p = 0 and no detector motion every SFT reads the same bin, round(f0 T_SFT)
+  (zero-Doppler tracks collapse to fixed bins);
+* on random templates and SFTs of a moving detector the oracle's FP64 position equals a
+  40-digit evaluation (mpmath) of Eq. (track) to 1e-9 bins, so its bins are those of the
+  exact track except within 1e-9 bins of a rounding boundary;
+* the statistic equals a Python sum over SFTs along the bins, and a noise-free track of unit
+  power recovers N_SFT;
 * the per-box selection returns each box's loudest templates.
 """
 import math
 
+import mpmath
 import numpy as np
 
 import ftsynth
@@ -28,44 +30,26 @@ import oracle
 DAY = 86400.0
 
 
-def _bank(n_div=(2, 2, 2, 2, 2, 2), n_per_box=40, seed=11, f0=(100.0, 100.05), ap=(5.0, 15.0)):
-    om = (2 * math.pi / (15 * DAY), 2 * math.pi / (7 * DAY))
-    return ftsynth.BinaryBank(lo=(f0[0], 0.0, -1.0, ap[0], om[0], 0.0),
-                              hi=(f0[1], 1.0, 1.0, ap[1], om[1], 1.0),
+def _bank(n_div=(2, 2, 2, 2, 2, 2), n_per_box=40, seed=11, f0=(100.0, 100.05), ap=(5.0, 15.0),
+          alpha=(0.0, 1.0), sind=(-1.0, 1.0), om=None):
+    om = om or (2 * math.pi / (15 * DAY), 2 * math.pi / (7 * DAY))
+    return ftsynth.BinaryBank(lo=(f0[0], alpha[0], sind[0], ap[0], om[0], 0.0),
+                              hi=(f0[1], alpha[1], sind[1], ap[1], om[1], 1.0),
                               n_div=n_div, n_per_box=n_per_box, seed=seed)
 
 
-def _sfts(n_sft=(70, 60), W=200, wings=55, seed=3, k_band=180_000, moving=True):
+def _sfts(n_sft=(70, 60), W=200, wings=55, seed=3, k_band=180_000, moving=True, t0=0.0):
     g = np.random.default_rng(seed)
     t_mid, v = [], []
     for X, n in enumerate(n_sft):
-        t = np.sort(g.uniform(0, ftsynth.YEAR_S, n)) + 900
+        t = np.sort(g.uniform(0, ftsynth.YEAR_S, n)) + 900 + t0
         t_mid.append(t)
         v.append(ftsynth.detector_velocity(t, X) if moving else np.zeros((n, 3)))
     t_mid = np.concatenate(t_mid)
     N = len(t_mid)
     return ftsynth.SFTSet(power=g.exponential(2.0, (N, W)), t_mid=t_mid, v=np.concatenate(v),
                           s_n=np.ones(N), n_sft=list(n_sft), k_lo=k_band - wings, t_sft=1800.0,
-                          t0=0.0)
-
-
-def test_canonical_cosine():
-    g = np.random.default_rng(1)
-    th = np.concatenate([g.integers(0, 2 ** 32, 20000, dtype=np.uint64),
-                         np.array([0, 1 << 29, (1 << 29) - 1, 1 << 30, 1 << 31, 3 << 30, 2 ** 32 - 1],
-                                  np.uint64)])
-    c = oracle.cos_q32(th).astype(np.float64)
-    ref = np.cos(2 * np.pi * th.astype(np.float64) / 2 ** 32)
-    bound = (2 * np.pi / 1024) ** 2 / 8 + 1.2e-7
-    assert np.max(np.abs(c - ref)) < bound
-    s = oracle.cos_q32((th - (1 << 30)) % 2 ** 32).astype(np.float64)
-    assert np.max(np.abs(s - np.sin(2 * np.pi * th.astype(np.float64) / 2 ** 32))) < bound
-    assert oracle.cos_q32([0])[0] == 1.0
-    # nodes: the FP32 rounding of cos at multiples of 2 pi / 1024, exactly
-    nodes = np.arange(0, 1024, dtype=np.uint64) << np.uint64(22)
-    want = np.cos(np.arange(1024) * (2 * np.pi / 1024)).astype(np.float32)
-    got = oracle.cos_q32(nodes)
-    assert np.max(np.abs(got.astype(np.float64) - want.astype(np.float64))) < 1.2e-7
+                          t0=t0)
 
 
 def _xi(lam):
@@ -75,7 +59,7 @@ def _xi(lam):
 
 def test_templates_fill_their_boxes_uniformly():
     bank = _bank(n_per_box=200)
-    lam, _ = oracle.binary_templates(bank)
+    lam = oracle.binary_templates(bank)
     xi = _xi(lam)
     lo = _xi(np.array([bank.lo]))[0]
     hi = _xi(np.array([bank.hi]))[0]
@@ -94,39 +78,57 @@ def test_templates_fill_their_boxes_uniformly():
     # lambda inside the physical range
     assert np.all(lam >= np.array(bank.lo) - 1e-12) and np.all(lam <= np.array(bank.hi) + 1e-12)
     # a different seed draws different templates; the same seed the same ones
-    lam2, _ = oracle.binary_templates(bank)
-    assert np.array_equal(lam, lam2)
-    lam3, _ = oracle.binary_templates(ftsynth.BinaryBank(**{**bank.__dict__, "seed": 12}))
+    assert np.array_equal(lam, oracle.binary_templates(bank))
+    lam3 = oracle.binary_templates(ftsynth.BinaryBank(**{**bank.__dict__, "seed": 12}))
     assert not np.any(lam3[:, 0] == lam[:, 0])
 
 
-def test_orbit_phase_fixed_point():
-    bank = _bank(n_per_box=10)
-    sfts = _sfts()
-    lam, der = oracle.binary_templates(bank, None, sfts.t_sft, sfts.k_lo)
-    tq = oracle.binary_tq(sfts.t_mid, sfts.t0).astype(np.uint64)
-    for i in range(0, bank.n_templates, 37):
-        ph = (der["nu_q"][i] * tq - der["psi_q"][i]).astype(np.float64) / 2 ** 64
-        want = ((lam[i, 4] * (sfts.t_mid - sfts.t0) - 2 * np.pi * lam[i, 5]) / (2 * np.pi)) % 1.0
-        d = np.abs(ph - want)
-        assert np.all(np.minimum(d, 1 - d) < 1e-8)
+def test_orbit_term_closed_form():
+    """Detectors at rest; for each template, SFTs at the times where Omega t - 2 pi phi_b is
+    0, pi/2, pi, 3 pi/2 (+ whole orbits), counted from an observation start t0 != 0."""
+    bank = _bank(n_div=(1, 1, 1, 2, 2, 3), n_per_box=4)
+    lam = oracle.binary_templates(bank)
+    t0, T, k_lo = 5.0e5, 1800.0, 180_000 - 60
+    for i in range(bank.n_templates):
+        f0, _, _, ap, om, pb = lam[i]
+        theta = np.array([0.0, 0.5, 1.0, 1.5, 2.0, 2.5, 3.0, 3.5]) * math.pi + 2 * math.pi * 7
+        t_rel = (theta + 2 * math.pi * pb) / om
+        sf = ftsynth.SFTSet(power=np.ones((len(t_rel), 10)), t_mid=t0 + t_rel,
+                            v=np.zeros((len(t_rel), 3)), s_n=np.ones(len(t_rel)), n_sft=[len(t_rel)],
+                            k_lo=k_lo, t_sft=T, t0=t0)
+        b, dist = oracle.binary_bins(sf, bank, [i], with_dist=True)
+        F = f0 * T
+        want = F * (1.0 - ap * om * np.round(np.cos(theta))) - k_lo
+        kb = np.floor(want + 0.5)
+        d = np.minimum(want - (kb - 0.5), kb + 0.5 - want)
+        ok = d > 1e-6
+        assert np.array_equal(b[0][ok], kb[ok].astype(np.int64)), i
+        assert np.all(np.abs(dist[0] - d) < 1e-6)
 
 
-def test_canonical_bins_match_the_fp64_track():
-    bank = _bank(n_per_box=25)
-    sfts = _sfts()
-    b, b64, dist = oracle.binary_bins(sfts, bank, np.arange(bank.n_templates), with_fp64=True)
-    differ = b != b64
-    assert np.all(dist[differ] < 5e-4)
-    assert differ.mean() < 1e-3
-    # the orbit really moves the track: several bins of spread within each template
-    assert np.median(b.max(axis=1) - b.min(axis=1)) > 20
+def test_doppler_term_closed_form():
+    """An isolated source (a_p = 0) at n = x (alpha = 0, sin(delta) = 0), n = y (alpha = 1/4
+    turn) and n = z (sin(delta) = 1): the track is f0 T_SFT (1 + v.n)."""
+    sfts = _sfts(n_sft=(40, 30), moving=True, t0=1234.5)
+    for axis, (alpha, sind) in enumerate([(0.0, 0.0), (0.25, 0.0), (0.0, 1.0)]):
+        bank = _bank(n_div=(2, 1, 1, 1, 1, 1), n_per_box=5, ap=(0.0, 0.0), alpha=(alpha, alpha),
+                     sind=(sind, sind))
+        lam = oracle.binary_templates(bank)
+        b, dist = oracle.binary_bins(sfts, bank, np.arange(bank.n_templates), with_dist=True)
+        for i in range(bank.n_templates):
+            X = lam[i, 0] * sfts.t_sft * (1.0 + sfts.v[:, axis]) - sfts.k_lo
+            kb = np.floor(X + 0.5)
+            ok = np.abs(X - kb - 0.5) > 1e-6
+            ok &= np.abs(X - kb + 0.5) > 1e-6
+            assert np.array_equal(b[i][ok], kb[ok].astype(np.int64)), (axis, i)
+        # the Doppler really moves the track (about +-10 bins over the year at 100 Hz)
+        assert np.ptp(b) > 10
 
 
 def test_zero_doppler_isolated_limit():
     bank = _bank(n_per_box=30, ap=(0.0, 0.0))
     sfts = _sfts(moving=False)
-    lam, _ = oracle.binary_templates(bank, None, sfts.t_sft, sfts.k_lo)
+    lam = oracle.binary_templates(bank)
     b = oracle.binary_bins(sfts, bank, np.arange(bank.n_templates))
     F = lam[:, 0] * sfts.t_sft
     want = np.floor(F + 0.5).astype(np.int64) - sfts.k_lo
@@ -134,6 +136,41 @@ def test_zero_doppler_isolated_limit():
     ok = np.abs(frac - 0.5) > 1e-6
     assert np.all(b[ok] == want[ok, None])
     assert np.all(b == b[:, :1])
+
+
+def _mp_position(lam, v, t_mid, t0, t_sft, k_lo):
+    """Eq. (track) times T_SFT minus k_lo at 40 significant digits from the FP64 inputs."""
+    with mpmath.workdps(40):
+        f0, al, sd, ap, om, pb = (mpmath.mpf(float(x)) for x in lam)
+        cd = mpmath.sqrt(1 - sd * sd)
+        n = (cd * mpmath.cos(2 * mpmath.pi * al), cd * mpmath.sin(2 * mpmath.pi * al), sd)
+        vn = sum(mpmath.mpf(float(v[i])) * n[i] for i in range(3))
+        t = mpmath.mpf(float(t_mid)) - mpmath.mpf(float(t0))
+        f = f0 * (1 + vn - ap * om * mpmath.cos(om * t - 2 * mpmath.pi * pb))
+        X = f * mpmath.mpf(float(t_sft)) - int(k_lo)
+        k = mpmath.floor(X + mpmath.mpf(1) / 2)
+        d = min(X - (k - mpmath.mpf(1) / 2), (k + mpmath.mpf(1) / 2) - X)
+        return int(k), float(d)
+
+
+def test_bins_equal_high_precision_track():
+    bank = _bank(n_per_box=25, f0=(100.0, 100.125))
+    sfts = _sfts(t0=321.0)
+    g = np.random.default_rng(5)
+    tmpl = g.choice(bank.n_templates, 60, replace=False)
+    b, dist = oracle.binary_bins(sfts, bank, tmpl, with_dist=True)
+    lam = oracle.binary_templates(bank, tmpl)
+    checked = 0
+    for r, i in enumerate(tmpl):
+        for a in g.choice(sfts.n_total, 40, replace=False):
+            k, d = _mp_position(lam[r], sfts.v[a], sfts.t_mid[a], sfts.t0, sfts.t_sft, sfts.k_lo)
+            assert abs(dist[r, a] - d) < 1e-9, (i, a)
+            if d > 1e-9:
+                assert b[r, a] == k, (i, a)
+                checked += 1
+    assert checked > 2000
+    # the orbit really moves the track: several bins of spread within each template
+    assert np.median(b.max(axis=1) - b.min(axis=1)) > 20
 
 
 def test_statistic_brute_force_and_noise_free_track():
@@ -153,14 +190,13 @@ def test_statistic_brute_force_and_noise_free_track():
             else:
                 out += 1
         assert s[i] == acc and oob[i] == out
-    # unit power on the FP64 track of template 3 only
-    _, b64, dist = oracle.binary_bins(sfts, bank, [3], with_fp64=True)
+    # unit power on the track of template 3 only: it recovers every SFT, exactly
     P = np.zeros_like(sfts.power)
-    P[np.arange(sfts.n_total), b64[0]] = 1.0
+    assert np.all((b[3] >= 0) & (b[3] < W))
+    P[np.arange(sfts.n_total), b[3]] = 1.0
     sx = ftsynth.SFTSet(**{**sfts.__dict__, "power": P})
     s3, o3 = oracle.binary_statistic(sx, bank, [3])
-    assert o3[0] == 0
-    assert s3[0] >= sfts.n_total - np.sum(dist[0] < 5e-4)
+    assert o3[0] == 0 and s3[0] == sfts.n_total
 
 
 def test_topk_per_box():
@@ -179,7 +215,7 @@ def test_topk_per_box():
 def test_all_sky_weighted_statistic():
     """Sec. II.B weights on the binary bank: with one detector tensor and one S_n for every
     SFT the weights are 1/N (s = the plain sum / N, sigma_G = 2 / sqrt(N)); in general s is
-    the sum along the canonical bins with the normalised weights of the template's sky
+    the sum along the track's bins with the normalised weights of the template's sky
     direction (sky_weights of its unit vector)."""
     bank = _bank(n_div=(1, 1, 1, 1, 2, 2), n_per_box=4)
     sfts = _sfts(n_sft=(40, 33))
@@ -194,7 +230,7 @@ def test_all_sky_weighted_statistic():
     sx = ftsynth.SFTSet(**{**sfts.__dict__, "s_n": g.uniform(0.5, 2.0, N)})
     D = np.concatenate([ftsynth.detector_tensor(sx.t_mid[:40], 0), ftsynth.detector_tensor(sx.t_mid[40:], 1)])
     s_sky, sig, _ = oracle.binary_statistic_sky(sx, bank, D)
-    lam, _ = oracle.binary_templates(bank)
+    lam = oracle.binary_templates(bank)
     b = oracle.binary_bins(sx, bank, np.arange(bank.n_templates))
     W = sx.power.shape[1]
     for i in range(bank.n_templates):

@@ -52,17 +52,22 @@ PINS = [
 # the binary-orbit track and random bank (oracle/ft_oracle_bin.c), against its own pins
 BIN_SRC = os.path.join(os.path.dirname(obuild.SRC), "ft_oracle_bin.c")
 MUTATIONS_BIN = {
-    "orbit_sign": ("float X = (d->phi + dop) - m;", "float X = (d->phi + dop) + m;"),
-    "doppler_dropped": ("float dop = d->F * vn;", "float dop = 0.0f * vn;"),
-    "orbit_phase_sign": ("uint64_t ph = d->nu_q * (uint64_t)tq - d->psi_q;",
-                         "uint64_t ph = d->nu_q * (uint64_t)tq + d->psi_q;"),
-    "cos_half_turn_table": ("tab_c[i] = (float)cos((double)i * 6.135923151542565e-03);",
-                            "tab_c[i] = (float)cos((double)i * 3.0679615757712823e-03);"),
-    "cos_no_interpolation": ("return fmaf(f, tab_d[i], tab_c[i]);", "return tab_c[i] + 0.0f * f;"),
-    "cos_wrong_interval": ("uint32_t i = theta >> 22;", "uint32_t i = (theta >> 22) ^ 1u;"),
+    "orbit_sign": ("double f = lam[0] * (1.0 + vn - orbit);", "double f = lam[0] * (1.0 + vn + orbit);"),
+    "doppler_dropped": ("double f = lam[0] * (1.0 + vn - orbit);", "double f = lam[0] * (1.0 - orbit);"),
+    "doppler_sign": ("double f = lam[0] * (1.0 + vn - orbit);", "double f = lam[0] * (1.0 - vn - orbit);"),
+    "orbit_phase_sign": ("cos(lam[4] * t - TWO_PI * lam[5])", "cos(lam[4] * t + TWO_PI * lam[5])"),
+    "orbit_phase_in_radians": ("cos(lam[4] * t - TWO_PI * lam[5])", "cos(lam[4] * t - lam[5])"),
+    "orbit_sin_not_cos": ("cos(lam[4] * t - TWO_PI * lam[5])", "sin(lam[4] * t - TWO_PI * lam[5])"),
+    "amplitude_without_omega": ("double orbit = lam[3] * lam[4] * cos(", "double orbit = lam[3] * cos("),
+    "alpha_in_radians": ("n[0] = cd * cos(TWO_PI * lam[1]);", "n[0] = cd * cos(lam[1]);"),
+    "sky_z_dropped": ("n[2] = lam[2];", "n[2] = 0.0;"),
+    "time_from_zero": ("return t_mid[a] - t0;", "return t_mid[a];"),
+    "start_time_not_mid": ("return t_mid[a] - t0;", "return t_mid[a] - 900.0 - t0;"),
+    "floor_not_round": ("double k = floor(X + 0.5);", "double k = floor(X);"),
+    "k_lo_sign": ("return f * t_sft - (double)k_lo;", "return f * t_sft + (double)k_lo;"),
+    "weight_dropped": ("acc += (w ? w[a] : 1.0) * power[a * W + k];", "acc += power[a * W + k];"),
     "box_order_reversed": ("for (int d = 5; d >= 0; d--) {", "for (int d = 0; d < 6; d++) {"),
     "ap_root_wrong": ("case 3: return cbrt_newton(xi, b->hi[3]);", "case 3: return sqrt(xi);"),
-    "amplitude_without_omega": ("o->D = (float)((F * lam[3]) * lam[4]);", "o->D = (float)(F * lam[3]);"),
     "sky_weight_times_psd": ("double r = (aa * aa + bb * bb) / s_n[a];",
                              "double r = (aa * aa + bb * bb) * s_n[a];"),
 }
