@@ -299,7 +299,7 @@ def run_batch(args):
     line = {
         "metric": METRIC, "value": evals / (mb / 1e3), "unit": UNIT, "n_gpus": 1,
         "steps": steps, "warmup": args.warmup, "ms_per_step": mb, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": f"{args.dtype}-storage/f32-accumulate", "data": "synthetic",
         "config": {"workload": f"64-band batch: widths 0.05-0.5 Hz, starts 50-500 Hz, N_sky = "
                                f"{args.sky_scale} x 1e3 (f/50)^2 clamped, 10 f1, 2 det x 1 yr "
                                f"({N} SFTs)", "storage": args.dtype, "bands": len(bands),
@@ -343,11 +343,12 @@ def run_batch(args):
     return 0
 
 
-# per (template, SFT) operations of the binary track's canonical rule: orbit phase (64-bit
-# multiply, subtract, shift: 3), the table cosine (index, fraction 3, table read,
-# interpolation: 6), v.n (3), the two products (2), X (2), the bin (4), bounds + gather +
-# add (3)
-BT_OPS_PER_EVAL = 23
+# per (template, SFT) operations of the binary track's FP32 screen and gather: orbit phase
+# (three 32-bit multiply-adds: 3), the table node and offset (round, shift, table read,
+# shift, convert: 5), the second-order cosine (3), a.v + y0 (3), y (1), floor, fraction and
+# the two boundary tests (4), the bin (2), bounds + out-of-window count (2), address, read,
+# add (3); the FP64 decisions (about 2 delta of the evaluations) are not counted
+BT_OPS_PER_EVAL = 26
 ISSUE_LANES_PER_CLK_PER_SM = 128
 
 
@@ -399,9 +400,11 @@ def run_binary(args):
     flushbuf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     flush = lambda: flushbuf.fill_(1)
     evals = bank.n_templates * sfts.n_total
+    ft.binary_decisions(gb)
     with ClockSampler(local) as clk:
         times = time_steps(step, args.steps, args.warmup, stream, flush)
     ctx.check_status()
+    n64, delta = ft.binary_decisions(gb)
     mean_ms = statistics.mean(times)
     value = evals / (mean_ms / 1e3)
     peak_ops = 148 * ISSUE_LANES_PER_CLK_PER_SM * 2032e6
@@ -409,15 +412,16 @@ def run_binary(args):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": f"{args.dtype}-storage/f32-accumulate", "data": "synthetic",
         "config": {"workload": f"binary-orbit track, random hyperbox bank: f0 100-100.125 Hz, all sky, "
                                f"a_p 5-15 lt-s, P 7-15 d, phi_b full orbit; {bank.n_templates} templates "
                                f"in {bank.n_boxes} boxes; 2 det x 183 d of 1024 s SFTs at 70% duty "
                                f"({sfts.n_total} SFTs, {sfts.power.shape[1]}-bin window); loudest per box",
                    "n_sft": sfts.n_total, "n_templates": bank.n_templates, "n_boxes": bank.n_boxes,
                    "evals_per_step": evals, "storage": args.dtype,
-                   "track_bins": "canonical split rule: exact integer f0 T, 64-bit fixed-point orbit "
-                                 "phase, FP32 full-turn cosine table and sub-bin terms",
+                   "track_bins": "FP64 bins of Eq. (track): FP32 screen (integer orbit phase, "
+                                 "second-order table cosine) with a derived error bound delta, FP64 "
+                                 "decision within delta of a rounding boundary",
                    "l2": "flushed between timed steps (256 MB write, outside the per-step events)"},
         "roofline": {"bound": "alu", "kernel": "k_bt_eval (per-template track, gather, per-box top-k)",
                      "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Top/s",
@@ -428,6 +432,8 @@ def run_binary(args):
                      "traffic": profiled_traffic_binary(args.dtype)},
         "gpu_launches": 2 * args.steps,
         "clocks": clk.summary(),
+        "fp64_decisions": {"per_eval": n64 / (evals * (args.steps + args.warmup)), "delta_bins": delta,
+                           "expected_per_eval": 2 * delta},
     }
     if not args.no_cpu_baseline:
         g = np.random.default_rng(7)
@@ -623,7 +629,7 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": chosen["mean_ms_max"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": f"{args.dtype}-storage/f32-accumulate", "data": "synthetic",
         "config": workload_desc(sfts, bank, args.dtype),
         "roofline": roofline,
         "gpu_launches": 2 * args.steps,

@@ -356,22 +356,23 @@ FT_API int ft_pdet_q(ft_ctx *ctx, const ft_band *band, const double *det_tensor,
  * each (Sec. IV.B).  Templates are pure functions of (seed, index) and are never stored: the
  * kernels derive each one from a Philox4x32-10 counter.
  *
- * Canonical rule (evaluated identically on every path; the tests pin it to the FP64 track):
+ * Templates (the same on every path, and in the oracle):
  *   - template i is in box i / n_per_box (box index row-major over BINARY dims, f0 slowest);
  *     u_0..u_5 are 53-bit uniforms ((a >> 5) 2^26 + (b >> 6)) / 2^53 from Philox4x32-10 at
  *     counter (i lo, i hi, c, 0x62696e61), key (seed lo, seed hi), c = 0, 1, 2 (words 0,1 and
  *     2,3 of each call); xi_d = xi_lo + (box_d + u_d) (xi_hi - xi_lo) / n_div_d; f0 =
  *     sqrt(cbrt(xi_0)), a_p = cbrt(xi_3) (24 Newton steps y -= (y^3 - x) / (3 y^2) from the
- *     range's top), Omega = sqrt(sqrt(xi_4)); alpha and phi_b stay below 1 turn;
- *   - per template: F = f0 T_SFT, K = floor(F) - k_lo, phi = FP32(F - floor F); the sky vector
- *     n = (cos delta cos alpha, cos delta sin alpha, sin delta) in FP32; D = FP32(F a_p Omega);
- *     orbit frequency nu = Omega / 2 pi as round(nu 2^54) and phase phi_b as phi_b 2^64;
- *   - per SFT: t_q = round((t_mid - t0) 2^10); orbit phase theta = top 32 bits of
- *     (nu_q t_q - psi_q) mod 2^64; its cosine by linear interpolation in a full-turn table
- *     (1024 intervals; entries cos(i 2 pi / 1024) from the host's libm rounded to FP32, FP32
- *     differences; interval theta >> 22 at fraction (theta mod 2^22) 2^-22); X = (phi +
- *     F (v.n)) - D cos in FP32; bin = K + floor(X + 1/2).  The sky vector's cos / sin of alpha use the
- *     same table.
+ *     range's top), Omega = sqrt(sqrt(xi_4)); alpha and phi_b stay below 1 turn.
+ * Bins: the FP64 bin of Eq. (track), bin = floor(X + 1/2) with
+ *     X = f0 (1 + v.n - a_p Omega cos(Omega t - 2 pi phi_b)) T_SFT - k_lo,
+ *     n = (cos delta cos 2 pi alpha, cos delta sin 2 pi alpha, sin delta), t = t_mid - t0.
+ *   The kernels evaluate X first in FP32 (64-bit integer orbit phase, a second-order
+ *   cosine from a 1024-node table, one FMA chain) with an error below a bound delta derived
+ *   from the bank's largest f0 T_SFT |v|, f0 T_SFT a_p Omega and orbit frequency (about 1e-5
+ *   bins for the paper's search ranges); where that value lies within delta of a rounding
+ *   boundary they recompute X in FP64 from the template's FP64 terms and the SFT's FP64 v
+ *   and t, and that decides.  So every bin is the FP64 bin, except where the FP64 value
+ *   itself is within its own rounding (about 1e-10 bins) of the boundary.
  *   Bins outside the band contribute 0 and are counted, as for the isolated bank.
  */
 typedef struct ft_binary_bank ft_binary_bank;
@@ -389,8 +390,8 @@ typedef struct {
 
 /* Set up a binary bank for `band` (uses its SFT times, velocities and weights: the per-SFT
  * weights, or, when ft_band_set_sky_weights was called before, the all-sky weights
- * (a^2 + b^2)/S_n of each template's own sky direction (to FP32 accuracy; the track's
- * table cosine serves only the bin), normalised per template; then s =
+ * (a^2 + b^2)/S_n of each template's own sky direction (to FP32 accuracy), normalised per
+ * template; then s =
  * sum r P / sum r and z uses mu_G = m and sigma_G = d sqrt(sum r^2) / sum r, with one SFT's
  * noise mean m and deviation d: 2 and 2 for normalised power, p and sqrt(p (1 - p)) for a
  * number-count band).  Errors: FT_ERR_ARG (ranges, counts), FT_ERR_OOM. */
@@ -404,7 +405,13 @@ FT_API int ft_binary_bank_info(const ft_binary_bank *bank, int64_t *n_templates,
 FT_API int ft_binary_templates(ft_ctx *ctx, const ft_binary_bank *bank, int64_t first, int64_t n,
                                double *lambda_out, void *stream);
 
-/* Canonical bins of templates[0..n) in every SFT: bins [n][N_SFT] int32 columns of the band
+/* Running count of the FP64 decisions the binary kernels took on this bank (evaluations
+ * whose FP32 screen fell within delta of a rounding boundary) since the last call, and the
+ * bank's delta in bins (either pointer nullable).  Resets the count; synchronises the
+ * device.  Errors: FT_ERR_ARG (null bank), FT_ERR_CUDA. */
+FT_API int ft_binary_decisions(ft_binary_bank *bank, uint64_t *n_fp64, double *delta);
+
+/* Bins of templates[0..n) in every SFT (the kernels' rule above): bins [n][N_SFT] int32 columns of the band
  * (may lie outside [0, n_bins)).  templates / bins both host or both device (on_device). */
 FT_API int ft_binary_track_bins(ft_ctx *ctx, const ft_band *band, const ft_binary_bank *bank,
                                 const int64_t *templates, int64_t n, int32_t *bins, int on_device,

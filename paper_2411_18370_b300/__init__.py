@@ -103,6 +103,7 @@ def lib():
             "ft_binary_bank_destroy": (None, [_P]),
             "ft_binary_bank_info": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
             "ft_binary_templates": (_I, [_P, _P, _I64, _I64, _P, _P]),
+            "ft_binary_decisions": (_I, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]),
             "ft_binary_track_bins": (_I, [_P, _P, _P, _P, _I64, _P, _I, _P]),
             "ft_binary_eval": (_I, [_P, _P, _P, _I64, _I64, _P, _P, _P, _I, _P]),
             "ft_binary_topk_per_box": (_I, [_P, _P, _P, _I, _P, _I, _P]),
@@ -294,6 +295,15 @@ def make_binary_bank(ctx, band, lo, hi, n_div, n_per_box, seed) -> BinaryBank:
     h = _P()
     _check(lib().ft_make_binary_bank(ctx.handle, band.handle, ctypes.byref(d), ctypes.byref(h)))
     return BinaryBank(band, h)
+
+
+def binary_decisions(bank):
+    """ft_binary_decisions: (FP64 decisions since the last call, the bank's screening bound
+    delta in bins); resets the count."""
+    n = ctypes.c_uint64(0)
+    d = ctypes.c_double(0.0)
+    _check(lib().ft_binary_decisions(bank.handle, ctypes.byref(n), ctypes.byref(d)))
+    return int(n.value), float(d.value)
 
 
 def binary_templates(ctx, bank, first, n, stream=None):

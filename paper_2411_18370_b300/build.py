@@ -20,8 +20,9 @@ LIB = os.path.join(HERE, "libfasttracks.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fopenmp",
-         "-Xcompiler", "-fvisibility=hidden", "-cudart", "static", "-shared", "-lgomp"]
+COMPILE = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fopenmp",
+           "-Xcompiler", "-fvisibility=hidden"]
+LINK = ["-cudart", "static", "-shared", "-lgomp"]
 
 
 def sources():
@@ -37,17 +38,34 @@ def _stale() -> bool:
     return any(os.path.getmtime(p) > t for p in deps)
 
 
+def _compile(src: str, obj: str, verbose: bool):
+    cmd = [NVCC] + ARCH + COMPILE + (["-Xptxas", "-v"] if verbose else []) + ["-c", src, "-o", obj]
+    return subprocess.run(cmd, capture_output=True, text=True)
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every source to an object (in parallel), then link the shared library."""
     if not force and not _stale():
         return LIB
-    cmd = [NVCC] + ARCH + FLAGS + (["-Xptxas", "-v"] if verbose else []) + sources() + [
-        "-o", LIB + ".tmp"]
+    from concurrent.futures import ThreadPoolExecutor
+
+    objdir = os.path.join(HERE, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    srcs = sources()
+    objs = [os.path.join(objdir, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
+        results = list(ex.map(lambda so: _compile(so[0], so[1], verbose), zip(srcs, objs)))
+    for src, r in zip(srcs, results):
+        if r.returncode != 0:
+            sys.stderr.write(r.stdout + r.stderr)
+            raise RuntimeError(f"nvcc failed compiling {os.path.basename(src)}")
+        if verbose:
+            sys.stderr.write(r.stderr)
+    cmd = [NVCC] + ARCH + LINK + objs + ["-o", LIB + ".tmp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)
-        raise RuntimeError("nvcc failed building libfasttracks.so")
-    if verbose:
-        sys.stderr.write(r.stderr)
+        raise RuntimeError("nvcc failed linking libfasttracks.so")
     os.replace(LIB + ".tmp", LIB)
     return LIB
 

@@ -851,9 +851,11 @@ int ft_track_bins(ft_ctx *ctx, const ft_band *band, const ft_bank *bank, const i
     const size_t nb = static_cast<size_t>(n) * band->N * 4;
     if (!on_device) {
         void *buf = nullptr;
-        FT_TRY(ft_ctx_outbuf(ctx, nb + n * 8, &buf));
+        // the int64 template indices after the bins, at an aligned offset
+        const size_t off = (nb + 255) / 256 * 256;
+        FT_TRY(ft_ctx_outbuf(ctx, off + n * 8, &buf));
         db = static_cast<int *>(buf);
-        long long *tt = reinterpret_cast<long long *>(static_cast<char *>(buf) + nb);
+        long long *tt = reinterpret_cast<long long *>(static_cast<char *>(buf) + off);
         FT_CUDA(cudaMemcpyAsync(tt, templates, n * 8, cudaMemcpyHostToDevice, st));
         dt = tt;
     }

@@ -2,13 +2,18 @@
 // template bank in uniform coordinates (Sec. IV.A, App. A), cut into hyperboxes (Sec. IV.B).
 //
 // Templates are never stored: every thread derives its templates (kBtTPT of them, sharing
-// each row's records) from Philox counters and keeps the per-template terms of the canonical
-// bin rule in registers.  Each CTA evaluates up to kBtThreads templates of one box over all
-// SFTs; stages of S SFT rows (power row, FP32 velocity + weight, fixed-point time) are brought
-// into shared memory by bulk copies on two mbarrier-tracked buffers.  Per (template, SFT) the
-// work is integer phase arithmetic, a table cosine, the bin, one shared-memory read and one
-// add: the kernel is bound by instruction issue and shared-memory reads, not by HBM.  Every floating-point operation of the rule is an
-// explicit round-to-nearest intrinsic so that the compiler cannot contract or reorder it.
+// each row's records) from Philox counters and keeps the per-template terms of the track in
+// registers.  Each CTA evaluates up to kBtThreads templates of one box over all SFTs; stages
+// of S SFT rows (power row, FP32 velocity + weight, fixed-point time) are brought into shared
+// memory by bulk copies on two mbarrier-tracked buffers.
+//
+// The bin is the FP64 bin of Eq. (track), X = f0 (1 + v.n - a_p Omega cos(Omega t - phi_b))
+// T_SFT - k_lo rounded half up.  Per (template, SFT) the kernel first evaluates X in FP32
+// (integer orbit phase, second-order table cosine, FMA chain) with a derived error bound
+// delta; only when that value lies within delta of a rounding boundary (a fraction of about
+// 2 delta of all evaluations) is X recomputed in FP64 from the template's FP64 terms and the
+// SFT's FP64 velocity and time, so every bin equals the FP64 bin.  Then one shared-memory
+// read and one add: the kernel is bound by instruction issue, not by HBM.
 
 #include "ft_internal.cuh"
 #include "ft_ptx.cuh"
@@ -28,10 +33,13 @@ struct ft_binary_bank {
     int n_pad = 0;                 // rows of d_rowv / d_tq (N rounded up to kBtRowPad)
     float4 *d_rowv = nullptr;      // [n_pad] (v/c as FP32, weight); zero beyond N
     long long *d_tq = nullptr;     // [n_pad] round((t_mid - t0) 2^10)
-    float2 *d_costab = nullptr;    // [kBtTab + 1] full-turn cosine table (value, difference)
+    double *d_t64 = nullptr;       // [n_pad] t_mid - t0 (s), FP64
+    float4 *d_costab = nullptr;    // [kBtNodes][kBtSlots] the screen's cosine table
     // all-sky weights (band with detector tensors): per SFT D / sqrt(S_n) in FP32 as
     // (D00, D01, D02, D11), (D12, D22, |D|^2, tr D); zero beyond N
     float4 *d_rowd = nullptr;      // [n_pad][2]
+    unsigned long long *d_n64 = nullptr;  // running count of FP64 decisions
+    double delta = 0;              // screening bound of the last launch (bins)
 };
 
 namespace {
@@ -40,7 +48,19 @@ constexpr int kBtThreads = 512;              // templates per CTA
 constexpr int kBtTPT = 4;                    // templates per thread (they share each row's records)
 constexpr int kBtBlock = kBtThreads / kBtTPT;  // threads per CTA
 constexpr int kBtRowPad = 64;
-constexpr int kBtTab = 1024;  // intervals of the full-turn cosine table
+// The FP32 screen's cosine table: 128 nodes over the full turn, each stored once per lane
+// slot (8 slots: the four quarter-warps of a 128-bit shared load), so that lane l reads node
+// e from entry e 8 + (l mod 8) and a warp's 32 reads never share a bank: four wavefronts per
+// read whatever the nodes.  Entry e holds the Taylor coefficients of cos(2 pi e / 128 + b)
+// in the raw phase offset fb (b = fb kB): (C, S kB, C kB^2 / 2, S kB^3 / 6).  16 KB.
+constexpr int kBtNodes = 128;
+constexpr int kBtSlots = 8;
+constexpr int kBtTab = kBtNodes * kBtSlots;  // float4 entries
+constexpr int kBtSlow = 7;    // FP64 terms per template for the FP64 decisions
+// node e = round(phase 128 / 2^32); fb = (int)(phase << 7) is 2^7 x the signed remainder in
+// units of 2^-32 turns, so the angle past node e is b = fb kB rad
+constexpr double kB = 6.283185307179586476925286766559 / 549755813888.0;  // 2 pi / 2^39
+constexpr float kMagic = 12582912.0f;  // 1.5 2^23: t + kMagic rounds t to an integer in its low bits
 
 struct BtParams {
     double xlo[6], step[6];
@@ -56,10 +76,17 @@ struct BtParams {
     int W, N, S, n_stages;
     const float4 *rowv;
     const long long *tq;
-    const float2 *costab;          // (cos(i (pi/2) / 1024) in FP32, next minus this)
+    const double *v64;             // [N][3] v / c, FP64
+    const double *t64;             // [N] t_mid - t0, FP64
+    const float4 *costab;          // [kBtNodes][kBtSlots] Taylor coefficients (see kBtNodes)
     const float4 *rowd;            // null, or the all-sky weight records [n_pad][2]
+    float half_delta;              // screen: FP64 decision when |t - rint(t)| > 1/2 - delta
+    double vmax;                   // largest |v| / c of the band (window proof per CTA)
     double mu, sigma;
     double m1, sd1;                // one SFT's noise mean and deviation (2, 2 for power)
+    long long cta_base;            // CTA index of this launch's first CTA (launches are chunked)
+    double *slow;                  // [CTAs of the launch][kBtSlow][kBtThreads] FP64 terms
+    unsigned long long *n64;       // running count of FP64 decisions
     // eval mode (box_mode == 0): templates [first, first + count), CTA c takes kBtThreads of them
     long long first, count;
     float *s_out, *z_out;
@@ -72,11 +99,11 @@ struct BtParams {
     unsigned *status;
 };
 
-// ------------------------------------------------------------------ canonical rule
+// ------------------------------------------------------------------ templates
 //
-// Every step below is the canonical bin rule (header: the binary section): the same
-// operations in the same precision and order as its statement, so that the bins are a
-// function of (seed, template, SFT) alone.
+// The templates are a pure function of (seed, index): every FP64 step of their derivation
+// is an explicit round-to-nearest intrinsic, so that the compiler cannot contract or reorder
+// it and the host oracle derives the same lambda bit for bit.
 
 __device__ __forceinline__ double bt_u53(unsigned a, unsigned b)
 {
@@ -135,58 +162,108 @@ __device__ void bt_lambda(const BtParams &p, long long i, double lam[6])
     lam[2] = fmin(fmax(lam[2], -1.0), 1.0);
 }
 
-// cos(2 pi theta / 2^32): linear interpolation between entry theta >> 22 of the full-turn
-// table and the next, at the fraction given by the low 22 bits
-__device__ __forceinline__ float bt_cos_q32(unsigned theta, const float2 *tab)
-{
-    const float f = __fmul_rn(__uint2float_rn(theta & 0x3FFFFFu), 0x1p-22f);
-    const float2 e = tab[theta >> 22];
-    return __fmaf_rn(f, e.y, e.x);
-}
+// ------------------------------------------------------------------ the track
+//
+// Per template (FP64 once, then rounded): F = f0 T_SFT, K = floor(F) - k_lo,
+// t0 = F - floor(F), a = F n, A = F a_p Omega; the orbit frequency Omega / 2 pi in units
+// of 2^-54 turns/s (64-bit nu) and minus the top word of phi_b 2^64 (npsi).  Per SFT: the
+// 64-bit time t_q = round((t_mid - t0) 2^10).
+//
+// FP32 screen per (template, SFT), t = X - K:
+//   phase  ph = top word of (nu t_q) mod 2^64 + npsi, in 2^-32 turns, from three 32-bit
+//          multiplies (the low word's borrow is dropped: |error| < 1 unit);
+//   cosine node e = round(ph 128 / 2^32) of the 128-node table and the angle b past it:
+//          cos = C - S b - C b^2 / 2 + S b^3 / 6 (truncation <= |b|^4 / 24 + |b|^5 / 120
+//          with |b| <= pi / 128: 1.5e-8), three FMAs on the raw offset fb;
+//   t      = t0 + a.v - A cos (one FMA chain);
+//   bin    = K + rint(t) by the 1.5 2^23 rounding trick, and d = t - rint(t).
+// Its error against the exact real value is below the launch's delta (host: bt_delta); when
+// |d| > 1/2 - delta the FP64 decision replaces it (exact half-integers included).
 
 struct BtTmpl {
     int K;
-    float phi, F, nx, ny, nz, D;
-    float wx, wy;  // the sky vector's x and y to FP32 accuracy, for the all-sky weights
-    unsigned long long nu_q, psi_q;
+    float t0, ax, ay, az, A;
+    unsigned nlo, nhi, npsi;
+    float wx, wy, wz;  // the unit sky vector in FP32, for the all-sky weights
 };
 
-__device__ void bt_derive(const BtParams &p, const double lam[6], const float2 *tab, BtTmpl &t)
+// FP64 terms of the decision, slot q of the CTA: F - k_lo, F n (3), F a_p Omega, Omega,
+// 2 pi phi_b.  Returns whether every bin the track can reach (|v.n| <= vmax) lies in [0, W).
+__device__ bool bt_derive(const BtParams &p, const double lam[6], BtTmpl &t, double *sl, int q)
 {
-    const double F = __dmul_rn(lam[0], p.t_sft);
+    const double F = lam[0] * p.t_sft;
     const double Fl = floor(F);
-    t.K = static_cast<int>(__double2ll_rz(Fl) - p.k_lo);
-    t.phi = __double2float_rn(__dsub_rn(F, Fl));
-    t.F = __double2float_rn(F);
-    const double c2 = __dsub_rn(1.0, __dmul_rn(lam[2], lam[2]));
-    const float cd = __double2float_rn(__dsqrt_rn(c2 > 0.0 ? c2 : 0.0));
-    const unsigned ta = __double2uint_rz(__dmul_rn(lam[1], 4294967296.0));
-    t.nx = __fmul_rn(cd, bt_cos_q32(ta, tab));
-    t.ny = __fmul_rn(cd, bt_cos_q32(ta - 0x40000000u, tab));
-    // the weights follow the template's true direction, not the track's table cosine
+    t.K = static_cast<int>(static_cast<long long>(Fl) - p.k_lo);
+    t.t0 = __double2float_rn(F - Fl);
     double sa, ca;
-    sincospi(__dmul_rn(2.0, lam[1]), &sa, &ca);
-    const double cd64 = sqrt(c2 > 0.0 ? c2 : 0.0);
-    t.wx = __double2float_rn(cd64 * ca);
-    t.wy = __double2float_rn(cd64 * sa);
-    t.nz = __double2float_rn(lam[2]);
-    t.D = __double2float_rn(__dmul_rn(__dmul_rn(F, lam[3]), lam[4]));
-    const double nu = __ddiv_rn(lam[4], 6.283185307179586);
-    t.nu_q = __double2ull_rz(floor(__dadd_rn(__dmul_rn(nu, 18014398509481984.0), 0.5)));
-    t.psi_q = __double2ull_rz(__dmul_rn(lam[5], 18446744073709551616.0));
+    sincospi(2.0 * lam[1], &sa, &ca);
+    const double c2 = 1.0 - lam[2] * lam[2];
+    const double cd = sqrt(c2 > 0.0 ? c2 : 0.0);
+    const double n0 = cd * ca, n1 = cd * sa, n2 = lam[2];
+    const double A = F * lam[3] * lam[4];
+    t.ax = __double2float_rn(F * n0);
+    t.ay = __double2float_rn(F * n1);
+    t.az = __double2float_rn(F * n2);
+    t.A = __double2float_rn(A);
+    t.wx = __double2float_rn(n0);
+    t.wy = __double2float_rn(n1);
+    t.wz = __double2float_rn(n2);
+    const double nu = lam[4] * 0.15915494309189533577;  // Omega / 2 pi
+    const unsigned long long nu_q = __double2ull_rn(nu * 18014398509481984.0);
+    t.nlo = static_cast<unsigned>(nu_q);
+    t.nhi = static_cast<unsigned>(nu_q >> 32);
+    const unsigned long long psi_q = __double2ull_rz(lam[5] * 18446744073709551616.0);
+    t.npsi = 0u - static_cast<unsigned>(psi_q >> 32);
+    if (sl != nullptr) {
+        sl[0 * kBtThreads + q] = F - static_cast<double>(p.k_lo);
+        sl[1 * kBtThreads + q] = F * n0;
+        sl[2 * kBtThreads + q] = F * n1;
+        sl[3 * kBtThreads + q] = F * n2;
+        sl[4 * kBtThreads + q] = A;
+        sl[5 * kBtThreads + q] = lam[4];
+        sl[6 * kBtThreads + q] = 6.283185307179586476925286766559 * lam[5];
+    }
+    const double x = F - static_cast<double>(p.k_lo), reach = F * p.vmax + fabs(A) + 1e-3;
+    return floor(x - reach + 0.5) >= 0.0 && floor(x + reach + 0.5) <= static_cast<double>(p.W - 1);
 }
 
-__device__ __forceinline__ int bt_bin(const BtTmpl &t, float4 v, long long tq, const float2 *tab)
+// t = X - K of the FP32 screen (see above); tabl is this lane's slot of the table
+__device__ __forceinline__ float bt_t(const BtTmpl &t, float4 v, uint2 tq, const float4 *tabl)
 {
-    const unsigned long long ph = t.nu_q * static_cast<unsigned long long>(tq) - t.psi_q;
-    const float c = bt_cos_q32(static_cast<unsigned>(ph >> 32), tab);
-    const float a = __fmul_rn(v.z, t.nz);
-    const float b = __fmaf_rn(v.y, t.ny, a);
-    const float vn = __fmaf_rn(v.x, t.nx, b);
-    const float dop = __fmul_rn(t.F, vn);
-    const float m = __fmul_rn(t.D, c);
-    const float X = __fsub_rn(__fadd_rn(t.phi, dop), m);
-    return t.K + static_cast<int>(floorf(__fadd_rn(X, 0.5f)));
+    const unsigned ph = __umulhi(t.nlo, tq.x) + t.nlo * tq.y + t.nhi * tq.x + t.npsi;
+    const float4 e = tabl[((ph + (1u << 24)) >> 25) * kBtSlots];
+    const float fb = __int2float_rn(static_cast<int>(ph << 7));
+    const float c = __fmaf_rn(-fb, __fmaf_rn(fb, __fmaf_rn(-fb, e.w, e.z), e.y), e.x);
+    const float base = __fmaf_rn(v.x, t.ax, __fmaf_rn(v.y, t.ay, __fmaf_rn(v.z, t.az, t.t0)));
+    return __fmaf_rn(-t.A, c, base);
+}
+
+// rint(t) as an integer (|t| < 2^22) and whether t is within delta of a rounding boundary
+__device__ __forceinline__ int bt_round(float tv, float half_delta, bool &near)
+{
+    const float r = __fadd_rn(tv, kMagic);
+    const float d = __fsub_rn(tv, __fsub_rn(r, kMagic));
+    near = fabsf(d) > half_delta;
+    return __float_as_int(r) - __float_as_int(kMagic);
+}
+
+// The FP64 bin (band column) of one (template, SFT): Eq. (track) from the template's FP64
+// terms sl[0..6] (stride `st`) and the SFT's FP64 velocity and time.
+__device__ __noinline__ int bt_bin64(const double *sl, int st, const double *v, double t)
+{
+    const double vn = sl[st] * v[0] + sl[2 * st] * v[1] + sl[3 * st] * v[2];
+    const double X = (sl[0] + vn) - sl[4 * st] * cos(sl[5 * st] * t - sl[6 * st]);
+    return static_cast<int>(floor(X + 0.5));
+}
+
+// Bin of one (template, SFT): the screen, or the FP64 decision near a rounding boundary.
+__device__ __forceinline__ int bt_bin(const BtParams &p, const BtTmpl &t, const double *sl, int st,
+                                      int a, float4 v, uint2 tq, const float4 *tabl, bool &dec)
+{
+    const int kr = bt_round(bt_t(t, v, tq, tabl), p.half_delta, dec);
+    if (dec)
+        return bt_bin64(sl, st, p.v64 + 3ll * a, p.t64[a]);
+    return t.K + kr;
 }
 
 template <typename T>
@@ -205,6 +282,32 @@ template <>
 __device__ __forceinline__ float bt_load<__nv_bfloat16>(const unsigned char *row, int k)
 {
     return __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(row)[k]);
+}
+
+// acc += P[k] (0 outside the band) with an FP32 accumulator; 16-bit values go straight into
+// a mixed-precision FMA against 1 (exact product), with no conversion step.
+template <typename T>
+__device__ __forceinline__ void bt_add(float &acc, const unsigned char *row, int k, bool in);
+template <>
+__device__ __forceinline__ void bt_add<float>(float &acc, const unsigned char *row, int k, bool in)
+{
+    acc = __fadd_rn(acc, in ? reinterpret_cast<const float *>(row)[k] : 0.f);
+}
+template <>
+__device__ __forceinline__ void bt_add<__half>(float &acc, const unsigned char *row, int k, bool in)
+{
+    const unsigned short h = in ? reinterpret_cast<const unsigned short *>(row)[k] : 0;
+    asm("{\n\t.reg .b16 one;\n\tmov.b16 one, 0x3C00;\n\tfma.rn.f32.f16 %0, %1, one, %0;\n\t}"
+        : "+f"(acc)
+        : "h"(h));
+}
+template <>
+__device__ __forceinline__ void bt_add<__nv_bfloat16>(float &acc, const unsigned char *row, int k, bool in)
+{
+    const unsigned short h = in ? reinterpret_cast<const unsigned short *>(row)[k] : 0;
+    asm("{\n\t.reg .b16 one;\n\tmov.b16 one, 0x3F80;\n\tfma.rn.f32.bf16 %0, %1, one, %0;\n\t}"
+        : "+f"(acc)
+        : "h"(h));
 }
 
 // ------------------------------------------------------------------ kernels
@@ -253,6 +356,59 @@ __device__ __forceinline__ void fold2(float &hi, float &lo, float part)
     hi = s;
 }
 
+// The rows of one stage for this thread's templates.  CHECK: bins may leave [0, W) (then
+// they add 0 and are counted); without it every track of the CTA is proven inside.
+template <typename T, bool WEIGHTED, bool SKY, bool CHECK>
+__device__ __forceinline__ void bt_rows(const BtParams &p, const BtTmpl (&t)[kBtTPT], const bool (&valid)[kBtTPT],
+                                        const double *sl, int a0, int nr, const float4 *svb, const uint2 *tqs,
+                                        const unsigned char *rb, const float4 *sdb, const float4 *tabl,
+                                        float (&part)[kBtTPT], float (&partB)[kBtTPT], float (&partC)[kBtTPT],
+                                        int (&oob)[kBtTPT], unsigned &n64)
+{
+#pragma unroll 2
+    for (int r = 0; r < nr; ++r) {
+        const float4 v = svb[r];
+        const uint2 tq = tqs[r];
+        const unsigned char *row = rb + static_cast<size_t>(r) * p.row_bytes;
+        int k[kBtTPT];
+        bool dec[kBtTPT];
+        bool any = false;
+#pragma unroll
+        for (int u = 0; u < kBtTPT; ++u) {
+            k[u] = t[u].K + bt_round(bt_t(t[u], v, tq, tabl), p.half_delta, dec[u]);
+            any |= dec[u];
+        }
+        if (any) {
+            // near a rounding boundary: the FP64 bin decides
+            const int a = a0 + r;
+#pragma unroll
+            for (int u = 0; u < kBtTPT; ++u)
+                if (dec[u]) {
+                    k[u] = bt_bin64(sl + threadIdx.x + u * kBtBlock, kBtThreads, p.v64 + 3ll * a, p.t64[a]);
+                    n64 += valid[u] ? 1u : 0u;
+                }
+        }
+#pragma unroll
+        for (int u = 0; u < kBtTPT; ++u) {
+            const bool in = !CHECK || static_cast<unsigned>(k[u]) < static_cast<unsigned>(p.W);
+            if (CHECK)
+                oob[u] += in ? 0 : 1;
+            if (SKY) {
+                const float val = in ? bt_load<T>(row, k[u]) : 0.f;
+                const float rw = bt_sky_r(sdb[2 * r], sdb[2 * r + 1], t[u].wx, t[u].wy, t[u].wz);
+                part[u] = __fmaf_rn(rw, val, part[u]);
+                partB[u] = __fadd_rn(partB[u], rw);
+                partC[u] = __fmaf_rn(rw, rw, partC[u]);
+            } else if (WEIGHTED) {
+                const float val = in ? bt_load<T>(row, k[u]) : 0.f;
+                part[u] = __fmaf_rn(v.w, val, part[u]);
+            } else {
+                bt_add<T>(part[u], row, k[u], in);
+            }
+        }
+    }
+}
+
 template <typename T, bool WEIGHTED, bool SKY>
 __global__ void __launch_bounds__(kBtBlock) k_bt_eval(const BtParams p)
 {
@@ -264,19 +420,20 @@ __global__ void __launch_bounds__(kBtBlock) k_bt_eval(const BtParams p)
     long long *stq[2] = {reinterpret_cast<long long *>(sv[1] + p.S),
                          reinterpret_cast<long long *>(sv[1] + p.S) + p.S};
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(stq[1] + p.S);
-    float2 *tab = reinterpret_cast<float2 *>(bars + 2);
-    float4 *sd[2] = {reinterpret_cast<float4 *>(tab + kBtTab + 1 + 1), nullptr};  // 16-byte aligned
+    float4 *tab = reinterpret_cast<float4 *>(bars + 2);  // 16-byte aligned
+    float4 *sd[2] = {tab + kBtTab, nullptr};
     sd[1] = sd[0] + 2 * p.S;
 
     // this CTA's templates
+    const long long cta = p.cta_base + blockIdx.x;
     long long t_begin, t_end;
     if (p.box_mode) {
-        const long long box = blockIdx.x / p.tiles_per_box;
-        const long long tile = blockIdx.x % p.tiles_per_box;
+        const long long box = cta / p.tiles_per_box;
+        const long long tile = cta % p.tiles_per_box;
         t_begin = box * p.n_per_box + tile * kBtThreads;
         t_end = min(t_begin + kBtThreads, (box + 1) * p.n_per_box);
     } else {
-        t_begin = p.first + static_cast<long long>(blockIdx.x) * kBtThreads;
+        t_begin = p.first + cta * kBtThreads;
         t_end = min(t_begin + kBtThreads, p.first + p.count);
     }
     // this thread's templates: t_begin + threadIdx.x + u kBtBlock
@@ -293,7 +450,7 @@ __global__ void __launch_bounds__(kBtBlock) k_bt_eval(const BtParams p)
         ftp::mbar_init(&bars[1], 1);
         ftp::fence_mbar_init();
     }
-    for (int i = threadIdx.x; i <= kBtTab; i += kBtBlock)
+    for (int i = threadIdx.x; i < kBtTab; i += kBtBlock)
         tab[i] = p.costab[i];
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -302,13 +459,20 @@ __global__ void __launch_bounds__(kBtBlock) k_bt_eval(const BtParams p)
             bt_issue(p, 1, rows[1], sv[1], stq[1], sd[1], &bars[1]);
     }
 
+    // the templates' FP32 screen terms in registers, their FP64 terms in this CTA's slot of
+    // the launch scratch (read back by this thread only, for the FP64 decisions)
+    double *sl = p.slow + static_cast<size_t>(blockIdx.x) * (kBtSlow * kBtThreads);
     BtTmpl t[kBtTPT];
+    bool inside = true;
 #pragma unroll
     for (int u = 0; u < kBtTPT; ++u) {
         double lam[6];
         bt_lambda(p, valid[u] ? ti[u] : t_begin, lam);
-        bt_derive(p, lam, tab, t[u]);
+        inside &= bt_derive(p, lam, t[u], sl, threadIdx.x + u * kBtBlock);
     }
+    // one loop for the whole CTA: unchecked only when every track stays inside the band
+    inside = __syncthreads_and(inside) != 0;
+    const float4 *tabl = tab + (threadIdx.x & (kBtSlots - 1));
 
     float hi[kBtTPT], lo[kBtTPT];
     // all-sky weights: sum r, sum r^2 (r = (a^2 + b^2) / S_n), compensated like the sum
@@ -319,6 +483,7 @@ __global__ void __launch_bounds__(kBtBlock) k_bt_eval(const BtParams p)
         hi[u] = lo[u] = hiB[u] = loB[u] = hiC[u] = loC[u] = 0.f;
         oob[u] = 0;
     }
+    unsigned n64 = 0;
     bool failed = false;
     for (int st = 0; st < p.n_stages; ++st) {
         const int b = st & 1;
@@ -329,28 +494,13 @@ __global__ void __launch_bounds__(kBtBlock) k_bt_eval(const BtParams p)
         for (int u = 0; u < kBtTPT; ++u)
             part[u] = partB[u] = partC[u] = 0.f;
         if (ok) {
-            const unsigned char *rb = rows[b];
-#pragma unroll 2
-            for (int r = 0; r < nr; ++r) {
-                const float4 v = sv[b][r];
-                const long long tq = stq[b][r];
-                const unsigned char *row = rb + static_cast<size_t>(r) * p.row_bytes;
-#pragma unroll
-                for (int u = 0; u < kBtTPT; ++u) {
-                    const int k = bt_bin(t[u], v, tq, tab);
-                    const bool in = static_cast<unsigned>(k) < static_cast<unsigned>(p.W);
-                    const float val = in ? bt_load<T>(row, k) : 0.f;
-                    oob[u] += in ? 0 : 1;
-                    if (SKY) {
-                        const float rw = bt_sky_r(sd[b][2 * r], sd[b][2 * r + 1], t[u].wx, t[u].wy, t[u].nz);
-                        part[u] = __fmaf_rn(rw, val, part[u]);
-                        partB[u] = __fadd_rn(partB[u], rw);
-                        partC[u] = __fmaf_rn(rw, rw, partC[u]);
-                    } else {
-                        part[u] = WEIGHTED ? __fmaf_rn(v.w, val, part[u]) : __fadd_rn(part[u], val);
-                    }
-                }
-            }
+            const uint2 *tqs = reinterpret_cast<const uint2 *>(stq[b]);
+            if (inside)
+                bt_rows<T, WEIGHTED, SKY, false>(p, t, valid, sl, st * p.S, nr, sv[b], tqs, rows[b], sd[b], tabl,
+                                                 part, partB, partC, oob, n64);
+            else
+                bt_rows<T, WEIGHTED, SKY, true>(p, t, valid, sl, st * p.S, nr, sv[b], tqs, rows[b], sd[b], tabl,
+                                                part, partB, partC, oob, n64);
         }
         // compensated folds of the stage's partials (2Sum)
 #pragma unroll
@@ -367,6 +517,11 @@ __global__ void __launch_bounds__(kBtBlock) k_bt_eval(const BtParams p)
         }
         if (threadIdx.x < 32 && st + 2 < p.n_stages)
             bt_issue(p, st + 2, rows[b], sv[b], stq[b], sd[b], &bars[b]);
+    }
+    if (p.n64 != nullptr) {
+        const unsigned w64 = __reduce_add_sync(0xffffffffu, n64);
+        if ((threadIdx.x & 31) == 0 && w64 != 0)
+            atomicAdd(p.n64, static_cast<unsigned long long>(w64));
     }
     if (failed) {
         if (threadIdx.x == 0) {
@@ -423,7 +578,7 @@ __global__ void __launch_bounds__(kBtBlock) k_bt_eval(const BtParams p)
     const int n_here = static_cast<int>(t_end - t_begin);
     float last_s = INFINITY;
     long long last_t = -1;
-    ft_candidate *out = p.cand + static_cast<long long>(blockIdx.x) * p.k;
+    ft_candidate *out = p.cand + cta * p.k;
     for (int j = 0; j < p.k; ++j) {
         bool have = false;
         float bs = -INFINITY, bz = 0.f;
@@ -552,17 +707,32 @@ __global__ void k_bt_templates(const BtParams p, long long first, long long n, d
         lam_out[6 * i + d] = lam[d];
 }
 
-__global__ void k_bt_bins(const BtParams p, const long long *tmpl, long long n, int *bins)
+// Bins of templates tmpl[0..n) in every SFT: one CTA per template, the same screen and
+// FP64 decisions as the evaluation kernel.
+__global__ void __launch_bounds__(256) k_bt_bins(const BtParams p, const long long *tmpl, long long n, int *bins)
 {
+    __shared__ BtTmpl ts;
+    __shared__ double sl[kBtSlow * kBtThreads];
     const long long i = blockIdx.x;
     if (i >= n)
         return;
-    double lam[6];
-    bt_lambda(p, tmpl[i], lam);
-    BtTmpl t;
-    bt_derive(p, lam, p.costab, t);
-    for (int a = threadIdx.x; a < p.N; a += blockDim.x)
-        bins[i * p.N + a] = bt_bin(t, p.rowv[a], p.tq[a], p.costab);
+    if (threadIdx.x == 0) {
+        double lam[6];
+        bt_lambda(p, tmpl[i], lam);
+        BtTmpl t;
+        bt_derive(p, lam, t, sl, 0);
+        ts = t;
+    }
+    __syncthreads();
+    const BtTmpl t = ts;
+    for (int a = threadIdx.x; a < p.N; a += blockDim.x) {
+        const long long tq = p.tq[a];
+        bool dec;
+        bins[i * p.N + a] = bt_bin(p, t, sl, kBtThreads, a, p.rowv[a],
+                                   make_uint2(static_cast<unsigned>(tq), static_cast<unsigned>(
+                                                  static_cast<unsigned long long>(tq) >> 32)),
+                                   p.costab + (threadIdx.x & (kBtSlots - 1)), dec);
+    }
 }
 
 __global__ void k_bt_rowv(const double *v, const float *w, int N, int n_pad, float4 *out)
@@ -640,6 +810,35 @@ int elem_bytes(int dtype)
     return dtype == FT_F32 ? 4 : 2;
 }
 
+// The FP32 screen's error bound (bins) for this band and bank, against the exact real
+// t* = X - K (all terms below are bounds; u = 2^-24 is the FP32 unit roundoff):
+//   t0 = FP32(frac F) in [0, 1): u;
+//   a.v with a = FP32(F n), v = FP32(v / c): inputs 2u |a| |v| = 2u F|v| (Cauchy-Schwarz),
+//     three FMA roundings 3u (1 + F|v|) (every partial sum is below 1 + F|v|);
+//   A = FP32(F a_p Omega): u A;  the final FMA: u (1 + F|v| + A);
+//   the cosine (|c| <= 1): C's rounding 2^-25, the final FMA 2^-25, the inner FMAs and the
+//     scaled coefficients about 1e-8, truncation 1.5e-8: under 1.2e-7, times A;
+//   the orbit phase: the dropped borrow and fb's rounding to FP32 (2^-32 turn each), nu
+//     rounded to 2^-55 turn/s times the largest |t|, t rounded to 2^-11 s times the largest
+//     nu: times 2 pi A.
+// So delta = u (5 + 6 F|v| + 2 A) + A (1.2e-7 + e_phase), taken with a 1.5 safety factor
+// and the FP64 decision's own rounding (1e-9) added.  F, |v|, A and nu are the largest over
+// the bank and band.
+double bt_delta(const ft_band *band, const ft_binary_bank *bk)
+{
+    const double u = 0x1p-24;
+    const double F = std::fabs(bk->desc.hi[0]) * band->t_sft;
+    const double Fv = F * band->vmax;
+    const double A = F * std::fabs(bk->desc.hi[3]) * std::fabs(bk->desc.hi[4]);
+    double tmax = 0.0;
+    for (double t : band->h_dt)
+        tmax = std::max(tmax, std::fabs(t));
+    const double nu = std::fabs(bk->desc.hi[4]) / 6.283185307179586;
+    const double e_ph = 6.283185307179586 * (0x1p-31 + 0x1p-55 * tmax + 0x1p-11 * nu);
+    const double e = u * (5.0 + 6.0 * Fv + 2.0 * A) + A * (1.2e-7 + e_ph);
+    return 1.5 * e + 1e-9;
+}
+
 BtParams base_params(const ft_band *band, const ft_binary_bank *bk)
 {
     BtParams p;
@@ -665,7 +864,12 @@ BtParams base_params(const ft_band *band, const ft_binary_bank *bk)
     p.N = static_cast<int>(band->N);
     p.rowv = bk->d_rowv;
     p.tq = bk->d_tq;
+    p.v64 = band->d_v;
+    p.t64 = bk->d_t64;
     p.costab = bk->d_costab;
+    p.n64 = bk->d_n64;
+    p.half_delta = std::nextafter(static_cast<float>(0.5 - bk->delta), 0.0f);
+    p.vmax = band->vmax;
     p.rowd = band->d_D != nullptr ? bk->d_rowd : nullptr;
     p.mu = band->mu;
     p.m1 = band->m1;
@@ -688,21 +892,40 @@ int stage_rows(const ft_band *band)
 
 size_t eval_smem(const BtParams &p)
 {
-    return 2 * (static_cast<size_t>(p.S) * p.row_bytes + p.S * 24) + 16 + (kBtTab + 2) * sizeof(float2) +
+    return 2 * (static_cast<size_t>(p.S) * p.row_bytes + p.S * 24) + 16 + kBtTab * sizeof(float4) +
            (p.rowd != nullptr ? 2 * static_cast<size_t>(p.S) * 32 : 0);
 }
 
+// Launches n_cta CTAs in chunks of at most 8 waves: every chunk's CTAs keep their FP64
+// template terms in one scratch slot each (kBtSlow x kBtThreads doubles), reused by the next
+// chunk.  With cand_bytes > 0 the per-CTA candidate lists come first in the same scratch
+// (*cand set to them).
 template <typename T, bool Wt>
-int launch_t(long long n_cta, size_t smem, const BtParams &p, cudaStream_t st)
+int launch_t(ft_ctx *ctx, long long n_cta, size_t smem, BtParams p, size_t cand_bytes,
+             ft_candidate **cand, cudaStream_t st)
 {
     auto fn = p.rowd != nullptr ? k_bt_eval<T, false, true> : k_bt_eval<T, Wt, false>;
     FT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-    fn<<<static_cast<unsigned>(n_cta), kBtBlock, smem, st>>>(p);
-    FT_CUDA(cudaGetLastError());
+    int per_sm = 0;
+    FT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBtBlock, smem));
+    const long long chunk = std::min<long long>(n_cta, 8ll * std::max(per_sm, 1) * std::max(ctx->sm_count, 1));
+    const size_t off = (cand_bytes + 255) / 256 * 256;
+    void *scr = nullptr;
+    FT_TRY(ft_ctx_scratch(ctx, off + static_cast<size_t>(chunk) * kBtSlow * kBtThreads * sizeof(double), &scr));
+    if (cand != nullptr)
+        *cand = static_cast<ft_candidate *>(scr);
+    p.cand = static_cast<ft_candidate *>(scr);
+    p.slow = reinterpret_cast<double *>(static_cast<char *>(scr) + off);
+    for (long long c0 = 0; c0 < n_cta; c0 += chunk) {
+        p.cta_base = c0;
+        fn<<<static_cast<unsigned>(std::min(chunk, n_cta - c0)), kBtBlock, smem, st>>>(p);
+        FT_CUDA(cudaGetLastError());
+    }
     return FT_OK;
 }
 
-int launch_eval(const ft_band *band, long long n_cta, BtParams p, cudaStream_t st)
+int launch_eval(const ft_band *band, long long n_cta, BtParams p, size_t cand_bytes, ft_candidate **cand,
+                cudaStream_t st)
 {
     p.S = stage_rows(band);
     p.n_stages = static_cast<int>((band->N + p.S - 1) / p.S);
@@ -711,15 +934,18 @@ int launch_eval(const ft_band *band, long long n_cta, BtParams p, cudaStream_t s
         FT_FAIL(FT_ERR_RANGE, "binary: band rows too wide for the shared-memory stages");
     if (n_cta <= 0)
         return FT_OK;
-    if (n_cta > INT_MAX)
-        FT_FAIL(FT_ERR_RANGE, "binary: too many CTAs for one launch");
+    ft_ctx *ctx = band->ctx;
     const bool w = band->weighted;
     switch (band->dtype) {
-    case FT_F32: return w ? launch_t<float, true>(n_cta, smem, p, st) : launch_t<float, false>(n_cta, smem, p, st);
-    case FT_F16: return w ? launch_t<__half, true>(n_cta, smem, p, st) : launch_t<__half, false>(n_cta, smem, p, st);
+    case FT_F32:
+        return w ? launch_t<float, true>(ctx, n_cta, smem, p, cand_bytes, cand, st)
+                 : launch_t<float, false>(ctx, n_cta, smem, p, cand_bytes, cand, st);
+    case FT_F16:
+        return w ? launch_t<__half, true>(ctx, n_cta, smem, p, cand_bytes, cand, st)
+                 : launch_t<__half, false>(ctx, n_cta, smem, p, cand_bytes, cand, st);
     case FT_BF16:
-        return w ? launch_t<__nv_bfloat16, true>(n_cta, smem, p, st)
-                 : launch_t<__nv_bfloat16, false>(n_cta, smem, p, st);
+        return w ? launch_t<__nv_bfloat16, true>(ctx, n_cta, smem, p, cand_bytes, cand, st)
+                 : launch_t<__nv_bfloat16, false>(ctx, n_cta, smem, p, cand_bytes, cand, st);
     default: FT_FAIL(FT_ERR_ARG, "binary: unknown storage type");
     }
 }
@@ -805,25 +1031,36 @@ int ft_make_binary_bank(ft_ctx *ctx, const ft_band *band, const ft_binary_bank_d
         ft_binary_bank_destroy(b);
         return rc;
     };
-    // full-turn cosine table: cos(i 2 pi / 1024) from the host's libm in FP64, rounded
-    // to FP32, with the FP32 difference to the next entry (0 after the last)
-    float tc[kBtTab + 1];
-    for (int i = 0; i <= kBtTab; ++i)
-        tc[i] = static_cast<float>(std::cos(static_cast<double>(i) * 6.135923151542565e-03));
-    std::vector<float2> tab(kBtTab + 1);
-    for (int i = 0; i <= kBtTab; ++i)
-        tab[i] = make_float2(tc[i], i < kBtTab ? tc[i + 1] - tc[i] : 0.0f);
+    // the screen's cosine table: node e at angle 2 pi e / 128, the Taylor coefficients in
+    // the raw offset from the host's libm in FP64, rounded to FP32, once per lane slot
+    std::vector<float4> tab(kBtTab);
+    for (int e = 0; e < kBtNodes; ++e) {
+        const double ang = 6.283185307179586476925286766559 * e / kBtNodes;
+        const double C = std::cos(ang), S = std::sin(ang);
+        const float4 q = make_float4(static_cast<float>(C), static_cast<float>(S * kB),
+                                     static_cast<float>(C * kB * kB / 2.0), static_cast<float>(S * kB * kB * kB / 6.0));
+        for (int l = 0; l < kBtSlots; ++l)
+            tab[e * kBtSlots + l] = q;
+    }
+    std::vector<double> t64(b->n_pad, 0.0);
+    for (int a = 0; a < N; ++a)
+        t64[a] = band->h_dt[a];
     if (cudaMalloc(&b->d_rowv, static_cast<size_t>(b->n_pad) * sizeof(float4)) != cudaSuccess ||
         cudaMalloc(&b->d_tq, static_cast<size_t>(b->n_pad) * sizeof(long long)) != cudaSuccess ||
-        cudaMalloc(&b->d_costab, tab.size() * sizeof(float2)) != cudaSuccess) {
+        cudaMalloc(&b->d_t64, static_cast<size_t>(b->n_pad) * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&b->d_n64, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&b->d_costab, tab.size() * sizeof(float4)) != cudaSuccess) {
         ft_set_error("make_binary_bank: allocation failed");
         return fail(FT_ERR_OOM);
     }
     if (cudaMemcpy(b->d_tq, tq.data(), tq.size() * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(b->d_costab, tab.data(), tab.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpy(b->d_t64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->d_n64, 0, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemcpy(b->d_costab, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess) {
         ft_set_error("make_binary_bank: copy failed");
         return fail(FT_ERR_CUDA);
     }
+    b->delta = bt_delta(band, b);
     k_bt_rowv<<<(b->n_pad + 255) / 256, 256>>>(band->d_v, band->d_w, N, b->n_pad, b->d_rowv);
     if (band->d_D) {
         if (cudaMalloc(&b->d_rowd, static_cast<size_t>(b->n_pad) * 2 * sizeof(float4)) != cudaSuccess) {
@@ -848,6 +1085,8 @@ void ft_binary_bank_destroy(ft_binary_bank *b)
     Guard g(b->device);
     cudaFree(b->d_rowv);
     cudaFree(b->d_tq);
+    cudaFree(b->d_t64);
+    cudaFree(b->d_n64);
     cudaFree(b->d_costab);
     cudaFree(b->d_rowd);
     delete b;
@@ -861,6 +1100,22 @@ int ft_binary_bank_info(const ft_binary_bank *b, int64_t *n_templates, int64_t *
         *n_templates = b->n_templates;
     if (n_boxes)
         *n_boxes = b->n_boxes;
+    return FT_OK;
+}
+
+int ft_binary_decisions(ft_binary_bank *bank, uint64_t *n_fp64, double *delta)
+{
+    if (!bank)
+        FT_FAIL(FT_ERR_ARG, "binary_decisions: null bank");
+    Guard g(bank->device);
+    unsigned long long h = 0;
+    FT_CUDA(cudaDeviceSynchronize());
+    FT_CUDA(cudaMemcpy(&h, bank->d_n64, sizeof(h), cudaMemcpyDeviceToHost));
+    FT_CUDA(cudaMemset(bank->d_n64, 0, sizeof(unsigned long long)));
+    if (n_fp64)
+        *n_fp64 = h;
+    if (delta)
+        *delta = bank->delta;
     return FT_OK;
 }
 
@@ -902,9 +1157,11 @@ int ft_binary_track_bins(ft_ctx *ctx, const ft_band *band, const ft_binary_bank 
     int *db = reinterpret_cast<int *>(bins);
     if (!on_device) {
         void *buf = nullptr;
-        FT_TRY(ft_ctx_outbuf(ctx, nb + static_cast<size_t>(n) * 8, &buf));
+        // the int64 template indices after the bins, at an aligned offset
+        const size_t off = (nb + 255) / 256 * 256;
+        FT_TRY(ft_ctx_outbuf(ctx, off + static_cast<size_t>(n) * 8, &buf));
         db = static_cast<int *>(buf);
-        long long *t = reinterpret_cast<long long *>(static_cast<char *>(buf) + nb);
+        long long *t = reinterpret_cast<long long *>(static_cast<char *>(buf) + off);
         FT_CUDA(cudaMemcpyAsync(t, templates, static_cast<size_t>(n) * 8, cudaMemcpyHostToDevice, st));
         dt = t;
     }
@@ -948,7 +1205,7 @@ int ft_binary_eval(ft_ctx *ctx, const ft_band *band, const ft_binary_bank *bank,
     p.s_out = ds;
     p.z_out = dz;
     p.oob_out = doob;
-    FT_TRY(launch_eval(band, (n + kBtThreads - 1) / kBtThreads, p, st));
+    FT_TRY(launch_eval(band, (n + kBtThreads - 1) / kBtThreads, p, 0, nullptr, st));
     if (!out_on_device) {
         FT_CUDA(cudaMemcpyAsync(s_out, ds, nn * 4, cudaMemcpyDeviceToHost, st));
         if (z_out)
@@ -980,8 +1237,6 @@ int binary_topk(ft_ctx *ctx, const ft_band *band, const ft_binary_bank *bank, in
         FT_FAIL(FT_ERR_RANGE, "binary_topk_per_box: boxes too large");
     const size_t cand_bytes = static_cast<size_t>(n_cta) * k * sizeof(ft_candidate);
     const size_t out_bytes = static_cast<size_t>(bank->n_boxes) * k * sizeof(ft_candidate);
-    void *scr = nullptr;
-    FT_TRY(ft_ctx_scratch(ctx, cand_bytes, &scr));
     ft_candidate *dout = out;
     if (!out_on_device) {
         void *ob = nullptr;
@@ -994,9 +1249,9 @@ int binary_topk(ft_ctx *ctx, const ft_band *band, const ft_binary_bank *bank, in
     p.gate_min = gate_min;
     p.tiles_per_box = static_cast<int>(tiles);
     p.k = k;
-    p.cand = static_cast<ft_candidate *>(scr);
-    FT_TRY(launch_eval(band, n_cta, p, st));
-    k_bt_merge<<<static_cast<unsigned>(bank->n_boxes), 256, 0, st>>>(p.cand, p.tiles_per_box, k, dout);
+    ft_candidate *cand = nullptr;
+    FT_TRY(launch_eval(band, n_cta, p, cand_bytes, &cand, st));
+    k_bt_merge<<<static_cast<unsigned>(bank->n_boxes), 256, 0, st>>>(cand, p.tiles_per_box, k, dout);
     FT_CUDA(cudaGetLastError());
     if (!out_on_device) {
         FT_CUDA(cudaMemcpyAsync(out, dout, out_bytes, cudaMemcpyDeviceToHost, st));
