@@ -2,6 +2,7 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--dtype f16|bf16|f32] [--n-sky 10000] [--no-cpu-baseline] [--no-e2e]
+                    [--no-batch] [--batch-steps 2] [--workload search|batch|surrogate|binary]
 
 One step = the whole hot path over the search-shaped workload: for every template of the
 bank (180 f0 x 20 f1 x 1e4 sky = 3.6e7 templates) and every SFT (2 detectors x 1 yr at 70%
@@ -9,6 +10,12 @@ duty = 24,419 SFTs) the track bin, the power gather and the sum, then the critic
 and the top-10 per 0.01 Hz sub-band (ft_topk_per_band: one evaluation kernel with the
 selection fused in, plus one merge kernel).  Inputs are synthetic (seeded) and resident in
 HBM before timing; L2 is flushed (256 MB write) between timed steps, outside the events.
+
+The same line carries: the precision comparison (FP16, BF16 and plain FP32 storage, each
+timed on the full bank; relative error and per-sub-band candidate sets against the oracle on
+every template of a 1-in-100 sky sub-bank, which is also the CPU baseline's sample); the end-
+to-end rate from host buffers; and the batching workload (64 bands at the stated sky
+density, one persistent graph-captured launch per step, against the per-band loop).
 
 Under torchrun (N > 1) every rank runs its own replica of the workload (weak scaling, no
 data-path collective); rank 0 prints the JSON line.
@@ -221,19 +228,16 @@ def run_reference(args):
     return 0
 
 
-def run_batch(args):
+def batch_measure(args, ctx, local, sky_scale, steps, warmup, loop_steps, cpu_seconds=None):
     """The batching workload: 64 bands (0.05-0.5 Hz wide, 50-500 Hz, N_sky ~ f^2, 10 f1) on
     the same 1-yr 2-detector timeline, searched by one persistent graph-captured launch,
     against a per-band loop of the single-band path.  Power is chi^2_2 drawn on the device
-    with a seeded generator (the band matrices total several GB)."""
+    with a seeded generator (the band matrices total several GB).  Returns a dict."""
     import torch
 
     import ftsynth
     import paper_2411_18370_b300 as ft
 
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    ctx = ft.create(local)
     T = ftsynth.T_SFT
     n_slots = int(round(ftsynth.YEAR_S / T))
     starts = ftsynth.timeline(2, n_slots, T, 0.7, ftsynth.rng(3, 1))
@@ -241,7 +245,7 @@ def run_batch(args):
     v = np.concatenate([ftsynth.detector_velocity(st + 0.5 * T, X) for X, st in enumerate(starts)])
     n_sft = [len(st) for st in starts]
     N = len(t_mid)
-    specs = ftsynth.batch_bands(64, args.sky_scale)
+    specs = ftsynth.batch_bands(64, sky_scale)
 
     def band_power(b):
         """(power [N, W] on the device, first bin) of band b: chi^2_2 with a seeded generator."""
@@ -253,6 +257,7 @@ def run_batch(args):
                         device="cuda").exponential_(0.5, generator=g)
         return P, sp["k_band"] - wl
 
+    t_setup = time.perf_counter()
     bands, banks, evals = [], [], 0
     for b, sp in enumerate(specs):
         P, k_lo = band_power(b)
@@ -282,10 +287,10 @@ def run_batch(args):
     n_sub = sum(b.n_subbands for b in banks)
     out = torch.empty(n_sub * k * 16, dtype=torch.uint8, device="cuda")
     batch_step = lambda: batch.run(out, stream=stream)
-    steps = max(2, args.steps)
+    setup_s = time.perf_counter() - t_setup
     with ClockSampler(local) as clk:
-        t_batch = time_steps(batch_step, steps, args.warmup, stream, flush)
-    t_loop = time_steps(loop_step, max(2, steps // 2), 1, stream, flush)
+        t_batch = time_steps(batch_step, steps, warmup, stream, flush)
+    t_loop = time_steps(loop_step, loop_steps, 1, stream, flush)
     ctx.check_status()
     # the two paths must select the same candidates (identical per-tile code, same sums up
     # to accumulation order); report how many sub-bands differ
@@ -296,19 +301,16 @@ def run_batch(args):
     esize = ESIZE[args.dtype]
     achieved_gbs = evals * esize / (mb / 1e3) / 1e9
     peak_max_clk = 148 * SMEM_BYTES_PER_CLK_PER_SM * 2032e6 / 1e9
-    line = {
-        "metric": METRIC, "value": evals / (mb / 1e3), "unit": UNIT, "n_gpus": 1,
-        "steps": steps, "warmup": args.warmup, "ms_per_step": mb, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": f"{args.dtype}-storage/f32-accumulate", "data": "synthetic",
-        "config": {"workload": f"64-band batch: widths 0.05-0.5 Hz, starts 50-500 Hz, N_sky = "
-                               f"{args.sky_scale} x 1e3 (f/50)^2 clamped, 10 f1, 2 det x 1 yr "
-                               f"({N} SFTs)", "storage": args.dtype, "bands": len(bands),
-                   "templates": int(sum(b.n_templates for b in banks)), "evals_per_step": evals,
-                   "l2": "flushed between timed steps"},
-        "batch": {"tile_f0": batch.tile_f0, "stages": batch.stages, "rows_per_stage":
-                  batch.rows_per_stage, "resident_ctas": batch.n_ctas, "create_s": create_s,
-                  "gpu_launches_per_step": 2},
-        "per_band_loop": {"value": evals / (ml / 1e3), "ms_per_step": ml,
+    res = {
+        "value": evals / (mb / 1e3), "unit": UNIT, "ms_per_step": mb, "steps": steps, "warmup": warmup,
+        "workload": f"64-band batch: widths 0.05-0.5 Hz, starts 50-500 Hz, N_sky = {sky_scale} x 1e3 "
+                    f"(f/50)^2 clamped to [1e3, 1e5], 10 f1, 2 det x 1 yr ({N} SFTs)",
+        "storage": args.dtype, "bands": len(bands),
+        "templates": int(sum(b.n_templates for b in banks)), "evals_per_step": evals,
+        "launch": {"tile_f0": batch.tile_f0, "stages": batch.stages, "rows_per_stage": batch.rows_per_stage,
+                   "resident_ctas": batch.n_ctas, "create_s": create_s, "setup_s": setup_s,
+                   "gpu_launches_per_step": 2, "kind": "one persistent launch + merge, CUDA graph"},
+        "per_band_loop": {"value": evals / (ml / 1e3), "ms_per_step": ml, "steps": loop_steps,
                           "gpu_launches_per_step": 2 * len(bands)},
         "speedup_vs_loop": ml / mb, "subbands_with_different_sets": differ,
         "measured_gather_roof": {"evals_per_s": roof_e, "frac": (evals / (mb / 1e3)) / roof_e,
@@ -321,10 +323,10 @@ def run_batch(args):
                                    "2032 MHz max SM clock",
                      "algorithmic_bytes_per_launch": evals * esize, "bytes_per_eval": esize,
                      "traffic": None},
-        "gpu_launches": 2 * steps,
+        "l2": "flushed between timed steps",
         "clocks": clk.summary(),
     }
-    if not args.no_cpu_baseline:
+    if cpu_seconds:
         # the oracle on a template sample of the middle band (its power copied to the host)
         b = len(specs) // 2
         sp = specs[b]
@@ -334,11 +336,46 @@ def run_batch(args):
         del P
         bank_b = ftsynth.Bank(k0=sp["k_band"], n_f0=sp["n_bins"], f1=ftsynth.f1_grid(10, -1e-9, 0.0),
                               sky=ftsynth.fibonacci_sky(sp["n_sky"]), subband_bins=18)
-        cb, _, _ = cpu_baseline(sfts_b, bank_b, args.cpu_seconds)
+        cb, _, _ = cpu_baseline(sfts_b, bank_b, cpu_seconds)
         cb.pop("seconds")
         cb["sample"] = (f"band {b} of the batch ({sp['n_bins']} f0 bins x 10 f1 x {sp['n_sky']} sky "
                         f"points): " + cb["sample"])
-        line["cpu_baseline"] = cb
+        res["cpu_baseline"] = cb
+    batch.close()
+    for bk in banks:
+        bk.close()
+    for bd in bands:
+        bd.close()
+    del flushbuf, out, cands
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_batch(args):
+    """--workload batch: the batching workload's own JSON line."""
+    import torch
+
+    import paper_2411_18370_b300 as ft
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    ctx = ft.create(local)
+    r = batch_measure(args, ctx, local, args.sky_scale, max(2, args.steps), args.warmup,
+                      max(1, args.steps // 2), None if args.no_cpu_baseline else args.cpu_seconds)
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": r["steps"],
+        "warmup": r["warmup"], "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": f"{args.dtype}-storage/f32-accumulate",
+        "data": "synthetic",
+        "config": {"workload": r["workload"], "storage": r["storage"], "bands": r["bands"],
+                   "templates": r["templates"], "evals_per_step": r["evals_per_step"], "l2": r["l2"]},
+        "batch": r["launch"], "per_band_loop": r["per_band_loop"], "speedup_vs_loop": r["speedup_vs_loop"],
+        "subbands_with_different_sets": r["subbands_with_different_sets"],
+        "measured_gather_roof": r["measured_gather_roof"], "roofline": r["roofline"],
+        "gpu_launches": 2 * r["steps"], "clocks": r["clocks"],
+    }
+    if "cpu_baseline" in r:
+        line["cpu_baseline"] = r["cpu_baseline"]
     print(json.dumps(line), flush=True)
     return 0
 
@@ -518,6 +555,9 @@ def main():
     ap.add_argument("--k", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=2)
+    ap.add_argument("--sub-sky-stride", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-s", type=float, default=4.0)
     ap.add_argument("--workload", default="search", choices=["search", "batch", "surrogate", "binary"])
@@ -578,16 +618,18 @@ def main():
     def flush():
         flushbuf.fill_(1)
 
-    def mk(dtype):
+    def mk(dtype, bk_desc=bank):
         band = ft.load_sfts(ctx, P32d, sfts.t_mid, sfts.v, sfts.n_sft, sfts.k_lo, sfts.t_sft,
                             sfts.t0, dtype=dtype, s_n=sfts.s_n)
-        bk = ft.make_bank(ctx, band, bank.k0, bank.n_f0, bank.f1, bank.sky, bank.subband_bins)
+        bk = ft.make_bank(ctx, band, bk_desc.k0, bk_desc.n_f0, bk_desc.f1, bk_desc.sky, bk_desc.subband_bins)
         return band, bk
 
     cand = torch.empty(bank.n_subbands * args.k * 16, dtype=torch.uint8, device="cuda")
     evals = bank.n_templates * sfts.n_total
     runs = {}
-    for dtype in dict.fromkeys([args.dtype, "f32"]):
+    # the chosen storage type, then the others of the precision comparison (plain FP32 and
+    # BF16), each timed over the full bank
+    for dtype in dict.fromkeys([args.dtype, "f32", "bf16", "f16"]):
         band, bk = mk(dtype)
         assert bk.window_safe
         step = lambda: ft.topk_per_band(ctx, band, bk, args.k, cand, stream=stream)
@@ -629,7 +671,8 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": chosen["mean_ms_max"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": f"{args.dtype}-storage/f32-accumulate", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": f"{args.dtype}-storage/f32-accumulate",
+        "data": "synthetic",
         "config": workload_desc(sfts, bank, args.dtype),
         "roofline": roofline,
         "gpu_launches": 2 * args.steps,
@@ -637,6 +680,8 @@ def main():
         "plain_fp32": {"value": ws * evals / (runs["f32"]["mean_ms_max"] / 1e3),
                        "ms_per_step": runs["f32"]["mean_ms_max"], "clocks": runs["f32"]["clocks"],
                        "frac_of_measured_gather_roof": (evals / (runs["f32"]["mean_ms_max"] / 1e3)) / roof32_e},
+        "precision": {d: {"value": ws * evals / (r["mean_ms_max"] / 1e3), "ms_per_step": r["mean_ms_max"],
+                          "steps": len(r["times"])} for d, r in runs.items()},
         # the bare inner loop (rows resident in shared memory, no tables or pipeline), run in
         # the same process: the ceiling this kernel's design can reach on this GPU
         "measured_gather_roof": {"evals_per_s": roof_e, "evals_per_clk_per_sm": roof_c,
@@ -645,17 +690,57 @@ def main():
     }
 
     if rank == 0 and not args.no_cpu_baseline:
-        cb, samp, s_or = cpu_baseline(sfts, bank, args.cpu_seconds)
-        out["cpu_baseline"] = {k: v for k, v in cb.items() if k != "seconds"}
-        # relative error of each storage type at the oracle's sample (computed in this leg)
-        errs = {}
-        idx = torch.from_numpy(samp.astype(np.int64)).cuda()
-        for dtype, r in runs.items():
-            s_d = torch.empty(bank.n_templates, dtype=torch.float32, device="cuda")
-            ft.eval_statistic(ctx, r["band"], r["bank"], s_d, stream=stream)
-            errs[dtype] = rel_error(s_d[idx].cpu().numpy(), s_or)
-            del s_d
+        # The oracle on every template of a sub-bank of the same bank (every f0 and f1, one
+        # sky point in 100): its CPU rate, and for each storage type the GPU's relative error
+        # and per-sub-band top-k sets on that sub-bank against the oracle's.
+        import oracle
+
+        sub = ftsynth.Bank(k0=bank.k0, n_f0=bank.n_f0, f1=bank.f1, sky=bank.sky[::args.sub_sky_stride],
+                           subband_bins=bank.subband_bins)
+        t0 = time.perf_counter()
+        s_or, _ = oracle.statistic(sfts, sub)
+        dt = time.perf_counter() - t0
+        ev = sub.n_templates * sfts.n_total
+        out["cpu_baseline"] = {"value": ev / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                               "sample": f"every template of a sub-bank of the same bank ({bank.n_f0} f0 x "
+                                         f"{bank.n_f1} f1 x {sub.n_sky} sky points, one in "
+                                         f"{args.sub_sky_stride}) x all {sfts.n_total} SFTs ({ev:.3g} evals, "
+                                         f"{dt:.1f} s, FP64, OpenMP over templates)"}
+        k = args.k
+        o_idx, o_val = oracle.topk_per_subband(s_or, sub, k + 1)
+        n = sfts.n_total
+        # near-tie margins: the oracle's k-th and (k+1)-th values closer than twice the storage
+        # type's 6-sigma error of s (one rounding per stored value, unit roundoff u, independent:
+        # sigma(s)/s = u sqrt(2 / (3 N)) for exponential power); FP32: 2e-6
+        u = {"f16": 2.0 ** -11, "bf16": 2.0 ** -8}
+        agree, errs = {}, {}
+        for dtype in runs:
+            band_s, bk_s = mk(dtype, sub)
+            s_g = np.empty(sub.n_templates, np.float32)
+            ft.eval_statistic(ctx, band_s, bk_s, s_g)
+            errs[dtype] = rel_error(s_g, s_or)
+            c = np.zeros((sub.n_subbands, k), dtype=ft.CANDIDATE_DTYPE)
+            ft.topk_per_band(ctx, band_s, bk_s, k, c)
+            margin = 2 * 6 * u[dtype] * math.sqrt(2.0 / (3.0 * n)) if dtype in u else 2e-6
+            equal, ties, differ = 0, [], 0
+            for b in range(sub.n_subbands):
+                got = set(int(x) for x in c["template_idx"][b] if x >= 0)
+                want = set(int(x) for x in o_idx[b, :k] if x >= 0)
+                if got == want:
+                    equal += 1
+                    continue
+                gap = abs(o_val[b, k - 1] - o_val[b, k]) / abs(o_val[b, k - 1])
+                if gap < margin:
+                    ties.append({"subband": b, "rel_gap_kth_next": float(gap)})
+                else:
+                    differ += 1
+            agree[dtype] = {"subbands": sub.n_subbands, "equal_sets": equal, "near_ties": ties,
+                            "differ_beyond_margin": differ, "near_tie_margin_rel": margin}
+            bk_s.close()
+            band_s.close()
         out["rel_error_vs_oracle"] = errs
+        out["candidate_sets_vs_oracle"] = {"sample": f"the {sub.n_templates}-template sub-bank above, "
+                                                     f"top-{k} per 0.01 Hz sub-band", **agree}
 
     if not args.no_e2e:
         # end to end through the C ABI with host buffers: H2D of the SFT power and metadata,
@@ -671,8 +756,8 @@ def main():
             bk.close()
             band.close()
 
-        e2e_steps = max(3, args.steps // 4)
-        for _ in range(2):
+        e2e_steps = args.steps
+        for _ in range(args.warmup):
             e2e_step()
         barrier()
         wall = []
@@ -690,6 +775,20 @@ def main():
         out["e2e"] = {"value": ws * evals / e2e_mean, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_mean,
                       "steps": e2e_steps, "gpu_launches_per_step": 4}
+
+    for r in runs.values():
+        r["bank"].close()
+        r["band"].close()
+    del P32d
+    torch.cuda.empty_cache()
+    if not args.no_batch:
+        # the batching workload at its stated sky density, one persistent graph-captured
+        # launch per step, against the per-band loop (each rank its own replica)
+        b = batch_measure(args, ctx, local, 1.0, args.batch_steps, args.warmup, 1)
+        b["ms_per_step"] = max_over_ranks(b["ms_per_step"])
+        b["value"] = ws * b["evals_per_step"] / (b["ms_per_step"] / 1e3)
+        out["batch"] = b
+        out["gpu_launches"] += 2 * args.batch_steps
 
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -34,6 +34,7 @@
 #ifndef FASTTRACKS_H
 #define FASTTRACKS_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -81,6 +82,11 @@ FT_API void ft_destroy(ft_ctx *ctx);
 /* Synchronise `stream` and report any device-side failure recorded since the last check
  * (FT_ERR_TIMEOUT), then clear it. */
 FT_API int ft_check_status(ft_ctx *ctx, void *stream);
+
+/* Device bytes the context holds for scratch (per-CTA candidate lists and the like, grown on
+ * demand by the searches) and for staging host outputs (nullable pointers).  A diagnostic:
+ * the paper has no counterpart.  Errors: FT_ERR_ARG (null ctx). */
+FT_API int ft_ctx_memory(const ft_ctx *ctx, size_t *scratch_bytes, size_t *staging_bytes);
 
 /* ----------------------------------------------------------------------------- SFTs --
  * A narrow band of normalised SFT power, P = 4|x~|^2/(T_SFT S_n) (Sec. II.B, Eq. (s_tf)),

@@ -147,7 +147,7 @@ def load_library(path):
     L.or_injections.argtypes = [ctypes.POINTER(_InjProblem), ctypes.c_void_p, ctypes.c_int64,
                                 ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
                                 ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
-                                ctypes.c_void_p]
+                                ctypes.c_void_p, ctypes.c_void_p]
     return L
 
 
@@ -305,9 +305,10 @@ def inj_power(kabs, alpha, run_id, seed, amp, noise_scale=1.0):
 
 
 def injections(sfts, bank, D, inj, first_id, seed, K=64, half_f0=2, H=160, noise_scale=1.0,
-               w=None):
+               w=None, with_second=False):
     """Independent injection-recovery runs (run r uses run id first_id + r): max z over the
-    local bank, argmax template and out-of-window reads.  inj: structured INJ_DTYPE array."""
+    local bank, argmax template and out-of-window reads (and, with_second, the second largest
+    z of the local bank).  inj: structured INJ_DTYPE array."""
     keep = dict(t_mid=_c(sfts.t_mid, np.float64), v=_c(sfts.v, np.float64),
                 s_n=_c(sfts.s_n, np.float64), D=_c(D, np.float64), f1=_c(bank.f1, np.float64),
                 sky=_c(bank.sky, np.float64),
@@ -333,10 +334,11 @@ def injections(sfts, bank, D, inj, first_id, seed, K=64, half_f0=2, H=160, noise
     mz = np.empty(n, np.float64)
     am = np.empty(n, np.int64)
     oob = np.empty(n, np.int64)
+    z2 = np.empty(n, np.float64)
     lib().or_injections(ctypes.byref(p), arr.ctypes.data, n, int(first_id), int(seed), int(K),
                         int(half_f0), int(H), float(noise_scale), mz.ctypes.data, am.ctypes.data,
-                        oob.ctypes.data)
-    return mz, am, oob
+                        oob.ctypes.data, z2.ctypes.data)
+    return (mz, am, oob, z2) if with_second else (mz, am, oob)
 
 
 def pdet_q(s_n, t_sft, D, inj, w=None):

@@ -202,12 +202,14 @@ double or_inj_power(int64_t kabs, int64_t a, uint64_t run_id, uint64_t seed, dou
     return r * r + amp * amp + 2.0 * amp * r * cos(2.0 * M_PI * or_uniform24(o[1]));
 }
 
-/* One run: returns max z over the local bank, the argmax template index and the number of
- * reads outside the generated window.  h0 is in the units of sqrt(S_n T_SFT) of the data;
- * half_f0 and H set the local f0 span and the window half-width. */
+/* One run: returns max z over the local bank, the argmax template index, the number of
+ * reads outside the generated window and (second_z, nullable) the second largest z of the
+ * local bank, so that a caller can tell near-ties of the loudest template apart.  h0 is in the
+ * units of sqrt(S_n T_SFT) of the data; half_f0 and H set the local f0 span and the window
+ * half-width. */
 void or_injection(const or_inj_problem *p, const or_inj *inj_in, uint64_t run_id, uint64_t seed,
                   int K, int half_f0, int H, double noise_scale, double *max_z, int64_t *argmax,
-                  int64_t *oob_out)
+                  int64_t *oob_out, double *second_z)
 {
     or_inj inj = *inj_in;
     int64_t *sky = malloc(sizeof(int64_t) * K);
@@ -257,6 +259,7 @@ void or_injection(const or_inj_problem *p, const or_inj *inj_in, uint64_t run_id
             s[t] += w * P[q + H];
         }
     }
+    double second = -INFINITY;
     for (int64_t t = 0; t < ntl; t++) {
         int64_t jj = j_lo + t % nf0;
         int64_t r = t / nf0;
@@ -264,13 +267,18 @@ void or_injection(const or_inj_problem *p, const or_inj *inj_in, uint64_t run_id
         int64_t tg = (sky[ks_i] * p->n_f1 + if1) * p->n_f0 + jj;
         double z = (s[t] - mu) / sigma;
         if (z > best || (z == best && tg < best_t)) {
+            second = best;
             best = z;
             best_t = tg;
+        } else if (z > second) {
+            second = z;
         }
     }
     *max_z = best;
     *argmax = best_t;
     *oob_out = oob;
+    if (second_z)
+        *second_z = second;
     free(s);
     free(P);
     free(sky);
@@ -279,12 +287,12 @@ void or_injection(const or_inj_problem *p, const or_inj *inj_in, uint64_t run_id
 /* Many independent runs (OpenMP over runs): run r uses run id first_id + r. */
 void or_injections(const or_inj_problem *p, const or_inj *inj, int64_t n, uint64_t first_id,
                    uint64_t seed, int K, int half_f0, int H, double noise_scale, double *max_z,
-                   int64_t *argmax, int64_t *oob)
+                   int64_t *argmax, int64_t *oob, double *second_z)
 {
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t r = 0; r < n; r++)
         or_injection(p, inj + r, first_id + (uint64_t)r, seed, K, half_f0, H, noise_scale,
-                     max_z + r, argmax + r, oob + r);
+                     max_z + r, argmax + r, oob + r, second_z ? second_z + r : NULL);
 }
 
 /* ---------------------------------------------------------------- semi-analytic q */

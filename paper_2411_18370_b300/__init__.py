@@ -103,6 +103,7 @@ def lib():
             "ft_binary_bank_destroy": (None, [_P]),
             "ft_binary_bank_info": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
             "ft_binary_templates": (_I, [_P, _P, _I64, _I64, _P, _P]),
+            "ft_ctx_memory": (_I, [_P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
             "ft_binary_decisions": (_I, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]),
             "ft_binary_track_bins": (_I, [_P, _P, _P, _P, _I64, _P, _I, _P]),
             "ft_binary_eval": (_I, [_P, _P, _P, _I64, _I64, _P, _P, _P, _I, _P]),
@@ -164,6 +165,32 @@ def _ptr(x):
     return x.ctypes.data, False
 
 
+def _nbytes(x):
+    if _is_torch(x):
+        return x.numel() * x.element_size()
+    return int(x.nbytes)
+
+
+def _need(x, n_bytes, what):
+    """Raise ValueError unless buffer x holds at least n_bytes (the library writes that many)."""
+    if x is None:
+        return
+    if _nbytes(x) < n_bytes:
+        raise ValueError(f"{what}: buffer of {_nbytes(x)} bytes, the call writes {n_bytes}")
+
+
+def _gate_ptr(gate, n_templates, what):
+    """Device pointer of a gate: a contiguous CUDA float32 tensor of n_templates values."""
+    pg, gdev = _ptr(gate)
+    if not gdev:
+        raise ValueError(f"{what}: gate must be a CUDA tensor")
+    if str(gate.dtype) != "torch.float32":
+        raise ValueError(f"{what}: gate must be float32")
+    if gate.numel() != n_templates:
+        raise ValueError(f"{what}: gate has {gate.numel()} values, the bank {n_templates} templates")
+    return pg
+
+
 def _stream(stream, on_device):
     if stream is not None:
         return stream if isinstance(stream, int) else stream.cuda_stream
@@ -189,6 +216,12 @@ class Context:
         if self.handle:
             lib().ft_destroy(self.handle)
             self.handle = None
+
+    def memory(self):
+        """ft_ctx_memory: (scratch bytes, staging bytes) the context holds on its device."""
+        a, b = ctypes.c_size_t(0), ctypes.c_size_t(0)
+        _check(lib().ft_ctx_memory(self.handle, ctypes.byref(a), ctypes.byref(b)))
+        return int(a.value), int(b.value)
 
     def check_status(self, stream=None):
         _check(lib().ft_check_status(self.handle, _stream(stream, True)))
@@ -320,12 +353,17 @@ def binary_track_bins(ctx, band, bank, templates, out, stream=None):
     pb, dev2 = _ptr(out)
     if dev != dev2:
         raise ValueError("templates and out must both be host or both device")
+    if str(templates.dtype) not in ("int64", "torch.int64"):
+        raise ValueError("binary_track_bins: templates must be int64")
+    _need(out, 4 * int(templates.shape[0]) * band.n_sft, "binary_track_bins out")
     _check(lib().ft_binary_track_bins(ctx.handle, band.handle, bank.handle, pt, int(templates.shape[0]),
                                       pb, int(dev), _stream(stream, dev)))
 
 
 def binary_eval(ctx, band, bank, first, n, s_out, z_out=None, n_oob_out=None, stream=None):
     """ft_binary_eval: s (and z, out-of-window counts) of templates first .. first + n - 1."""
+    for x, nm in ((s_out, "s_out"), (z_out, "z_out"), (n_oob_out, "n_oob_out")):
+        _need(x, 4 * max(int(n), 0), f"binary_eval {nm}")
     ps, dev = _ptr(s_out)
     pz, _ = _ptr(z_out)
     po, _ = _ptr(n_oob_out)
@@ -336,6 +374,7 @@ def binary_eval(ctx, band, bank, first, n, s_out, z_out=None, n_oob_out=None, st
 def binary_topk_per_box(ctx, band, bank, k, out, stream=None):
     """ft_binary_topk_per_box into a CANDIDATE_DTYPE [n_boxes, k] array or a device byte
     tensor of n_boxes * k * 16 bytes."""
+    _need(out, bank.n_boxes * int(k) * 16, "binary_topk_per_box out")
     po, dev = _ptr(out)
     _check(lib().ft_binary_topk_per_box(ctx.handle, band.handle, bank.handle, int(k), po, int(dev),
                                         _stream(stream, dev)))
@@ -343,9 +382,8 @@ def binary_topk_per_box(ctx, band, bank, k, out, stream=None):
 
 def binary_topk_per_box_gated(ctx, band, bank, k, gate, gate_min, out, stream=None):
     """ft_binary_topk_per_box_gated: gate is a CUDA float32 tensor of n_templates values."""
-    pg, gdev = _ptr(gate)
-    if not gdev:
-        raise ValueError("gate must be a CUDA tensor")
+    pg = _gate_ptr(gate, bank.n_templates, "binary_topk_per_box_gated")
+    _need(out, bank.n_boxes * int(k) * 16, "binary_topk_per_box_gated out")
     po, dev = _ptr(out)
     _check(lib().ft_binary_topk_per_box_gated(ctx.handle, band.handle, bank.handle, int(k), pg,
                                               float(gate_min), po, int(dev), _stream(stream, dev)))
@@ -597,7 +635,9 @@ def make_bank(ctx, band, k0, n_f0, f1, sky, subband_bins, stream=None) -> Bank:
     h = _P()
     _check(lib().ft_make_bank(ctx.handle, band.handle, ctypes.byref(desc), _stream(stream, False),
                               ctypes.byref(h)))
-    return Bank(band, h)
+    b = Bank(band, h)
+    b.n_f0, b.n_f1, b.n_sky = int(desc.n_f0), int(desc.n_f1), int(desc.n_sky)
+    return b
 
 
 def required_wings(n_sft, t_mid, v_over_c, t_sft, t0, k0, n_f0, f1, sky, subband_bins=1):
@@ -613,6 +653,8 @@ def required_wings(n_sft, t_mid, v_over_c, t_sft, t0, k0, n_f0, f1, sky, subband
 
 def eval_statistic(ctx, band, bank, s_out, z_out=None, n_oob_out=None, stream=None):
     """ft_eval_statistic into caller-owned float32 s_out (and z_out, int32 n_oob_out)."""
+    for x, nm in ((s_out, "s_out"), (z_out, "z_out"), (n_oob_out, "n_oob_out")):
+        _need(x, 4 * bank.n_templates, f"eval_statistic {nm}")
     ps, dev = _ptr(s_out)
     pz, _ = _ptr(z_out)
     po, _ = _ptr(n_oob_out)
@@ -623,6 +665,7 @@ def eval_statistic(ctx, band, bank, s_out, z_out=None, n_oob_out=None, stream=No
 def topk_per_band(ctx, band, bank, k, out, stream=None):
     """ft_topk_per_band into `out`: a host numpy array of CANDIDATE_DTYPE [n_sub, k] or a
     device byte tensor of n_sub * k * 16 bytes (decode with decode_candidates)."""
+    _need(out, bank.n_subbands * int(k) * 16, "topk_per_band out")
     po, dev = _ptr(out)
     _check(lib().ft_topk_per_band(ctx.handle, band.handle, bank.handle, int(k), po, int(dev),
                                   _stream(stream, dev)))
@@ -631,9 +674,8 @@ def topk_per_band(ctx, band, bank, k, out, stream=None):
 def topk_per_band_gated(ctx, band, bank, k, gate, gate_min, out, stream=None):
     """ft_topk_per_band_gated: as topk_per_band over the templates with gate[t] >= gate_min;
     gate is a CUDA float32 tensor of n_templates values (e.g. the weighted number count)."""
-    pg, gdev = _ptr(gate)
-    if not gdev:
-        raise ValueError("gate must be a CUDA tensor")
+    pg = _gate_ptr(gate, bank.n_templates, "topk_per_band_gated")
+    _need(out, bank.n_subbands * int(k) * 16, "topk_per_band_gated out")
     po, dev = _ptr(out)
     _check(lib().ft_topk_per_band_gated(ctx.handle, band.handle, bank.handle, int(k), pg,
                                         float(gate_min), po, int(dev), _stream(stream, dev)))
@@ -642,6 +684,8 @@ def topk_per_band_gated(ctx, band, bank, k, gate, gate_min, out, stream=None):
 def topk_per_skybox(ctx, band, bank, sky_box, k, out, stream=None):
     """ft_topk_per_skybox into `out` (CANDIDATE_DTYPE [n_sky_boxes, n_sub, k] host array or a
     device byte tensor)."""
+    if int(sky_box) >= 1:
+        _need(out, -(-bank.n_sky // int(sky_box)) * bank.n_subbands * int(k) * 16, "topk_per_skybox out")
     po, dev = _ptr(out)
     _check(lib().ft_topk_per_skybox(ctx.handle, band.handle, bank.handle, int(sky_box), int(k), po,
                                     int(dev), _stream(stream, dev)))
@@ -653,17 +697,21 @@ def topk_per_box(ctx, band, bank, sky_box, f1_box, k, out, gate=None, gate_min=0
     as in topk_per_band_gated."""
     pg = None
     if gate is not None:
-        pg, gdev = _ptr(gate)
-        if not gdev:
-            raise ValueError("gate must be a CUDA tensor")
+        pg = _gate_ptr(gate, bank.n_templates, "topk_per_box")
+    if int(sky_box) >= 1 and int(f1_box) >= 1:
+        nb = -(-bank.n_sky // int(sky_box)) * -(-bank.n_f1 // int(f1_box))
+        _need(out, nb * bank.n_subbands * int(k) * 16, "topk_per_box out")
     po, dev = _ptr(out)
     _check(lib().ft_topk_per_box(ctx.handle, band.handle, bank.handle, int(sky_box), int(f1_box),
                                  int(k), pg, float(gate_min), po, int(dev), _stream(stream, dev)))
 
 
-def bank_sky_order(bank, n_sky):
-    """ft_bank_sky_order: the bank's sky order (int32 [n_sky])."""
-    out = np.empty(int(n_sky), np.int32)
+def bank_sky_order(bank, n_sky=None):
+    """ft_bank_sky_order: the bank's sky order (int32 [n_sky]); n_sky, when given, must be the
+    bank's."""
+    if n_sky is not None and int(n_sky) != bank.n_sky:
+        raise ValueError(f"bank_sky_order: the bank has {bank.n_sky} sky points, not {n_sky}")
+    out = np.empty(bank.n_sky, np.int32)
     _check(lib().ft_bank_sky_order(bank.handle, out.ctypes.data))
     return out
 
@@ -671,6 +719,7 @@ def bank_sky_order(bank, n_sky):
 def topk_per_band_noalloc(ctx, band, bank, k, out, stream=None):
     """ft_topk_per_band_noalloc: as topk_per_band, with the candidate scratch in the
     library's fixed device array instead of memory allocated during the call."""
+    _need(out, bank.n_subbands * int(k) * 16, "topk_per_band_noalloc out")
     po, dev = _ptr(out)
     _check(lib().ft_topk_per_band_noalloc(ctx.handle, band.handle, bank.handle, int(k), po,
                                           int(dev), _stream(stream, dev)))
@@ -691,5 +740,8 @@ def track_bins(ctx, band, bank, templates, out, stream=None):
     if dev != dev2:
         raise ValueError("templates and out must both be host or both device")
     n = templates.shape[0]
+    if str(templates.dtype) not in ("int64", "torch.int64"):
+        raise ValueError("track_bins: templates must be int64")
+    _need(out, 4 * n * band.n_sft, "track_bins out")
     _check(lib().ft_track_bins(ctx.handle, band.handle, bank.handle, pt, n, pb, int(dev),
                                _stream(stream, dev)))

@@ -235,6 +235,17 @@ int ft_gather_roof(ft_ctx *ctx, int dtype, double *evals_per_s, double *evals_pe
     return ft_run_gather_roof(dtype, ctx->sm_count, evals_per_s, evals_per_clk_sm);
 }
 
+int ft_ctx_memory(const ft_ctx *ctx, size_t *scratch_bytes, size_t *staging_bytes)
+{
+    if (!ctx)
+        FT_FAIL(FT_ERR_ARG, "ft_ctx_memory: null ctx");
+    if (scratch_bytes)
+        *scratch_bytes = ctx->scratch_bytes;
+    if (staging_bytes)
+        *staging_bytes = ctx->outbuf_bytes;
+    return FT_OK;
+}
+
 int ft_check_status(ft_ctx *ctx, void *stream)
 {
     if (!ctx)
@@ -649,33 +660,7 @@ int ft_required_wings(const ft_band_desc *d, const double *t_mid, const double *
 
 static EvalParams base_params(const ft_band *band, const ft_bank *bank)
 {
-    EvalParams p;
-    std::memset(&p, 0, sizeof(p));
-    p.power = band->d_power;
-    p.W = band->W;
-    p.N = band->N;
-    p.tau = band->d_tau;
-    p.v = band->d_v;
-    p.w = band->d_w;
-    if (band->d_D) {
-        p.D = band->d_D;
-        p.sn = band->d_sn;
-        p.sky_inv = bank->d_sky_inv;
-        p.sky_mu = bank->d_sky_mu;
-        p.sky_sig = bank->d_sky_sig;
-    }
-    p.sky = bank->d_sky;
-    p.G = bank->d_G;
-    p.f1 = bank->d_f1;
-    p.K0 = bank->k0;
-    p.k_lo = band->k_lo;
-    p.n_f0 = bank->n_f0;
-    p.n_f1 = bank->n_f1;
-    p.n_sky = bank->n_sky;
-    p.mu = band->mu;
-    p.sigma = band->sigma;
-    p.status = band->ctx->d_status;
-    return p;
+    return ft_eval_base_params(band, bank);
 }
 
 static int check_pair(ft_ctx *ctx, const ft_band *band, const ft_bank *bank)

@@ -147,35 +147,12 @@ int build(ft_ctx *ctx, int n, const ft_band *const *bands, const ft_bank *const 
         const ft_band *bd = bands[i];
         const ft_bank *bk = banks[i];
         EvalParams &p = params[i];
-        std::memset(&p, 0, sizeof(p));
-        p.power = bd->d_power;
-        p.W = bd->W;
-        p.N = bd->N;
-        p.tau = bd->d_tau;
-        p.v = bd->d_v;
-        p.w = bd->d_w;
-        if (bd->d_D) {
-            p.D = bd->d_D;
-            p.sn = bd->d_sn;
-            p.sky_inv = bk->d_sky_inv;
-            p.sky_mu = bk->d_sky_mu;
-            p.sky_sig = bk->d_sky_sig;
-        }
-        p.sky = bk->d_sky;
+        p = ft_eval_base_params(bd, bk);
+        p.status = ctx->d_status;
         p.P = bP[i];
         p.F1 = bF1[i];
         p.n_skyg = (bk->n_sky + bP[i] - 1) / bP[i];
         p.sky_order = bP[i] > 1 ? bk->d_sky_order : nullptr;
-        p.G = bk->d_G;
-        p.f1 = bk->d_f1;
-        p.K0 = bk->k0;
-        p.k_lo = bd->k_lo;
-        p.n_f0 = bk->n_f0;
-        p.n_f1 = bk->n_f1;
-        p.n_sky = bk->n_sky;
-        p.mu = bd->mu;
-        p.sigma = bd->sigma;
-        p.status = ctx->d_status;
         p.k = k;
         p.sub = bk->sub;
         const int Ws = ft_window_bins(bd, bk, J, bP[i]);

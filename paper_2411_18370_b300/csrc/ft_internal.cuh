@@ -6,6 +6,7 @@
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <string>
 #include <vector>
@@ -173,6 +174,39 @@ struct EvalParams {
     int k, sub, lsub_max;
     unsigned int *status;
 };
+
+// The evaluation parameters every search of (band, bank) shares: data, bank, weights,
+// noise moments and the status word; the launch shape and the outputs are left zero.
+inline EvalParams ft_eval_base_params(const ft_band *band, const ft_bank *bank)
+{
+    EvalParams p;
+    memset(&p, 0, sizeof(p));
+    p.power = band->d_power;
+    p.W = band->W;
+    p.N = band->N;
+    p.tau = band->d_tau;
+    p.v = band->d_v;
+    p.w = band->d_w;
+    if (band->d_D) {
+        p.D = band->d_D;
+        p.sn = band->d_sn;
+        p.sky_inv = bank->d_sky_inv;
+        p.sky_mu = bank->d_sky_mu;
+        p.sky_sig = bank->d_sky_sig;
+    }
+    p.sky = bank->d_sky;
+    p.G = bank->d_G;
+    p.f1 = bank->d_f1;
+    p.K0 = bank->k0;
+    p.k_lo = band->k_lo;
+    p.n_f0 = bank->n_f0;
+    p.n_f1 = bank->n_f1;
+    p.n_sky = bank->n_sky;
+    p.mu = band->mu;
+    p.sigma = band->sigma;
+    p.status = band->ctx->d_status;
+    return p;
+}
 
 // Persistent multi-band launch: band-major work list of tiles, running candidate lists.
 struct BatchParams {

@@ -86,32 +86,7 @@ extern "C" int ft_topk_per_band_noalloc(ft_ctx *ctx, const ft_band *band, const 
     unsigned char *scr = static_cast<unsigned char *>(base);
     ft_candidate *dout = out_on_device ? out : reinterpret_cast<ft_candidate *>(scr + out_off);
 
-    EvalParams p;
-    std::memset(&p, 0, sizeof(p));
-    p.power = band->d_power;
-    p.W = band->W;
-    p.N = band->N;
-    p.tau = band->d_tau;
-    p.v = band->d_v;
-    p.w = band->d_w;
-    if (band->d_D) {
-        p.D = band->d_D;
-        p.sn = band->d_sn;
-        p.sky_inv = bank->d_sky_inv;
-        p.sky_mu = bank->d_sky_mu;
-        p.sky_sig = bank->d_sky_sig;
-    }
-    p.sky = bank->d_sky;
-    p.G = bank->d_G;
-    p.f1 = bank->d_f1;
-    p.K0 = bank->k0;
-    p.k_lo = band->k_lo;
-    p.n_f0 = bank->n_f0;
-    p.n_f1 = bank->n_f1;
-    p.n_sky = bank->n_sky;
-    p.mu = band->mu;
-    p.sigma = band->sigma;
-    p.status = ctx->d_status;
+    EvalParams p = ft_eval_base_params(band, bank);
     p.cand = reinterpret_cast<FtCand *>(scr + cand_off);
     p.k = k;
     p.sub = bank->sub;
@@ -123,14 +98,7 @@ extern "C" int ft_topk_per_band_noalloc(ft_ctx *ctx, const ft_band *band, const 
     if (out_on_device)
         return FT_OK;
     FT_CUDA(cudaMemcpyAsync(out, dout, out_bytes, cudaMemcpyDeviceToHost, st));
-    unsigned int status = 0;
-    FT_CUDA(cudaMemcpyAsync(&status, ctx->d_status, sizeof(status), cudaMemcpyDeviceToHost, st));
-    FT_CUDA(cudaStreamSynchronize(st));
-    if (status != 0) {
-        FT_CUDA(cudaMemsetAsync(ctx->d_status, 0, sizeof(status), st));
-        FT_CUDA(cudaStreamSynchronize(st));
-        FT_FAIL(status & FT_STATUS_TIMEOUT ? FT_ERR_TIMEOUT : FT_ERR_CUDA,
-                "topk_per_band_noalloc: device-side failure recorded");
-    }
+    // synchronise, report and clear the device status word exactly as ft_topk_per_band does
+    FT_TRY(ft_read_status(ctx, st));
     return FT_OK;
 }

@@ -113,8 +113,9 @@ def test_full_bank_boxes(ctx, search_cfg):
     """The full search-shaped bank (3.6e7 templates, 24 419 SFTs) in boxes of 100 sky points x
     5 f1 values x one 0.01 Hz sub-band, plain and gated: the CPU selection over the GPU's s of
     every template (from the default launch shape, whose stage lengths may differ from the
-    box launch's, so sets may differ only at near-ties and values by FP32 rounding), and every
-    candidate's s against the oracle."""
+    box launch's, so sets may differ only at near-ties and values by FP32 rounding), every
+    candidate's s against the oracle, and, on 8 sampled boxes, the sets against the oracle's
+    selection over its own s of every template in the box (same near-tie rule)."""
     from tests.test_gpu_parity import assert_s_close
 
     sfts, bank = search_cfg
@@ -148,3 +149,12 @@ def test_full_bank_boxes(ctx, search_cfg):
         assert np.all(np.abs(val.ravel() - s[flat]) <= 2e-6 * np.abs(s[flat]))
         s_or, _ = oracle.statistic(sfts, bank, flat)
         assert_s_close(val.ravel(), s_or)
+        # sampled boxes: every template of the box through the oracle
+        boxes = np.random.default_rng(9).choice(n_keys, 8, replace=False)
+        ts = t[np.isin(key[t], boxes)]
+        s_box, _ = oracle.statistic(sfts, bank, ts)
+        o_idx, o_val = oracle.topk_per_key(s_box, key[ts], n_keys, K + 1, ts)
+        for bx in boxes:
+            if set(idx[bx].tolist()) != set(o_idx[bx, :K].tolist()):
+                kth, nxt = o_val[bx, K - 1], o_val[bx, K]
+                assert abs(kth - nxt) < 2e-6 * abs(kth), f"box {bx} against the oracle"

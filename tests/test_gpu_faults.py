@@ -74,3 +74,35 @@ def test_corrupt_bank_inputs(ctx):
     s, _, _ = H.eval_host(ctx, band, bk, bank.n_templates)
     s_or, _ = oracle.statistic(sfts, bank)
     assert np.all(np.abs(s - s_or) <= 1e-6 * s_or)
+
+
+def test_binding_refuses_bad_gates_and_short_device_buffers(ctx):
+    """A gate must be a float32 CUDA tensor of one value per template, and a device output
+    buffer must hold what the call writes; the binding refuses both before the library runs,
+    and the context still searches correctly afterwards."""
+    import torch
+
+    sfts, bank, _ = ftsynth.tiny_workload("auto")
+    band = H.band_from(ctx, sfts)
+    bk = H.bank_from(ctx, band, bank)
+    n = bank.n_templates
+    out = torch.empty(bank.n_subbands * 5 * 16, dtype=torch.uint8, device="cuda")
+    for bad in (torch.zeros(n, dtype=torch.float64, device="cuda"),
+                torch.zeros(n - 1, dtype=torch.float32, device="cuda")):
+        with pytest.raises(ValueError):
+            ft.topk_per_band_gated(ctx, band, bk, 5, bad, 0.0, out)
+        with pytest.raises(ValueError):
+            ft.topk_per_box(ctx, band, bk, 4, 1, 5, torch.empty(10 ** 6, dtype=torch.uint8, device="cuda"),
+                            gate=bad)
+    with pytest.raises(ValueError):
+        ft.topk_per_band(ctx, band, bk, 5, out[:-1])
+    with pytest.raises(ValueError):
+        ft.eval_statistic(ctx, band, bk, torch.empty(n - 1, dtype=torch.float32, device="cuda"))
+    ft.topk_per_band(ctx, band, bk, 5, out)
+    torch.cuda.synchronize()
+    idx, _, _ = ft.decode_candidates(out, bank.n_subbands, 5)
+    s, _, _ = H.eval_host(ctx, band, bk, n)
+    s_or, _ = oracle.statistic(sfts, bank)
+    assert np.all(np.abs(s - s_or) <= 1e-6 * s_or)
+    c_idx, _ = oracle.topk_per_subband(s.astype(np.float64), bank, 5)
+    assert np.array_equal(idx, c_idx)

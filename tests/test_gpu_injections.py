@@ -40,14 +40,24 @@ def _random_injections(n, bank, g, h0_max=0.08, t_sft=1800.0):
     return inj
 
 
+ZTOL = 2e-4
+
+
 def test_injections_match_oracle(setup):
+    """Every run's loudest z within ZTOL of the oracle's, and its loudest template the
+    oracle's, except in runs whose oracle loudest and runner-up z are closer than 2 ZTOL
+    (each can move by ZTOL); those runs are counted, and must be rare."""
     ctx, sfts, bank, D, band, bk = setup
     inj = _random_injections(40, bank, np.random.default_rng(8))
     got = ft.run_injections(ctx, band, bk, D, inj, seed=2024, first_run_id=100, k_sky=32)
-    oz, oa, oo = oracle.injections(sfts, bank, D, inj.astype(oracle.INJ_DTYPE), 100, 2024, K=32)
+    oz, oa, oo, o2 = oracle.injections(sfts, bank, D, inj.astype(oracle.INJ_DTYPE), 100, 2024, K=32,
+                                       with_second=True)
     assert np.array_equal(got["n_out_of_window"], oo) and np.all(oo == 0)
-    assert np.all(np.abs(got["max_z"] - oz) < 2e-4), np.max(np.abs(got["max_z"] - oz))
-    assert np.mean(got["template_idx"] == oa) >= 0.9
+    assert np.all(np.abs(got["max_z"] - oz) < ZTOL), np.max(np.abs(got["max_z"] - oz))
+    differ = np.nonzero(got["template_idx"] != oa)[0]
+    near_tie = oz - o2 < 2 * ZTOL
+    assert np.all(near_tie[differ]), [(int(r), float(oz[r] - o2[r])) for r in differ if not near_tie[r]]
+    assert len(differ) <= 2, [(int(r), float(oz[r] - o2[r])) for r in differ]
 
 
 def test_noise_free_grid_injection(setup):

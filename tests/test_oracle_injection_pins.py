@@ -6,7 +6,8 @@
 * Antenna patterns: the zenith case of an L-shaped detector, psi-invariance of F+^2 + Fx^2,
   and its isotropic average 2/5 for a 90-degree interferometer.
 * rho^2 closed form for a face-on source at the zenith.
-* A noise-free injection on a grid template recovers exactly sum_alpha w_alpha rho^2_alpha.
+* A noise-free injection on a grid template recovers exactly sum_alpha w_alpha rho^2_alpha;
+  the reported runner-up z equals a brute-force pass over the local bank.
 """
 import math
 from fractions import Fraction as F
@@ -121,13 +122,31 @@ def test_noise_free_injection_on_grid_template_is_exact():
         x = exact.position(bank.k0, sfts.k_lo, j, bank.f1[f1i], sfts.t_mid[a], sfts.t0,
                            sfts.t_sft, sfts.v[a], bank.sky[ski])
         assert exact.bin_and_tie_distance(x)[1] > 1e-6
-    mz, am, oob = oracle.injections(sfts, bank, D, inj, 0, 123, K=8, noise_scale=0.0)
+    mz, am, oob, z2 = oracle.injections(sfts, bank, D, inj, 0, 123, K=8, noise_scale=0.0,
+                                        with_second=True)
     rho2 = np.array([oracle.rho2(D[a], bank.sky[ski], 0.05, 0.3, 0.7, 1800.0, sfts.s_n[a])
                      for a in range(sfts.n_total)])
     mu, sig = oracle.mu_sigma(sfts.n_total)
-    assert am[0] == (ski * bank.n_f1 + f1i) * bank.n_f0 + j
+    t_inj = (ski * bank.n_f1 + f1i) * bank.n_f0 + j
+    assert am[0] == t_inj
     assert abs(mz[0] - (rho2.sum() - mu) / sig) < 1e-9 * abs(mz[0])
     assert oob[0] == 0
+    # brute force over the local bank (f0 within 2 bins, every f1, the 8 sky points nearest
+    # the source): noise-free, a template collects rho^2 in the SFTs where its bin is the
+    # signal's; the second largest z is the runner-up's
+    near = np.argsort(-(bank.sky @ bank.sky[ski]), kind="stable")[:8]
+    loc = np.array([(sk * bank.n_f1 + f) * bank.n_f0 + jj for sk in near for f in range(bank.n_f1)
+                    for jj in range(j - 2, j + 3)])
+    b = oracle.bins(sfts, bank, loc)
+    b_sig = oracle.bins(sfts, bank, [t_inj])[0]
+    z = np.sort(((b == b_sig[None, :]) * rho2[None, :]).sum(axis=1) - mu) / sig
+    assert abs(z[-1] - mz[0]) < 1e-9 * abs(mz[0])
+    assert abs(z[-2] - z2[0]) < 1e-9 * abs(z2[0]) and z2[0] < mz[0]
+    # with no signal every template has z = -mu/sigma: the runner-up ties the loudest
+    inj["h0"] = 0.0
+    mz0, _, _, z20 = oracle.injections(sfts, bank, D, inj, 0, 123, K=8, noise_scale=0.0,
+                                       with_second=True)
+    assert z20[0] == mz0[0] == -mu / sig
 
 
 def test_window_too_narrow_is_counted():

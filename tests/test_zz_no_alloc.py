@@ -60,6 +60,38 @@ def test_noalloc_matches_allocating_entry_point_twice(search):
         _same(got, ref)
 
 
+def test_noalloc_allocates_nothing():
+    """On a context whose search scratch was never grown, two no-allocation searches (host
+    output, then device output) leave its scratch at zero bytes and its staging buffer as it
+    was: the candidate lists live in the library's fixed array, not in memory allocated during
+    the call."""
+    import torch
+
+    ctx = ft.create(0)
+    try:
+        sfts, bank, _ = ftsynth.tiny_workload("auto")
+        band = ft.load_sfts(ctx, sfts.power.astype(np.float32), sfts.t_mid, sfts.v, sfts.n_sft,
+                            sfts.k_lo, sfts.t_sft, sfts.t0, dtype="f32")
+        bk = ft.make_bank(ctx, band, bank.k0, bank.n_f0, bank.f1, bank.sky, bank.subband_bins)
+        before = ctx.memory()
+        assert before[0] == 0, before
+        got = np.zeros((bank.n_subbands, 5), dtype=ft.CANDIDATE_DTYPE)
+        ft.topk_per_band_noalloc(ctx, band, bk, 5, got)
+        dev = torch.zeros(bank.n_subbands * 5 * 16, dtype=torch.uint8, device="cuda")
+        ft.topk_per_band_noalloc(ctx, band, bk, 5, dev)
+        torch.cuda.synchronize()
+        assert ctx.memory() == before
+        # the allocating entry point, for contrast, grows the context's scratch
+        ref = np.zeros_like(got)
+        ft.topk_per_band(ctx, band, bk, 5, ref)
+        assert ctx.memory()[0] > 0
+        _same(got, ref)
+        bk.close()
+        band.close()
+    finally:
+        ctx.close()
+
+
 def test_noalloc_rejects_requests_beyond_its_scratch(search):
     ctx, band, bk, bank = search
     out = np.zeros((bank.n_subbands, 32), dtype=ft.CANDIDATE_DTYPE)
