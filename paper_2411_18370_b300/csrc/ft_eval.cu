@@ -584,7 +584,7 @@ __device__ __forceinline__ float read_bin(const unsigned char *rows, int row_wor
 // the window start);
 // per evaluating warp its own row offsets and correction list for the slot it works on.
 constexpr int kMaxStages = 4;
-constexpr int kFoldRows = 256;  // FP32 partials cover at most this many SFT rows
+constexpr int kFoldRows = 512;  // FP32 partials cover at most this many SFT rows
 
 // ------------------------------------------------------------------ tensor memory
 //
@@ -659,12 +659,14 @@ __device__ __forceinline__ void tm_wait_st()
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-struct RowRec {
-    long long C;     // C + 2^31 + j0 E: the track's Q32 origin at the tile's first f0, before G
+// One row's track terms for one sky point of the tile (16 bytes: one shared load per lane).
+struct __align__(16) RowRec {
+    // C + 2^31 + j0 E + (j0 - start) 2^32: the track's Q32 origin at the tile's first f0,
+    // before G, with the integer part counted from the first bin of the row's window in
+    // shared memory (start, a multiple of 16)
+    long long C;
     int E;
-    unsigned span;   // (J - 1) |E|: how far the fraction moves across the tile
     float w;
-    int start;       // first bin of the row's window in shared memory (multiple of 16)
 };
 
 struct FastLayout {
@@ -871,7 +873,6 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
                     RowRec r;
                     track_ec(va, skyn[3 * q], skyn[3 * q + 1], skyn[3 * q + 2], p.K0, p.k_lo, r.E, r.C);
                     r.C += (1ll << 31) + static_cast<long long>(c.j0) * r.E;
-                    r.span = static_cast<unsigned>(J - 1) * static_cast<unsigned>(abs(r.E));
                     r.w = wa;
                     if (sky_w) {
                         // all-sky weight of this row for sky point q
@@ -880,7 +881,6 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
                                                                   skyn[3 * q + 2]) /
                                                  p.sn[alpha] * p.sky_inv[sk < 0 ? c.sky : sk]);
                     }
-                    r.start = 0;
                     rq[q * S] = r;
                     if (p.Ws < p.Wp) {
                         const int x1 = c.j0 + static_cast<int>((r.C + G1 + cross_q32(G1, r.E)) >> 32);
@@ -918,11 +918,13 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
                             len = p.Ws;
                         }
                     }
-                    for (int q = 0; q < p.P; ++q)
-                        rq[q * S].start = s0;
                     start = s0;
                 }
             }
+            // the records' integer part counts bins from the window's first bin
+            if (lane < nr)
+                for (int q = 0; q < p.P; ++q)
+                    rq[q * S].C += static_cast<long long>(c.j0 - start) << 32;
             unsigned row_tot;  // bytes of the stage's copies
             if (p.Ws == p.Wp) {
                 row_tot = static_cast<unsigned>(nr) * static_cast<unsigned>(p.row_bytes);
@@ -1041,21 +1043,28 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
             if (lane < nr) {
                 const RowRec r = rr[lane];
                 const long long acc0 = r.C + g_cur + cross_q32(g_cur, r.E);
-                const int base = c.j0 + static_cast<int>(acc0 >> 32) - r.start;  // within the window
+                const int base = static_cast<int>(acc0 >> 32);  // within the window
                 const unsigned L0 = static_cast<unsigned>(acc0);
-                const unsigned span = r.span;
-                ev = r.E > 0 ? (span != 0u && L0 >= 0u - span) : (L0 < span);
+                // the fraction L0 + j E leaves [0, 2^32) for some j < J: the bin steps once
+                const unsigned span = static_cast<unsigned>(J - 1) * static_cast<unsigned>(abs(r.E));
+                ev = r.E > 0 ? (L0 + span < L0) : (L0 < span);
                 tabB[lane] = PAIR ? lane * row_words + (base & 1) * (row_words >> 1) + (base >> 1)
                                   : lane * row_words + base;
                 packed = lane | (r.E < 0 ? (1 << 20) : 0);
                 basev = base;
                 if (ev) {
-                    // first tile offset at which the bin steps (rare: one division)
-                    // (E > 0: the first j with L0 + j E >= 2^32 is ceil((2^32 - L0) / E),
-                    // written with a 32-bit numerator)
-                    const int jc = r.E > 0 ? static_cast<int>((0xffffffffu - L0) / static_cast<unsigned>(r.E)) + 1
-                                           : static_cast<int>(L0 / static_cast<unsigned>(-r.E)) + 1;
-                    packed |= jc << 8;
+                    // first tile offset jc at which the bin steps: jc = floor(num / |E|) + 1
+                    // with num = 2^32 - 1 - L0 (E > 0: the first j with L0 + j E >= 2^32) or
+                    // num = L0 (E < 0: the first j with L0 + j E < 0).  An FP32 quotient,
+                    // then one exact integer step each way (the quotient is below J, so its
+                    // FP32 error is far under one)
+                    const unsigned num = r.E > 0 ? 0xffffffffu - L0 : L0;
+                    const unsigned den = static_cast<unsigned>(abs(r.E));
+                    int q = static_cast<int>(__fmul_rz(__uint2float_rz(num), __frcp_rz(__uint2float_rn(den))));
+                    const unsigned t = static_cast<unsigned>(q) * den;
+                    q -= t > num ? 1 : 0;
+                    q += (t <= num && num - t >= den) ? 1 : 0;
+                    packed |= (q + 1) << 8;
                 }
             }
             const unsigned m = __ballot_sync(0xffffffffu, ev);
@@ -1094,13 +1103,19 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
                     }
                 } else {
                     // one 32-bit word of the pair layout holds (P[k'], P[k'+1]) for any k';
-                    // with k' = k + min(sg, 0) the change is sg (P[k'+1] - P[k'])
+                    // with k' = k + min(sg, 0) the change is sg (P[k'+1] - P[k']).  Slot
+                    // 2m of the lane reads k' = K0 + 64 m and slot 2m + 1 reads K0 + 1 + 64 m
+                    // (K0 = base + 2 lane + min(sg, 0)): the two words sit 32 m words past
+                    // one address each, in the copy matching their parity
                     const unsigned *row = reinterpret_cast<const unsigned *>(rows) + a * row_words;
+                    const int K0 = base + 2 * lane + (sg < 0 ? -1 : 0);
+                    const int K1 = K0 + 1;
+                    const unsigned *we = row + (K0 & 1) * (row_words >> 1) + (K0 >> 1);
+                    const unsigned *wo = row + (K1 & 1) * (row_words >> 1) + (K1 >> 1);
 #pragma unroll
                     for (int i = 0; i < NS; ++i) {
                         if (jrel[i] >= jc && (i >> 1) < ract) {
-                            const int kp = base + jrel[i] + (sg < 0 ? -1 : 0);
-                            const unsigned u = row[(kp & 1) * (row_words >> 1) + (kp >> 1)];
+                            const unsigned u = (i & 1 ? wo : we)[32 * (i >> 1)];
                             if (WEIGHTED) {
                                 const float d = __fsub_rn(hi_to_float<MODE>(u), lo_to_float<MODE>(u));
                                 part[i] = __fmaf_rn(sg < 0 ? -wa : wa, d, part[i]);
@@ -1297,13 +1312,20 @@ __global__ void __maxnreg__(FT_FAST_MAXNREG) k_eval_batched(const BatchParams bp
         if (b < 0)
             break;
         const EvalParams &p = s_params;
+        // Tickets of a band run every (sky group, f1 group) of one f0 tile before the next
+        // f0 tile: the CTAs in flight then read the same window of the band's rows, so a wide
+        // band's working set is that window (about a third of its rows' bytes) and stays in
+        // L2, instead of the whole band.  The tile index itself keeps the f0 tile fastest.
+        const long long per_f0t = p.n_skyg * static_cast<long long>(p.n_f1g);
+        const long long t_f0 = tile / per_f0t;
+        const long long tile_id = (tile - t_f0 * per_f0t) * p.n_f0t + t_f0;
         // (the tensor map is used from global memory, where a copy can be read from)
-        const bool done = fast_tile<MODE, R, WEIGHTED, true>(p, tile, smem, tl, tm, &bp.params[b].rows_map);
+        const bool done = fast_tile<MODE, R, WEIGHTED, true>(p, tile_id, smem, tl, tm, &bp.params[b].rows_map);
         __syncthreads();
         if (!done)
             break;  // a bounded wait ran out (status already set): stop taking tiles
         // merge this tile's lists into the band's running lists
-        const int j0 = static_cast<int>(tile % p.n_f0t) * J;
+        const int j0 = static_cast<int>(t_f0) * J;
         const int lb0 = j0 / p.sub, lb1 = (min(j0 + J, p.n_f0) - 1) / p.sub;
         for (int lb = lb0 + warp; lb <= lb1; lb += nw)
             warp_merge_lists(run + lb * bp.k, tl + (lb - lb0) * bp.k, bp.k);
