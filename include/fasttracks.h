@@ -479,8 +479,13 @@ FT_API int ft_mlp_adam_step(ft_mlp *mlp, float lr, float beta1, float beta2, flo
  * batch loss. */
 FT_API int ft_mlp_train(ft_mlp *mlp, const float *X, const float *y, int64_t n, int batch,
                         int epochs, float lr, uint64_t seed, float *loss_history);
-/* p = sigmoid(network(X)) for n samples; bf16 selects BF16 inference; X and p both host
- * (on_device 0) or both device (1, asynchronous on `stream`). */
+/* p = sigmoid(network(X)) for n samples; X and p both host (on_device 0) or both device (1,
+ * asynchronous on `stream`).  bf16: 0 = FP32 forward; 1 = BF16 inference (BF16 inputs,
+ * weights and activations, FP32 sums) on the tensor cores -- each hidden layer one
+ * tcgen05.mma product of 128 samples, FP32 accumulators in tensor memory -- when the width
+ * is a multiple of 16 up to 128 and d_in is at most 64, else on the CUDA cores; 2 = the same
+ * BF16 inference on the CUDA cores (one warp per sample).  Errors: FT_ERR_ARG, FT_ERR_OOM,
+ * FT_ERR_CUDA. */
 FT_API int ft_mlp_predict(ft_mlp *mlp, const float *X, int64_t n, float *p, int bf16,
                           int on_device, void *stream);
 

@@ -549,17 +549,20 @@ class MLP:
                                   int(epochs), float(lr), int(seed), hist.ctypes.data))
         return hist[:epochs]
 
-    def predict(self, X, bf16=True):
+    def predict(self, X, bf16=True, tensor_cores=True):
+        """ft_mlp_predict: p for the rows of X.  bf16: BF16 inference (on the tensor cores
+        unless tensor_cores is False), else the FP32 forward."""
+        mode = 0 if not bf16 else (1 if tensor_cores else 2)
         if _is_torch(X) and X.is_cuda:
             import torch
 
             p = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
             _check(lib().ft_mlp_predict(self.handle, X.data_ptr(), X.shape[0], p.data_ptr(),
-                                        int(bf16), 1, _stream(None, True)))
+                                        mode, 1, _stream(None, True)))
             return p
         X = np.ascontiguousarray(X, dtype=np.float32)
         p = np.empty(len(X), np.float32)
-        _check(lib().ft_mlp_predict(self.handle, X.ctypes.data, len(X), p.ctypes.data, int(bf16),
+        _check(lib().ft_mlp_predict(self.handle, X.ctypes.data, len(X), p.ctypes.data, mode,
                                     0, None))
         return p
 

@@ -11,6 +11,7 @@
 // Determinism: every reduction (over the batch for weight gradients, over a row for a
 // layer output) runs in a fixed order, so a training run is bit-reproducible.
 #include "ft_internal.cuh"
+#include "ft_ptx.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -241,6 +242,257 @@ __global__ void k_infer_bf16(const float *X, long long n, int d, int w, const __
             acc += __shfl_xor_sync(0xffffffffu, acc, off);
         if (lane == 0)
             p[s] = 1.f / (1.f + expf(-(acc + __bfloat162float(th[ob4]))));
+    }
+}
+
+// ------------------------------------------------------------------ BF16 inference on
+// the tensor cores
+//
+// One CTA of 128 threads infers 128 samples: each layer is one M = 128 matrix product
+// D[m][n] = sum_k A[m][k] W[n][k] by tcgen05.mma (kind::f16, BF16 operands from shared
+// memory, FP32 accumulators in tensor memory), issued by one thread and tracked by an
+// mbarrier; each thread then reads its sample's row of D from tensor memory, adds the bias,
+// applies the ReLU and writes the BF16 activations back to shared memory as the next
+// layer's A.  The last layer (width -> 1) and the sigmoid run on the CUDA cores in FP32.
+// Numerics match the SIMT BF16 path: BF16 inputs, weights and activations, FP32 sums.
+//
+// Shared-memory operands use the no-swizzle K-major layout of the tcgen05 matrix
+// descriptors: an R x K BF16 matrix (K a multiple of 16) is a grid of 8 x 8-element core
+// matrices of 128 contiguous bytes, element (r, k) at byte
+//     (r / 8) (16 K) + (k / 8) 128 + (r % 8) 16 + (k % 8) 2,
+// so core matrices adjacent in K are 128 bytes apart (the descriptor's leading-dimension
+// offset) and adjacent 8-row groups 16 K bytes apart (its stride-dimension offset); the
+// product over k in [16 i, 16 i + 16) starts 256 i bytes into each operand.
+
+constexpr int kTcM = 128;       // samples per CTA (the MMA's M)
+constexpr int kTcMaxW = 128;    // hidden widths 16 .. 128 (multiples of 16)
+constexpr int kTcMaxK = 64;     // padded inputs 16 .. 64
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ int kmaj_off(int r, int k, int K)
+{
+    return (r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+// tcgen05 shared-memory matrix descriptor: start address >> 4 (bits 0-13), leading-
+// dimension byte offset >> 4 (bits 16-29), stride-dimension byte offset >> 4 (bits 32-45),
+// the fixed value 1 at bits 46-48, no base offset, no swizzle (bits 61-63 = 0)
+__device__ __forceinline__ unsigned long long tc_desc(unsigned addr, int K)
+{
+    return static_cast<unsigned long long>((addr & 0x3FFFFu) >> 4) |
+           (static_cast<unsigned long long>(128 >> 4) << 16) |
+           (static_cast<unsigned long long>((K * 16) >> 4) << 32) | (1ull << 46);
+}
+
+// tcgen05 instruction descriptor, kind::f16: FP32 D (bits 4-5 = 1), BF16 A (bits 7-9 = 1)
+// and B (bits 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 at bits 17-22, M / 16 at
+// bits 24-28
+__host__ __device__ constexpr unsigned tc_idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<unsigned>(N >> 3) << 17) |
+           (static_cast<unsigned>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(unsigned tmem_d, unsigned long long a, unsigned long long b,
+                                       unsigned idesc, int accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(unsigned long long *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// generic-proxy writes to shared memory made visible to the tensor cores' reads
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this thread's tensor-memory lane
+__device__ __forceinline__ void tc_ld16(unsigned taddr, float (&v)[16])
+{
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+        v[i] = __uint_as_float(r[i]);
+}
+
+struct TcSmem {
+    size_t w1, w2, w3, act, bias, bar, tm, total;
+};
+
+__host__ __device__ inline TcSmem tc_layout(int K1, int W)
+{
+    TcSmem L;
+    size_t o = 0;
+    L.w1 = o;
+    o += static_cast<size_t>(W) * K1 * 2;
+    L.w2 = o;
+    o += static_cast<size_t>(W) * W * 2;
+    L.w3 = o;
+    o += static_cast<size_t>(W) * W * 2;
+    L.act = o;
+    o += static_cast<size_t>(kTcM) * (K1 > W ? K1 : W) * 2;
+    L.bias = o;  // b1, b2, b3, W4 as FP32 [4][W], then b4
+    o += (4 * static_cast<size_t>(W) + 4) * 4;
+    o = (o + 15) / 16 * 16;
+    L.bar = o;
+    o += 16;
+    L.tm = o;
+    o += 16;
+    L.total = o;
+    return L;
+}
+
+// rows [0, R) x k in [0, K) of a BF16 matrix into the K-major operand layout, zero past
+// (rows_valid, k_valid); the source row r starts at src + r * ld
+__device__ void tc_stage_bf16(unsigned char *dst, const __nv_bfloat16 *src, long long ld, int R, int K,
+                              int rows_valid, int k_valid)
+{
+    for (int i = threadIdx.x; i < R * (K / 8); i += blockDim.x) {
+        const int r = i / (K / 8), k0 = (i - r * (K / 8)) * 8;
+        __align__(16) __nv_bfloat16 e[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            e[j] = (r < rows_valid && k0 + j < k_valid) ? src[r * ld + k0 + j] : __float2bfloat16_rn(0.f);
+        *reinterpret_cast<uint4 *>(dst + kmaj_off(r, k0, K)) = *reinterpret_cast<const uint4 *>(e);
+    }
+}
+
+// One layer's products: D (tensor-memory columns col..col+W) = A (128 x K) x W^T (W x K).
+__device__ __forceinline__ void tc_layer(unsigned tm, int col, const unsigned char *A, const unsigned char *Wt, int K,
+                                         int W, unsigned long long *bar)
+{
+    const unsigned a0 = smem_u32(A), b0 = smem_u32(Wt), idesc = tc_idesc_bf16(kTcM, W);
+    for (int i = 0; i < K / 16; ++i)
+        tc_mma(tm + static_cast<unsigned>(col), tc_desc(a0 + 256u * i, K), tc_desc(b0 + 256u * i, K), idesc, i > 0);
+    tc_commit(bar);
+}
+
+__global__ void __launch_bounds__(kTcM) k_infer_tc(const float *X, long long n, int d, int K1, int W,
+                                                  const __nv_bfloat16 *th, long long oW1, long long ob1,
+                                                  long long oW2, long long ob2, long long oW3, long long ob3,
+                                                  long long oW4, long long ob4, float *p, unsigned *status)
+{
+    extern __shared__ __align__(128) unsigned char tsm[];
+    const TcSmem L = tc_layout(K1, W);
+    unsigned char *sW1 = tsm + L.w1, *sW2 = tsm + L.w2, *sW3 = tsm + L.w3, *sA = tsm + L.act;
+    float *sb = reinterpret_cast<float *>(tsm + L.bias);
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(tsm + L.bar);
+    unsigned *s_tm = reinterpret_cast<unsigned *>(tsm + L.tm);
+    const int warp = threadIdx.x >> 5;
+    const long long s0 = static_cast<long long>(blockIdx.x) * kTcM;
+    const int rows = static_cast<int>(min(static_cast<long long>(kTcM), n - s0));
+    const unsigned ncols = W <= 16 ? 32u : W <= 32 ? 64u : W <= 64 ? 128u : 256u;  // two layers' D
+
+    if (threadIdx.x == 0) {
+        ftp::mbar_init(bar, 1);
+        ftp::fence_mbar_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tm)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // operands: weights, this CTA's samples (features rounded to BF16), biases and W4 in FP32
+    tc_stage_bf16(sW1, th + oW1, d, W, K1, W, d);
+    tc_stage_bf16(sW2, th + oW2, W, W, W, W, W);
+    tc_stage_bf16(sW3, th + oW3, W, W, W, W, W);
+    for (int i = threadIdx.x; i < kTcM * (K1 / 8); i += blockDim.x) {
+        const int r = i / (K1 / 8), k0 = (i - r * (K1 / 8)) * 8;
+        __align__(16) __nv_bfloat16 e[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            e[j] = __float2bfloat16_rn(r < rows && k0 + j < d ? X[(s0 + r) * d + k0 + j] : 0.f);
+        *reinterpret_cast<uint4 *>(sA + kmaj_off(r, k0, K1)) = *reinterpret_cast<const uint4 *>(e);
+    }
+    for (int i = threadIdx.x; i < W; i += blockDim.x) {
+        sb[i] = __bfloat162float(th[ob1 + i]);
+        sb[W + i] = __bfloat162float(th[ob2 + i]);
+        sb[2 * W + i] = __bfloat162float(th[ob3 + i]);
+        sb[3 * W + i] = __bfloat162float(th[oW4 + i]);
+    }
+    if (threadIdx.x == 0)
+        sb[4 * W] = __bfloat162float(th[ob4]);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tm = *s_tm;
+    // this thread's sample: row m = tensor-memory lane 32 warp + lane
+    const int m = threadIdx.x;
+    const unsigned trow = tm + (static_cast<unsigned>(warp * 32) << 16);
+    bool ok = true;
+    float logit = 0.f;
+    for (int l = 0; l < 3 && ok; ++l) {
+        const int col = (l & 1) * W;  // layers 1 and 3 in columns [0, W), layer 2 in [W, 2W)
+        if (threadIdx.x == 0)
+            tc_layer(tm, col, sA, l == 0 ? sW1 : l == 1 ? sW2 : sW3, l == 0 ? K1 : W, W, bar);
+        ok = ftp::mbar_wait_bounded(bar, static_cast<unsigned>(l & 1));
+        if (__syncthreads_or(!ok)) {
+            ok = false;
+            break;
+        }
+        tc_fence_after();
+        // bias, ReLU, BF16; layers 1-2 back to shared memory as the next A, layer 3 into the
+        // last layer's dot product
+        const float *b = sb + l * W;
+        for (int c = 0; c < W; c += 16) {
+            float v[16];
+            tc_ld16(trow + static_cast<unsigned>(col + c), v);
+            __align__(16) __nv_bfloat16 e[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float a = v[i] + b[c + i];
+                e[i] = __float2bfloat16_rn(a > 0.f ? a : 0.f);
+            }
+            if (l < 2) {
+                *reinterpret_cast<uint4 *>(sA + kmaj_off(m, c, W)) = *reinterpret_cast<const uint4 *>(e);
+                *reinterpret_cast<uint4 *>(sA + kmaj_off(m, c + 8, W)) = *reinterpret_cast<const uint4 *>(e + 8);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    logit = __fmaf_rn(sb[3 * W + c + i], __bfloat162float(e[i]), logit);
+            }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
+    if (ok && m < rows)
+        p[s0 + m] = 1.f / (1.f + expf(-(logit + sb[4 * W])));
+    if (!ok && threadIdx.x == 0) {
+        atomicOr(status, FT_STATUS_TIMEOUT);
+        // products still in flight finish (bounded) before their tensor memory is freed
+        (void)ftp::mbar_wait_bounded(bar, 0);
+        (void)ftp::mbar_wait_bounded(bar, 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(ncols) : "memory");
     }
 }
 
@@ -531,10 +783,25 @@ int ft_mlp_predict(ft_mlp *m, const float *X, int64_t n, float *p, int bf16, int
                                                                                           m->n_params);
             m->bf16_stale = false;
         }
-        const int warps = 8;
-        k_infer_bf16<<<static_cast<unsigned>((n + warps - 1) / warps), 32 * warps,
-                       warps * 2 * m->width * sizeof(__nv_bfloat16), st>>>(
-            dX, n, m->d_in, m->width, m->d_theta_bf16, L.W1, L.b1, L.W2, L.b2, L.W3, L.b3, L.W4, L.b4, dp);
+        const int W = m->width, K1 = (m->d_in + 15) / 16 * 16;
+        const bool tc = bf16 != 2 && W % 16 == 0 && W <= kTcMaxW && K1 <= kTcMaxK;
+        if (tc) {
+            // tensor cores: 128 samples per CTA
+            const size_t smem = tc_layout(K1, W).total;
+            if (cudaFuncSetAttribute(k_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(smem)) != cudaSuccess)
+                rc = FT_ERR_CUDA;
+            else
+                k_infer_tc<<<static_cast<unsigned>((n + kTcM - 1) / kTcM), kTcM, smem, st>>>(
+                    dX, n, m->d_in, K1, W, m->d_theta_bf16, L.W1, L.b1, L.W2, L.b2, L.W3, L.b3, L.W4, L.b4, dp,
+                    m->ctx->d_status);
+        } else {
+            // CUDA cores: one warp per sample
+            const int warps = 8;
+            k_infer_bf16<<<static_cast<unsigned>((n + warps - 1) / warps), 32 * warps,
+                           warps * 2 * m->width * sizeof(__nv_bfloat16), st>>>(
+                dX, n, m->d_in, m->width, m->d_theta_bf16, L.W1, L.b1, L.W2, L.b2, L.W3, L.b3, L.W4, L.b4, dp);
+        }
     } else {
         // FP32 forward in chunks through the training kernels
         const int chunk = 4096;

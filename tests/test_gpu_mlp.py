@@ -72,3 +72,33 @@ def test_training_learns_and_is_deterministic(ctx):
     assert np.max(np.abs(p32 - p_or)) < 1e-5
     for n in nets:
         n.close()
+
+
+@pytest.mark.parametrize("d,w,n", [(D, W, 1000), (13, 128, 4096), (40, 64, 300), (9, 48, 129)])
+def test_bf16_inference_on_tensor_cores(ctx, d, w, n):
+    """BF16 inference with each hidden layer one tcgen05.mma product of 128 samples (FP32
+    accumulators in tensor memory) against (a) the same BF16 inference on the CUDA cores and
+    (b) the FP64 oracle.  Both BF16 paths round inputs, weights and activations to BF16 and sum
+    in FP32, so they differ only by summation order (an activation near a BF16 rounding
+    boundary can round the other way): at most 5e-3 in p, 5e-4 on average.  Against the FP64
+    network the BF16 roundings (unit roundoff 2^-8 per layer) allow 0.05, the tolerance of the
+    BF16 path.  Sample counts that are not a multiple of 128 leave a ragged last tile."""
+    net = ft.MLP(ctx, d, w, seed=5 + d)
+    g = np.random.default_rng(d * 100 + w)
+    X = g.standard_normal((4096, d)).astype(np.float32)
+    y = (X[:, 0] - 0.7 * X[:, 1] + 0.3 * g.standard_normal(4096) > 0).astype(np.float32)
+    net.train(X, y, batch=512, epochs=3, lr=2e-3, seed=7)
+    Xt = g.standard_normal((n, d)).astype(np.float32)
+    p_tc = net.predict(Xt, bf16=True)
+    p_cc = net.predict(Xt, bf16=True, tensor_cores=False)
+    p_or = omlp.predict(net.get_params().astype(np.float64), Xt, d, w)
+    assert np.all(np.isfinite(p_tc)) and np.all((p_tc >= 0) & (p_tc <= 1))
+    diff = np.abs(p_tc.astype(np.float64) - p_cc)
+    assert diff.max() < 5e-3 and diff.mean() < 5e-4, (diff.max(), diff.mean())
+    assert np.max(np.abs(p_tc - p_or)) < 0.05
+    # device input and output take the same path
+    import torch
+
+    p_dev = net.predict(torch.from_numpy(Xt).cuda(), bf16=True).cpu().numpy()
+    assert np.array_equal(p_dev, p_tc)
+    net.close()
