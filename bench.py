@@ -540,8 +540,39 @@ def run_surrogate(args):
     line = {"workload": "learned p_det surrogate across the batching workload's bands",
             "wall_s": time.perf_counter() - t0}
     line.update(res)
+    line["inference"] = inference_rates(ctx, local)
     print(json.dumps(line), flush=True)
     return 0
+
+
+def inference_rates(ctx, local, n=1 << 22, d=13, w=128):
+    """Samples/s of the surrogate's BF16 inference (the study's network shape: 13 features,
+    width 128) on the tensor cores and on the CUDA cores, device input and output; FLOP
+    counts 2 (d w + 2 w^2 + w) per sample."""
+    import torch
+
+    import paper_2411_18370_b300 as ft
+
+    net = ft.MLP(ctx, d, w, seed=1)
+    X = torch.randn(n, d, device="cuda")
+    out = {}
+    for name, tcores in (("tensor_cores", True), ("cuda_cores", False)):
+        for _ in range(3):
+            net.predict(X, bf16=True, tensor_cores=tcores)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for _ in range(5):
+            net.predict(X, bf16=True, tensor_cores=tcores)
+        ev[1].record()
+        torch.cuda.synchronize()
+        dt = ev[0].elapsed_time(ev[1]) / 5 / 1e3
+        out[name] = {"samples_per_s": n / dt, "ms": 1e3 * dt,
+                     "tflops": 2.0 * (d * w + 2 * w * w + w) * n / dt / 1e12}
+    out["samples"] = n
+    out["speedup"] = out["cuda_cores"]["ms"] / out["tensor_cores"]["ms"]
+    net.close()
+    return out
 
 
 def main():

@@ -248,7 +248,8 @@ __global__ void k_infer_bf16(const float *X, long long n, int d, int w, const __
 // ------------------------------------------------------------------ BF16 inference on
 // the tensor cores
 //
-// One CTA of 128 threads infers 128 samples: each layer is one M = 128 matrix product
+// A persistent CTA of 128 threads keeps the weights in shared memory and infers tiles of 128
+// samples (two CTAs per SM): each layer of a tile is one M = 128 matrix product
 // D[m][n] = sum_k A[m][k] W[n][k] by tcgen05.mma (kind::f16, BF16 operands from shared
 // memory, FP32 accumulators in tensor memory), issued by one thread and tracked by an
 // mbarrier; each thread then reads its sample's row of D from tensor memory, adds the bias,
@@ -400,9 +401,8 @@ __global__ void __launch_bounds__(kTcM) k_infer_tc(const float *X, long long n, 
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(tsm + L.bar);
     unsigned *s_tm = reinterpret_cast<unsigned *>(tsm + L.tm);
     const int warp = threadIdx.x >> 5;
-    const long long s0 = static_cast<long long>(blockIdx.x) * kTcM;
-    const int rows = static_cast<int>(min(static_cast<long long>(kTcM), n - s0));
     const unsigned ncols = W <= 16 ? 32u : W <= 32 ? 64u : W <= 64 ? 128u : 256u;  // two layers' D
+    const long long n_tiles = (n + kTcM - 1) / kTcM;
 
     if (threadIdx.x == 0) {
         ftp::mbar_init(bar, 1);
@@ -414,18 +414,10 @@ __global__ void __launch_bounds__(kTcM) k_infer_tc(const float *X, long long n, 
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // operands: weights, this CTA's samples (features rounded to BF16), biases and W4 in FP32
+    // the weights, once per CTA (persistent over sample tiles); biases and W4 in FP32
     tc_stage_bf16(sW1, th + oW1, d, W, K1, W, d);
     tc_stage_bf16(sW2, th + oW2, W, W, W, W, W);
     tc_stage_bf16(sW3, th + oW3, W, W, W, W, W);
-    for (int i = threadIdx.x; i < kTcM * (K1 / 8); i += blockDim.x) {
-        const int r = i / (K1 / 8), k0 = (i - r * (K1 / 8)) * 8;
-        __align__(16) __nv_bfloat16 e[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            e[j] = __float2bfloat16_rn(r < rows && k0 + j < d ? X[(s0 + r) * d + k0 + j] : 0.f);
-        *reinterpret_cast<uint4 *>(sA + kmaj_off(r, k0, K1)) = *reinterpret_cast<const uint4 *>(e);
-    }
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
         sb[i] = __bfloat162float(th[ob1 + i]);
         sb[W + i] = __bfloat162float(th[ob2 + i]);
@@ -434,59 +426,76 @@ __global__ void __launch_bounds__(kTcM) k_infer_tc(const float *X, long long n, 
     }
     if (threadIdx.x == 0)
         sb[4 * W] = __bfloat162float(th[ob4]);
-    fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const unsigned tm = *s_tm;
-    // this thread's sample: row m = tensor-memory lane 32 warp + lane
+    // this thread's sample of a tile: row m = tensor-memory lane 32 warp + lane
     const int m = threadIdx.x;
     const unsigned trow = tm + (static_cast<unsigned>(warp * 32) << 16);
     bool ok = true;
-    float logit = 0.f;
-    for (int l = 0; l < 3 && ok; ++l) {
-        const int col = (l & 1) * W;  // layers 1 and 3 in columns [0, W), layer 2 in [W, 2W)
-        if (threadIdx.x == 0)
-            tc_layer(tm, col, sA, l == 0 ? sW1 : l == 1 ? sW2 : sW3, l == 0 ? K1 : W, W, bar);
-        ok = ftp::mbar_wait_bounded(bar, static_cast<unsigned>(l & 1));
-        if (__syncthreads_or(!ok)) {
-            ok = false;
-            break;
-        }
-        tc_fence_after();
-        // bias, ReLU, BF16; layers 1-2 back to shared memory as the next A, layer 3 into the
-        // last layer's dot product
-        const float *b = sb + l * W;
-        for (int c = 0; c < W; c += 16) {
-            float v[16];
-            tc_ld16(trow + static_cast<unsigned>(col + c), v);
-            __align__(16) __nv_bfloat16 e[16];
+    unsigned phase = 0;  // parity of the barrier's next completion
+    for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        const long long s0 = tile * kTcM;
+        const int rows = static_cast<int>(min(static_cast<long long>(kTcM), n - s0));
+        // this tile's features rounded to BF16 (the previous tile's last product has read A)
+        for (int i = threadIdx.x; i < kTcM * (K1 / 8); i += blockDim.x) {
+            const int r = i / (K1 / 8), k0 = (i - r * (K1 / 8)) * 8;
+            __align__(16) __nv_bfloat16 e[8];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const float a = v[i] + b[c + i];
-                e[i] = __float2bfloat16_rn(a > 0.f ? a : 0.f);
-            }
-            if (l < 2) {
-                *reinterpret_cast<uint4 *>(sA + kmaj_off(m, c, W)) = *reinterpret_cast<const uint4 *>(e);
-                *reinterpret_cast<uint4 *>(sA + kmaj_off(m, c + 8, W)) = *reinterpret_cast<const uint4 *>(e + 8);
-            } else {
-#pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    logit = __fmaf_rn(sb[3 * W + c + i], __bfloat162float(e[i]), logit);
-            }
+            for (int j = 0; j < 8; ++j)
+                e[j] = __float2bfloat16_rn(r < rows && k0 + j < d ? X[(s0 + r) * d + k0 + j] : 0.f);
+            *reinterpret_cast<uint4 *>(sA + kmaj_off(r, k0, K1)) = *reinterpret_cast<const uint4 *>(e);
         }
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
+        float logit = 0.f;
+        for (int l = 0; l < 3; ++l) {
+            const int col = (l & 1) * W;  // layers 1 and 3 in columns [0, W), layer 2 in [W, 2W)
+            if (threadIdx.x == 0)
+                tc_layer(tm, col, sA, l == 0 ? sW1 : l == 1 ? sW2 : sW3, l == 0 ? K1 : W, W, bar);
+            ok = ftp::mbar_wait_bounded(bar, phase);
+            phase ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            // bias, ReLU, BF16; layers 1-2 back to shared memory as the next A, layer 3 into
+            // the last layer's dot product
+            const float *b = sb + l * W;
+            for (int c = 0; c < W; c += 16) {
+                float v[16];
+                tc_ld16(trow + static_cast<unsigned>(col + c), v);
+                __align__(16) __nv_bfloat16 e[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const float a = v[i] + b[c + i];
+                    e[i] = __float2bfloat16_rn(a > 0.f ? a : 0.f);
+                }
+                if (l < 2) {
+                    *reinterpret_cast<uint4 *>(sA + kmaj_off(m, c, W)) = *reinterpret_cast<const uint4 *>(e);
+                    *reinterpret_cast<uint4 *>(sA + kmaj_off(m, c + 8, W)) = *reinterpret_cast<const uint4 *>(e + 8);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        logit = __fmaf_rn(sb[3 * W + c + i], __bfloat162float(e[i]), logit);
+                }
+            }
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+        }
+        if (ok && m < rows)
+            p[s0 + m] = 1.f / (1.f + expf(-(logit + sb[4 * W])));
     }
-    if (ok && m < rows)
-        p[s0 + m] = 1.f / (1.f + expf(-(logit + sb[4 * W])));
     if (!ok && threadIdx.x == 0) {
         atomicOr(status, FT_STATUS_TIMEOUT);
         // products still in flight finish (bounded) before their tensor memory is freed
-        (void)ftp::mbar_wait_bounded(bar, 0);
-        (void)ftp::mbar_wait_bounded(bar, 1);
+        (void)ftp::mbar_wait_bounded(bar, phase);
     }
     tc_fence_before();
     __syncthreads();
@@ -792,7 +801,9 @@ int ft_mlp_predict(ft_mlp *m, const float *X, int64_t n, float *p, int bf16, int
                                      static_cast<int>(smem)) != cudaSuccess)
                 rc = FT_ERR_CUDA;
             else
-                k_infer_tc<<<static_cast<unsigned>((n + kTcM - 1) / kTcM), kTcM, smem, st>>>(
+                k_infer_tc<<<static_cast<unsigned>(std::min<long long>((n + kTcM - 1) / kTcM,
+                                                                          2ll * std::max(m->ctx->sm_count, 1))),
+                             kTcM, smem, st>>>(
                     dX, n, m->d_in, K1, W, m->d_theta_bf16, L.W1, L.b1, L.W2, L.b2, L.W3, L.b3, L.W4, L.b4, dp,
                     m->ctx->d_status);
         } else {
