@@ -1055,15 +1055,21 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
                 if (ev) {
                     // first tile offset jc at which the bin steps: jc = floor(num / |E|) + 1
                     // with num = 2^32 - 1 - L0 (E > 0: the first j with L0 + j E >= 2^32) or
-                    // num = L0 (E < 0: the first j with L0 + j E < 0).  An FP32 quotient,
-                    // then one exact integer step each way (the quotient is below J, so its
-                    // FP32 error is far under one)
+                    // num = L0 (E < 0: the first j with L0 + j E < 0).  16-bit storage: an
+                    // FP32 quotient, then one exact integer step each way (the quotient is
+                    // below J, so its FP32 error is far under one); FP32 storage keeps the
+                    // integer division (measured faster there, at the register cap)
                     const unsigned num = r.E > 0 ? 0xffffffffu - L0 : L0;
                     const unsigned den = static_cast<unsigned>(abs(r.E));
-                    int q = static_cast<int>(__fmul_rz(__uint2float_rz(num), __frcp_rz(__uint2float_rn(den))));
-                    const unsigned t = static_cast<unsigned>(q) * den;
-                    q -= t > num ? 1 : 0;
-                    q += (t <= num && num - t >= den) ? 1 : 0;
+                    int q;
+                    if constexpr (PAIR) {
+                        q = static_cast<int>(__fmul_rz(__uint2float_rz(num), __frcp_rz(__uint2float_rn(den))));
+                        const unsigned t = static_cast<unsigned>(q) * den;
+                        q -= t > num ? 1 : 0;
+                        q += (t <= num && num - t >= den) ? 1 : 0;
+                    } else {
+                        q = static_cast<int>(num / den);
+                    }
                     packed |= (q + 1) << 8;
                 }
             }
