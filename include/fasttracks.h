@@ -233,9 +233,9 @@ FT_API int ft_topk_per_band_gated(ft_ctx *ctx, const ft_band *band, const ft_ban
 
 /* Ahead-of-time boxes across the sky (Sec. IV.B) for the regular bank: box (x, b) holds the
  * templates of sub-band b whose sky point is among positions x sky_box .. (x + 1) sky_box - 1
- * of the bank's sky order (ft_bank_sky_order: declination zones of about sqrt(2 n_sky) points
- * walked alternately east and west, so a box is a strip of neighbouring sky points), every f1
- * value.  out: [n_sky_boxes][n_subbands][k]
+ * of the bank's sky order (ft_bank_sky_order: a Hilbert curve over the equal-area map
+ * ((z + 1)/2, (longitude + pi)/2pi) of the sphere, so a box is a compact patch of
+ * neighbouring sky points), every f1 value.  out: [n_sky_boxes][n_subbands][k]
  * ft_candidate with n_sky_boxes = ceil(n_sky / sky_box), each list as in ft_topk_per_band.
  * The launch shape keeps every CTA's sky points inside one box.  Errors: FT_ERR_ARG
  * (sky_box < 1), FT_ERR_RANGE (more than 65535 sky boxes, k), else as ft_topk_per_band. */
@@ -258,8 +258,8 @@ FT_API int ft_topk_per_box(ft_ctx *ctx, const ft_band *band, const ft_bank *bank
                            int f1_box, int k, const float *gate, float gate_min,
                            ft_candidate *out, int out_on_device, void *stream);
 
-/* The bank's sky order: order[i] = index (in the bank's sky list) of the sky point at position
- * i; host [n_sky] int32. */
+/* The bank's sky order (the Hilbert-curve order described at ft_topk_per_skybox): order[i] =
+ * index (in the bank's sky list) of the sky point at position i; host [n_sky] int32. */
 FT_API int ft_bank_sky_order(const ft_bank *bank, int32_t *order);
 
 /* Same search and same output as ft_topk_per_band, for callers that cannot let the library

@@ -509,21 +509,48 @@ int ft_band_info(const ft_band *b, int64_t *n, int *n_bins, int *stride, int *dt
     return FT_OK;
 }
 
-// Sky points ordered so that runs of a few consecutive points are close on the sky:
-// bands of equal area in z (about 2 points per band per row of the run), longitude
-// ascending in even bands and descending in odd ones.  dmax[P] is the largest distance
+// Position of cell (x, y) along the Hilbert curve that fills a 2^bits x 2^bits grid: the
+// curve visits the four quadrants of every square in turn (each reflected so that it starts
+// next to where the last one ended), so cells close along the curve are close in the grid.
+static uint64_t hilbert_position(uint32_t x, uint32_t y, int bits)
+{
+    uint64_t d = 0;
+    for (uint32_t s = 1u << (bits - 1); s > 0; s >>= 1) {
+        const uint32_t rx = (x & s) ? 1u : 0u, ry = (y & s) ? 1u : 0u;
+        d += static_cast<uint64_t>(s) * s * ((3u * rx) ^ ry);
+        // bring the quadrant into the curve's base orientation for the next level
+        x &= s - 1;
+        y &= s - 1;
+        if (ry == 0) {
+            if (rx == 1) {
+                x = s - 1 - x;
+                y = s - 1 - y;
+            }
+            std::swap(x, y);
+        }
+    }
+    return d;
+}
+
+// Sky points ordered along a Hilbert curve over the equal-area map ((z + 1)/2, (phi + pi)/2pi)
+// of the sphere, so that any run of consecutive points is a compact patch of sky: a CTA's
+// group of P points, a sky box, and the few hundred groups the resident CTAs of a launch
+// work on at once (whose rows' windows then overlap in L2).  dmax[P] is the largest distance
 // between two points of one run g*P .. g*P + P - 1 of the order.
 static void sky_proximity_order(const double *sky, int64_t n, std::vector<int> &order,
                                 double dmax[kMaxSkyGroup + 1])
 {
-    const int nz = std::max<int>(1, static_cast<int>(std::lround(std::sqrt(n / 2.0))));
-    std::vector<std::pair<std::pair<int, double>, int>> key(n);
+    constexpr int bits = 16;
+    constexpr double kPi = 3.14159265358979323846;
+    const double cells = static_cast<double>(1u << bits);
+    auto cell = [&](double u) {
+        return static_cast<uint32_t>(std::min(std::max(u * cells, 0.0), cells - 1.0));
+    };
+    std::vector<std::pair<uint64_t, int>> key(n);
     for (int64_t i = 0; i < n; ++i) {
         const double x = sky[3 * i], y = sky[3 * i + 1], z = sky[3 * i + 2];
-        int zone = static_cast<int>(std::floor((z + 1.0) * 0.5 * nz));
-        zone = std::min(std::max(zone, 0), nz - 1);
-        const double phi = std::atan2(y, x);
-        key[i] = {{zone, (zone & 1) ? -phi : phi}, static_cast<int>(i)};
+        const double u = (z + 1.0) * 0.5, v = (std::atan2(y, x) + kPi) / (2.0 * kPi);
+        key[i] = {hilbert_position(cell(u), cell(v), bits), static_cast<int>(i)};
     }
     std::sort(key.begin(), key.end());
     order.resize(n);
