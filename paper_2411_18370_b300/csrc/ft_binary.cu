@@ -445,10 +445,17 @@ __global__ void __launch_bounds__(kBtBlock) k_bt_eval(const BtParams p)
         valid[u] = ti[u] < t_end;
     }
 
+    __shared__ unsigned s_done[2];
+    __shared__ int s_issued[2];  // the last stage copied into each buffer (-1: none)
+    __shared__ int s_abort;
     if (threadIdx.x == 0) {
         ftp::mbar_init(&bars[0], 1);
         ftp::mbar_init(&bars[1], 1);
         ftp::fence_mbar_init();
+        s_done[0] = s_done[1] = 0;
+        s_issued[0] = 0;
+        s_issued[1] = p.n_stages > 1 ? 1 : -1;
+        s_abort = 0;
     }
     for (int i = threadIdx.x; i < kBtTab; i += kBtBlock)
         tab[i] = p.costab[i];
@@ -484,24 +491,34 @@ __global__ void __launch_bounds__(kBtBlock) k_bt_eval(const BtParams p)
         oob[u] = 0;
     }
     unsigned n64 = 0;
-    bool failed = false;
+    // No CTA barrier per stage: each warp releases a buffer when it is done with it, and the
+    // last warp to release it refills it with the stage after next, so a warp slowed down by
+    // FP64 decisions holds the others back only when they are a whole stage ahead.
+    // s_done[b] counts releases of buffer b: stage st is its (st / 2)-th use.
+    const int lane = threadIdx.x & 31;
+    constexpr unsigned kWarps = kBtBlock / 32;
     for (int st = 0; st < p.n_stages; ++st) {
         const int b = st & 1;
-        const bool ok = ftp::mbar_wait_bounded(&bars[b], (st >> 1) & 1);
+        if (*reinterpret_cast<volatile int *>(&s_abort) != 0)
+            break;
+        const bool ok = __all_sync(0xffffffffu, ftp::mbar_wait_bounded(&bars[b], (st >> 1) & 1));
+        if (!ok) {
+            if (lane == 0)
+                atomicExch(&s_abort, 1);
+            break;
+        }
         const int nr = min(p.S, p.N - st * p.S);
         float part[kBtTPT], partB[kBtTPT], partC[kBtTPT];
 #pragma unroll
         for (int u = 0; u < kBtTPT; ++u)
             part[u] = partB[u] = partC[u] = 0.f;
-        if (ok) {
-            const uint2 *tqs = reinterpret_cast<const uint2 *>(stq[b]);
-            if (inside)
-                bt_rows<T, WEIGHTED, SKY, false>(p, t, valid, sl, st * p.S, nr, sv[b], tqs, rows[b], sd[b], tabl,
-                                                 part, partB, partC, oob, n64);
-            else
-                bt_rows<T, WEIGHTED, SKY, true>(p, t, valid, sl, st * p.S, nr, sv[b], tqs, rows[b], sd[b], tabl,
-                                                part, partB, partC, oob, n64);
-        }
+        const uint2 *tqs = reinterpret_cast<const uint2 *>(stq[b]);
+        if (inside)
+            bt_rows<T, WEIGHTED, SKY, false>(p, t, valid, sl, st * p.S, nr, sv[b], tqs, rows[b], sd[b], tabl,
+                                             part, partB, partC, oob, n64);
+        else
+            bt_rows<T, WEIGHTED, SKY, true>(p, t, valid, sl, st * p.S, nr, sv[b], tqs, rows[b], sd[b], tabl,
+                                            part, partB, partC, oob, n64);
         // compensated folds of the stage's partials (2Sum)
 #pragma unroll
         for (int u = 0; u < kBtTPT; ++u) {
@@ -511,24 +528,37 @@ __global__ void __launch_bounds__(kBtBlock) k_bt_eval(const BtParams p)
                 fold2(hiC[u], loC[u], partC[u]);
             }
         }
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
+        // release buffer b: the warp's reads of it are done before lane 0 counts the release
+        __syncwarp();
+        unsigned last = 0;
+        if (lane == 0) {
+            __threadfence_block();
+            last = atomicAdd(&s_done[b], 1u) + 1u == kWarps * static_cast<unsigned>((st >> 1) + 1) ? 1u : 0u;
         }
-        if (threadIdx.x < 32 && st + 2 < p.n_stages)
+        if (__shfl_sync(0xffffffffu, last, 0) != 0 && st + 2 < p.n_stages) {
+            // every warp's reads of the buffer come before the copies that overwrite it
+            __threadfence_block();
+            ftp::fence_proxy_async_smem();
             bt_issue(p, st + 2, rows[b], sv[b], stq[b], sd[b], &bars[b]);
+            if (lane == 0)
+                s_issued[b] = st + 2;
+        }
     }
     if (p.n64 != nullptr) {
         const unsigned w64 = __reduce_add_sync(0xffffffffu, n64);
-        if ((threadIdx.x & 31) == 0 && w64 != 0)
+        if (lane == 0 && w64 != 0)
             atomicAdd(p.n64, static_cast<unsigned long long>(w64));
     }
-    if (failed) {
+    // every warp is past its last read of the stage buffers (the epilogue reuses them)
+    __syncthreads();
+    if (s_abort != 0) {
         if (threadIdx.x == 0) {
             atomicOr(p.status, FT_STATUS_TIMEOUT);
-            // let copies still in flight land before the shared memory is released
-            (void)ftp::mbar_wait_bounded(&bars[0], 0);
-            (void)ftp::mbar_wait_bounded(&bars[1], 0);
+            // let the last copies issued into each buffer land before the shared memory is
+            // released (stage s is phase s / 2 of its buffer's barrier)
+            for (int b2 = 0; b2 < 2; ++b2)
+                if (s_issued[b2] >= 0)
+                    (void)ftp::mbar_wait_bounded(&bars[b2], (s_issued[b2] >> 1) & 1);
         }
         __syncthreads();
         return;
@@ -574,7 +604,6 @@ __global__ void __launch_bounds__(kBtBlock) k_bt_eval(const BtParams p)
     __syncthreads();
     if (threadIdx.x >= 32)
         return;
-    const int lane = threadIdx.x;
     const int n_here = static_cast<int>(t_end - t_begin);
     float last_s = INFINITY;
     long long last_t = -1;

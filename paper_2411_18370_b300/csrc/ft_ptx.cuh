@@ -32,6 +32,13 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, u
         : "memory");
 }
 
+// Orders this thread's earlier shared-memory accesses (generic proxy) before later bulk or
+// tensor copies (async proxy) into the same memory.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
 {
     asm volatile(
