@@ -248,13 +248,17 @@ __global__ void k_infer_bf16(const float *X, long long n, int d, int w, const __
 // ------------------------------------------------------------------ BF16 inference on
 // the tensor cores
 //
-// A persistent CTA of 128 threads keeps the weights in shared memory and infers tiles of 128
-// samples (two CTAs per SM): each layer of a tile is one M = 128 matrix product
-// D[m][n] = sum_k A[m][k] W[n][k] by tcgen05.mma (kind::f16, BF16 operands from shared
-// memory, FP32 accumulators in tensor memory), issued by one thread and tracked by an
-// mbarrier; each thread then reads its sample's row of D from tensor memory, adds the bias,
-// applies the ReLU and writes the BF16 activations back to shared memory as the next
-// layer's A.  The last layer (width -> 1) and the sigmoid run on the CUDA cores in FP32.
+// One persistent CTA per SM keeps the weights in shared memory and runs four groups of 128
+// threads, each inferring its own tiles of 128 samples, so that four tiles are in flight per
+// SM and one group's products overlap the others' epilogues.  Each layer of a tile is one
+// M = 128 matrix product D[m][n] = sum_k A[m][k] W[n][k] by tcgen05.mma (kind::f16, BF16
+// operands from shared memory, FP32 accumulators in the group's tensor-memory columns),
+// issued by one thread of the group and tracked by the group's mbarrier; the products
+// accumulate onto the layer's bias, stored into those columns beforehand.  Sample m's row of
+// D sits in tensor-memory lane m, read by thread m of the group, which applies the ReLU with
+// the rounding to BF16 (one conversion per pair) and writes the activations back to the
+// group's shared-memory A for the next layer.  The last layer (width -> 1) and the sigmoid
+// run on the CUDA cores in FP32.  The groups synchronise with named barriers only.
 // Numerics match the SIMT BF16 path: BF16 inputs, weights and activations, FP32 sums.
 //
 // Shared-memory operands use the no-swizzle K-major layout of the tcgen05 matrix
@@ -265,7 +269,9 @@ __global__ void k_infer_bf16(const float *X, long long n, int d, int w, const __
 // offset) and adjacent 8-row groups 16 K bytes apart (its stride-dimension offset); the
 // product over k in [16 i, 16 i + 16) starts 256 i bytes into each operand.
 
-constexpr int kTcM = 128;       // samples per CTA (the MMA's M)
+constexpr int kTcM = 128;       // samples per tile (the MMA's M)
+constexpr int kTcGroups = 4;    // tiles in flight per CTA (one group of kTcM threads each)
+constexpr int kTcThreads = kTcM * kTcGroups;
 constexpr int kTcMaxW = 128;    // hidden widths 16 .. 128 (multiples of 16)
 constexpr int kTcMaxK = 64;     // padded inputs 16 .. 64
 
@@ -320,25 +326,62 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 // generic-proxy writes to shared memory made visible to the tensor cores' reads
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// 16 consecutive FP32 columns of this thread's tensor-memory lane
-__device__ __forceinline__ void tc_ld16(unsigned taddr, float (&v)[16])
+// 8 consecutive FP32 columns of this thread's tensor-memory lane, as raw bits; the values
+// are usable after tc_wait_ld()
+__device__ __forceinline__ void tc_ld8(unsigned taddr, unsigned *r)
 {
-    unsigned r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-        "%12, %13, %14, %15}, [%16];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
         : "r"(taddr)
         : "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i)
-        v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 8 consecutive FP32 columns of this thread's tensor-memory lane from shared memory (bias
+// values); complete after tc_wait_st()
+__device__ __forceinline__ void tc_st8(unsigned taddr, const float *v)
+{
+    const float4 a = *reinterpret_cast<const float4 *>(v), b = *reinterpret_cast<const float4 *>(v + 4);
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(__float_as_uint(a.x)), "r"(__float_as_uint(a.y)), "r"(__float_as_uint(a.z)),
+                 "r"(__float_as_uint(a.w)), "r"(__float_as_uint(b.x)), "r"(__float_as_uint(b.y)),
+                 "r"(__float_as_uint(b.z)), "r"(__float_as_uint(b.w))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// the kTcM threads of group g (named barrier g + 1; barrier 0 is __syncthreads)
+__device__ __forceinline__ void group_sync(int g)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kTcM) : "memory");
+}
+
+// group_sync that also returns whether v holds on every thread of the group
+__device__ __forceinline__ bool group_all(int g, bool v)
+{
+    unsigned r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(v ? 1u : 0u), "r"(g + 1), "r"(kTcM)
+        : "memory");
+    return r != 0;
+}
+
+// bf16(max(a, 0)) in the low half and bf16(max(b, 0)) in the high half, round to nearest
+__device__ __forceinline__ unsigned relu_bf16x2(float a, float b)
+{
+    unsigned d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+    return d;
 }
 
 struct TcSmem {
-    size_t w1, w2, w3, act, bias, bar, tm, total;
+    size_t w1, w2, w3, act, act_bytes, bias, bar, tm, total;
 };
 
 __host__ __device__ inline TcSmem tc_layout(int K1, int W)
@@ -351,13 +394,14 @@ __host__ __device__ inline TcSmem tc_layout(int K1, int W)
     o += static_cast<size_t>(W) * W * 2;
     L.w3 = o;
     o += static_cast<size_t>(W) * W * 2;
-    L.act = o;
-    o += static_cast<size_t>(kTcM) * (K1 > W ? K1 : W) * 2;
+    L.act = o;  // one A operand per group
+    L.act_bytes = static_cast<size_t>(kTcM) * (K1 > W ? K1 : W) * 2;
+    o += kTcGroups * L.act_bytes;
     L.bias = o;  // b1, b2, b3, W4 as FP32 [4][W], then b4
     o += (4 * static_cast<size_t>(W) + 4) * 4;
     o = (o + 15) / 16 * 16;
-    L.bar = o;
-    o += 16;
+    L.bar = o;  // one mbarrier per group
+    o += 8 * kTcGroups;
     L.tm = o;
     o += 16;
     L.total = o;
@@ -379,33 +423,40 @@ __device__ void tc_stage_bf16(unsigned char *dst, const __nv_bfloat16 *src, long
     }
 }
 
-// One layer's products: D (tensor-memory columns col..col+W) = A (128 x K) x W^T (W x K).
+// One layer's products: D (tensor-memory columns col..col+W) += A (128 x K) x W^T (W x K),
+// onto the bias already stored in those columns.
 __device__ __forceinline__ void tc_layer(unsigned tm, int col, const unsigned char *A, const unsigned char *Wt, int K,
                                          int W, unsigned long long *bar)
 {
     const unsigned a0 = smem_u32(A), b0 = smem_u32(Wt), idesc = tc_idesc_bf16(kTcM, W);
     for (int i = 0; i < K / 16; ++i)
-        tc_mma(tm + static_cast<unsigned>(col), tc_desc(a0 + 256u * i, K), tc_desc(b0 + 256u * i, K), idesc, i > 0);
+        tc_mma(tm + static_cast<unsigned>(col), tc_desc(a0 + 256u * i, K), tc_desc(b0 + 256u * i, K), idesc, 1);
     tc_commit(bar);
 }
 
-__global__ void __launch_bounds__(kTcM) k_infer_tc(const float *X, long long n, int d, int K1, int W,
-                                                  const __nv_bfloat16 *th, long long oW1, long long ob1,
-                                                  long long oW2, long long ob2, long long oW3, long long ob3,
-                                                  long long oW4, long long ob4, float *p, unsigned *status)
+template <int W>
+__global__ void __launch_bounds__(kTcThreads, 1) k_infer_tc(const float *X, long long n, int d, int K1,
+                                                           const __nv_bfloat16 *th, long long oW1, long long ob1,
+                                                           long long oW2, long long ob2, long long oW3, long long ob3,
+                                                           long long oW4, long long ob4, float *p, unsigned *status)
 {
+    // tensor-memory columns per group (a power of two, so that the allocation is one)
+    constexpr int Wc = W <= 32 ? 32 : W <= 64 ? 64 : 128;
+    constexpr unsigned ncols = kTcGroups * Wc;
     extern __shared__ __align__(128) unsigned char tsm[];
     const TcSmem L = tc_layout(K1, W);
-    unsigned char *sW1 = tsm + L.w1, *sW2 = tsm + L.w2, *sW3 = tsm + L.w3, *sA = tsm + L.act;
-    float *sb = reinterpret_cast<float *>(tsm + L.bias);
-    unsigned long long *bar = reinterpret_cast<unsigned long long *>(tsm + L.bar);
-    unsigned *s_tm = reinterpret_cast<unsigned *>(tsm + L.tm);
+    const int g = threadIdx.x / kTcM, m = threadIdx.x % kTcM;  // group; sample row and lane
     const int warp = threadIdx.x >> 5;
-    const unsigned ncols = W <= 16 ? 32u : W <= 32 ? 64u : W <= 64 ? 128u : 256u;  // two layers' D
+    unsigned char *sW1 = tsm + L.w1, *sW2 = tsm + L.w2, *sW3 = tsm + L.w3;
+    unsigned char *sA = tsm + L.act + g * L.act_bytes;
+    float *sb = reinterpret_cast<float *>(tsm + L.bias);
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(tsm + L.bar) + g;
+    unsigned *s_tm = reinterpret_cast<unsigned *>(tsm + L.tm);
     const long long n_tiles = (n + kTcM - 1) / kTcM;
 
     if (threadIdx.x == 0) {
-        ftp::mbar_init(bar, 1);
+        for (int i = 0; i < kTcGroups; ++i)
+            ftp::mbar_init(reinterpret_cast<unsigned long long *>(tsm + L.bar) + i, 1);
         ftp::fence_mbar_init();
     }
     if (warp == 0) {
@@ -429,17 +480,23 @@ __global__ void __launch_bounds__(kTcM) k_infer_tc(const float *X, long long n, 
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const unsigned tm = *s_tm;
-    // this thread's sample of a tile: row m = tensor-memory lane 32 warp + lane
-    const int m = threadIdx.x;
-    const unsigned trow = tm + (static_cast<unsigned>(warp * 32) << 16);
+    // the group's accumulator columns; this thread's lane m (warp w reads lanes 32 (w % 4) ..)
+    const unsigned tg = *s_tm + static_cast<unsigned>(g * Wc);
+    const unsigned trow = tg + (static_cast<unsigned>((warp & 3) * 32) << 16);
+    // layer 1's bias into this row's accumulator columns
+#pragma unroll
+    for (int c = 0; c < W; c += 8)
+        tc_st8(trow + static_cast<unsigned>(c), sb + c);
+    tc_wait_st();
     bool ok = true;
-    unsigned phase = 0;  // parity of the barrier's next completion
-    for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+    unsigned phase = 0;  // parity of the group's barrier's next completion
+    const long long stride = static_cast<long long>(gridDim.x) * kTcGroups;
+    for (long long tile = static_cast<long long>(blockIdx.x) * kTcGroups + g; tile < n_tiles && ok;
+         tile += stride) {
         const long long s0 = tile * kTcM;
         const int rows = static_cast<int>(min(static_cast<long long>(kTcM), n - s0));
         // this tile's features rounded to BF16 (the previous tile's last product has read A)
-        for (int i = threadIdx.x; i < kTcM * (K1 / 8); i += blockDim.x) {
+        for (int i = m; i < kTcM * (K1 / 8); i += kTcM) {
             const int r = i / (K1 / 8), k0 = (i - r * (K1 / 8)) * 8;
             __align__(16) __nv_bfloat16 e[8];
 #pragma unroll
@@ -449,59 +506,106 @@ __global__ void __launch_bounds__(kTcM) k_infer_tc(const float *X, long long n, 
         }
         fence_async_smem();
         tc_fence_before();
-        __syncthreads();
+        group_sync(g);
         tc_fence_after();
         float logit = 0.f;
         for (int l = 0; l < 3; ++l) {
-            const int col = (l & 1) * W;  // layers 1 and 3 in columns [0, W), layer 2 in [W, 2W)
-            if (threadIdx.x == 0)
-                tc_layer(tm, col, sA, l == 0 ? sW1 : l == 1 ? sW2 : sW3, l == 0 ? K1 : W, W, bar);
-            ok = ftp::mbar_wait_bounded(bar, phase);
+            if (m == 0)
+                tc_layer(tg, 0, sA, l == 0 ? sW1 : l == 1 ? sW2 : sW3, l == 0 ? K1 : W, W, bar);
+            ok = group_all(g, ftp::mbar_wait_bounded(bar, phase));
             phase ^= 1u;
-            if (__syncthreads_or(!ok)) {
-                ok = false;
+            if (!ok)
                 break;
-            }
             tc_fence_after();
-            // bias, ReLU, BF16; layers 1-2 back to shared memory as the next A, layer 3 into
-            // the last layer's dot product
-            const float *b = sb + l * W;
-            for (int c = 0; c < W; c += 16) {
-                float v[16];
-                tc_ld16(trow + static_cast<unsigned>(col + c), v);
-                __align__(16) __nv_bfloat16 e[16];
+            // 32 columns at a time: ReLU and BF16, layers 1-2 back to shared memory as the
+            // next A, layer 3 into the last layer's dot product; then the next product's bias
+            // into the columns just read (layer l + 1's, or layer 1's of the next tile)
+            const float *nb = sb + (l == 2 ? 0 : l + 1) * W;
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const float a = v[i] + b[c + i];
-                    e[i] = __float2bfloat16_rn(a > 0.f ? a : 0.f);
-                }
-                if (l < 2) {
-                    *reinterpret_cast<uint4 *>(sA + kmaj_off(m, c, W)) = *reinterpret_cast<const uint4 *>(e);
-                    *reinterpret_cast<uint4 *>(sA + kmaj_off(m, c + 8, W)) = *reinterpret_cast<const uint4 *>(e + 8);
-                } else {
+            for (int c0 = 0; c0 < W; c0 += 32) {
+                constexpr int kC = W < 32 ? W : 32;
+                unsigned raw[kC];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        logit = __fmaf_rn(sb[3 * W + c + i], __bfloat162float(e[i]), logit);
+                for (int c = 0; c < kC; c += 8)
+                    tc_ld8(trow + static_cast<unsigned>(c0 + c), raw + c);
+                tc_wait_ld();
+#pragma unroll
+                for (int c = 0; c < kC && c0 + c < W; c += 8) {
+                    uint4 e;
+                    e.x = relu_bf16x2(__uint_as_float(raw[c]), __uint_as_float(raw[c + 1]));
+                    e.y = relu_bf16x2(__uint_as_float(raw[c + 2]), __uint_as_float(raw[c + 3]));
+                    e.z = relu_bf16x2(__uint_as_float(raw[c + 4]), __uint_as_float(raw[c + 5]));
+                    e.w = relu_bf16x2(__uint_as_float(raw[c + 6]), __uint_as_float(raw[c + 7]));
+                    if (l < 2) {
+                        *reinterpret_cast<uint4 *>(sA + kmaj_off(m, c0 + c, W)) = e;
+                    } else {
+                        const float *w4 = sb + 3 * W + c0 + c;
+                        const unsigned u[4] = {e.x, e.y, e.z, e.w};
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            logit = __fmaf_rn(w4[2 * i], __uint_as_float(u[i] << 16), logit);
+                            logit = __fmaf_rn(w4[2 * i + 1], __uint_as_float(u[i] & 0xffff0000u), logit);
+                        }
+                    }
+                    tc_st8(trow + static_cast<unsigned>(c0 + c), nb + c0 + c);
                 }
             }
+            tc_wait_st();
             fence_async_smem();
             tc_fence_before();
-            __syncthreads();
+            group_sync(g);
             tc_fence_after();
         }
         if (ok && m < rows)
             p[s0 + m] = 1.f / (1.f + expf(-(logit + sb[4 * W])));
     }
-    if (!ok && threadIdx.x == 0) {
+    if (!ok && m == 0) {
         atomicOr(status, FT_STATUS_TIMEOUT);
-        // products still in flight finish (bounded) before their tensor memory is freed
+        // a product still in flight finishes (bounded) before its tensor memory is freed
         (void)ftp::mbar_wait_bounded(bar, phase);
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(ncols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*s_tm), "r"(ncols) : "memory");
+    }
+}
+
+// the tensor-core inference for hidden width W (a multiple of 16, at most kTcMaxW)
+template <int W>
+cudaError_t tc_launch(const float *X, long long n, int d, int K1, const __nv_bfloat16 *th, const Layout &L,
+                      float *p, unsigned *status, int sms, size_t smem_optin, cudaStream_t st)
+{
+    const size_t smem = tc_layout(K1, W).total;
+    if (smem > smem_optin)
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_infer_tc<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess)
+        return e;
+    const long long grid =
+        std::min<long long>(((n + kTcM - 1) / kTcM + kTcGroups - 1) / kTcGroups, std::max(sms, 1));
+    k_infer_tc<W><<<static_cast<unsigned>(grid), kTcThreads, smem, st>>>(X, n, d, K1, th, L.W1, L.b1,
+                                                                          L.W2, L.b2, L.W3, L.b3, L.W4, L.b4, p,
+                                                                          status);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_dispatch(int W, const float *X, long long n, int d, int K1, const __nv_bfloat16 *th,
+                        const Layout &L, float *p, unsigned *status, int sms, size_t smem_optin,
+                        cudaStream_t st)
+{
+    switch (W) {
+    case 16: return tc_launch<16>(X, n, d, K1, th, L, p, status, sms, smem_optin, st);
+    case 32: return tc_launch<32>(X, n, d, K1, th, L, p, status, sms, smem_optin, st);
+    case 48: return tc_launch<48>(X, n, d, K1, th, L, p, status, sms, smem_optin, st);
+    case 64: return tc_launch<64>(X, n, d, K1, th, L, p, status, sms, smem_optin, st);
+    case 80: return tc_launch<80>(X, n, d, K1, th, L, p, status, sms, smem_optin, st);
+    case 96: return tc_launch<96>(X, n, d, K1, th, L, p, status, sms, smem_optin, st);
+    case 112: return tc_launch<112>(X, n, d, K1, th, L, p, status, sms, smem_optin, st);
+    case 128: return tc_launch<128>(X, n, d, K1, th, L, p, status, sms, smem_optin, st);
+    default: return cudaErrorInvalidValue;
     }
 }
 
@@ -796,16 +900,9 @@ int ft_mlp_predict(ft_mlp *m, const float *X, int64_t n, float *p, int bf16, int
         const bool tc = bf16 != 2 && W % 16 == 0 && W <= kTcMaxW && K1 <= kTcMaxK;
         if (tc) {
             // tensor cores: 128 samples per CTA
-            const size_t smem = tc_layout(K1, W).total;
-            if (cudaFuncSetAttribute(k_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(smem)) != cudaSuccess)
+            if (tc_dispatch(W, dX, n, m->d_in, K1, m->d_theta_bf16, L, dp, m->ctx->d_status, m->ctx->sm_count,
+                            m->ctx->smem_optin, st) != cudaSuccess)
                 rc = FT_ERR_CUDA;
-            else
-                k_infer_tc<<<static_cast<unsigned>(std::min<long long>((n + kTcM - 1) / kTcM,
-                                                                          2ll * std::max(m->ctx->sm_count, 1))),
-                             kTcM, smem, st>>>(
-                    dX, n, m->d_in, K1, W, m->d_theta_bf16, L.W1, L.b1, L.W2, L.b2, L.W3, L.b3, L.W4, L.b4, dp,
-                    m->ctx->d_status);
         } else {
             // CUDA cores: one warp per sample
             const int warps = 8;
