@@ -182,6 +182,31 @@ def profiled_traffic(dtype):
         return None
 
 
+def profiled_traffic_batch(dtype, sky_scale):
+    """DRAM bytes (read + write) per full-density launch of the persistent batch kernel from
+    the committed ncu capture, or None for another storage type or density, or when the
+    kernel source or the sky order's source changed since it was taken."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", f"k_eval_batched_{dtype}_full_dram.md")
+    if sky_scale != 1.0 or not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line and not line.startswith((" ", "#", "`")):
+            k, v = line.split(":", 1)
+            fields[k.strip()] = v.strip()
+    csrc = os.path.join(ROOT, "paper_2411_18370_b300", "csrc")
+    for key, name in (("kernel source sha256 prefix", "ft_eval.cu"), ("sky order source sha256 prefix", "ft_api.cu")):
+        sha = hashlib.sha256(open(os.path.join(csrc, name), "rb").read()).hexdigest()[:16]
+        if fields.get(key) != sha:
+            return None
+    try:
+        return float(fields["dram bytes per launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def rel_error(s_gpu, s_or):
     r = np.abs(np.asarray(s_gpu, np.float64) - s_or) / np.abs(s_or)
     return {"max": float(r.max()), "rms": float(math.sqrt(np.mean(r * r))), "n": int(len(r))}
@@ -322,7 +347,8 @@ def batch_measure(args, ctx, local, sky_scale, steps, warmup, loop_steps, cpu_se
                      "peak_basis": "derived: 148 SMs x 128 B/clk shared-memory load bandwidth x "
                                    "2032 MHz max SM clock",
                      "algorithmic_bytes_per_launch": evals * esize, "bytes_per_eval": esize,
-                     "traffic": None},
+                     # DRAM bytes: the stored rows are 3.2 GB; L2 serves the tiles' re-reads
+                     "traffic": profiled_traffic_batch(args.dtype, sky_scale)},
         "l2": "flushed between timed steps",
         "clocks": clk.summary(),
     }
