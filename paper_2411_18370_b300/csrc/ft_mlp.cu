@@ -704,20 +704,18 @@ int ft_mlp_create(ft_ctx *ctx, int d_in, int width, uint64_t seed, ft_mlp **out)
     fill(L.W2, 1ll * width * width, width);
     fill(L.W3, 1ll * width * width, width);
     fill(L.W4, width, width);
-    cudaError_t e;
-    if ((e = cudaMalloc(&m->d_theta, L.n * 4)) != cudaSuccess ||
-        (e = cudaMalloc(&m->d_grad, L.n * 4)) != cudaSuccess ||
-        (e = cudaMalloc(&m->d_m, L.n * 4)) != cudaSuccess ||
-        (e = cudaMalloc(&m->d_v, L.n * 4)) != cudaSuccess ||
-        (e = cudaMalloc(&m->d_theta_bf16, L.n * 2)) != cudaSuccess ||
-        (e = cudaMalloc(&m->d_loss, 4)) != cudaSuccess) {
+    if (cudaMalloc(&m->d_theta, L.n * 4) != cudaSuccess || cudaMalloc(&m->d_grad, L.n * 4) != cudaSuccess ||
+        cudaMalloc(&m->d_m, L.n * 4) != cudaSuccess || cudaMalloc(&m->d_v, L.n * 4) != cudaSuccess ||
+        cudaMalloc(&m->d_theta_bf16, L.n * 2) != cudaSuccess || cudaMalloc(&m->d_loss, 4) != cudaSuccess) {
         ft_mlp_destroy(m);
         FT_FAIL(FT_ERR_OOM, "mlp_create: allocation failed");
     }
-    cudaMemcpy(m->d_theta, th.data(), L.n * 4, cudaMemcpyHostToDevice);
-    cudaMemset(m->d_grad, 0, L.n * 4);
-    cudaMemset(m->d_m, 0, L.n * 4);
-    cudaMemset(m->d_v, 0, L.n * 4);
+    if (cudaMemcpy(m->d_theta, th.data(), L.n * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(m->d_grad, 0, L.n * 4) != cudaSuccess || cudaMemset(m->d_m, 0, L.n * 4) != cudaSuccess ||
+        cudaMemset(m->d_v, 0, L.n * 4) != cudaSuccess) {
+        ft_mlp_destroy(m);
+        FT_FAIL(FT_ERR_CUDA, "mlp_create: initialisation failed");
+    }
     *out = m;
     return FT_OK;
 }
@@ -825,8 +823,7 @@ int ft_mlp_train(ft_mlp *m, const float *X, const float *y, int64_t n, int batch
     const int B = static_cast<int>(std::min<int64_t>(batch, n));
     FT_TRY(ensure_batch(m, B));
     float *dX = nullptr, *dy = nullptr;
-    cudaError_t e;
-    if ((e = cudaMalloc(&dX, n * m->d_in * 4)) != cudaSuccess || (e = cudaMalloc(&dy, n * 4)) != cudaSuccess) {
+    if (cudaMalloc(&dX, n * m->d_in * 4) != cudaSuccess || cudaMalloc(&dy, n * 4) != cudaSuccess) {
         cudaFree(dX);
         FT_FAIL(FT_ERR_OOM, "mlp_train: allocation failed");
     }
