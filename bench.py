@@ -2,7 +2,8 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--dtype f16|bf16|f32] [--n-sky 10000] [--no-cpu-baseline] [--no-e2e]
-                    [--no-batch] [--batch-steps 2] [--workload search|batch|surrogate|binary]
+                    [--no-batch] [--batch-steps 2]
+                    [--workload search|batch|surrogate|binary|inference]
 
 One step = the whole hot path over the search-shaped workload: for every template of the
 bank (180 f0 x 20 f1 x 1e4 sky = 3.6e7 templates) and every SFT (2 detectors x 1 yr at 70%
@@ -16,6 +17,10 @@ timed on the full bank; relative error and per-sub-band candidate sets against t
 every template of a 1-in-100 sky sub-bank, which is also the CPU baseline's sample); the end-
 to-end rate from host buffers; and the batching workload (64 bands at the stated sky
 density, one persistent graph-captured launch per step, against the per-band loop).
+
+Other workloads print their own line: the batch alone at a chosen sky density, the
+binary-orbit track over a random hyperbox bank, the learned-surrogate study, and the
+surrogate's BF16 inference on the tensor cores alone (`inference`).
 
 Under torchrun (N > 1) every rank runs its own replica of the workload (weak scaling, no
 data-path collective); rank 0 prints the JSON line.
@@ -571,6 +576,42 @@ def run_surrogate(args):
     return 0
 
 
+def run_inference(args):
+    """The surrogate's BF16 inference alone (the study's network shape, 4.2e6 samples, device
+    input and output), against the measured dense BF16 tensor peak."""
+    import torch
+
+    import paper_2411_18370_b300 as ft
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    ctx = ft.create(local)
+    r = inference_rates(ctx, local)
+    peak = measured_bf16_peak()
+    tc = r["tensor_cores"]
+    line = {"metric": "p_det surrogate BF16 inference samples/s (width 128, 13 features)",
+            "value": tc["samples_per_s"], "unit": "samples/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "bf16-operands/f32-accumulate", "data": "synthetic",
+            "config": {"workload": "4-layer MLP, widths 13-128-128-128-1, 4.2e6 samples per call"},
+            "gpu_launches_per_call": 1,
+            "roofline": {"bound": "tensor", "kernel": "k_infer_tc", "achieved": tc["tflops"],
+                         "peak": peak, "unit": "TFLOP/s", "frac": tc["tflops"] / peak if peak else None,
+                         "peak_basis": "measured dense BF16 burst (MEASURED_PEAKS.json bf16_tflops)",
+                         "flops_per_sample": 2 * (13 * 128 + 2 * 128 * 128 + 128)},
+            "inference": r}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def measured_bf16_peak():
+    """Dense BF16 TFLOP/s (burst) from MEASURED_PEAKS.json, or the recipe's fallback 1800."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1800.0
+
+
 def inference_rates(ctx, local, n=1 << 22, d=13, w=128):
     """Samples/s of the surrogate's BF16 inference (the study's network shape: 13 features,
     width 128) on the tensor cores and on the CUDA cores, device input and output; FLOP
@@ -617,7 +658,7 @@ def main():
     ap.add_argument("--sub-sky-stride", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-s", type=float, default=4.0)
-    ap.add_argument("--workload", default="search", choices=["search", "batch", "surrogate", "binary"])
+    ap.add_argument("--workload", default="search", choices=["search", "batch", "surrogate", "binary", "inference"])
     ap.add_argument("--sky-scale", type=float, default=0.1)
     ap.add_argument("--n-bands", type=int, default=64)
     ap.add_argument("--n-held", type=int, default=4)
@@ -638,6 +679,8 @@ def main():
         return run_surrogate(args)
     if args.workload == "binary":
         return run_binary(args)
+    if args.workload == "inference":
+        return run_inference(args)
 
     import torch
 
