@@ -612,6 +612,64 @@ def measured_bf16_peak():
         return 1800.0
 
 
+def weighted_searches(args, ctx, sfts, bank, P32d, cand, stream, flush, barrier, max_over_ranks, ws, evals):
+    """The search of the same bank and storage type with the all-sky weights (a^2 + b^2)/S_n
+    of each template's own sky point (Sec. II.B), over the number-count band 1[P > 3.2]
+    (Eq. (number_count)), and the loudest s among templates whose weighted count passes the
+    noise mean + 3 sigma gate (Sec. VI.B), each timed like the main step."""
+    import torch
+
+    import ftsynth
+    import paper_2411_18370_b300 as ft
+
+    parts, off = [], 0
+    for X, n in enumerate(sfts.n_sft):
+        parts.append(ftsynth.detector_tensor(sfts.t_mid[off:off + n], X))
+        off += n
+    D = np.concatenate(parts)
+    steps = max(5, args.steps // 4)
+
+    def timed(step):
+        barrier()
+        times = time_steps(step, steps, args.warmup, stream, flush)
+        barrier()
+        ctx.check_status()
+        m = max_over_ranks(statistics.mean(times))
+        return {"value": ws * evals / (m / 1e3), "unit": UNIT, "ms_per_step": m, "steps": steps}
+
+    def load():
+        return ft.load_sfts(ctx, P32d, sfts.t_mid, sfts.v, sfts.n_sft, sfts.k_lo, sfts.t_sft, sfts.t0,
+                            dtype=args.dtype, s_n=sfts.s_n)
+
+    out = {}
+    # all-sky weights: the producer warp forms a^2 + b^2 per (SFT, sky point) in FP64
+    band = load()
+    ft.band_set_sky_weights(band, D)
+    bk = ft.make_bank(ctx, band, bank.k0, bank.n_f0, bank.f1, bank.sky, bank.subband_bins)
+    out["all_sky_weights"] = timed(lambda: ft.topk_per_band(ctx, band, bk, args.k, cand, stream=stream))
+    out["all_sky_weights"]["gpu_launches_per_step"] = 2
+    # the number count over the same weights, and the count-gated loudest s
+    ncb = ft.number_count_band(ctx, band, 3.2)
+    nbk = ft.make_bank(ctx, ncb, bank.k0, bank.n_f0, bank.f1, bank.sky, bank.subband_bins)
+    out["number_count"] = timed(lambda: ft.topk_per_band(ctx, ncb, nbk, args.k, cand, stream=stream))
+    out["number_count"]["gpu_launches_per_step"] = 2
+    # the gate is the count's critical ratio (its noise moments depend on the sky point
+    # under all-sky weights): templates whose count lies 3 sigma above its noise mean
+    count = torch.empty(bank.n_templates, dtype=torch.float32, device="cuda")
+    zc = torch.empty(bank.n_templates, dtype=torch.float32, device="cuda")
+    ft.eval_statistic(ctx, ncb, nbk, count, zc, stream=stream)
+    torch.cuda.synchronize()
+    out["count_gated"] = timed(lambda: ft.topk_per_band_gated(ctx, band, bk, args.k, zc, 3.0, cand,
+                                                              stream=stream))
+    out["count_gated"]["gpu_launches_per_step"] = 2
+    out["count_gated"]["gate"] = {"threshold": 3.2, "count_z_min": 3.0,
+                                  "templates_passing": int((zc >= 3.0).sum().item())}
+    del count, zc
+    for b_ in (nbk, ncb, bk, band):
+        b_.close()
+    return out
+
+
 def inference_rates(ctx, local, n=1 << 22, d=13, w=128):
     """Samples/s of the surrogate's BF16 inference (the study's network shape: 13 features,
     width 128) on the tensor cores and on the CUDA cores, device input and output; FLOP
@@ -654,6 +712,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-weighted", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--sub-sky-stride", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -743,6 +802,11 @@ def main():
         runs[dtype] = {"band": band, "bank": bk, "times": times, "mean_ms": mean_ms,
                        "mean_ms_max": max_over_ranks(mean_ms), "clocks": clk.summary()}
 
+    # the weighted searches on the same bank and storage type (Sec. II.B, VI.B): all-sky
+    # weights, the number count, and the loudest among templates whose count passes the gate
+    weighted = {} if args.no_weighted else weighted_searches(args, ctx, sfts, bank, P32d, cand, stream,
+                                                               flush, barrier, max_over_ranks, ws, evals)
+
     chosen = runs[args.dtype]
     value = ws * evals / (chosen["mean_ms_max"] / 1e3)
     clocks = chosen["clocks"] or {}
@@ -788,6 +852,10 @@ def main():
                                  "frac": (evals / (chosen["mean_ms"] / 1e3)) / roof_e,
                                  "entry": "ft_gather_roof", "storage": args.dtype},
     }
+    if weighted:
+        out["weighted_searches"] = weighted
+        out["gpu_launches"] += sum(w["gpu_launches_per_step"] * w["steps"] for w in weighted.values()
+                                   if isinstance(w, dict) and "steps" in w)
 
     if rank == 0 and not args.no_cpu_baseline:
         # The oracle on every template of a sub-bank of the same bank (every f0 and f1, one

@@ -390,6 +390,7 @@ void ft_band_destroy(ft_band *b)
     cudaFree(b->d_w);
     cudaFree(b->d_sn);
     cudaFree(b->d_D);
+    cudaFree(b->d_rowd);
     delete b;
 }
 
@@ -401,7 +402,9 @@ int ft_band_set_sky_weights(ft_band *band, const double *det_tensor, void *strea
     cudaStream_t st = as_stream(stream);
     if (!det_tensor) {
         cudaFree(band->d_D);
+        cudaFree(band->d_rowd);
         band->d_D = nullptr;
+        band->d_rowd = nullptr;
         return FT_OK;
     }
     if (!band->d_sn)
@@ -411,7 +414,10 @@ int ft_band_set_sky_weights(ft_band *band, const double *det_tensor, void *strea
         FT_FAIL(FT_ERR_ARG, "band_set_sky_weights: non-finite detector tensor");
     if (!band->d_D)
         FT_CUDA(cudaMalloc(&band->d_D, n6 * sizeof(double)));
+    if (!band->d_rowd)
+        FT_CUDA(cudaMalloc(&band->d_rowd, static_cast<size_t>(band->N) * 2 * sizeof(float4)));
     FT_CUDA(cudaMemcpyAsync(band->d_D, det_tensor, n6 * sizeof(double), cudaMemcpyHostToDevice, st));
+    FT_TRY(ft_launch_rowd(band->d_D, band->d_sn, band->N, band->N, band->d_rowd, st));
     FT_CUDA(cudaStreamSynchronize(st));
     return FT_OK;
 }
@@ -438,6 +444,7 @@ int ft_number_count_band(ft_ctx *ctx, const ft_band *band, double threshold, voi
     b->d_w = nullptr;
     b->d_sn = nullptr;
     b->d_D = nullptr;
+    b->d_rowd = nullptr;
     auto fail = [&](int rc) {
         ft_band_destroy(b);
         return rc;
@@ -460,7 +467,7 @@ int ft_number_count_band(ft_ctx *ctx, const ft_band *band, double threshold, voi
     int rc;
     if ((rc = dup(&b->d_tau, band->d_tau, N)) != FT_OK || (rc = dup(&b->d_v, band->d_v, 3 * N)) != FT_OK ||
         (rc = dup(&b->d_w, band->d_w, N)) != FT_OK || (rc = dup(&b->d_sn, band->d_sn, N)) != FT_OK ||
-        (rc = dup(&b->d_D, band->d_D, 6 * N)) != FT_OK)
+        (rc = dup(&b->d_D, band->d_D, 6 * N)) != FT_OK || (rc = dup(&b->d_rowd, band->d_rowd, 2 * N)) != FT_OK)
         return fail(rc);
     if (cudaMalloc(&b->d_power, N * band->Wp * 4) != cudaSuccess) {
         b->d_power = nullptr;

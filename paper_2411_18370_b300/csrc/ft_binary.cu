@@ -334,20 +334,6 @@ __device__ __forceinline__ void bt_issue(const BtParams &p, int st, unsigned cha
     }
 }
 
-// (a^2 + b^2)(D, n) / S_n for the FP32 record of D / sqrt(S_n): with u = D n and c = n.u,
-// a^2 + b^2 = 2 |TT(D)|^2 = 2 |D|^2 - 4 |u|^2 + 2 c^2 - (tr D - c)^2 for a unit n (the
-// transverse-traceless projection; no wave frame needed).
-__device__ __forceinline__ float bt_sky_r(float4 d0, float4 d1, float nx, float ny, float nz)
-{
-    const float u0 = d0.x * nx + d0.y * ny + d0.z * nz;
-    const float u1 = d0.y * nx + d0.w * ny + d1.x * nz;
-    const float u2 = d0.z * nx + d1.x * ny + d1.y * nz;
-    const float c = nx * u0 + ny * u1 + nz * u2;
-    const float uu = u0 * u0 + u1 * u1 + u2 * u2;
-    const float tc = d1.w - c;
-    return 2.f * d1.z - 4.f * uu + 2.f * c * c - tc * tc;
-}
-
 __device__ __forceinline__ void fold2(float &hi, float &lo, float part)
 {
     const float s = __fadd_rn(hi, part);
@@ -395,7 +381,7 @@ __device__ __forceinline__ void bt_rows(const BtParams &p, const BtTmpl (&t)[kBt
                 oob[u] += in ? 0 : 1;
             if (SKY) {
                 const float val = in ? bt_load<T>(row, k[u]) : 0.f;
-                const float rw = bt_sky_r(sdb[2 * r], sdb[2 * r + 1], t[u].wx, t[u].wy, t[u].wz);
+                const float rw = ft_sky_r32(sdb[2 * r], sdb[2 * r + 1], t[u].wx, t[u].wy, t[u].wz);
                 part[u] = __fmaf_rn(rw, val, part[u]);
                 partB[u] = __fadd_rn(partB[u], rw);
                 partC[u] = __fmaf_rn(rw, rw, partC[u]);
@@ -776,25 +762,6 @@ __global__ void k_bt_rowv(const double *v, const float *w, int N, int n_pad, flo
     out[a] = r;
 }
 
-__global__ void k_bt_rowd(const double *D, const double *sn, int N, int n_pad, float4 *out)
-{
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= n_pad)
-        return;
-    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
-    if (a < N) {
-        const double g = 1.0 / sqrt(sn[a]);
-        const double *d = D + 6 * a;
-        const double e0 = d[0] * g, e1 = d[1] * g, e2 = d[2] * g, e3 = d[3] * g, e4 = d[4] * g, e5 = d[5] * g;
-        const double dd = e0 * e0 + e3 * e3 + e5 * e5 + 2.0 * (e1 * e1 + e2 * e2 + e4 * e4);
-        r0 = make_float4(static_cast<float>(e0), static_cast<float>(e1), static_cast<float>(e2), static_cast<float>(e3));
-        r1 = make_float4(static_cast<float>(e4), static_cast<float>(e5), static_cast<float>(dd),
-                         static_cast<float>(e0 + e3 + e5));
-    }
-    out[2 * a] = r0;
-    out[2 * a + 1] = r1;
-}
-
 // ------------------------------------------------------------------ host side
 
 struct Guard {
@@ -1097,7 +1064,8 @@ int ft_make_binary_bank(ft_ctx *ctx, const ft_band *band, const ft_binary_bank_d
             ft_set_error("make_binary_bank: allocation failed");
             return fail(FT_ERR_OOM);
         }
-        k_bt_rowd<<<(b->n_pad + 255) / 256, 256>>>(band->d_D, band->d_sn, N, b->n_pad, b->d_rowd);
+        if (ft_launch_rowd(band->d_D, band->d_sn, N, b->n_pad, b->d_rowd, 0) != FT_OK)
+            return fail(FT_ERR_CUDA);
     }
     if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
         ft_set_error("make_binary_bank: set-up kernel failed");

@@ -220,8 +220,9 @@ __device__ __forceinline__ void stage_table_a(const EvalParams &p, const CtaTile
         tabE[tb * p.S + a] = E;
         tabC[tb * p.S + a] = C;
         tabW[tb * p.S + a] =
-            p.D != nullptr ? static_cast<float>(ft_response_a2b2(p.D + 6 * alpha, c.n0, c.n1, c.n2) /
-                                                p.sn[alpha] * p.sky_inv[c.sky])
+            p.D != nullptr ? ft_sky_r32(p.rowd[2 * alpha], p.rowd[2 * alpha + 1], static_cast<float>(c.n0),
+                                        static_cast<float>(c.n1), static_cast<float>(c.n2)) *
+                                 static_cast<float>(p.sky_inv[c.sky])
                            : p.w[alpha];
     }
 }
@@ -862,6 +863,13 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
                 const double va[3] = {p.v[3 * alpha], p.v[3 * alpha + 1], p.v[3 * alpha + 2]};
                 const bool sky_w = WEIGHTED && p.D != nullptr;
                 const float wa = sky_w ? 0.f : p.w[alpha];
+                // all-sky weights: the row's FP32 record of D / sqrt(S_n), once for the
+                // group's sky points
+                float4 rd0 = make_float4(0.f, 0.f, 0.f, 0.f), rd1 = rd0;
+                if (sky_w) {
+                    rd0 = p.rowd[2 * alpha];
+                    rd1 = p.rowd[2 * alpha + 1];
+                }
                 // track terms per sky point and, per sky point, the track origins of the
                 // group's smallest and largest f1 (the origin is linear in f1)
                 long long G1 = 0, G2 = 0;
@@ -877,9 +885,9 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
                     if (sky_w) {
                         // all-sky weight of this row for sky point q
                         const long long sk = sky_of(p, c.skyg, q);
-                        r.w = static_cast<float>(ft_response_a2b2(p.D + 6 * alpha, skyn[3 * q], skyn[3 * q + 1],
-                                                                  skyn[3 * q + 2]) /
-                                                 p.sn[alpha] * p.sky_inv[sk < 0 ? c.sky : sk]);
+                        r.w = ft_sky_r32(rd0, rd1, static_cast<float>(skyn[3 * q]), static_cast<float>(skyn[3 * q + 1]),
+                                         static_cast<float>(skyn[3 * q + 2])) *
+                              static_cast<float>(p.sky_inv[sk < 0 ? c.sky : sk]);
                     }
                     rq[q * S] = r;
                     if (p.Ws < p.Wp) {
@@ -2282,6 +2290,25 @@ int ft_run_gather_roof(int dtype, int sm_count, double *evals_per_s, double *eva
 
 namespace {
 
+__global__ void k_rowd(const double *D, const double *sn, long long N, long long n_pad, float4 *out)
+{
+    const long long a = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (a >= n_pad)
+        return;
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+    if (a < N) {
+        const double g = 1.0 / sqrt(sn[a]);
+        const double *d = D + 6 * a;
+        const double e0 = d[0] * g, e1 = d[1] * g, e2 = d[2] * g, e3 = d[3] * g, e4 = d[4] * g, e5 = d[5] * g;
+        const double dd = e0 * e0 + e3 * e3 + e5 * e5 + 2.0 * (e1 * e1 + e2 * e2 + e4 * e4);
+        r0 = make_float4(static_cast<float>(e0), static_cast<float>(e1), static_cast<float>(e2), static_cast<float>(e3));
+        r1 = make_float4(static_cast<float>(e4), static_cast<float>(e5), static_cast<float>(dd),
+                         static_cast<float>(e0 + e3 + e5));
+    }
+    out[2 * a] = r0;
+    out[2 * a + 1] = r1;
+}
+
 constexpr int kNormThreads = 256;
 
 __global__ void __launch_bounds__(kNormThreads)
@@ -2315,6 +2342,16 @@ __global__ void __launch_bounds__(kNormThreads)
 }
 
 }  // namespace
+
+int ft_launch_rowd(const double *D, const double *sn, long long N, long long n_pad, float4 *out,
+                   cudaStream_t st)
+{
+    if (n_pad <= 0)
+        return FT_OK;
+    k_rowd<<<static_cast<unsigned>((n_pad + 255) / 256), 256, 0, st>>>(D, sn, N, n_pad, out);
+    FT_CUDA(cudaGetLastError());
+    return FT_OK;
+}
 
 int ft_launch_sky_norms(const ft_band *band, const ft_bank *bank, cudaStream_t st)
 {

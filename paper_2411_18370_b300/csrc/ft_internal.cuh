@@ -81,6 +81,9 @@ struct ft_band {
     double tau_absmax = 0;
     double vmax = 0;  // largest |v| / c over the SFTs
     double *d_D = nullptr;  // [N][6] detector tensors when the all-sky weights are on
+    // [N][2] their FP32 records for the kernels: D / sqrt(S_n) as (D00, D01, D02, D11),
+    // (D12, D22, |D|^2, tr D), so that (a^2 + b^2) / S_n = ft_sky_r32(record, n)
+    float4 *d_rowd = nullptr;
     // mean and variance of one SFT's value in Gaussian noise: 2 and 4 for normalised power
     // (exponential with mean 2); p and p (1 - p) for a number-count band, p = exp(-threshold / 2)
     double m1 = 2.0, v1 = 4.0;
@@ -150,6 +153,7 @@ struct EvalParams {
     // all-sky weights (null: per-SFT w): w_alpha(n) = (a^2 + b^2)(D_alpha, n) / S_n,alpha
     // times sky_inv[n]; z uses sky_mu[n], sky_sig[n]
     const double *D, *sn, *sky_inv, *sky_mu, *sky_sig;
+    const float4 *rowd;  // [N][2] FP32 records of D / sqrt(S_n) (see ft_band::d_rowd)
     // candidate gate (null: none): template t takes part in the selection only when
     // gate[t] >= gate_min (e.g. its weighted number count)
     const float *gate;
@@ -190,6 +194,7 @@ inline EvalParams ft_eval_base_params(const ft_band *band, const ft_bank *bank)
     if (band->d_D) {
         p.D = band->d_D;
         p.sn = band->d_sn;
+        p.rowd = band->d_rowd;
         p.sky_inv = bank->d_sky_inv;
         p.sky_mu = bank->d_sky_mu;
         p.sky_sig = bank->d_sky_sig;
@@ -248,27 +253,45 @@ constexpr int kMaxSkyGroup = 4;
 // and sets *ok = 0 when the shape cannot be expressed (box larger than the hardware allows).
 int ft_encode_rows_map(const ft_band *band, int Ws, int S, CUtensorMap *map, int *ok);
 
-// a = D : e+, b = D : ex of detector tensor D (xx, xy, xz, yy, yz, zz) for direction n, with
-// the wave frame X = z x n / |z x n| (any X perpendicular to n at the poles), Y = n x X.
+// a^2 + b^2 of detector tensor D (xx, xy, xz, yy, yz, zz) for unit direction n, where
+// a = D : e+ and b = D : ex in any wave frame (X, Y) perpendicular to n (Sec. II.B): a^2 + b^2
+// is twice the squared norm of the transverse-traceless part of D,
+//     a^2 + b^2 = 2 |D|^2 - 4 |u|^2 + 2 c^2 - (tr D - c)^2,   u = D n, c = n . u,
+// which needs no frame (no square root or division; exact algebraically, and the terms are
+// O(1), so the FP64 result is good to about 1e-16 absolute).
 __device__ __forceinline__ double ft_response_a2b2(const double *D, double n0, double n1, double n2)
 {
-    const double rho = sqrt(n0 * n0 + n1 * n1);
-    double X0 = 1.0, X1 = 0.0;
-    if (rho > 0) {
-        X0 = -n1 / rho;
-        X1 = n0 / rho;
-    }
-    const double Y0 = -n2 * X1, Y1 = n2 * X0, Y2 = n0 * X1 - n1 * X0;  // n x X (X2 = 0)
     const double M00 = D[0], M01 = D[1], M02 = D[2], M11 = D[3], M12 = D[4], M22 = D[5];
-    // a = X^T M X - Y^T M Y, b = 2 X^T M Y
-    const double MX0 = M00 * X0 + M01 * X1, MX1 = M01 * X0 + M11 * X1, MX2 = M02 * X0 + M12 * X1;
-    const double MY0 = M00 * Y0 + M01 * Y1 + M02 * Y2, MY1 = M01 * Y0 + M11 * Y1 + M12 * Y2,
-                 MY2 = M02 * Y0 + M12 * Y1 + M22 * Y2;
-    const double a = (X0 * MX0 + X1 * MX1) - (Y0 * MY0 + Y1 * MY1 + Y2 * MY2);
-    const double b = 2.0 * (X0 * MY0 + X1 * MY1);
-    (void)MX2;
-    return a * a + b * b;
+    const double u0 = M00 * n0 + M01 * n1 + M02 * n2;
+    const double u1 = M01 * n0 + M11 * n1 + M12 * n2;
+    const double u2 = M02 * n0 + M12 * n1 + M22 * n2;
+    const double c = n0 * u0 + n1 * u1 + n2 * u2;
+    const double dd = M00 * M00 + M11 * M11 + M22 * M22 + 2.0 * (M01 * M01 + M02 * M02 + M12 * M12);
+    const double uu = u0 * u0 + u1 * u1 + u2 * u2;
+    const double tc = (M00 + M11 + M22) - c;
+    return 2.0 * dd - 4.0 * uu + 2.0 * c * c - tc * tc;
 }
+
+// (a^2 + b^2) / S_n in FP32 from an SFT's record d0 = (e00, e01, e02, e11), d1 = (e12, e22,
+// |e|^2, tr e) of e = D / sqrt(S_n), for unit direction n: the same frame-free identity as
+// ft_response_a2b2, 2 |e|^2 - 4 |u|^2 + 2 c^2 - (tr e - c)^2 with u = e n and c = n . u.
+// The terms are O(1 / S_n), so the result is good to a few FP32 ulps of 1 / S_n in absolute
+// terms: the weights it makes are stored in FP32 anyway.
+__device__ __forceinline__ float ft_sky_r32(float4 d0, float4 d1, float nx, float ny, float nz)
+{
+    const float u0 = d0.x * nx + d0.y * ny + d0.z * nz;
+    const float u1 = d0.y * nx + d0.w * ny + d1.x * nz;
+    const float u2 = d0.z * nx + d1.x * ny + d1.y * nz;
+    const float c = nx * u0 + ny * u1 + nz * u2;
+    const float uu = u0 * u0 + u1 * u1 + u2 * u2;
+    const float tc = d1.w - c;
+    return 2.f * d1.z - 4.f * uu + 2.f * c * c - tc * tc;
+}
+
+// The FP32 records of D / sqrt(S_n) for rows [0, N) of D [N][6], zeros for rows [N, n_pad);
+// out [n_pad][2].
+int ft_launch_rowd(const double *D, const double *sn, long long N, long long n_pad, float4 *out,
+                   cudaStream_t st);
 
 // Per sky point of the bank: 1 / sum (a^2+b^2)/S_n and mu_G, sigma_G of the normalised
 // all-sky weights (one CTA per sky point; the band must carry detector tensors).
