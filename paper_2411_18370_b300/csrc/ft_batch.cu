@@ -182,7 +182,7 @@ int build(ft_ctx *ctx, int n, const ft_band *const *bands, const ft_bank *const 
         sub_prefix[i + 1] = sub_prefix[i] + bk->n_sub;
         b->n_sub_max = std::max(b->n_sub_max, bk->n_sub);
         b->lsub_max = std::max(b->lsub_max, p.lsub_max);
-        tile_smem = std::max(tile_smem, ft_batch_tile_smem(Ws, S, F, bP[i], J, nst));
+        tile_smem = std::max(tile_smem, ft_batch_tile_smem(Ws, S, F, bP[i], J, nst, ft_band_weighted(bands[0])));
     }
     b->n_sub_total = sub_prefix[n];
     b->sub_prefix_h.assign(sub_prefix.begin(), sub_prefix.end());

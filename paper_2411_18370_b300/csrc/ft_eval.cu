@@ -671,11 +671,11 @@ struct __align__(16) RowRec {
 };
 
 struct FastLayout {
-    size_t full, empty, skyn, rec, tabB, evA, evK, buf, total, stage_bytes;
+    size_t full, empty, skyn, rec, wts, tabB, evA, evK, buf, total, stage_bytes;
 };
 
 __host__ __device__ inline FastLayout fast_layout(int S, int F, int P, int row_bytes, int J,
-                                                  bool topk, int nst)
+                                                  bool topk, int nst, bool weighted)
 {
     FastLayout L;
     size_t o = 0;
@@ -687,6 +687,8 @@ __host__ __device__ inline FastLayout fast_layout(int S, int F, int P, int row_b
     o = align_up(o + (size_t)kMaxSkyGroup * 3 * sizeof(double), 16);
     L.rec = o;   // per stage (a ring of nst + 1), sky point and row
     o = align_up(o + (size_t)(nst + 1) * P * S * sizeof(RowRec), 16);
+    L.wts = o;   // weighted kernels: the records' weights again, contiguous per (stage, sky point)
+    o = align_up(o + (weighted ? (size_t)(nst + 1) * P * S * sizeof(float) : 0), 16);
     L.tabB = o;
     o = align_up(o + (size_t)F * S * sizeof(int), 16);
     L.evA = o;
@@ -729,7 +731,7 @@ __device__ __forceinline__ long long cross_q32(long long G, int E)
 // lane's bins and their accumulation; the row offsets come four at a time from tabB.
 template <int MODE, int RA, bool WEIGHTED, int NS>
 __device__ __forceinline__ void stage_rows(const unsigned char *lane_rows, const int *tabB,
-                                           const RowRec *rr, int nr, float (&part)[NS])
+                                           const float *wr, int nr, float (&part)[NS])
 {
     auto row_sum = [&](int off, float wa) {
         if (MODE == MODE_F32) {
@@ -756,10 +758,11 @@ __device__ __forceinline__ void stage_rows(const unsigned char *lane_rows, const
     for (int a = 0; a < nr4; a += 4) {
         const int4 o4 = *reinterpret_cast<const int4 *>(tabB + a);
         if (WEIGHTED) {
-            row_sum(o4.x, rr[a].w);
-            row_sum(o4.y, rr[a + 1].w);
-            row_sum(o4.z, rr[a + 2].w);
-            row_sum(o4.w, rr[a + 3].w);
+            const float4 w4 = *reinterpret_cast<const float4 *>(wr + a);
+            row_sum(o4.x, w4.x);
+            row_sum(o4.y, w4.y);
+            row_sum(o4.z, w4.z);
+            row_sum(o4.w, w4.w);
         } else {
             row_sum(o4.x, 1.f);
             row_sum(o4.y, 1.f);
@@ -768,22 +771,22 @@ __device__ __forceinline__ void stage_rows(const unsigned char *lane_rows, const
         }
     }
     for (int a = nr4; a < nr; ++a)
-        row_sum(tabB[a], WEIGHTED ? rr[a].w : 1.f);
+        row_sum(tabB[a], WEIGHTED ? wr[a] : 1.f);
 }
 
 // stage_rows with the slot count ract chosen at run time (uniform over the CTA).
 template <int MODE, int RA, bool WEIGHTED, int NS>
 __device__ __forceinline__ void stage_rows_upto(int ract, const unsigned char *lane_rows,
-                                                const int *tabB, const RowRec *rr, int nr,
+                                                const int *tabB, const float *wr, int nr,
                                                 float (&part)[NS])
 {
     if constexpr (RA > 1) {
         if (ract < RA) {
-            stage_rows_upto<MODE, RA - 1, WEIGHTED>(ract, lane_rows, tabB, rr, nr, part);
+            stage_rows_upto<MODE, RA - 1, WEIGHTED>(ract, lane_rows, tabB, wr, nr, part);
             return;
         }
     }
-    stage_rows<MODE, RA, WEIGHTED>(lane_rows, tabB, rr, nr, part);
+    stage_rows<MODE, RA, WEIGHTED>(lane_rows, tabB, wr, nr, part);
 }
 
 template <int MODE, int R, bool WEIGHTED, bool RAGGED>
@@ -798,11 +801,12 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
     const int S = p.S;
     const int nst = p.nst;
     const int row_words = p.srow_bytes >> 2;  // shared-memory row: Ws bins
-    const FastLayout L = fast_layout(S, F, p.P, p.srow_bytes, J, p.cand != nullptr, nst);
+    const FastLayout L = fast_layout(S, F, p.P, p.srow_bytes, J, p.cand != nullptr, nst, WEIGHTED);
     double *skyn = reinterpret_cast<double *>(smem + L.skyn);
     unsigned long long *full = reinterpret_cast<unsigned long long *>(smem + L.full);
     unsigned long long *empty = reinterpret_cast<unsigned long long *>(smem + L.empty);
     RowRec *rec = reinterpret_cast<RowRec *>(smem + L.rec);
+    float *wts = reinterpret_cast<float *>(smem + L.wts);
     unsigned char *buf = smem + L.buf;
     const CtaTile c = decode_tile(p, J, tile);
     const int n_stages = p.n_stages;
@@ -890,6 +894,8 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
                               static_cast<float>(p.sky_inv[sk < 0 ? c.sky : sk]);
                     }
                     rq[q * S] = r;
+                    if (WEIGHTED)
+                        wts[(static_cast<size_t>(rs) * p.P + q) * S + lane] = r.w;
                     if (p.Ws < p.Wp) {
                         const int x1 = c.j0 + static_cast<int>((r.C + G1 + cross_q32(G1, r.E)) >> 32);
                         const int x2 = c.j0 + static_cast<int>((r.C + G2 + cross_q32(G2, r.E)) >> 32);
@@ -1044,6 +1050,7 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
             const int nr = min(st == n_stages - 1 ? last_nr : S, rows_max);
             const unsigned char *rows = buf + slot * L.stage_bytes;
             const RowRec *rr = rec + (rs * p.P + wq) * S;
+            const float *wr = wts + (rs * p.P + wq) * S;
             // row offset of this warp's track origin and, if the track steps by sign(E)
             // inside the tile, a correction entry (lane = row)
             bool ev = false;
@@ -1092,9 +1099,9 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
             // main loop over the stage's rows, with as many slots per lane as the tile has
             // f0 values (a ragged last tile skips the rest)
             if (RAGGED)
-                stage_rows_upto<MODE, R, WEIGHTED>(ract, rows + 4 * lane, tabB, rr, nr, part);
+                stage_rows_upto<MODE, R, WEIGHTED>(ract, rows + 4 * lane, tabB, wr, nr, part);
             else
-                stage_rows<MODE, R, WEIGHTED>(rows + 4 * lane, tabB, rr, nr, part);
+                stage_rows<MODE, R, WEIGHTED>(rows + 4 * lane, tabB, wr, nr, part);
             // corrections for the rows whose bin steps by sign(E) inside the tile: from
             // slot jc on the track reads bin k + sg instead of k (slots past n_f0 are
             // computed and discarded, like in the main loop; their bins stay in the window)
@@ -1104,7 +1111,7 @@ __device__ __forceinline__ bool fast_tile(const EvalParams &p, long long tile, u
                 const int jc = (pk >> 8) & 0xfff;
                 const int sg = (pk >> 20) ? -1 : 1;
                 const int base = evK[e];
-                const float wa = WEIGHTED ? rr[a].w : 1.f;
+                const float wa = WEIGHTED ? wr[a] : 1.f;
                 if (MODE == MODE_F32) {
 #pragma unroll
                     for (int i = 0; i < NS; ++i) {
@@ -1853,7 +1860,7 @@ int ft_window_bins(const ft_band *band, const ft_bank *bank, int J, int P)
 size_t ft_eval_smem_bytes(const ft_band *band, const EvalShape &sh, int k)
 {
     if (sh.fast)
-        return fast_layout(sh.S, sh.F, sh.P, sh.Ws * 4, sh.J, k > 0, sh.nbuf).total;
+        return fast_layout(sh.S, sh.F, sh.P, sh.Ws * 4, sh.J, k > 0, sh.nbuf, ft_band_weighted(band)).total;
     return smem_layout(sh.S, sh.F, row_bytes_of(band), sh.J, false, k > 0).total;
 }
 
@@ -2121,9 +2128,9 @@ int batched_r(int R, const BatchParams &bp, int threads, size_t smem, int *grid,
 
 }  // namespace
 
-size_t ft_batch_tile_smem(int Ws, int S, int F, int P, int J, int nst)
+size_t ft_batch_tile_smem(int Ws, int S, int F, int P, int J, int nst, bool weighted)
 {
-    return fast_layout(S, F, P, Ws * 4, J, true, nst).total;
+    return fast_layout(S, F, P, Ws * 4, J, true, nst, weighted).total;
 }
 
 int ft_batch_row_bytes(const ft_band *band)

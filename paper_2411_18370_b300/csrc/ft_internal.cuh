@@ -328,7 +328,7 @@ int ft_launch_gtable(const double *f1, int n_f1, const double *tau, long long N,
 int ft_launch_track_bins(const ft_band *band, const ft_bank *bank, const long long *tmpl,
                          long long n, int *bins, cudaStream_t st);
 
-size_t ft_batch_tile_smem(int Ws, int S, int F, int P, int J, int nst);
+size_t ft_batch_tile_smem(int Ws, int S, int F, int P, int J, int nst, bool weighted);
 int ft_batch_row_bytes(const ft_band *band);
 int ft_launch_batched(int dtype, bool weighted, int J, int F, const BatchParams &bp, size_t smem,
                       int *grid, bool launch, cudaStream_t st);
