@@ -2319,14 +2319,17 @@ __global__ void k_rowd(const double *D, const double *sn, long long N, long long
 constexpr int kNormThreads = 256;
 
 __global__ void __launch_bounds__(kNormThreads)
-    k_sky_norms(long long N, const double *D, const double *sn, const double *sky, double m1,
-                double sd1, double *inv, double *mu, double *sig)
+    k_sky_norms(long long N, const float4 *rowd, const double *sky, double m1, double sd1, double *inv,
+                double *mu, double *sig)
 {
     __shared__ double s1[kNormThreads], s2[kNormThreads];
     const double *n = sky + 3 * blockIdx.x;
+    const float n0 = static_cast<float>(n[0]), n1 = static_cast<float>(n[1]), n2 = static_cast<float>(n[2]);
     double a1 = 0.0, a2 = 0.0;
     for (long long a = threadIdx.x; a < N; a += kNormThreads) {
-        const double r = ft_response_a2b2(D + 6 * a, n[0], n[1], n[2]) / sn[a];
+        // the same FP32 value of (a^2 + b^2) / S_n as the evaluation kernels' weights, so
+        // that the weights of a sky point sum to 1 up to the FP32 rounding of the product
+        const double r = ft_sky_r32(rowd[2 * a], rowd[2 * a + 1], n0, n1, n2);
         a1 += r;
         a2 += r * r;
     }
@@ -2364,8 +2367,10 @@ int ft_launch_sky_norms(const ft_band *band, const ft_bank *bank, cudaStream_t s
 {
     if (bank->n_sky > INT_MAX)
         FT_FAIL(FT_ERR_RANGE, "sky weights: too many sky points");
+    if (!band->d_rowd)
+        FT_FAIL(FT_ERR_ARG, "sky weights: the band has no weight records");
     k_sky_norms<<<static_cast<unsigned>(bank->n_sky), kNormThreads, 0, st>>>(
-        static_cast<long long>(band->N), band->d_D, band->d_sn, bank->d_sky, band->m1, std::sqrt(band->v1),
+        static_cast<long long>(band->N), band->d_rowd, bank->d_sky, band->m1, std::sqrt(band->v1),
         bank->d_sky_inv, bank->d_sky_mu, bank->d_sky_sig);
     FT_CUDA(cudaGetLastError());
     return FT_OK;

@@ -253,30 +253,14 @@ constexpr int kMaxSkyGroup = 4;
 // and sets *ok = 0 when the shape cannot be expressed (box larger than the hardware allows).
 int ft_encode_rows_map(const ft_band *band, int Ws, int S, CUtensorMap *map, int *ok);
 
-// a^2 + b^2 of detector tensor D (xx, xy, xz, yy, yz, zz) for unit direction n, where
-// a = D : e+ and b = D : ex in any wave frame (X, Y) perpendicular to n (Sec. II.B): a^2 + b^2
-// is twice the squared norm of the transverse-traceless part of D,
-//     a^2 + b^2 = 2 |D|^2 - 4 |u|^2 + 2 c^2 - (tr D - c)^2,   u = D n, c = n . u,
-// which needs no frame (no square root or division; exact algebraically, and the terms are
-// O(1), so the FP64 result is good to about 1e-16 absolute).
-__device__ __forceinline__ double ft_response_a2b2(const double *D, double n0, double n1, double n2)
-{
-    const double M00 = D[0], M01 = D[1], M02 = D[2], M11 = D[3], M12 = D[4], M22 = D[5];
-    const double u0 = M00 * n0 + M01 * n1 + M02 * n2;
-    const double u1 = M01 * n0 + M11 * n1 + M12 * n2;
-    const double u2 = M02 * n0 + M12 * n1 + M22 * n2;
-    const double c = n0 * u0 + n1 * u1 + n2 * u2;
-    const double dd = M00 * M00 + M11 * M11 + M22 * M22 + 2.0 * (M01 * M01 + M02 * M02 + M12 * M12);
-    const double uu = u0 * u0 + u1 * u1 + u2 * u2;
-    const double tc = (M00 + M11 + M22) - c;
-    return 2.0 * dd - 4.0 * uu + 2.0 * c * c - tc * tc;
-}
-
-// (a^2 + b^2) / S_n in FP32 from an SFT's record d0 = (e00, e01, e02, e11), d1 = (e12, e22,
-// |e|^2, tr e) of e = D / sqrt(S_n), for unit direction n: the same frame-free identity as
-// ft_response_a2b2, 2 |e|^2 - 4 |u|^2 + 2 c^2 - (tr e - c)^2 with u = e n and c = n . u.
-// The terms are O(1 / S_n), so the result is good to a few FP32 ulps of 1 / S_n in absolute
-// terms: the weights it makes are stored in FP32 anyway.
+// (a^2 + b^2) / S_n in FP32 (Sec. II.B), where a = D : e+ and b = D : ex in any wave frame
+// perpendicular to the unit direction n, from an SFT's record d0 = (e00, e01, e02, e11),
+// d1 = (e12, e22, |e|^2, tr e) of e = D / sqrt(S_n) (D = xx, xy, xz, yy, yz, zz).  a^2 + b^2
+// is twice the squared norm of the transverse-traceless part of D, so
+//     (a^2 + b^2) / S_n = 2 |e|^2 - 4 |u|^2 + 2 c^2 - (tr e - c)^2,   u = e n, c = n . u,
+// which needs no frame (no square root or division; exact algebraically).  The terms are
+// O(1 / S_n), so the result is good to a few FP32 ulps of 1 / S_n in absolute terms: the
+// weights it makes are stored in FP32 anyway.
 __device__ __forceinline__ float ft_sky_r32(float4 d0, float4 d1, float nx, float ny, float nz)
 {
     const float u0 = d0.x * nx + d0.y * ny + d0.z * nz;
