@@ -102,3 +102,28 @@ def test_bf16_inference_on_tensor_cores(ctx, d, w, n):
     p_dev = net.predict(torch.from_numpy(Xt).cuda(), bf16=True).cpu().numpy()
     assert np.array_equal(p_dev, p_tc)
     net.close()
+
+
+def test_tensor_core_inference_many_tiles_per_group(ctx):
+    """Enough samples that every SM's four tile groups loop over several 128-sample tiles
+    (the bias stored back into the accumulator columns after each layer carries from one
+    tile to the next), with a ragged last tile: the same probabilities as the CUDA-core BF16
+    path up to summation order, and the FP64 oracle within the BF16 tolerance on a sample."""
+    import torch
+
+    d, w = 13, 128
+    net = ft.MLP(ctx, d, w, seed=11)
+    g = np.random.default_rng(17)
+    X = g.standard_normal((4096, d)).astype(np.float32)
+    y = (X[:, 0] - 0.4 * X[:, 3] + 0.3 * g.standard_normal(4096) > 0).astype(np.float32)
+    net.train(X, y, batch=512, epochs=2, lr=2e-3, seed=5)
+    n = 4 * 148 * 128 * 3 + 77
+    Xt = torch.randn(n, d, device="cuda", generator=torch.Generator(device="cuda").manual_seed(3))
+    p_tc = net.predict(Xt, bf16=True).cpu().numpy().astype(np.float64)
+    p_cc = net.predict(Xt, bf16=True, tensor_cores=False).cpu().numpy().astype(np.float64)
+    diff = np.abs(p_tc - p_cc)
+    assert diff.max() < 5e-3 and diff.mean() < 5e-4, (diff.max(), diff.mean())
+    idx = np.random.default_rng(1).choice(n, 2000, replace=False)
+    p_or = omlp.predict(net.get_params().astype(np.float64), Xt.cpu().numpy()[idx], d, w)
+    assert np.max(np.abs(p_tc[idx] - p_or)) < 0.05
+    net.close()
