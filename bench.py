@@ -15,8 +15,10 @@ HBM before timing; L2 is flushed (256 MB write) between timed steps, outside the
 The same line carries: the precision comparison (FP16, BF16 and plain FP32 storage, each
 timed on the full bank; relative error and per-sub-band candidate sets against the oracle on
 every template of a 1-in-100 sky sub-bank, which is also the CPU baseline's sample); the end-
-to-end rate from host buffers; and the batching workload (64 bands at the stated sky
-density, one persistent graph-captured launch per step, against the per-band loop).
+to-end rate from host buffers; the weighted searches of the same bank (all-sky weights,
+number count, count-gated); the batching workload (64 bands at the stated sky density, one
+persistent graph-captured launch per step, against the per-band loop); the binary-orbit
+track's search; and the surrogate's BF16 inference on the tensor cores.
 
 Other workloads print their own line: the batch alone at a chosen sky density, the
 binary-orbit track over a random hyperbox bank, the learned-surrogate study, and the
@@ -443,19 +445,15 @@ def profiled_traffic_binary(dtype):
         return None
 
 
-def run_binary(args):
-    """The binary-orbit workload: a random hyperbox bank (2^20 templates in 32 boxes) for
-    0.125 Hz at 100 Hz, all sky, a_p 5-15 lt-s, P 7-15 d, over 2 detectors x 183 days of 1024 s
-    SFTs; one step = the loudest template of every box (evaluation + merge)."""
+def binary_core(args, ctx, local, steps=None):
+    """The timed part of the binary-orbit workload (see run_binary): its JSON object and the
+    inputs it made."""
     import torch
 
     import ftsynth
-    import oracle
     import paper_2411_18370_b300 as ft
 
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    ctx = ft.create(local)
+    steps = args.steps if steps is None else steps
     sfts, bank = ftsynth.binary_workload()
     stream = torch.cuda.current_stream()
     P32 = torch.from_numpy(sfts.power.astype(np.float32))
@@ -470,7 +468,7 @@ def run_binary(args):
     evals = bank.n_templates * sfts.n_total
     ft.binary_decisions(gb)
     with ClockSampler(local) as clk:
-        times = time_steps(step, args.steps, args.warmup, stream, flush)
+        times = time_steps(step, steps, args.warmup, stream, flush)
     ctx.check_status()
     n64, delta = ft.binary_decisions(gb)
     mean_ms = statistics.mean(times)
@@ -478,7 +476,7 @@ def run_binary(args):
     peak_ops = 148 * ISSUE_LANES_PER_CLK_PER_SM * 2032e6
     achieved = BT_OPS_PER_EVAL * value
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": steps,
         "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": f"{args.dtype}-storage/f32-accumulate", "data": "synthetic",
         "config": {"workload": f"binary-orbit track, random hyperbox bank: f0 100-100.125 Hz, all sky, "
@@ -498,11 +496,28 @@ def run_binary(args):
                                    "(one operation per lane per clock)",
                      "ops_per_eval": BT_OPS_PER_EVAL, "algorithmic_ops_per_launch": BT_OPS_PER_EVAL * evals,
                      "traffic": profiled_traffic_binary(args.dtype)},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": 2 * steps,
         "clocks": clk.summary(),
-        "fp64_decisions": {"per_eval": n64 / (evals * (args.steps + args.warmup)), "delta_bins": delta,
+        "fp64_decisions": {"per_eval": n64 / (evals * (steps + args.warmup)), "delta_bins": delta,
                            "expected_per_eval": 2 * delta},
     }
+    return out, sfts, bank, band, gb, P32, k
+
+
+def run_binary(args):
+    """The binary-orbit workload: a random hyperbox bank (2^20 templates in 32 boxes) for
+    0.125 Hz at 100 Hz, all sky, a_p 5-15 lt-s, P 7-15 d, over 2 detectors x 183 days of 1024 s
+    SFTs; one step = the loudest template of every box (evaluation + merge)."""
+    import torch
+
+    import ftsynth
+    import oracle
+    import paper_2411_18370_b300 as ft
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    ctx = ft.create(local)
+    out, sfts, bank, band, gb, P32, k = binary_core(args, ctx, local)
     if not args.no_cpu_baseline:
         g = np.random.default_rng(7)
         n = 256
@@ -523,6 +538,9 @@ def run_binary(args):
     if not args.no_e2e:
         Ph = P32.pin_memory()
         cand_h = np.zeros((bank.n_boxes, k), dtype=ft.CANDIDATE_DTYPE)
+        evals = bank.n_templates * sfts.n_total
+        flushbuf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        flush = lambda: flushbuf.fill_(1)
 
         def e2e_step():
             b2 = ft.load_sfts(ctx, Ph, sfts.t_mid, sfts.v, sfts.n_sft, sfts.k_lo, sfts.t_sft, sfts.t0,
@@ -713,6 +731,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-weighted", action="store_true")
+    ap.add_argument("--no-binary", action="store_true")
+    ap.add_argument("--no-inference", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--sub-sky-stride", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -957,6 +977,26 @@ def main():
         b["value"] = ws * b["evals_per_step"] / (b["ms_per_step"] / 1e3)
         out["batch"] = b
         out["gpu_launches"] += 2 * args.batch_steps
+
+    if not args.no_binary:
+        # the binary-orbit track's search (each rank its own replica), its own timed steps
+        bt, *_ = binary_core(args, ctx, local, steps=max(5, args.steps // 2))
+        out["binary_track"] = {k_: bt[k_] for k_ in ("value", "unit", "ms_per_step", "steps", "roofline",
+                                                     "fp64_decisions", "clocks", "gpu_launches")}
+        out["binary_track"]["workload"] = bt["config"]["workload"]
+        out["binary_track"]["value"] = ws * bt["value"]
+        out["gpu_launches"] += bt["gpu_launches"]
+    if not args.no_inference:
+        # the surrogate's BF16 inference on the tensor cores (4.2e6 samples per call)
+        inf = inference_rates(ctx, local)
+        tc = inf["tensor_cores"]
+        peak = measured_bf16_peak()
+        out["surrogate_inference"] = {
+            "value": ws * tc["samples_per_s"], "unit": "samples/s", "tflops": tc["tflops"],
+            "roofline": {"bound": "tensor", "kernel": "k_infer_tc", "achieved": tc["tflops"], "peak": peak,
+                         "unit": "TFLOP/s", "frac": tc["tflops"] / peak,
+                         "peak_basis": "measured dense BF16 burst (MEASURED_PEAKS.json bf16_tflops)"},
+            "cuda_cores_samples_per_s": inf["cuda_cores"]["samples_per_s"], "samples": inf["samples"]}
 
     if rank == 0:
         print(json.dumps(out), flush=True)
