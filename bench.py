@@ -414,11 +414,11 @@ def run_batch(args):
 
 
 # per (template, SFT) operations of the binary track's FP32 screen and gather: orbit phase
-# (three 32-bit multiply-adds: 3), the table node and offset (round, shift, table read,
-# shift, convert: 5), the second-order cosine (3), a.v + y0 (3), y (1), floor, fraction and
-# the two boundary tests (4), the bin (2), bounds + out-of-window count (2), address, read,
-# add (3); the FP64 decisions (about 2 delta of the evaluations) are not counted
-BT_OPS_PER_EVAL = 26
+# (three 32-bit multiply-adds: 3), the cosine (convert the phase, scale it to radians, the
+# special-function unit's cosine: 3), a.v + y0 (3), y (1), floor, fraction and the two
+# boundary tests (4), the bin (2), bounds + out-of-window count (2), address, read, add (3);
+# the FP64 decisions (about 2 delta of the evaluations) are not counted
+BT_OPS_PER_EVAL = 21
 ISSUE_LANES_PER_CLK_PER_SM = 128
 
 
@@ -486,7 +486,7 @@ def binary_core(args, ctx, local, steps=None):
                    "n_sft": sfts.n_total, "n_templates": bank.n_templates, "n_boxes": bank.n_boxes,
                    "evals_per_step": evals, "storage": args.dtype,
                    "track_bins": "FP64 bins of Eq. (track): FP32 screen (integer orbit phase, "
-                                 "second-order table cosine) with a derived error bound delta, FP64 "
+                                 "special-function-unit cosine) with a derived error bound delta, FP64 "
                                  "decision within delta of a rounding boundary",
                    "l2": "flushed between timed steps (256 MB write, outside the per-step events)"},
         "roofline": {"bound": "alu", "kernel": "k_bt_eval (per-template track, gather, per-box top-k)",
@@ -501,6 +501,9 @@ def binary_core(args, ctx, local, steps=None):
         "fp64_decisions": {"per_eval": n64 / (evals * (steps + args.warmup)), "delta_bins": delta,
                            "expected_per_eval": 2 * delta},
     }
+    # the screen's cosine step over all 2^32 orbit phases against the bound delta assumes
+    cos_err, cos_bound = ft.binary_cos_screen_check(ctx)
+    out["cos_screen"] = {"max_abs_err": cos_err, "bound": cos_bound, "phases": 1 << 32}
     return out, sfts, bank, band, gb, P32, k
 
 

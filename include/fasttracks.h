@@ -372,9 +372,9 @@ FT_API int ft_pdet_q(ft_ctx *ctx, const ft_band *band, const double *det_tensor,
  * Bins: the FP64 bin of Eq. (track), bin = floor(X + 1/2) with
  *     X = f0 (1 + v.n - a_p Omega cos(Omega t - 2 pi phi_b)) T_SFT - k_lo,
  *     n = (cos delta cos 2 pi alpha, cos delta sin 2 pi alpha, sin delta), t = t_mid - t0.
- *   The kernels evaluate X first in FP32 (64-bit integer orbit phase, a second-order
- *   cosine from a 1024-node table, one FMA chain) with an error below a bound delta derived
- *   from the bank's largest f0 T_SFT |v|, f0 T_SFT a_p Omega and orbit frequency (about 1e-5
+ *   The kernels evaluate X first in FP32 (64-bit integer orbit phase, the special-function
+ *   unit's cosine of that phase, one FMA chain) with an error below a bound delta derived
+ *   from the bank's largest f0 T_SFT |v|, f0 T_SFT a_p Omega and orbit frequency (about 3e-5
  *   bins for the paper's search ranges); where that value lies within delta of a rounding
  *   boundary they recompute X in FP64 from the template's FP64 terms and the SFT's FP64 v
  *   and t, and that decides.  So every bin is the FP64 bin, except where the FP64 value
@@ -416,6 +416,15 @@ FT_API int ft_binary_templates(ft_ctx *ctx, const ft_binary_bank *bank, int64_t 
  * bank's delta in bins (either pointer nullable).  Resets the count; synchronises the
  * device.  Errors: FT_ERR_ARG (null bank), FT_ERR_CUDA. */
 FT_API int ft_binary_decisions(ft_binary_bank *bank, uint64_t *n_fp64, double *delta);
+
+/* The FP32 screen's cosine step (the orbit phase ph in 2^-32 turns as a signed FP32 angle,
+ * then the special-function unit's cosine) against cos(2 pi ph / 2^32), over all 2^32 phases
+ * on the context's device: the largest absolute error, and the bound the screen's delta
+ * assumes for it (bound nullable).  This checks the one step of the screen whose error comes
+ * from hardware rather than from FP32 rounding (Sec. II.A Eq. (track): its cosine term).
+ * Synchronises the device; about a second.  Errors: FT_ERR_ARG (null ctx or max_abs_err),
+ * FT_ERR_OOM, FT_ERR_CUDA. */
+FT_API int ft_binary_cos_screen_check(ft_ctx *ctx, double *max_abs_err, double *bound);
 
 /* Bins of templates[0..n) in every SFT (the kernels' rule above): bins [n][N_SFT] int32 columns of the band
  * (may lie outside [0, n_bins)).  templates / bins both host or both device (on_device). */

@@ -105,6 +105,7 @@ def lib():
             "ft_binary_templates": (_I, [_P, _P, _I64, _I64, _P, _P]),
             "ft_ctx_memory": (_I, [_P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
             "ft_binary_decisions": (_I, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]),
+            "ft_binary_cos_screen_check": (_I, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
             "ft_binary_track_bins": (_I, [_P, _P, _P, _P, _I64, _P, _I, _P]),
             "ft_binary_eval": (_I, [_P, _P, _P, _I64, _I64, _P, _P, _P, _I, _P]),
             "ft_binary_topk_per_box": (_I, [_P, _P, _P, _I, _P, _I, _P]),
@@ -337,6 +338,15 @@ def binary_decisions(bank):
     d = ctypes.c_double(0.0)
     _check(lib().ft_binary_decisions(bank.handle, ctypes.byref(n), ctypes.byref(d)))
     return int(n.value), float(d.value)
+
+
+def binary_cos_screen_check(ctx):
+    """ft_binary_cos_screen_check: (largest error of the binary screen's cosine step over all
+    2^32 orbit phases, the bound the screen's delta assumes)."""
+    m = ctypes.c_double(0.0)
+    bnd = ctypes.c_double(0.0)
+    _check(lib().ft_binary_cos_screen_check(ctx.handle, ctypes.byref(m), ctypes.byref(bnd)))
+    return float(m.value), float(bnd.value)
 
 
 def binary_templates(ctx, bank, first, n, stream=None):

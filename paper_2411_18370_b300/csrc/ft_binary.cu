@@ -9,8 +9,8 @@
 //
 // The bin is the FP64 bin of Eq. (track), X = f0 (1 + v.n - a_p Omega cos(Omega t - phi_b))
 // T_SFT - k_lo rounded half up.  Per (template, SFT) the kernel first evaluates X in FP32
-// (integer orbit phase, second-order table cosine, FMA chain) with a derived error bound
-// delta; only when that value lies within delta of a rounding boundary (a fraction of about
+// (integer orbit phase, the special-function unit's cosine, FMA chain) with a derived error
+// bound delta; only when that value lies within delta of a rounding boundary (a fraction of about
 // 2 delta of all evaluations) is X recomputed in FP64 from the template's FP64 terms and the
 // SFT's FP64 velocity and time, so every bin equals the FP64 bin.  Then one shared-memory
 // read and one add: the kernel is bound by instruction issue, not by HBM.
@@ -34,7 +34,6 @@ struct ft_binary_bank {
     float4 *d_rowv = nullptr;      // [n_pad] (v/c as FP32, weight); zero beyond N
     long long *d_tq = nullptr;     // [n_pad] round((t_mid - t0) 2^10)
     double *d_t64 = nullptr;       // [n_pad] t_mid - t0 (s), FP64
-    float4 *d_costab = nullptr;    // [kBtNodes][kBtSlots] the screen's cosine table
     // all-sky weights (band with detector tensors): per SFT D / sqrt(S_n) in FP32 as
     // (D00, D01, D02, D11), (D12, D22, |D|^2, tr D); zero beyond N
     float4 *d_rowd = nullptr;      // [n_pad][2]
@@ -48,18 +47,16 @@ constexpr int kBtThreads = 512;              // templates per CTA
 constexpr int kBtTPT = 4;                    // templates per thread (they share each row's records)
 constexpr int kBtBlock = kBtThreads / kBtTPT;  // threads per CTA
 constexpr int kBtRowPad = 64;
-// The FP32 screen's cosine table: 128 nodes over the full turn, each stored once per lane
-// slot (8 slots: the four quarter-warps of a 128-bit shared load), so that lane l reads node
-// e from entry e 8 + (l mod 8) and a warp's 32 reads never share a bank: four wavefronts per
-// read whatever the nodes.  Entry e holds the Taylor coefficients of cos(2 pi e / 128 + b)
-// in the raw phase offset fb (b = fb kB): (C, S kB, C kB^2 / 2, S kB^3 / 6).  16 KB.
-constexpr int kBtNodes = 128;
-constexpr int kBtSlots = 8;
-constexpr int kBtTab = kBtNodes * kBtSlots;  // float4 entries
 constexpr int kBtSlow = 7;    // FP64 terms per template for the FP64 decisions
-// node e = round(phase 128 / 2^32); fb = (int)(phase << 7) is 2^7 x the signed remainder in
-// units of 2^-32 turns, so the angle past node e is b = fb kB rad
-constexpr double kB = 6.283185307179586476925286766559 / 549755813888.0;  // 2 pi / 2^39
+// The screen's cosine: the orbit phase ph (2^-32 turns, read as a signed angle in [-pi, pi))
+// is converted to FP32 radians and passed to the special-function unit's cosine (__cosf).
+// Its error against cos(2 pi ph / 2^32) is at most kBtCosErr: the conversion of ph rounds by
+// at most 2^7 units (2 pi 2^-25 rad), the FP32 scale 2 pi / 2^32 and the product add at most
+// 2 u pi (u = 2^-24), and __cosf is documented to within 2^-21.19 for arguments in
+// [-pi, pi] (taken here as 2^-21).  ft_binary_cos_screen_check measures the whole step over
+// all 2^32 phases against this bound.
+constexpr float kBtPhRad = 1.46291807926715968e-9f;  // 2 pi / 2^32
+constexpr double kBtCosErr = 6.283185307179586 * 0x1p-25 + 3.141592653589793 * 0x1p-23 + 0x1p-21;
 constexpr float kMagic = 12582912.0f;  // 1.5 2^23: t + kMagic rounds t to an integer in its low bits
 
 struct BtParams {
@@ -78,7 +75,6 @@ struct BtParams {
     const long long *tq;
     const double *v64;             // [N][3] v / c, FP64
     const double *t64;             // [N] t_mid - t0, FP64
-    const float4 *costab;          // [kBtNodes][kBtSlots] Taylor coefficients (see kBtNodes)
     const float4 *rowd;            // null, or the all-sky weight records [n_pad][2]
     float half_delta;              // screen: FP64 decision when |t - rint(t)| > 1/2 - delta
     double vmax;                   // largest |v| / c of the band (window proof per CTA)
@@ -172,9 +168,7 @@ __device__ void bt_lambda(const BtParams &p, long long i, double lam[6])
 // FP32 screen per (template, SFT), t = X - K:
 //   phase  ph = top word of (nu t_q) mod 2^64 + npsi, in 2^-32 turns, from three 32-bit
 //          multiplies (the low word's borrow is dropped: |error| < 1 unit);
-//   cosine node e = round(ph 128 / 2^32) of the 128-node table and the angle b past it:
-//          cos = C - S b - C b^2 / 2 + S b^3 / 6 (truncation <= |b|^4 / 24 + |b|^5 / 120
-//          with |b| <= pi / 128: 1.5e-8), three FMAs on the raw offset fb;
+//   cosine __cosf of ph as a signed FP32 angle (bt_cos, error below kBtCosErr);
 //   t      = t0 + a.v - A cos (one FMA chain);
 //   bin    = K + rint(t) by the 1.5 2^23 rounding trick, and d = t - rint(t).
 // Its error against the exact real value is below the launch's delta (host: bt_delta); when
@@ -227,15 +221,18 @@ __device__ bool bt_derive(const BtParams &p, const double lam[6], BtTmpl &t, dou
     return floor(x - reach + 0.5) >= 0.0 && floor(x + reach + 0.5) <= static_cast<double>(p.W - 1);
 }
 
-// t = X - K of the FP32 screen (see above); tabl is this lane's slot of the table
-__device__ __forceinline__ float bt_t(const BtTmpl &t, float4 v, uint2 tq, const float4 *tabl)
+// cos(2 pi ph / 2^32) of the screen, within kBtCosErr
+__device__ __forceinline__ float bt_cos(unsigned ph)
+{
+    return __cosf(__fmul_rn(__int2float_rn(static_cast<int>(ph)), kBtPhRad));
+}
+
+// t = X - K of the FP32 screen (see above)
+__device__ __forceinline__ float bt_t(const BtTmpl &t, float4 v, uint2 tq)
 {
     const unsigned ph = __umulhi(t.nlo, tq.x) + t.nlo * tq.y + t.nhi * tq.x + t.npsi;
-    const float4 e = tabl[((ph + (1u << 24)) >> 25) * kBtSlots];
-    const float fb = __int2float_rn(static_cast<int>(ph << 7));
-    const float c = __fmaf_rn(-fb, __fmaf_rn(fb, __fmaf_rn(-fb, e.w, e.z), e.y), e.x);
     const float base = __fmaf_rn(v.x, t.ax, __fmaf_rn(v.y, t.ay, __fmaf_rn(v.z, t.az, t.t0)));
-    return __fmaf_rn(-t.A, c, base);
+    return __fmaf_rn(-t.A, bt_cos(ph), base);
 }
 
 // rint(t) as an integer (|t| < 2^22) and whether t is within delta of a rounding boundary
@@ -258,9 +255,9 @@ __device__ __noinline__ int bt_bin64(const double *sl, int st, const double *v, 
 
 // Bin of one (template, SFT): the screen, or the FP64 decision near a rounding boundary.
 __device__ __forceinline__ int bt_bin(const BtParams &p, const BtTmpl &t, const double *sl, int st,
-                                      int a, float4 v, uint2 tq, const float4 *tabl, bool &dec)
+                                      int a, float4 v, uint2 tq, bool &dec)
 {
-    const int kr = bt_round(bt_t(t, v, tq, tabl), p.half_delta, dec);
+    const int kr = bt_round(bt_t(t, v, tq), p.half_delta, dec);
     if (dec)
         return bt_bin64(sl, st, p.v64 + 3ll * a, p.t64[a]);
     return t.K + kr;
@@ -347,7 +344,7 @@ __device__ __forceinline__ void fold2(float &hi, float &lo, float part)
 template <typename T, bool WEIGHTED, bool SKY, bool CHECK>
 __device__ __forceinline__ void bt_rows(const BtParams &p, const BtTmpl (&t)[kBtTPT], const bool (&valid)[kBtTPT],
                                         const double *sl, int a0, int nr, const float4 *svb, const uint2 *tqs,
-                                        const unsigned char *rb, const float4 *sdb, const float4 *tabl,
+                                        const unsigned char *rb, const float4 *sdb,
                                         float (&part)[kBtTPT], float (&partB)[kBtTPT], float (&partC)[kBtTPT],
                                         int (&oob)[kBtTPT], unsigned &n64)
 {
@@ -361,7 +358,7 @@ __device__ __forceinline__ void bt_rows(const BtParams &p, const BtTmpl (&t)[kBt
         bool any = false;
 #pragma unroll
         for (int u = 0; u < kBtTPT; ++u) {
-            k[u] = t[u].K + bt_round(bt_t(t[u], v, tq, tabl), p.half_delta, dec[u]);
+            k[u] = t[u].K + bt_round(bt_t(t[u], v, tq), p.half_delta, dec[u]);
             any |= dec[u];
         }
         if (any) {
@@ -406,8 +403,7 @@ __global__ void __launch_bounds__(kBtBlock) k_bt_eval(const BtParams p)
     long long *stq[2] = {reinterpret_cast<long long *>(sv[1] + p.S),
                          reinterpret_cast<long long *>(sv[1] + p.S) + p.S};
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(stq[1] + p.S);
-    float4 *tab = reinterpret_cast<float4 *>(bars + 2);  // 16-byte aligned
-    float4 *sd[2] = {tab + kBtTab, nullptr};
+    float4 *sd[2] = {reinterpret_cast<float4 *>(bars + 2), nullptr};  // 16-byte aligned
     sd[1] = sd[0] + 2 * p.S;
 
     // this CTA's templates
@@ -443,8 +439,6 @@ __global__ void __launch_bounds__(kBtBlock) k_bt_eval(const BtParams p)
         s_issued[1] = p.n_stages > 1 ? 1 : -1;
         s_abort = 0;
     }
-    for (int i = threadIdx.x; i < kBtTab; i += kBtBlock)
-        tab[i] = p.costab[i];
     __syncthreads();
     if (threadIdx.x < 32) {
         bt_issue(p, 0, rows[0], sv[0], stq[0], sd[0], &bars[0]);
@@ -465,7 +459,6 @@ __global__ void __launch_bounds__(kBtBlock) k_bt_eval(const BtParams p)
     }
     // one loop for the whole CTA: unchecked only when every track stays inside the band
     inside = __syncthreads_and(inside) != 0;
-    const float4 *tabl = tab + (threadIdx.x & (kBtSlots - 1));
 
     float hi[kBtTPT], lo[kBtTPT];
     // all-sky weights: sum r, sum r^2 (r = (a^2 + b^2) / S_n), compensated like the sum
@@ -500,10 +493,10 @@ __global__ void __launch_bounds__(kBtBlock) k_bt_eval(const BtParams p)
             part[u] = partB[u] = partC[u] = 0.f;
         const uint2 *tqs = reinterpret_cast<const uint2 *>(stq[b]);
         if (inside)
-            bt_rows<T, WEIGHTED, SKY, false>(p, t, valid, sl, st * p.S, nr, sv[b], tqs, rows[b], sd[b], tabl,
+            bt_rows<T, WEIGHTED, SKY, false>(p, t, valid, sl, st * p.S, nr, sv[b], tqs, rows[b], sd[b],
                                              part, partB, partC, oob, n64);
         else
-            bt_rows<T, WEIGHTED, SKY, true>(p, t, valid, sl, st * p.S, nr, sv[b], tqs, rows[b], sd[b], tabl,
+            bt_rows<T, WEIGHTED, SKY, true>(p, t, valid, sl, st * p.S, nr, sv[b], tqs, rows[b], sd[b],
                                             part, partB, partC, oob, n64);
         // compensated folds of the stage's partials (2Sum)
 #pragma unroll
@@ -746,7 +739,7 @@ __global__ void __launch_bounds__(256) k_bt_bins(const BtParams p, const long lo
         bins[i * p.N + a] = bt_bin(p, t, sl, kBtThreads, a, p.rowv[a],
                                    make_uint2(static_cast<unsigned>(tq), static_cast<unsigned>(
                                                   static_cast<unsigned long long>(tq) >> 32)),
-                                   p.costab + (threadIdx.x & (kBtSlots - 1)), dec);
+                                   dec);
     }
 }
 
@@ -760,6 +753,26 @@ __global__ void k_bt_rowv(const double *v, const float *w, int N, int n_pad, flo
         r = make_float4(__double2float_rn(v[3 * a]), __double2float_rn(v[3 * a + 1]),
                         __double2float_rn(v[3 * a + 2]), w[a]);
     out[a] = r;
+}
+
+// Largest |bt_cos(ph) - cos(2 pi ph / 2^32)| over every 32-bit phase: thread i of the grid
+// takes ph = i, i + stride, ... (stride = grid size, a power of two), the reference is the
+// FP64 cospi of the exact argument ph 2^-31 (ph read as a signed angle).  The non-negative
+// maximum is kept as the bit pattern of a double, whose integer order is its numeric order.
+__global__ void __launch_bounds__(256) k_bt_cos_check(unsigned long long *max_bits)
+{
+    const unsigned stride = gridDim.x * blockDim.x;
+    double m = 0.0;
+    for (unsigned long long ph = blockIdx.x * blockDim.x + threadIdx.x; ph < (1ull << 32); ph += stride) {
+        const unsigned u = static_cast<unsigned>(ph);
+        const double ref = cospi(static_cast<double>(static_cast<int>(u)) * 0x1p-31);
+        m = fmax(m, fabs(static_cast<double>(bt_cos(u)) - ref));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(max_bits, static_cast<unsigned long long>(__double_as_longlong(m)));
 }
 
 // ------------------------------------------------------------------ host side
@@ -812,12 +825,10 @@ int elem_bytes(int dtype)
 //   a.v with a = FP32(F n), v = FP32(v / c): inputs 2u |a| |v| = 2u F|v| (Cauchy-Schwarz),
 //     three FMA roundings 3u (1 + F|v|) (every partial sum is below 1 + F|v|);
 //   A = FP32(F a_p Omega): u A;  the final FMA: u (1 + F|v| + A);
-//   the cosine (|c| <= 1): C's rounding 2^-25, the final FMA 2^-25, the inner FMAs and the
-//     scaled coefficients about 1e-8, truncation 1.5e-8: under 1.2e-7, times A;
-//   the orbit phase: the dropped borrow and fb's rounding to FP32 (2^-32 turn each), nu
-//     rounded to 2^-55 turn/s times the largest |t|, t rounded to 2^-11 s times the largest
-//     nu: times 2 pi A.
-// So delta = u (5 + 6 F|v| + 2 A) + A (1.2e-7 + e_phase), taken with a 1.5 safety factor
+//   the cosine of the integer phase: kBtCosErr (conversion, scale and __cosf), times A;
+//   the orbit phase: the dropped borrow (2^-32 turn), nu rounded to 2^-55 turn/s times the
+//     largest |t|, t rounded to 2^-11 s times the largest nu: times 2 pi A.
+// So delta = u (5 + 6 F|v| + 2 A) + A (kBtCosErr + e_phase), taken with a 1.5 safety factor
 // and the FP64 decision's own rounding (1e-9) added.  F, |v|, A and nu are the largest over
 // the bank and band.
 double bt_delta(const ft_band *band, const ft_binary_bank *bk)
@@ -830,8 +841,8 @@ double bt_delta(const ft_band *band, const ft_binary_bank *bk)
     for (double t : band->h_dt)
         tmax = std::max(tmax, std::fabs(t));
     const double nu = std::fabs(bk->desc.hi[4]) / 6.283185307179586;
-    const double e_ph = 6.283185307179586 * (0x1p-31 + 0x1p-55 * tmax + 0x1p-11 * nu);
-    const double e = u * (5.0 + 6.0 * Fv + 2.0 * A) + A * (1.2e-7 + e_ph);
+    const double e_ph = 6.283185307179586 * (0x1p-32 + 0x1p-55 * tmax + 0x1p-11 * nu);
+    const double e = u * (5.0 + 6.0 * Fv + 2.0 * A) + A * (kBtCosErr + e_ph);
     return 1.5 * e + 1e-9;
 }
 
@@ -862,7 +873,6 @@ BtParams base_params(const ft_band *band, const ft_binary_bank *bk)
     p.tq = bk->d_tq;
     p.v64 = band->d_v;
     p.t64 = bk->d_t64;
-    p.costab = bk->d_costab;
     p.n64 = bk->d_n64;
     p.half_delta = std::nextafter(static_cast<float>(0.5 - bk->delta), 0.0f);
     p.vmax = band->vmax;
@@ -877,8 +887,8 @@ BtParams base_params(const ft_band *band, const ft_binary_bank *bk)
 
 int stage_rows(const ft_band *band)
 {
-    // at most 16 KB of rows per stage, 8..64 rows (a divisor of kBtRowPad): two stages and
-    // the cosine table leave room for 4 CTAs per SM, as many as the registers allow
+    // at most 16 KB of rows per stage, 8..64 rows (a divisor of kBtRowPad): two stages
+    // leave room for 4 CTAs per SM, as many as the registers allow
     const int rb = band->Wp * elem_bytes(band->dtype);
     int S = 64;
     while (S > 8 && S * rb > 16 * 1024)
@@ -888,7 +898,7 @@ int stage_rows(const ft_band *band)
 
 size_t eval_smem(const BtParams &p)
 {
-    return 2 * (static_cast<size_t>(p.S) * p.row_bytes + p.S * 24) + 16 + kBtTab * sizeof(float4) +
+    return 2 * (static_cast<size_t>(p.S) * p.row_bytes + p.S * 24) + 16 +
            (p.rowd != nullptr ? 2 * static_cast<size_t>(p.S) * 32 : 0);
 }
 
@@ -1027,32 +1037,19 @@ int ft_make_binary_bank(ft_ctx *ctx, const ft_band *band, const ft_binary_bank_d
         ft_binary_bank_destroy(b);
         return rc;
     };
-    // the screen's cosine table: node e at angle 2 pi e / 128, the Taylor coefficients in
-    // the raw offset from the host's libm in FP64, rounded to FP32, once per lane slot
-    std::vector<float4> tab(kBtTab);
-    for (int e = 0; e < kBtNodes; ++e) {
-        const double ang = 6.283185307179586476925286766559 * e / kBtNodes;
-        const double C = std::cos(ang), S = std::sin(ang);
-        const float4 q = make_float4(static_cast<float>(C), static_cast<float>(S * kB),
-                                     static_cast<float>(C * kB * kB / 2.0), static_cast<float>(S * kB * kB * kB / 6.0));
-        for (int l = 0; l < kBtSlots; ++l)
-            tab[e * kBtSlots + l] = q;
-    }
     std::vector<double> t64(b->n_pad, 0.0);
     for (int a = 0; a < N; ++a)
         t64[a] = band->h_dt[a];
     if (cudaMalloc(&b->d_rowv, static_cast<size_t>(b->n_pad) * sizeof(float4)) != cudaSuccess ||
         cudaMalloc(&b->d_tq, static_cast<size_t>(b->n_pad) * sizeof(long long)) != cudaSuccess ||
         cudaMalloc(&b->d_t64, static_cast<size_t>(b->n_pad) * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&b->d_n64, sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMalloc(&b->d_costab, tab.size() * sizeof(float4)) != cudaSuccess) {
+        cudaMalloc(&b->d_n64, sizeof(unsigned long long)) != cudaSuccess) {
         ft_set_error("make_binary_bank: allocation failed");
         return fail(FT_ERR_OOM);
     }
     if (cudaMemcpy(b->d_tq, tq.data(), tq.size() * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->d_t64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(b->d_n64, 0, sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMemcpy(b->d_costab, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemset(b->d_n64, 0, sizeof(unsigned long long)) != cudaSuccess) {
         ft_set_error("make_binary_bank: copy failed");
         return fail(FT_ERR_CUDA);
     }
@@ -1084,7 +1081,6 @@ void ft_binary_bank_destroy(ft_binary_bank *b)
     cudaFree(b->d_tq);
     cudaFree(b->d_t64);
     cudaFree(b->d_n64);
-    cudaFree(b->d_costab);
     cudaFree(b->d_rowd);
     delete b;
 }
@@ -1113,6 +1109,28 @@ int ft_binary_decisions(ft_binary_bank *bank, uint64_t *n_fp64, double *delta)
         *n_fp64 = h;
     if (delta)
         *delta = bank->delta;
+    return FT_OK;
+}
+
+int ft_binary_cos_screen_check(ft_ctx *ctx, double *max_abs_err, double *bound)
+{
+    if (!ctx || !max_abs_err)
+        FT_FAIL(FT_ERR_ARG, "binary_cos_screen_check: null argument");
+    Guard g(ctx->device);
+    void *scr = nullptr;
+    FT_TRY(ft_ctx_scratch(ctx, sizeof(unsigned long long), &scr));
+    auto *d = static_cast<unsigned long long *>(scr);
+    FT_CUDA(cudaMemset(d, 0, sizeof(unsigned long long)));
+    // 2^18 threads of 2^14 phases each
+    k_bt_cos_check<<<1024, 256>>>(d);
+    FT_CUDA(cudaGetLastError());
+    unsigned long long h = 0;
+    FT_CUDA(cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost));
+    double m;
+    std::memcpy(&m, &h, sizeof(m));
+    *max_abs_err = m;
+    if (bound)
+        *bound = kBtCosErr;
     return FT_OK;
 }
 

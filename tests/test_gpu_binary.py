@@ -1,5 +1,6 @@
 """The binary-orbit track over a random hyperbox bank on the GPU, against the oracle:
 
+* the screen's cosine step is within the bound its delta assumes, over all 2^32 phases;
 * the templates the kernels derive from their Philox counters equal the oracle's, bit for bit;
 * the bins of every (template, SFT) pair are the FP64 bins of Eq. (track): equal to the
   oracle's except where the oracle's FP64 position lies within TIE = 1e-9 bins of a rounding
@@ -102,6 +103,15 @@ def _check_bins_and_s(ctx, band, gb, stored, bank, tmpl, s_gpu, w=None, rel=REL)
             want = want + np.sum(wv[a] * (pg - po))
         assert abs(float(s_gpu[r]) - want) <= rel * max(abs(want), 1.0), (int(tmpl[r]), float(s_gpu[r]), want)
     return int(diff.sum())
+
+
+def test_cos_screen_within_its_bound(ctx):
+    """The screen's cosine step (integer orbit phase -> FP32 angle -> the special-function
+    unit's cosine), over every one of the 2^32 phases, stays within the bound the screen's
+    delta assumes for it; that bound is what makes every bin the FP64 bin."""
+    m, bound = ft.binary_cos_screen_check(ctx)
+    assert 0.0 < m <= bound, (m, bound)
+    assert bound < 2e-6
 
 
 def test_templates_and_bins_equal_the_fp64_track(ctx):
