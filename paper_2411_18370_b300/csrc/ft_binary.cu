@@ -47,6 +47,7 @@ constexpr int kBtThreads = 512;              // templates per CTA
 constexpr int kBtTPT = 4;                    // templates per thread (they share each row's records)
 constexpr int kBtBlock = kBtThreads / kBtTPT;  // threads per CTA
 constexpr int kBtRowPad = 64;
+constexpr int kBtRowGroup = 2;  // SFT rows whose screens run before one branch to the FP64 decisions
 constexpr int kBtSlow = 7;    // FP64 terms per template for the FP64 decisions
 // The screen's cosine: the orbit phase ph (2^-32 turns, read as a signed angle in [-pi, pi))
 // is converted to FP32 radians and passed to the special-function unit's cosine (__cosf).
@@ -341,6 +342,69 @@ __device__ __forceinline__ void fold2(float &hi, float &lo, float part)
 
 // The rows of one stage for this thread's templates.  CHECK: bins may leave [0, W) (then
 // they add 0 and are counted); without it every track of the CTA is proven inside.
+// Rows r0 .. r0 + RG - 1 of one stage for this thread's templates: the screen of all RG x
+// kBtTPT (template, SFT) pairs first, one branch to the FP64 decisions for any of them, then
+// the reads and adds.  CHECK: bins may leave [0, W) (then they add 0 and are counted);
+// without it every track of the CTA is proven inside.
+template <typename T, bool WEIGHTED, bool SKY, bool CHECK, int RG>
+__device__ __forceinline__ void bt_row_group(const BtParams &p, const BtTmpl (&t)[kBtTPT], const bool (&valid)[kBtTPT],
+                                             const double *sl, int a0, int r0, const float4 *svb, const uint2 *tqs,
+                                             const unsigned char *rb, const float4 *sdb,
+                                             float (&part)[kBtTPT], float (&partB)[kBtTPT], float (&partC)[kBtTPT],
+                                             int (&oob)[kBtTPT], unsigned &n64)
+{
+    int k[RG][kBtTPT];
+    bool dec[RG][kBtTPT];
+    bool any = false;
+#pragma unroll
+    for (int g = 0; g < RG; ++g) {
+        const float4 v = svb[r0 + g];
+        const uint2 tq = tqs[r0 + g];
+#pragma unroll
+        for (int u = 0; u < kBtTPT; ++u) {
+            k[g][u] = t[u].K + bt_round(bt_t(t[u], v, tq), p.half_delta, dec[g][u]);
+            any |= dec[g][u];
+        }
+    }
+    if (any) {
+        // near a rounding boundary: the FP64 bin decides
+#pragma unroll
+        for (int g = 0; g < RG; ++g) {
+            const int a = a0 + r0 + g;
+#pragma unroll
+            for (int u = 0; u < kBtTPT; ++u)
+                if (dec[g][u]) {
+                    k[g][u] = bt_bin64(sl + threadIdx.x + u * kBtBlock, kBtThreads, p.v64 + 3ll * a, p.t64[a]);
+                    n64 += valid[u] ? 1u : 0u;
+                }
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < RG; ++g) {
+        const int r = r0 + g;
+        const unsigned char *row = rb + static_cast<size_t>(r) * p.row_bytes;
+#pragma unroll
+        for (int u = 0; u < kBtTPT; ++u) {
+            const bool in = !CHECK || static_cast<unsigned>(k[g][u]) < static_cast<unsigned>(p.W);
+            if (CHECK)
+                oob[u] += in ? 0 : 1;
+            if (SKY) {
+                const float val = in ? bt_load<T>(row, k[g][u]) : 0.f;
+                const float rw = ft_sky_r32(sdb[2 * r], sdb[2 * r + 1], t[u].wx, t[u].wy, t[u].wz);
+                part[u] = __fmaf_rn(rw, val, part[u]);
+                partB[u] = __fadd_rn(partB[u], rw);
+                partC[u] = __fmaf_rn(rw, rw, partC[u]);
+            } else if (WEIGHTED) {
+                const float val = in ? bt_load<T>(row, k[g][u]) : 0.f;
+                part[u] = __fmaf_rn(svb[r].w, val, part[u]);
+            } else {
+                bt_add<T>(part[u], row, k[g][u], in);
+            }
+        }
+    }
+}
+
+// The rows of one stage for this thread's templates, kBtRowGroup at a time.
 template <typename T, bool WEIGHTED, bool SKY, bool CHECK>
 __device__ __forceinline__ void bt_rows(const BtParams &p, const BtTmpl (&t)[kBtTPT], const bool (&valid)[kBtTPT],
                                         const double *sl, int a0, int nr, const float4 *svb, const uint2 *tqs,
@@ -348,48 +412,15 @@ __device__ __forceinline__ void bt_rows(const BtParams &p, const BtTmpl (&t)[kBt
                                         float (&part)[kBtTPT], float (&partB)[kBtTPT], float (&partC)[kBtTPT],
                                         int (&oob)[kBtTPT], unsigned &n64)
 {
-#pragma unroll 2
-    for (int r = 0; r < nr; ++r) {
-        const float4 v = svb[r];
-        const uint2 tq = tqs[r];
-        const unsigned char *row = rb + static_cast<size_t>(r) * p.row_bytes;
-        int k[kBtTPT];
-        bool dec[kBtTPT];
-        bool any = false;
-#pragma unroll
-        for (int u = 0; u < kBtTPT; ++u) {
-            k[u] = t[u].K + bt_round(bt_t(t[u], v, tq), p.half_delta, dec[u]);
-            any |= dec[u];
-        }
-        if (any) {
-            // near a rounding boundary: the FP64 bin decides
-            const int a = a0 + r;
-#pragma unroll
-            for (int u = 0; u < kBtTPT; ++u)
-                if (dec[u]) {
-                    k[u] = bt_bin64(sl + threadIdx.x + u * kBtBlock, kBtThreads, p.v64 + 3ll * a, p.t64[a]);
-                    n64 += valid[u] ? 1u : 0u;
-                }
-        }
-#pragma unroll
-        for (int u = 0; u < kBtTPT; ++u) {
-            const bool in = !CHECK || static_cast<unsigned>(k[u]) < static_cast<unsigned>(p.W);
-            if (CHECK)
-                oob[u] += in ? 0 : 1;
-            if (SKY) {
-                const float val = in ? bt_load<T>(row, k[u]) : 0.f;
-                const float rw = ft_sky_r32(sdb[2 * r], sdb[2 * r + 1], t[u].wx, t[u].wy, t[u].wz);
-                part[u] = __fmaf_rn(rw, val, part[u]);
-                partB[u] = __fadd_rn(partB[u], rw);
-                partC[u] = __fmaf_rn(rw, rw, partC[u]);
-            } else if (WEIGHTED) {
-                const float val = in ? bt_load<T>(row, k[u]) : 0.f;
-                part[u] = __fmaf_rn(v.w, val, part[u]);
-            } else {
-                bt_add<T>(part[u], row, k[u], in);
-            }
-        }
-    }
+    // (the all-sky weighted loop keeps one row per group: its weight terms need the registers)
+    constexpr int RG = SKY ? 1 : kBtRowGroup;
+    int r = 0;
+    for (; r + RG <= nr; r += RG)
+        bt_row_group<T, WEIGHTED, SKY, CHECK, RG>(p, t, valid, sl, a0, r, svb, tqs, rb, sdb, part, partB,
+                                                           partC, oob, n64);
+    for (; r < nr; ++r)
+        bt_row_group<T, WEIGHTED, SKY, CHECK, 1>(p, t, valid, sl, a0, r, svb, tqs, rb, sdb, part, partB, partC,
+                                                 oob, n64);
 }
 
 template <typename T, bool WEIGHTED, bool SKY>
