@@ -985,7 +985,7 @@ def main():
         # the binary-orbit track's search (each rank its own replica), its own timed steps
         bt, *_ = binary_core(args, ctx, local, steps=max(5, args.steps // 2))
         out["binary_track"] = {k_: bt[k_] for k_ in ("value", "unit", "ms_per_step", "steps", "roofline",
-                                                     "fp64_decisions", "clocks", "gpu_launches")}
+                                                     "fp64_decisions", "cos_screen", "clocks", "gpu_launches")}
         out["binary_track"]["workload"] = bt["config"]["workload"]
         out["binary_track"]["value"] = ws * bt["value"]
         out["gpu_launches"] += bt["gpu_launches"]
