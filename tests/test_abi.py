@@ -84,3 +84,11 @@ def test_required_wings_rejects_bad_bank(built):
 
 def test_candidate_dtype_is_16_bytes():
     assert ft.CANDIDATE_DTYPE.itemsize == 16
+
+
+def test_cos_screen_check_refuses_null_arguments(built):
+    """The cosine-step check rejects a null context or output before touching a device."""
+    L = ft.lib()
+    m = ctypes.c_double(0.0)
+    assert L.ft_binary_cos_screen_check(None, ctypes.byref(m), None) == -1  # FT_ERR_ARG
+    assert "null" in L.ft_last_error().decode()
